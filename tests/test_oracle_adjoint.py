@@ -1,0 +1,84 @@
+"""Pins of the oracle's FP64 adjoint (reverse-time sweep of eq. frac_final) against
+complex-step and central finite-difference derivatives of the forward oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_5128_gb300 import synth
+
+H_CS = 1e-30
+
+
+def adj_problem(bc, ndim=2):
+    nx, ny = (9, 7) if ndim == 2 else (23, 1)
+    g = synth.SplitMix64(77)
+    u0 = g.uniform(nx * ny, 0.0, 1.0)
+    target = g.uniform(nx * ny, 0.0, 0.8)
+    dt = 0.01
+    p = synth.problem(ndim, nx, ny, 0.7, 0.8, dt, 1.0, bc, react=(0.05, -0.3, 0.2, -0.1), K=40,
+                      u0=u0)
+    return p, target
+
+
+def J_of(p, target, **over):
+    q = dict(p)
+    q.update(over)
+    if "react" in over:
+        q["react"] = list(over["react"])
+    u = oracle.run(q)
+    return 0.5 * float(np.sum((u - target) ** 2))
+
+
+def cs_grad(p, target, **im):
+    re, imu = oracle.run_cs(p, **im)
+    return float(np.sum((re - target) * imu)) / H_CS
+
+
+@pytest.mark.parametrize("bc,ndim", [(synth.BC_DIRICHLET0, 2), (synth.BC_NOFLUX, 2),
+                                     (synth.BC_NOFLUX, 1)])
+def test_adjoint_matches_complex_step(bc, ndim):
+    p, target = adj_problem(bc, ndim)
+    a = oracle.adjoint(p, target)
+    assert abs(a["J"] - J_of(p, target)) < 1e-14 * a["J"]
+    dg = cs_grad(p, target, gamma_im=H_CS)
+    da = cs_grad(p, target, alpha_im=H_CS)
+    assert abs(a["dgamma"] - dg) < 1e-11 * abs(dg)
+    assert abs(a["dalpha"] - da) < 1e-11 * abs(da)
+    for i in range(4):
+        e = np.zeros(4)
+        e[i] = H_CS
+        dr = cs_grad(p, target, react_im=e)
+        assert abs(a["dreact"][i] - dr) < 1e-11 * abs(dr), i
+    # dot-product test for dJ/du0: <lambda^0, v> = directional derivative along v
+    v = synth.SplitMix64(5).uniform(p["u0"].size, -1.0, 1.0)
+    dv = cs_grad(p, target, u0_im=H_CS * v)
+    assert abs(float(a["du0"] @ v) - dv) < 1e-11 * abs(dv)
+
+
+def test_adjoint_matches_central_differences():
+    p, target = adj_problem(synth.BC_DIRICHLET0)
+    a = oracle.adjoint(p, target)
+    h = 1e-4
+    fd = (J_of(p, target, gamma=p["gamma"] + h) - J_of(p, target, gamma=p["gamma"] - h)) / (2 * h)
+    assert abs(a["dgamma"] - fd) < 1e-6 * abs(fd)
+    fd = (J_of(p, target, alpha=p["alpha"] + h) - J_of(p, target, alpha=p["alpha"] - h)) / (2 * h)
+    assert abs(a["dalpha"] - fd) < 1e-6 * abs(fd)
+    r = np.array(p["react"])
+    for i in range(4):
+        rp, rm = r.copy(), r.copy()
+        rp[i] += h
+        rm[i] -= h
+        fd = (J_of(p, target, react=rp) - J_of(p, target, react=rm)) / (2 * h)
+        assert abs(a["dreact"][i] - fd) < 1e-6 * abs(fd)
+    j = 31
+    up, um = p["u0"].copy(), p["u0"].copy()
+    up[j] += h
+    um[j] -= h
+    fd = (J_of(p, target, u0=up) - J_of(p, target, u0=um)) / (2 * h)
+    assert abs(a["du0"][j] - fd) < 1e-6 * abs(fd)
+
+
+def test_complex_step_forward_matches_real_forward():
+    p, _ = adj_problem(synth.BC_NOFLUX)
+    re, im = oracle.run_cs(p)
+    assert np.max(np.abs(re - oracle.run(p))) < 1e-13 and np.all(im == 0)
