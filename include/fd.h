@@ -1,0 +1,187 @@
+/*
+ * fd.h -- C ABI of the GB300 (sm_103a) fractional reaction-diffusion engine.
+ *
+ * The library advances the explicit Grunwald-Letnikov scheme of Sprouse,
+ * MacDonald & Silva for d^g u/dt^g = alpha Lap u + f(u) (eq. fracdiff):
+ *
+ *     u^{k+1} = u^k + dt f(u^k) + S sum_{(m,c) in sched(k)} c delta^{k-m},
+ *     S = alpha dt^g / dx^2,  delta^r = L u^r  (eq. frac_final, eq. deltasimp),
+ *
+ * where sched(k) is the full memory (m = 0..k, c = psi(g,m); eq. frac_norxn),
+ * the short memory (m <= min(L, k); eq. frac_shortmemory) or the adaptive
+ * memory (Definitions 3.1/3.2, Proposition 3.1, eq. eq:adapttime).  The GL
+ * weights psi(g,m) follow the recurrence of Section 2.1.  f is a cubic
+ * polynomial, applied as an explicit term outside the memory sum (the reading
+ * of eq. frac_final).
+ *
+ * Conventions for every entry point:
+ *  - Return value: FD_OK (0) or a negative FD_ERR_* code; nothing throws,
+ *    asserts or traps across this boundary.  fd_strerror() names a code.
+ *  - Device memory: the caller owns every buffer.  The library never calls
+ *    cudaMalloc; all device state lives in a caller-provided workspace whose
+ *    size fd_workspace_bytes() reports (256-byte aligned base required).
+ *    A handle owns host memory only.
+ *  - Streams: all device work is enqueued on the cudaStream_t passed to
+ *    fd_init (NULL = legacy default stream).  Calls returning only after the
+ *    stream drains say so.
+ *  - Field layout: N = nx*ny points, row-major with x fastest
+ *    (point (x, y) at index y*nx + x), in the problem's state_dtype.
+ *  - State pointers may be device or host memory (cudaMemcpyDefault under
+ *    unified addressing; pinned host memory keeps copies asynchronous).
+ */
+#ifndef FD_H
+#define FD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FD_OK 0
+#define FD_ERR_INVALID_ARG (-1) /* a field or pointer is out of range */
+#define FD_ERR_UNSTABLE (-2)    /* S above the von Neumann bound 2^g/(4 ndim) */
+#define FD_ERR_WORKSPACE (-3)   /* workspace missing, misaligned or too small */
+#define FD_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define FD_ERR_NONFINITE (-5)   /* a NaN/Inf appeared in the state (sticky) */
+#define FD_ERR_TIMEOUT (-6)     /* a device-side wait ran past timeout_ms */
+#define FD_ERR_STATE (-7)       /* call out of order (e.g. adjoint without tape) */
+#define FD_ERR_UNSUPPORTED (-8) /* valid but not implemented combination */
+
+/* ---- enumerations ---- */
+enum { FD_BC_DIRICHLET0 = 0, FD_BC_NOFLUX = 1 };           /* ghosts: 0 | mirror u_-1=u_0 */
+enum { FD_MEM_FULL = 0, FD_MEM_SHORT = 1, FD_MEM_ADAPTIVE = 2 };
+enum { FD_ADAPT_PAPER = 0, FD_ADAPT_PARTITION = 1 };
+enum { FD_F64 = 0, FD_F32 = 1, FD_BF16 = 2, FD_F16 = 3 };
+
+#define FD_FLAG_KAHAN 1u           /* compensated FP32 accumulation of the memory sum */
+#define FD_FLAG_ALLOW_UNSTABLE 2u  /* skip the stability pre-check */
+#define FD_FLAG_KEEP_TAPE 4u       /* keep what fd_adjoint needs (u checkpoints, adjoint buffers) */
+#define FD_FLAG_INJECT_STALL 8u    /* fault injection: the first tile's first update waits on a
+                                      counter nothing advances, so the wait times out and the
+                                      launch ends with FD_ERR_TIMEOUT (GPU stays usable) */
+
+typedef struct fd_problem {
+    int ndim;            /* 1 or 2 */
+    int nx, ny;          /* interior points per axis (ny = 1 in 1-D), N = nx*ny >= 1 */
+    double gamma;        /* anomalous exponent, 0 < gamma < 2 */
+    double alpha;        /* diffusivity > 0 */
+    double dt, dx;       /* time step and grid spacing > 0 */
+    int bc;              /* FD_BC_DIRICHLET0 | FD_BC_NOFLUX (cell-centred mirror) */
+    double react[4];     /* f(u) = react[0] + react[1] u + react[2] u^2 + react[3] u^3 */
+    int mem_mode;        /* FD_MEM_FULL | FD_MEM_SHORT | FD_MEM_ADAPTIVE */
+    int mem_L;           /* short memory window in steps: lags 0..min(mem_L, k), mem_L >= 1 */
+    int mem_a;           /* adaptive base interval [0, a], a >= 2 */
+    int adaptive_rule;   /* FD_ADAPT_PAPER (literal Prop. 3.1) | FD_ADAPT_PARTITION */
+    int state_dtype;     /* FD_F64 | FD_F32 */
+    int hist_dtype;      /* FD_F64 (with F64 state) | FD_F32 | FD_BF16 | FD_F16 (F32 state) */
+    int accum_dtype;     /* FD_F64 (with F64 state) | FD_F32 */
+    unsigned flags;      /* FD_FLAG_* */
+    int max_steps;       /* capacity: total steps this handle may advance (>= 1) */
+    int ckpt_every;      /* adjoint checkpoint interval in steps (0 = 200) */
+    int timeout_ms;      /* limit on any device-side wait (0 = 10000) */
+    /* launch geometry (0 = automatic) */
+    int tile_threads;    /* threads per CTA: 64..512, multiple of 32; tile = threads*16/elt bytes */
+    int chunk_terms;     /* memory terms per work unit */
+    int stage_rows;      /* history rows per TMA stage */
+    int stages;          /* stages in the shared-memory ring */
+    int ctas_per_sm;     /* resident CTAs per SM for the persistent grid */
+} fd_problem;
+
+typedef struct fd_handle fd_handle;
+typedef struct fd_batch fd_batch;
+
+/* Host, FP64: GL weights psi(g, m) for m = 0..n-1 by the recurrence of Section 2.1
+ * (psi(g,0) = 1, psi(g,m) = psi(g,m-1) (m-2+g)/m) and, if dpsi != NULL, their
+ * derivative in g by differentiating the recurrence.  n >= 1. */
+int fd_weights(double gamma, int64_t n, double *psi, double *dpsi);
+
+/* Host: the memory terms sched(k) as the engine uses them (ascending lag; lag 0
+ * included, weight multiplicity 1 or d_i = 2i-1 for an adaptive median).  Writes
+ * at most cap entries into lags/mult and the term count into *n.  Defined by
+ * eq. frac_final, eq. frac_shortmemory and Proposition 3.1. */
+int fd_schedule(const fd_problem *p, int64_t k, int64_t *lags, int64_t *mult, int64_t cap,
+                int64_t *n);
+
+/* Host: bytes of device workspace a handle for *p needs (includes the adjoint's
+ * buffers when FD_FLAG_KEEP_TAPE is set). */
+int fd_workspace_bytes(const fd_problem *p, size_t *bytes);
+
+/* Bind a handle to a caller-owned device workspace and stream.  Validates p,
+ * checks stability (unless FD_FLAG_ALLOW_UNSTABLE), builds the weight and
+ * schedule tables on the host and uploads them.  The handle is at step 0 with
+ * an all-zero state until fd_set_state.  Synchronises the stream once. */
+int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_stream,
+            fd_handle **out);
+
+/* Copy u^0 (N values of state_dtype; device or host pointer) and reset to step 0. */
+int fd_set_state(fd_handle *h, const void *u0);
+
+/* Enqueue nsteps steps (one persistent launch); returns without synchronising.
+ * Fails with FD_ERR_STATE if the total would exceed max_steps. */
+int fd_step(fd_handle *h, int nsteps);
+
+/* fd_step(nsteps), then copy u^k to u_out (device or host; NULL = no copy),
+ * synchronise the stream and return the device status (FD_ERR_NONFINITE,
+ * FD_ERR_TIMEOUT, ...). */
+int fd_run(fd_handle *h, int nsteps, void *u_out);
+
+/* Enqueue a copy of the current state u^k to u_out (device or host). */
+int fd_get_state(fd_handle *h, void *u_out);
+
+/* Current step k of the handle. */
+int64_t fd_current_step(fd_handle *h);
+
+/* Reverse-time adjoint of J(u^K) for the K steps taken since fd_set_state
+ * (full memory, F32 or F64 state/history, FD_FLAG_KEEP_TAPE required).
+ * dJ_duK: N values (state dtype, device or host) = dJ/du^K.  Outputs dJ/du^0
+ * (N values, device or host; may be NULL) and the scalar gradients with respect
+ * to gamma (through psi and dt^g), alpha and react[0..3] (each may be NULL).
+ * Recomputes u between checkpoints every ckpt_every steps.  Synchronises. */
+int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma,
+               double *dJ_dalpha, double dJ_dreact[4]);
+
+/* Sticky device status of the last launches (synchronises the stream). */
+int fd_get_status(fd_handle *h);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+int fd_destroy(fd_handle *h);
+
+/* Launch geometry the handle resolved (for tuning and reports). */
+typedef struct fd_geometry {
+    int tile_threads, tile_points, tiles, chunk_terms, stage_rows, stages, ctas_per_sm, grid;
+    int64_t units_total;     /* work units for max_steps steps */
+    int64_t hist_rows_total; /* sum_k n(k): history rows read over max_steps steps (lags >= 1) */
+    int64_t terms_total;     /* sum_k N (n(k) + 1): GL terms over max_steps steps, lag 0 included */
+} fd_geometry;
+int fd_get_geometry(fd_handle *h, fd_geometry *g);
+
+/* ---- batches: many independent instances in one persistent launch ----
+ * Instance i runs probs[i].max_steps steps; all instances share one device
+ * work queue ordered by step, so uneven sizes and step counts balance across
+ * the GPU.  The launch is recorded once as a CUDA graph (workspace reset +
+ * persistent kernel) and replayed by fd_batch_run.  Histories and geometry
+ * follow each problem's fields; all instances must share state/history/accum
+ * dtypes and flags. */
+int fd_batch_workspace_bytes(const fd_problem *probs, int count, size_t *bytes);
+int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws_bytes,
+                  void *cuda_stream, fd_batch **out);
+int fd_batch_set_state(fd_batch *b, int i, const void *u0);   /* device or host */
+int fd_batch_run(fd_batch *b);                                 /* enqueue all steps */
+int fd_batch_get_state(fd_batch *b, int i, void *u_out);       /* enqueue copy of u^{K_i} */
+int fd_batch_get_status(fd_batch *b);                          /* synchronises */
+int fd_batch_destroy(fd_batch *b);
+
+/* One-shot batch: init, set u_io[i] as u^0, run, write u^{K_i} back to u_io[i]
+ * (device or host pointers), synchronise, destroy. */
+int fd_run_batch(const fd_problem *probs, int count, void *const *u_io, void *workspace,
+                 size_t ws_bytes, void *cuda_stream);
+
+const char *fd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FD_H */

@@ -1,0 +1,1076 @@
+// fd_api.cu -- host runtime behind include/fd.h.
+//
+// Builds the GL weights (Section 2.1 recurrence) and the memory schedule of each
+// step (eq. frac_final, eq. frac_shortmemory, Proposition 3.1) on the host in
+// FP64/integers, lays out the caller's workspace, uploads the tables and drives
+// the persistent engine (fd_engine.cuh): forward launches, the checkpointed
+// reverse-time adjoint, and multi-instance batches recorded as a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fd.h"
+#include "fd_kernels.h"
+
+using fdk::Inst;
+using fdk::Launch;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int dtype_size(int d)
+{
+    switch (d) {
+    case FD_F64: return 8;
+    case FD_F32: return 4;
+    case FD_BF16:
+    case FD_F16: return 2;
+    default: return 0;
+    }
+}
+
+// Bump allocator over the caller's workspace (base == nullptr: size only).
+struct Carve {
+    char *base;
+    size_t off = 0;
+    explicit Carve(char *b) : base(b) {}
+    char *take(size_t bytes)
+    {
+        off = align_up(off, kAlign);
+        char *p = base ? base + off : nullptr;
+        off += align_up(bytes, kAlign);
+        return p;
+    }
+};
+
+// ------------------------------------------------------------ weights, schedule
+
+// psi(g,0) = 1, psi(g,m) = psi(g,m-1) (m-2+g)/m ; dpsi is its derivative in g.
+void gl_weights(double g, int64_t n, double *psi, double *dpsi)
+{
+    psi[0] = 1.0;
+    if (dpsi) dpsi[0] = 0.0;
+    for (int64_t m = 1; m < n; ++m) {
+        const double f = ((double)m - 2.0 + g) / (double)m;
+        psi[m] = psi[m - 1] * f;
+        if (dpsi) dpsi[m] = dpsi[m - 1] * f + psi[m - 1] / (double)m;
+    }
+}
+
+struct Median {
+    int lag, mult;
+    int64_t end;  // last lag the increment stands for
+};
+
+// Adaptive medians in order of increment end, up to increments ending <= kmax.
+std::vector<Median> adaptive_medians(int64_t a, int rule, int64_t kmax)
+{
+    std::vector<Median> G;
+    if (a < 2) return G;
+    if (rule == FD_ADAPT_PAPER) {
+        // interval i >= 2: medians a^{i-1} + i + (eta-1)(2i-1) up to a^i, each standing for
+        // lags m-(i-1) .. m+(i-1); intervals restart at a^{i-1}+1 whatever the previous end
+        int64_t lo = a;  // a^{i-1}
+        for (int64_t i = 2; lo + 1 <= kmax; ++i) {
+            const int64_t hi = (lo > (int64_t)4e15 / a) ? (int64_t)4e15 : lo * a;
+            const int64_t d = 2 * i - 1;
+            for (int64_t m = lo + i; m <= hi; m += d) {
+                if (m + i - 1 > kmax) return G;
+                G.push_back({(int)m, (int)d, m + i - 1});
+            }
+            lo = hi;
+        }
+    } else {
+        // a cursor tiles lags a+1.. with consecutive increments of width 2i-1
+        int64_t c = a + 1, hi = a;
+        for (int64_t i = 2;; ++i) {
+            hi = (hi > (int64_t)4e15 / a) ? (int64_t)4e15 : hi * a;
+            const int64_t d = 2 * i - 1;
+            for (int64_t m = c + i - 1; m <= hi; m = c + i - 1) {
+                if (c + d - 1 > kmax) return G;
+                G.push_back({(int)m, (int)d, c + d - 1});
+                c += d;
+            }
+        }
+    }
+    return G;
+}
+
+// Per-step device schedule (lags >= 1): nb base lags 1..nb, ng medians G[0..ng),
+// tail lags tail_lo..tail_hi.
+struct Sched {
+    std::vector<int4> step;  // per k
+    std::vector<Median> G;
+};
+
+int build_schedule(const fd_problem &p, int64_t K, Sched &s)
+{
+    s.step.resize(K);
+    if (p.mem_mode == FD_MEM_ADAPTIVE) s.G = adaptive_medians(p.mem_a, p.adaptive_rule, K);
+    size_t g = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        int4 e = make_int4(0, 0, 1, 0);
+        if (p.mem_mode == FD_MEM_FULL) {
+            e.x = (int)k;
+        } else if (p.mem_mode == FD_MEM_SHORT) {
+            e.x = (int)std::min<int64_t>(p.mem_L, k);
+        } else if (k <= p.mem_a) {
+            e.x = (int)k;
+        } else {
+            e.x = p.mem_a;
+            while (g < s.G.size() && s.G[g].end <= k) ++g;
+            e.y = (int)g;
+            const int64_t last = g ? s.G[g - 1].end : p.mem_a;
+            e.z = (int)(last + 1);
+            e.w = (int)k;
+        }
+        s.step[k] = e;
+    }
+    return FD_OK;
+}
+
+inline int64_t n_terms(const int4 &e) { return (int64_t)e.x + e.y + (e.w >= e.z ? e.w - e.z + 1 : 0); }
+
+// ------------------------------------------------------------------ validation
+
+int validate(const fd_problem *p)
+{
+    if (!p) return FD_ERR_INVALID_ARG;
+    if (p->ndim != 1 && p->ndim != 2) return FD_ERR_INVALID_ARG;
+    if (p->nx < 1 || p->ny < 1 || (p->ndim == 1 && p->ny != 1)) return FD_ERR_INVALID_ARG;
+    if ((int64_t)p->nx * p->ny > (int64_t)1 << 30) return FD_ERR_INVALID_ARG;
+    if (!(p->gamma > 0.0 && p->gamma < 2.0)) return FD_ERR_INVALID_ARG;
+    if (!(p->alpha > 0.0) || !(p->dt > 0.0) || !(p->dx > 0.0)) return FD_ERR_INVALID_ARG;
+    for (double r : p->react)
+        if (!std::isfinite(r)) return FD_ERR_INVALID_ARG;
+    if (p->bc != FD_BC_DIRICHLET0 && p->bc != FD_BC_NOFLUX) return FD_ERR_INVALID_ARG;
+    if (p->mem_mode < FD_MEM_FULL || p->mem_mode > FD_MEM_ADAPTIVE) return FD_ERR_INVALID_ARG;
+    if (p->mem_mode == FD_MEM_SHORT && p->mem_L < 1) return FD_ERR_INVALID_ARG;
+    if (p->mem_mode == FD_MEM_ADAPTIVE && p->mem_a < 2) return FD_ERR_INVALID_ARG;
+    if (p->mem_mode == FD_MEM_ADAPTIVE && p->adaptive_rule != FD_ADAPT_PAPER &&
+        p->adaptive_rule != FD_ADAPT_PARTITION)
+        return FD_ERR_INVALID_ARG;
+    if (p->max_steps < 1 || p->max_steps > (1 << 28)) return FD_ERR_INVALID_ARG;
+    if (p->ckpt_every < 0 || p->timeout_ms < 0) return FD_ERR_INVALID_ARG;
+    if (p->tile_threads && (p->tile_threads < 32 || p->tile_threads > 512 || p->tile_threads % 32))
+        return FD_ERR_INVALID_ARG;
+    if (p->chunk_terms < 0 || p->stage_rows < 0 || p->stages < 0 || p->ctas_per_sm < 0)
+        return FD_ERR_INVALID_ARG;
+    if (p->stage_rows > 64 || p->stages > 16 || p->ctas_per_sm > 8) return FD_ERR_INVALID_ARG;
+    const bool kahan = p->flags & FD_FLAG_KAHAN;
+    const bool adj = p->flags & FD_FLAG_KEEP_TAPE;
+    if (!fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false))
+        return FD_ERR_UNSUPPORTED;
+    if (adj && (p->mem_mode != FD_MEM_FULL ||
+                !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)))
+        return FD_ERR_UNSUPPORTED;
+    if (!(p->flags & FD_FLAG_ALLOW_UNSTABLE)) {
+        // von Neumann bound of the full-memory scheme (checkerboard mode):
+        // S * 4 ndim * sum_m psi_m (-1)^m = 2 with sum_m psi_m (-1)^m = 2^{1-g}
+        const double S = p->alpha * std::pow(p->dt, p->gamma) / (p->dx * p->dx);
+        if (S > std::pow(2.0, p->gamma) / (4.0 * p->ndim) * (1.0 + 1e-12)) return FD_ERR_UNSTABLE;
+    }
+    return FD_OK;
+}
+
+// ------------------------------------------------------------------- geometry
+
+struct Geo {
+    int threads, V, P, T, R, RS, NS, ctas, grid, maxC;
+    int sh, ss, sa;  // element sizes: history, state, accumulator
+    int cap;
+    int64_t pitch, part_pitch;
+    size_t smem;
+    int planes;
+};
+
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
+{
+    const int64_t N = (int64_t)p.nx * p.ny;
+    g.sh = dtype_size(p.hist_dtype);
+    g.ss = dtype_size(p.state_dtype);
+    g.sa = dtype_size(p.accum_dtype);
+    g.V = 16 / g.sh;
+    g.planes = (p.flags & FD_FLAG_KEEP_TAPE) ? 2 : 1;
+    int th = threads_override ? threads_override : p.tile_threads;
+    if (!th) {
+        th = 256;
+        const int64_t need = (N + g.V - 1) / g.V;
+        while (th > 64 && need <= th / 2) th /= 2;
+    }
+    g.threads = th;
+    g.P = th * g.V;
+    g.T = (int)((N + g.P - 1) / g.P);
+    g.RS = p.stage_rows ? p.stage_rows : 8;
+    g.NS = p.stages ? p.stages : 4;
+    g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 1;
+    int sms = device_sms();
+    if (sms <= 0) sms = 152;
+    g.grid = sms * g.ctas;
+    int64_t nmax = 0;
+    for (const int4 &e : s.step) nmax = std::max(nmax, n_terms(e));
+    if (p.chunk_terms) {
+        g.R = p.chunk_terms;
+    } else {
+        int64_t r = (nmax * g.T + 4LL * g.grid - 1) / (4LL * g.grid);
+        r = std::max<int64_t>(r, 2 * g.RS);
+        r = std::min<int64_t>(r, 256);
+        r = (r + g.RS - 1) / g.RS * g.RS;
+        g.R = (int)r;
+    }
+    g.maxC = (int)std::max<int64_t>(1, (nmax + g.R - 1) / g.R);
+    g.cap = p.max_steps;
+    if (p.mem_mode == FD_MEM_SHORT) g.cap = (int)std::min<int64_t>((int64_t)p.mem_L + 1, p.max_steps);
+    g.cap = std::max(g.cap, 1);
+    g.pitch = (int64_t)align_up((size_t)N * g.sh, kAlign);
+    g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
+    g.smem = (size_t)g.NS * g.RS * g.threads * 16 + 2 * (size_t)g.NS * g.RS * g.sa + 16 + 8 * g.NS;
+}
+
+// Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
+inline int64_t step_units(const Geo &g, const int4 &e)
+{
+    const int64_t n = n_terms(e);
+    return (int64_t)g.T * std::max<int64_t>(1, (n + g.R - 1) / g.R);
+}
+
+// Device-side layout of one instance inside the workspace.
+struct Layout {
+    char *ubuf[2];
+    char *hist;
+    float *hscale;
+    char *part;
+    unsigned *arrive, *done;
+    char *psi, *dpsi, *gcoef;
+    int *glag;
+    int4 *sched;
+    // adjoint
+    char *ckpt, *seg, *rec[2], *ahist, *abuf[2];
+    double *dots;
+    int ckpt_rows, seg_rows;
+};
+
+void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s, Layout &L,
+                    unsigned *counters = nullptr, bool external_counters = false)
+{
+    const int64_t N = (int64_t)p.nx * p.ny;
+    const size_t ubytes = align_up((size_t)N * g.ss, kAlign);
+    L.ubuf[0] = c.take(ubytes);
+    L.ubuf[1] = c.take(ubytes);
+    L.hist = c.take((size_t)g.cap * g.pitch);
+    L.hscale = (p.hist_dtype == FD_F16) ? (float *)c.take((size_t)g.cap * g.T * sizeof(float)) : nullptr;
+    L.part = c.take((size_t)2 * g.maxC * g.planes * g.part_pitch);
+    L.arrive = external_counters ? counters : (unsigned *)c.take(sizeof(unsigned) * 3 * (size_t)g.T);
+    L.done = L.arrive ? L.arrive + 2 * g.T : nullptr;
+    L.psi = c.take((size_t)(p.max_steps + 1) * g.sa);
+    L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1) * g.sa) : nullptr;
+    L.sched = (int4 *)c.take(sizeof(int4) * (size_t)p.max_steps);
+    const size_t ng = std::max<size_t>(1, s.G.size());
+    L.glag = (int *)c.take(sizeof(int) * ng);
+    L.gcoef = c.take((size_t)g.sa * ng);
+    L.ckpt = L.seg = L.rec[0] = L.rec[1] = L.ahist = L.abuf[0] = L.abuf[1] = nullptr;
+    L.dots = nullptr;
+    L.ckpt_rows = L.seg_rows = 0;
+    if (p.flags & FD_FLAG_KEEP_TAPE) {
+        const int C = p.ckpt_every ? p.ckpt_every : 200;
+        L.ckpt_rows = p.max_steps / C + 1;
+        L.seg_rows = std::min(C, p.max_steps);
+        L.ckpt = c.take((size_t)L.ckpt_rows * N * g.ss);
+        L.seg = c.take((size_t)L.seg_rows * N * g.ss);
+        L.rec[0] = c.take(ubytes);
+        L.rec[1] = c.take(ubytes);
+        L.ahist = c.take((size_t)p.max_steps * g.pitch);
+        L.abuf[0] = c.take(ubytes);
+        L.abuf[1] = c.take(ubytes);
+        L.dots = (double *)c.take(sizeof(double) * 8 * (size_t)g.T);
+    }
+}
+
+// Control words shared by every launch of a handle / batch.
+struct Ctrl {
+    unsigned long long *queue;
+    int *err;
+    unsigned *nonfinite;
+};
+
+Ctrl carve_ctrl(Carve &c)
+{
+    char *b = c.take(256);
+    Ctrl r;
+    r.queue = (unsigned long long *)b;
+    r.err = b ? (int *)(b + 64) : nullptr;
+    r.nonfinite = b ? (unsigned *)(b + 128) : nullptr;
+    return r;
+}
+
+// Host-side tables of an instance, converted to the accumulator type.
+struct Tables {
+    std::vector<double> psi, dpsi;
+    std::vector<unsigned char> psi_a, dpsi_a, gcoef_a;
+    std::vector<int> glag;
+};
+
+template <class TA> void to_acc(const std::vector<double> &x, std::vector<unsigned char> &out)
+{
+    out.resize(x.size() * sizeof(TA));
+    TA *o = reinterpret_cast<TA *>(out.data());
+    for (size_t i = 0; i < x.size(); ++i) o[i] = (TA)x[i];
+}
+
+void build_tables(const fd_problem &p, const Sched &s, const Geo &g, Tables &t)
+{
+    const int64_t n = (int64_t)p.max_steps + 1;
+    t.psi.resize(n);
+    t.dpsi.resize(n);
+    gl_weights(p.gamma, n, t.psi.data(), t.dpsi.data());
+    std::vector<double> gc(std::max<size_t>(1, s.G.size()), 0.0);
+    t.glag.assign(gc.size(), 0);
+    for (size_t i = 0; i < s.G.size(); ++i) {
+        gc[i] = (double)s.G[i].mult * t.psi[s.G[i].lag];
+        t.glag[i] = s.G[i].lag;
+    }
+    if (g.sa == 8) {
+        to_acc<double>(t.psi, t.psi_a);
+        to_acc<double>(t.dpsi, t.dpsi_a);
+        to_acc<double>(gc, t.gcoef_a);
+    } else {
+        to_acc<float>(t.psi, t.psi_a);
+        to_acc<float>(t.dpsi, t.dpsi_a);
+        to_acc<float>(gc, t.gcoef_a);
+    }
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        if ((call) != cudaSuccess) {               \
+            (void)cudaGetLastError();              \
+            return FD_ERR_CUDA;                    \
+        }                                          \
+    } while (0)
+
+int upload_tables(const fd_problem &p, const Sched &s, const Tables &t, const Layout &L, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(L.psi, t.psi_a.data(), t.psi_a.size(), cudaMemcpyHostToDevice, st));
+    if (L.dpsi) CK(cudaMemcpyAsync(L.dpsi, t.dpsi_a.data(), t.dpsi_a.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(L.sched, s.step.data(), sizeof(int4) * s.step.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(L.glag, t.glag.data(), sizeof(int) * t.glag.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(L.gcoef, t.gcoef_a.data(), t.gcoef_a.size(), cudaMemcpyHostToDevice, st));
+    (void)p;
+    return FD_OK;
+}
+
+Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
+{
+    Inst I;
+    std::memset(&I, 0, sizeof(I));
+    I.ndim = p.ndim;
+    I.nx = p.nx;
+    I.ny = p.ny;
+    I.bc = p.bc;
+    I.N = p.nx * p.ny;
+    I.T = g.T;
+    I.P = g.P;
+    I.R = g.R;
+    I.hist_write = 1;
+    I.cap = adj ? p.max_steps : g.cap;
+    I.maxC = g.maxC;
+    I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
+    I.tape_every = 1;
+    I.S = p.alpha * std::pow(p.dt, p.gamma) / (p.dx * p.dx);
+    I.dt = p.dt;
+    for (int i = 0; i < 4; ++i) I.react[i] = p.react[i];
+    I.pitch = g.pitch;
+    I.part_pitch = g.part_pitch;
+    I.hist = adj ? L.ahist : L.hist;
+    I.hscale = adj ? nullptr : L.hscale;
+    I.ubuf[0] = adj ? L.abuf[0] : L.ubuf[0];
+    I.ubuf[1] = adj ? L.abuf[1] : L.ubuf[1];
+    I.part = L.part;
+    I.arrive = L.arrive;
+    I.done = L.done;
+    I.psi = L.psi;
+    I.dpsi = L.dpsi;
+    I.sched = L.sched;
+    I.g_lag = L.glag;
+    I.g_coef = L.gcoef;
+    if (!adj && L.ckpt) {
+        I.tape = L.ckpt;
+        I.tape_k0 = 0;
+        I.tape_every = p.ckpt_every ? p.ckpt_every : 200;
+        I.tape_rows = L.ckpt_rows;
+    }
+    if (adj) {
+        I.stall = 0;
+        I.uadj = L.seg;
+        I.dots = L.dots;
+    }
+    return I;
+}
+
+int set_smem_attr(const void *fn, size_t smem)
+{
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FD_ERR_CUDA;
+    }
+    return FD_OK;
+}
+
+int resolve_grid(const void *fn, Geo &g)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, g.threads, g.smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FD_ERR_CUDA;
+    }
+    if (occ < 1) return FD_ERR_INVALID_ARG;  // stage ring does not fit in shared memory
+    g.ctas = std::min(g.ctas, occ);
+    int sms = device_sms();
+    if (sms <= 0) return FD_ERR_CUDA;
+    g.grid = sms * g.ctas;
+    return FD_OK;
+}
+
+int status_from(int err, unsigned nonfinite)
+{
+    if (err == fdk::ERR_TIMEOUT || err == fdk::ERR_PIPE) return FD_ERR_TIMEOUT;
+    if (nonfinite) return FD_ERR_NONFINITE;
+    return FD_OK;
+}
+
+}  // namespace
+
+// ================================================================== handle
+
+struct fd_handle {
+    fd_problem p;
+    cudaStream_t st;
+    char *ws;
+    size_t ws_bytes;
+    Geo g;
+    Sched s;
+    Tables t;
+    Layout L;
+    Ctrl ctrl;
+    char *ctrl_zero_base;    // counters region to clear per launch
+    size_t ctrl_zero_bytes;
+    Inst inst_fwd, inst_adj;
+    Inst *d_inst;            // [0] forward, [1] adjoint / recompute scratch
+    long long *d_goff;
+    int2 *d_ginfo;
+    std::vector<long long> goff;
+    const void *kfwd, *kadj;
+    int64_t k;
+    int bad;                 // state invalid after a failed launch
+};
+
+static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin, int g_end, int k0)
+{
+    Launch L;
+    std::memset(&L, 0, sizeof(L));
+    L.inst = d_inst;
+    L.g_off = h->d_goff;
+    L.g_info = h->d_ginfo;
+    L.g_begin = g_begin;
+    L.g_end = g_end;
+    L.k0 = k0;
+    L.stage_rows = h->g.RS;
+    L.stages = h->g.NS;
+    L.queue = h->ctrl.queue;
+    L.err = h->ctrl.err;
+    L.nonfinite = h->ctrl.nonfinite;
+    L.timeout_ns = (long long)(h->p.timeout_ms ? h->p.timeout_ms : 10000) * 1000000LL;
+    CK(cudaMemsetAsync(h->ctrl.queue, 0, sizeof(unsigned long long), h->st));
+    CK(cudaMemsetAsync(h->ctrl_zero_base, 0, h->ctrl_zero_bytes, h->st));
+    const int64_t units = h->goff[g_end] - h->goff[g_begin];
+    const int grid = (int)std::min<int64_t>(h->g.grid, units);
+    void *args[] = {&L};
+    CK(cudaLaunchKernel(fn, dim3(grid), dim3(h->g.threads), args, h->g.smem, h->st));
+    return FD_OK;
+}
+
+static int prepare(const fd_problem *p, Sched &s, Geo &g, size_t *bytes, Layout *Lout, char *ws,
+                   Ctrl *ctrl)
+{
+    int rc = validate(p);
+    if (rc) return rc;
+    build_schedule(*p, p->max_steps, s);
+    make_geo(*p, s, 0, g);
+    Carve c(ws);
+    Ctrl cc = carve_ctrl(c);
+    Layout L;
+    carve_instance(c, *p, g, s, L);
+    c.take(sizeof(Inst) * 2);                                     // device instance descriptors
+    c.take(sizeof(long long) * (size_t)(p->max_steps + 1));       // group offsets
+    c.take(sizeof(int2) * (size_t)(p->max_steps + 1));            // group info
+    if (bytes) *bytes = c.off;
+    if (Lout) *Lout = L;
+    if (ctrl) *ctrl = cc;
+    return FD_OK;
+}
+
+extern "C" {
+
+int fd_weights(double gamma, int64_t n, double *psi, double *dpsi)
+{
+    if (n < 1 || !psi || !std::isfinite(gamma)) return FD_ERR_INVALID_ARG;
+    gl_weights(gamma, n, psi, dpsi);
+    return FD_OK;
+}
+
+int fd_schedule(const fd_problem *p, int64_t k, int64_t *lags, int64_t *mult, int64_t cap, int64_t *n)
+{
+    if (!p || k < 0 || !n || (cap > 0 && (!lags || !mult))) return FD_ERR_INVALID_ARG;
+    if (p->mem_mode == FD_MEM_SHORT && p->mem_L < 1) return FD_ERR_INVALID_ARG;
+    if (p->mem_mode == FD_MEM_ADAPTIVE && p->mem_a < 2) return FD_ERR_INVALID_ARG;
+    if (p->mem_mode < FD_MEM_FULL || p->mem_mode > FD_MEM_ADAPTIVE) return FD_ERR_INVALID_ARG;
+    fd_problem q = *p;
+    Sched s;
+    build_schedule(q, k + 1, s);
+    const int4 e = s.step[k];
+    int64_t cnt = 0;
+    auto put = [&](int64_t lag, int64_t m) {
+        if (cnt < cap) {
+            lags[cnt] = lag;
+            mult[cnt] = m;
+        }
+        ++cnt;
+    };
+    put(0, 1);
+    for (int i = 1; i <= e.x; ++i) put(i, 1);
+    for (int i = 0; i < e.y; ++i) put(s.G[i].lag, s.G[i].mult);
+    for (int i = e.z; i <= e.w; ++i) put(i, 1);
+    *n = cnt;
+    return FD_OK;
+}
+
+int fd_workspace_bytes(const fd_problem *p, size_t *bytes)
+{
+    if (!bytes) return FD_ERR_INVALID_ARG;
+    Sched s;
+    Geo g;
+    return prepare(p, s, g, bytes, nullptr, nullptr, nullptr);
+}
+
+int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_stream, fd_handle **out)
+{
+    if (!out) return FD_ERR_INVALID_ARG;
+    *out = nullptr;
+    fd_handle *h = new (std::nothrow) fd_handle();
+    if (!h) return FD_ERR_INVALID_ARG;
+    size_t need = 0;
+    int rc = prepare(p, h->s, h->g, &need, nullptr, nullptr, nullptr);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) || ws_bytes < need) {
+        delete h;
+        return FD_ERR_WORKSPACE;
+    }
+    h->p = *p;
+    h->st = (cudaStream_t)cuda_stream;
+    h->ws = (char *)workspace;
+    h->ws_bytes = ws_bytes;
+    prepare(p, h->s, h->g, nullptr, &h->L, h->ws, &h->ctrl);
+    {
+        Carve c(h->ws);
+        carve_ctrl(c);
+        Layout tmp;
+        carve_instance(c, *p, h->g, h->s, tmp);
+        h->d_inst = (Inst *)c.take(sizeof(Inst) * 2);
+        h->d_goff = (long long *)c.take(sizeof(long long) * (size_t)(p->max_steps + 1));
+        h->d_ginfo = (int2 *)c.take(sizeof(int2) * (size_t)(p->max_steps + 1));
+    }
+    h->ctrl_zero_base = (char *)h->L.arrive;
+    h->ctrl_zero_bytes = sizeof(unsigned) * 3 * (size_t)h->g.T;
+    const bool kahan = p->flags & FD_FLAG_KAHAN;
+    h->kfwd = fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
+    h->kadj = (p->flags & FD_FLAG_KEEP_TAPE)
+                  ? fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)
+                  : nullptr;
+    rc = set_smem_attr(h->kfwd, h->g.smem);
+    if (!rc && h->kadj) rc = set_smem_attr(h->kadj, h->g.smem);
+    if (!rc) rc = resolve_grid(h->kfwd, h->g);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    // group table: group k = step k of instance 0
+    h->goff.resize((size_t)p->max_steps + 1);
+    std::vector<int2> info((size_t)p->max_steps + 1);
+    long long acc = 0;
+    for (int k = 0; k < p->max_steps; ++k) {
+        h->goff[k] = acc;
+        info[k] = make_int2(0, k);
+        acc += step_units(h->g, h->s.step[k]);
+    }
+    h->goff[p->max_steps] = acc;
+    info[p->max_steps] = make_int2(0, p->max_steps);
+    build_tables(*p, h->s, h->g, h->t);
+    h->inst_fwd = make_inst(*p, h->g, h->L, false);
+    h->inst_adj = (p->flags & FD_FLAG_KEEP_TAPE) ? make_inst(*p, h->g, h->L, true) : h->inst_fwd;
+    cudaStream_t st = h->st;
+    // zero state, history (ragged padding included), scales and status words, then upload
+    const size_t used = (size_t)((char *)h->d_inst - h->ws);
+    if (cudaMemsetAsync(h->ws, 0, used, st) != cudaSuccess) rc = FD_ERR_CUDA;
+    if (!rc) rc = upload_tables(*p, h->s, h->t, h->L, st);
+    if (!rc && cudaMemcpyAsync(h->d_goff, h->goff.data(), sizeof(long long) * h->goff.size(),
+                               cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    if (!rc && cudaMemcpyAsync(h->d_ginfo, info.data(), sizeof(int2) * info.size(), cudaMemcpyHostToDevice,
+                               st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    Inst both[2] = {h->inst_fwd, h->inst_adj};
+    if (!rc && cudaMemcpyAsync(h->d_inst, both, sizeof(both), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = FD_ERR_CUDA;
+    if (rc) {
+        (void)cudaGetLastError();
+        delete h;
+        return rc;
+    }
+    h->k = 0;
+    h->bad = 0;
+    *out = h;
+    return FD_OK;
+}
+
+int fd_set_state(fd_handle *h, const void *u0)
+{
+    if (!h || !u0) return FD_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)h->p.nx * h->p.ny * h->g.ss;
+    CK(cudaMemcpyAsync(h->L.ubuf[0], u0, bytes, cudaMemcpyDefault, h->st));
+    if (h->L.ckpt) CK(cudaMemcpyAsync(h->L.ckpt, u0, bytes, cudaMemcpyDefault, h->st));
+    CK(cudaMemsetAsync(h->ctrl.err, 0, sizeof(int), h->st));
+    CK(cudaMemsetAsync(h->ctrl.nonfinite, 0, sizeof(unsigned), h->st));
+    h->k = 0;
+    h->bad = 0;
+    return FD_OK;
+}
+
+int fd_step(fd_handle *h, int nsteps)
+{
+    if (!h || nsteps < 0) return FD_ERR_INVALID_ARG;
+    if (h->bad) return FD_ERR_STATE;
+    if (h->k + nsteps > h->p.max_steps) return FD_ERR_STATE;
+    if (nsteps == 0) return FD_OK;
+    const int rc = launch(h, h->kfwd, h->d_inst, (int)h->k, (int)(h->k + nsteps), (int)h->k);
+    if (rc) return rc;
+    h->k += nsteps;
+    return FD_OK;
+}
+
+int fd_get_state(fd_handle *h, void *u_out)
+{
+    if (!h || !u_out) return FD_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)h->p.nx * h->p.ny * h->g.ss;
+    CK(cudaMemcpyAsync(u_out, h->L.ubuf[h->k & 1], bytes, cudaMemcpyDefault, h->st));
+    return FD_OK;
+}
+
+int64_t fd_current_step(fd_handle *h) { return h ? h->k : -1; }
+
+int fd_get_status(fd_handle *h)
+{
+    if (!h) return FD_ERR_INVALID_ARG;
+    int err = 0;
+    unsigned nf = 0;
+    CK(cudaMemcpyAsync(&err, h->ctrl.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&nf, h->ctrl.nonfinite, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const int s = status_from(err, nf);
+    if (s == FD_ERR_TIMEOUT) h->bad = 1;
+    return s;
+}
+
+int fd_run(fd_handle *h, int nsteps, void *u_out)
+{
+    int rc = fd_step(h, nsteps);
+    if (rc) return rc;
+    if (u_out) {
+        rc = fd_get_state(h, u_out);
+        if (rc) return rc;
+    }
+    return fd_get_status(h);
+}
+
+int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma, double *dJ_dalpha,
+               double dJ_dreact[4])
+{
+    if (!h || !dJ_duK) return FD_ERR_INVALID_ARG;
+    if (!(h->p.flags & FD_FLAG_KEEP_TAPE) || !h->kadj || h->bad || h->k < 1) return FD_ERR_STATE;
+    const fd_problem &p = h->p;
+    const int K = (int)h->k;
+    const int C = p.ckpt_every ? p.ckpt_every : 200;
+    const int64_t N = (int64_t)p.nx * p.ny;
+    const size_t ub = (size_t)N * h->g.ss;
+    cudaStream_t st = h->st;
+    int rc = FD_OK;
+    CK(cudaMemcpyAsync(h->L.abuf[0], dJ_duK, ub, cudaMemcpyDefault, st));
+    CK(cudaMemsetAsync(h->L.dots, 0, sizeof(double) * 8 * (size_t)h->g.T, st));
+    const int nseg = (K + C - 1) / C;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int c = sgi * C, ce = std::min(K, c + C);
+        // forward recompute of u^c .. u^{ce-1} into the segment buffer (history rows kept)
+        Inst rec = h->inst_fwd;
+        rec.ubuf[0] = h->L.rec[0];
+        rec.ubuf[1] = h->L.rec[1];
+        rec.hist_write = 0;
+        rec.stall = 0;
+        rec.tape = h->L.seg;
+        rec.tape_k0 = c;
+        rec.tape_every = 1;
+        rec.tape_rows = h->L.seg_rows;
+        Inst adj = h->inst_adj;
+        adj.uadj_r0 = c;
+        adj.adj_K = K;
+        CK(cudaMemcpyAsync(&h->d_inst[0], &rec, sizeof(Inst), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(&h->d_inst[1], &adj, sizeof(Inst), cudaMemcpyHostToDevice, st));
+        const char *uc = h->L.ckpt + (size_t)sgi * ub;
+        CK(cudaMemcpyAsync(h->L.rec[c & 1], uc, ub, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(h->L.seg, uc, ub, cudaMemcpyDeviceToDevice, st));
+        if (ce - c > 1) {
+            rc = launch(h, h->kfwd, &h->d_inst[0], c, ce - 1, c);
+            if (rc) break;
+        }
+        // adjoint steps q = K-ce .. K-1-c  (r = K-1-q from ce-1 down to c)
+        rc = launch(h, h->kadj, &h->d_inst[1], K - ce, K - c, K - ce);
+        if (rc) break;
+    }
+    // restore the forward descriptor
+    Inst both[2] = {h->inst_fwd, h->inst_adj};
+    if (cudaMemcpyAsync(h->d_inst, both, sizeof(both), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    if (rc) return rc;
+    std::vector<double> dots((size_t)8 * h->g.T);
+    CK(cudaMemcpyAsync(dots.data(), h->L.dots, sizeof(double) * dots.size(), cudaMemcpyDeviceToHost, st));
+    if (dJ_du0) CK(cudaMemcpyAsync(dJ_du0, h->L.abuf[K & 1], ub, cudaMemcpyDefault, st));
+    const int s = fd_get_status(h);  // synchronises
+    if (s) return s;
+    double d[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < h->g.T; ++t)
+        for (int i = 0; i < 6; ++i) d[i] += dots[(size_t)t * 8 + i];
+    const double S = p.alpha * std::pow(p.dt, p.gamma) / (p.dx * p.dx);
+    if (dJ_dalpha) *dJ_dalpha = (S / p.alpha) * d[0];
+    if (dJ_dgamma) *dJ_dgamma = S * (std::log(p.dt) * d[0] + d[1]);
+    if (dJ_dreact)
+        for (int i = 0; i < 4; ++i) dJ_dreact[i] = p.dt * d[2 + i];
+    return FD_OK;
+}
+
+int fd_get_geometry(fd_handle *h, fd_geometry *g)
+{
+    if (!h || !g) return FD_ERR_INVALID_ARG;
+    g->tile_threads = h->g.threads;
+    g->tile_points = h->g.P;
+    g->tiles = h->g.T;
+    g->chunk_terms = h->g.R;
+    g->stage_rows = h->g.RS;
+    g->stages = h->g.NS;
+    g->ctas_per_sm = h->g.ctas;
+    g->grid = h->g.grid;
+    g->units_total = h->goff.back();
+    int64_t rows = 0;
+    for (const int4 &e : h->s.step) rows += n_terms(e);
+    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    g->hist_rows_total = rows;
+    g->terms_total = (rows + (int64_t)h->s.step.size()) * N;
+    return FD_OK;
+}
+
+int fd_destroy(fd_handle *h)
+{
+    delete h;
+    return FD_OK;
+}
+
+const char *fd_strerror(int code)
+{
+    switch (code) {
+    case FD_OK: return "ok";
+    case FD_ERR_INVALID_ARG: return "invalid argument";
+    case FD_ERR_UNSTABLE: return "S exceeds the explicit stability bound 2^gamma/(4 ndim)";
+    case FD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case FD_ERR_CUDA: return "CUDA runtime error";
+    case FD_ERR_NONFINITE: return "non-finite value in the state";
+    case FD_ERR_TIMEOUT: return "device-side wait timed out";
+    case FD_ERR_STATE: return "call out of order for this handle";
+    case FD_ERR_UNSUPPORTED: return "unsupported dtype / mode combination";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"
+
+// =================================================================== batches
+
+struct fd_batch {
+    std::vector<fd_problem> p;
+    cudaStream_t st;
+    char *ws;
+    std::vector<Geo> g;
+    std::vector<Sched> s;
+    std::vector<Tables> t;
+    std::vector<Layout> L;
+    Ctrl ctrl;
+    unsigned *counters;
+    size_t counter_bytes;
+    Inst *d_inst;
+    long long *d_goff;
+    int2 *d_ginfo;
+    std::vector<long long> goff;
+    std::vector<int2> ginfo;
+    const void *kfn;
+    int threads, RS, NS, grid;
+    size_t smem;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+int batch_plan(const fd_problem *probs, int count, fd_batch &b, size_t *bytes, char *ws)
+{
+    if (!probs || count < 1) return FD_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        const int rc = validate(&probs[i]);
+        if (rc) return rc;
+        if (probs[i].state_dtype != probs[0].state_dtype || probs[i].hist_dtype != probs[0].hist_dtype ||
+            probs[i].accum_dtype != probs[0].accum_dtype ||
+            ((probs[i].flags ^ probs[0].flags) & (FD_FLAG_KAHAN | FD_FLAG_KEEP_TAPE)))
+            return FD_ERR_INVALID_ARG;
+        if (probs[i].flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
+    }
+    b.p.assign(probs, probs + count);
+    b.s.resize(count);
+    b.g.resize(count);
+    b.L.resize(count);
+    const int threads = probs[0].tile_threads ? probs[0].tile_threads : 256;
+    int64_t tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        build_schedule(probs[i], probs[i].max_steps, b.s[i]);
+        make_geo(probs[i], b.s[i], threads, b.g[i]);
+        tiles += b.g[i].T;
+    }
+    b.threads = threads;
+    b.RS = b.g[0].RS;
+    b.NS = b.g[0].NS;
+    b.smem = b.g[0].smem;
+    Carve c(ws);
+    b.ctrl = carve_ctrl(c);
+    b.counter_bytes = sizeof(unsigned) * 3 * (size_t)tiles;
+    b.counters = (unsigned *)c.take(b.counter_bytes);
+    int64_t toff = 0;
+    for (int i = 0; i < count; ++i) {
+        unsigned *cnt = b.counters ? b.counters + toff : nullptr;
+        carve_instance(c, probs[i], b.g[i], b.s[i], b.L[i], cnt, true);
+        toff += 3 * (int64_t)b.g[i].T;
+    }
+    // groups: step-major, then instance
+    int maxK = 0;
+    for (int i = 0; i < count; ++i) maxK = std::max(maxK, probs[i].max_steps);
+    b.goff.clear();
+    b.ginfo.clear();
+    long long acc = 0;
+    for (int k = 0; k < maxK; ++k)
+        for (int i = 0; i < count; ++i) {
+            if (k >= probs[i].max_steps) continue;
+            b.goff.push_back(acc);
+            b.ginfo.push_back(make_int2(i, k));
+            acc += step_units(b.g[i], b.s[i].step[k]);
+        }
+    b.goff.push_back(acc);
+    b.ginfo.push_back(make_int2(0, 0));
+    b.d_inst = (Inst *)c.take(sizeof(Inst) * (size_t)count);
+    b.d_goff = (long long *)c.take(sizeof(long long) * b.goff.size());
+    b.d_ginfo = (int2 *)c.take(sizeof(int2) * b.ginfo.size());
+    if (bytes) *bytes = c.off;
+    return FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fd_batch_workspace_bytes(const fd_problem *probs, int count, size_t *bytes)
+{
+    if (!bytes) return FD_ERR_INVALID_ARG;
+    fd_batch b;
+    return batch_plan(probs, count, b, bytes, nullptr);
+}
+
+int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws_bytes, void *cuda_stream,
+                  fd_batch **out)
+{
+    if (!out) return FD_ERR_INVALID_ARG;
+    *out = nullptr;
+    fd_batch *b = new (std::nothrow) fd_batch();
+    if (!b) return FD_ERR_INVALID_ARG;
+    b->graph = nullptr;
+    b->exec = nullptr;
+    size_t need = 0;
+    int rc = batch_plan(probs, count, *b, &need, nullptr);
+    if (!rc && (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) || ws_bytes < need))
+        rc = FD_ERR_WORKSPACE;
+    if (!rc) rc = batch_plan(probs, count, *b, nullptr, (char *)workspace);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    b->ws = (char *)workspace;
+    b->st = (cudaStream_t)cuda_stream;
+    const bool kahan = probs[0].flags & FD_FLAG_KAHAN;
+    b->kfn = fdk::kernel_for(probs[0].state_dtype, probs[0].hist_dtype, probs[0].accum_dtype, kahan, false);
+    Geo g0 = b->g[0];
+    rc = set_smem_attr(b->kfn, b->smem);
+    if (!rc) rc = resolve_grid(b->kfn, g0);
+    b->grid = g0.grid;
+    cudaStream_t st = b->st;
+    const size_t used = (size_t)((char *)b->d_inst - b->ws);
+    if (!rc && cudaMemsetAsync(b->ws, 0, used, st) != cudaSuccess) rc = FD_ERR_CUDA;
+    b->t.resize(count);
+    std::vector<Inst> insts(count);
+    for (int i = 0; i < count && !rc; ++i) {
+        build_tables(probs[i], b->s[i], b->g[i], b->t[i]);
+        rc = upload_tables(probs[i], b->s[i], b->t[i], b->L[i], st);
+        insts[i] = make_inst(probs[i], b->g[i], b->L[i], false);
+    }
+    if (!rc && cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst) * insts.size(), cudaMemcpyHostToDevice,
+                               st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    if (!rc && cudaMemcpyAsync(b->d_goff, b->goff.data(), sizeof(long long) * b->goff.size(),
+                               cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    if (!rc && cudaMemcpyAsync(b->d_ginfo, b->ginfo.data(), sizeof(int2) * b->ginfo.size(),
+                               cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = FD_ERR_CUDA;
+    // graph: clear control words and counters, then the persistent kernel
+    if (!rc) {
+        Launch L;
+        std::memset(&L, 0, sizeof(L));
+        L.inst = b->d_inst;
+        L.g_off = b->d_goff;
+        L.g_info = b->d_ginfo;
+        L.g_begin = 0;
+        L.g_end = (int)b->goff.size() - 1;
+        L.k0 = 0;
+        L.stage_rows = b->RS;
+        L.stages = b->NS;
+        L.queue = b->ctrl.queue;
+        L.err = b->ctrl.err;
+        L.nonfinite = b->ctrl.nonfinite;
+        L.timeout_ns = (long long)(probs[0].timeout_ms ? probs[0].timeout_ms : 10000) * 1000000LL;
+        cudaGraphNode_t m1, m2, kn;
+        cudaMemsetParams mp;
+        std::memset(&mp, 0, sizeof(mp));
+        mp.dst = b->ctrl.queue;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 256 / 4;  // queue, err and nonfinite share the 256-byte control block
+        mp.height = 1;
+        cudaMemsetParams mc = mp;
+        mc.dst = b->counters;
+        mc.width = b->counter_bytes / 4;
+        cudaKernelNodeParams kp;
+        std::memset(&kp, 0, sizeof(kp));
+        void *args[] = {&L};
+        kp.func = (void *)b->kfn;
+        kp.gridDim = dim3((unsigned)std::min<long long>(b->grid, b->goff.back()));
+        kp.blockDim = dim3(b->threads);
+        kp.sharedMemBytes = (unsigned)b->smem;
+        kp.kernelParams = args;
+        if (cudaGraphCreate(&b->graph, 0) != cudaSuccess ||
+            cudaGraphAddMemsetNode(&m1, b->graph, nullptr, 0, &mp) != cudaSuccess ||
+            cudaGraphAddMemsetNode(&m2, b->graph, &m1, 1, &mc) != cudaSuccess ||
+            cudaGraphAddKernelNode(&kn, b->graph, &m2, 1, &kp) != cudaSuccess ||
+            cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+            rc = FD_ERR_CUDA;
+    }
+    if (rc) {
+        (void)cudaGetLastError();
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return FD_OK;
+}
+
+int fd_batch_set_state(fd_batch *b, int i, const void *u0)
+{
+    if (!b || !u0 || i < 0 || i >= (int)b->p.size()) return FD_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)b->p[i].nx * b->p[i].ny * b->g[i].ss;
+    CK(cudaMemcpyAsync(b->L[i].ubuf[0], u0, bytes, cudaMemcpyDefault, b->st));
+    return FD_OK;
+}
+
+int fd_batch_run(fd_batch *b)
+{
+    if (!b) return FD_ERR_INVALID_ARG;
+    CK(cudaGraphLaunch(b->exec, b->st));
+    return FD_OK;
+}
+
+int fd_batch_get_state(fd_batch *b, int i, void *u_out)
+{
+    if (!b || !u_out || i < 0 || i >= (int)b->p.size()) return FD_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)b->p[i].nx * b->p[i].ny * b->g[i].ss;
+    CK(cudaMemcpyAsync(u_out, b->L[i].ubuf[b->p[i].max_steps & 1], bytes, cudaMemcpyDefault, b->st));
+    return FD_OK;
+}
+
+int fd_batch_get_status(fd_batch *b)
+{
+    if (!b) return FD_ERR_INVALID_ARG;
+    int err = 0;
+    unsigned nf = 0;
+    CK(cudaMemcpyAsync(&err, b->ctrl.err, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    CK(cudaMemcpyAsync(&nf, b->ctrl.nonfinite, sizeof(unsigned), cudaMemcpyDeviceToHost, b->st));
+    CK(cudaStreamSynchronize(b->st));
+    return status_from(err, nf);
+}
+
+int fd_batch_destroy(fd_batch *b)
+{
+    if (!b) return FD_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+    return FD_OK;
+}
+
+int fd_run_batch(const fd_problem *probs, int count, void *const *u_io, void *workspace, size_t ws_bytes,
+                 void *cuda_stream)
+{
+    if (!u_io) return FD_ERR_INVALID_ARG;
+    fd_batch *b = nullptr;
+    int rc = fd_batch_init(probs, count, workspace, ws_bytes, cuda_stream, &b);
+    if (rc) return rc;
+    for (int i = 0; i < count && !rc; ++i) rc = fd_batch_set_state(b, i, u_io[i]);
+    if (!rc) rc = fd_batch_run(b);
+    for (int i = 0; i < count && !rc; ++i) rc = fd_batch_get_state(b, i, u_io[i]);
+    if (!rc) rc = fd_batch_get_status(b);
+    fd_batch_destroy(b);
+    return rc;
+}
+
+}  // extern "C"

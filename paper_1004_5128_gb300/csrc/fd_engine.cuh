@@ -1,0 +1,709 @@
+// fd_engine.cuh -- persistent dataflow engine for the Grunwald-Letnikov memory sum.
+//
+// One launch advances one or many problem instances by a range of steps of
+// the explicit scheme (eq. frac_final):
+//     u^{k+1} = u^k + dt f(u^k) + S ( delta^k + H^k ),
+//     H^k     = sum_{(m,c) in sched(k), m >= 1} c delta^{k-m}        (the memory sum)
+// with delta^r = L u^r (eq. deltasimp) kept in a history ring, one row per step.
+//
+// Work decomposition.  For each (instance, step k) the N points are cut into
+// tiles of P points (P = threads x one 16-byte vector) and the memory terms of
+// sched(k) (ascending lag) into chunks of R terms.  A work unit is one
+// (tile, chunk); units are numbered step-major and claimed from a global
+// counter, so every unit waits only on units with smaller numbers and the
+// persistent grid cannot deadlock.  Within a step the oldest-lag chunks come
+// first; the chunk holding lag 1 (the only one needing the row written by the
+// previous step) comes last.
+//
+// Per unit: the CTA's elected thread streams the chunk's history row segments
+// (one cp.async.bulk per row, 16-byte aligned, no multicast) into a ring of
+// shared-memory stages completed by mbarrier transaction counts; every thread
+// owns one 16-byte vector column and accumulates c * row (optionally Kahan)
+// from shared memory.  A unit writes its partial sum; the last unit of a
+// (step, tile) to arrive (atomic arrival counter) sums the partials in fixed
+// chunk order (deterministic), evaluates the stencil on u^k, appends
+// delta^k to the history, applies the update and publishes the tile's step
+// counter.  Dependencies are per tile: a unit needs the rows it reads, the
+// fixup needs the halo tiles of u^k.  Every spin-wait is bounded by a
+// globaltimer limit after which the launch records FD_ERR_TIMEOUT and exits.
+//
+// Adjoint mode (ADJ) runs the same machinery on the reverse-time recursion
+//     mu^{r+1} = L lambda^{r+1},
+//     lambda^r = lambda^{r+1} + dt f'(u^r) lambda^{r+1} + S sum_{m>=0} psi_m mu^{r+1+m}
+// (L is symmetric for both boundary rules, so L^T g^r = sum psi_m L lambda),
+// with a second accumulator for psi' = d psi / d gamma and per-tile FP64 dot
+// products for the parameter gradients.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdk {
+
+enum { ERR_NONE = 0, ERR_TIMEOUT = 1, ERR_PIPE = 2 };
+
+// One problem instance as the device sees it (copied to shared memory per unit).
+struct Inst {
+    int ndim, nx, ny, bc;
+    int N, T, P, R;          // points, tiles, points per tile, terms per chunk
+    int hist_write;          // 0: history rows already hold delta (adjoint recompute pass)
+    int cap;                 // history ring rows
+    int maxC;                // partial rows per parity
+    int stall;               // fault injection: first fixup waits on a counter nothing advances
+    int tape_k0, tape_every, tape_rows;
+    int adj_K, uadj_r0;      // adjoint: u^r is row (adj_K-1-k) - uadj_r0 of uadj
+    double S, dt;
+    double react[4];
+    long long pitch;         // history row pitch (bytes, multiple of 256)
+    long long part_pitch;    // partial row pitch (bytes)
+    char *hist;
+    float *hscale;           // [cap][T] row-tile scales (FP16 history) or null
+    char *ubuf[2];           // state double buffer: u^k lives in ubuf[k & 1]
+    char *part;              // [2][maxC][planes] partial rows
+    unsigned *arrive;        // [2][T]
+    unsigned *done;          // [T] steps completed by each tile in this launch
+    const char *psi;         // weights in accumulator type
+    const char *dpsi;        // d psi / d gamma (adjoint)
+    const int4 *sched;       // per step: (nb, ng, tail_lo, tail_hi)
+    const int *g_lag;        // adaptive medians (prefix-ordered)
+    const char *g_coef;      // d * psi at the medians
+    char *tape;              // optional u rows (checkpoints / recompute segment)
+    const char *uadj;        // adjoint: forward states u^r
+    double *dots;            // adjoint: [T][8] per-tile gradient partials
+};
+
+struct Launch {
+    const Inst *inst;
+    const long long *g_off;  // unit offset of each (instance, step) group, +1 sentinel
+    const int2 *g_info;      // (instance, step) of each group
+    int g_begin, g_end;
+    int k0;                  // first step of the launch: tile step counters count from it
+    int stage_rows, stages;
+    unsigned long long *queue;
+    int *err;
+    unsigned *nonfinite;
+    long long timeout_ns;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return static_cast<long long>(t);
+}
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int *p)
+{
+    return *reinterpret_cast<const volatile int *>(p);
+}
+
+// Bounded wait until *p >= need (thread 0 only).  Returns false on timeout or
+// when another CTA has already recorded an error.
+__device__ __forceinline__ bool wait_counter(const unsigned *p, unsigned need, const Launch &L)
+{
+    if (ld_acquire(p) >= need) return true;
+    const long long t0 = globaltimer();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+        if (ld_acquire(p) >= need) return true;
+        if (ld_volatile(L.err) != ERR_NONE) return false;
+        if (globaltimer() - t0 > L.timeout_ns) {
+            atomicCAS(L.err, ERR_NONE, ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// ------------------------------------------------------- history vector traits
+template <class TH> struct HVec;
+template <> struct HVec<double> {
+    static constexpr int V = 2;
+    template <class TA> __device__ static void unpack(uint4 w, TA *x)
+    {
+        x[0] = (TA)__hiloint2double((int)w.y, (int)w.x);
+        x[1] = (TA)__hiloint2double((int)w.w, (int)w.z);
+    }
+    __device__ static uint4 pack(const double *d, float)
+    {
+        uint4 w;
+        w.x = (unsigned)__double2loint(d[0]);
+        w.y = (unsigned)__double2hiint(d[0]);
+        w.z = (unsigned)__double2loint(d[1]);
+        w.w = (unsigned)__double2hiint(d[1]);
+        return w;
+    }
+};
+template <> struct HVec<float> {
+    static constexpr int V = 4;
+    template <class TA> __device__ static void unpack(uint4 w, TA *x)
+    {
+        x[0] = (TA)__uint_as_float(w.x);
+        x[1] = (TA)__uint_as_float(w.y);
+        x[2] = (TA)__uint_as_float(w.z);
+        x[3] = (TA)__uint_as_float(w.w);
+    }
+    template <class TS> __device__ static uint4 pack(const TS *d, float)
+    {
+        return make_uint4(__float_as_uint((float)d[0]), __float_as_uint((float)d[1]),
+                          __float_as_uint((float)d[2]), __float_as_uint((float)d[3]));
+    }
+};
+template <> struct HVec<__nv_bfloat16> {
+    static constexpr int V = 8;
+    template <class TA> __device__ static void unpack(uint4 w, TA *x)
+    {
+        const unsigned a[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = (TA)__uint_as_float(a[i] << 16);
+            x[2 * i + 1] = (TA)__uint_as_float(a[i] & 0xffff0000u);
+        }
+    }
+    template <class TS> __device__ static uint4 pack(const TS *d, float)
+    {
+        unsigned a[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn((float)d[2 * i], (float)d[2 * i + 1]);
+            a[i] = *reinterpret_cast<unsigned *>(&h);
+        }
+        return make_uint4(a[0], a[1], a[2], a[3]);
+    }
+};
+template <> struct HVec<__half> {
+    static constexpr int V = 8;
+    template <class TA> __device__ static void unpack(uint4 w, TA *x)
+    {
+        const unsigned a[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&a[i]);
+            float2 f = __half22float2(h);
+            x[2 * i] = (TA)f.x;
+            x[2 * i + 1] = (TA)f.y;
+        }
+    }
+    // scale = 2^e chosen per (row, tile) so the largest |delta| lands in [2^14, 2^15)
+    template <class TS> __device__ static uint4 pack(const TS *d, float scale)
+    {
+        unsigned a[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h = __floats2half2_rn((float)d[2 * i] * scale, (float)d[2 * i + 1] * scale);
+            a[i] = *reinterpret_cast<unsigned *>(&h);
+        }
+        return make_uint4(a[0], a[1], a[2], a[3]);
+    }
+};
+
+template <class T> __device__ __forceinline__ bool finite_(T x) { return isfinite(x); }
+
+// Unit descriptor broadcast from thread 0.
+struct Unit {
+    int valid, inst, k, tile, chunk, C, tau0, tau1;
+    int4 sc;
+    int last;  // set for the arrival election
+};
+
+// Term tau of sched(k) (lags >= 1, ascending): lag and coefficient(s).
+template <class TA, bool ADJ>
+__device__ __forceinline__ void term_of(const Inst &I, const int4 sc, int tau, int &lag, TA &c, TA &c2)
+{
+    const TA *psi = reinterpret_cast<const TA *>(I.psi);
+    if (tau < sc.x) {
+        lag = tau + 1;
+        c = psi[lag];
+        if (ADJ) c2 = reinterpret_cast<const TA *>(I.dpsi)[lag];
+    } else if (tau < sc.x + sc.y) {
+        const int g = tau - sc.x;
+        lag = I.g_lag[g];
+        c = reinterpret_cast<const TA *>(I.g_coef)[g];
+        c2 = TA(0);
+    } else {
+        lag = sc.z + (tau - sc.x - sc.y);
+        c = psi[lag];
+        if (ADJ) c2 = reinterpret_cast<const TA *>(I.dpsi)[lag];
+    }
+}
+
+__device__ __forceinline__ int find_group(const long long *off, int g, int g_end, long long u)
+{
+    if (u < off[g + 1]) return g;
+    int lo = g + 1, step = 1, hi = lo + 1;
+    while (hi < g_end && off[hi] <= u) {
+        lo = hi;
+        step <<= 1;
+        hi = lo + step;
+    }
+    if (hi > g_end) hi = g_end;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <class TS, class TH, class TA, bool KAHAN, bool ADJ>
+__global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
+{
+    constexpr int V = HVec<TH>::V;
+    constexpr int PLANES = ADJ ? 2 : 1;
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    const int RS = L.stage_rows, NS = L.stages;
+    const int row_bytes = nthr * 16;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *stages = smem;
+    TA *coef = reinterpret_cast<TA *>(smem + (size_t)NS * RS * row_bytes);
+    TA *coef2 = coef + NS * RS;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(coef2 + NS * RS) + 15) & ~uintptr_t(15));
+
+    __shared__ Inst I;
+    __shared__ Unit U;
+    __shared__ int s_cur_inst;
+    __shared__ int s_ok;
+    __shared__ int s_pipe;
+    __shared__ float s_red[32];
+    __shared__ double s_dred[32][6];
+
+    if (tid == 0) {
+        for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        s_cur_inst = -1;
+    }
+    __syncthreads();
+
+    uint32_t n_issued = 0, n_used = 0;  // ring counters (identical in all threads)
+    int ghint = L.g_begin;
+    const long long u_base = L.g_off[L.g_begin];
+    const long long u_end = L.g_off[L.g_end];
+    unsigned long long next = 0;
+    if (tid == 0) next = atomicAdd(L.queue, 1ull);
+
+    for (;;) {
+        // ---------------------------------------------------------- claim
+        if (tid == 0) {
+            const long long u = u_base + (long long)next;
+            int ok = (u < u_end) && (ld_volatile(L.err) == ERR_NONE);
+            if (ok) {
+                next = atomicAdd(L.queue, 1ull);
+                const int g = find_group(L.g_off, ghint, L.g_end, u);
+                ghint = g;
+                const int2 gi = L.g_info[g];
+                if (gi.x != s_cur_inst) {
+                    I = L.inst[gi.x];
+                    s_cur_inst = gi.x;
+                }
+                const long long local = u - L.g_off[g];
+                const int C = (int)((L.g_off[g + 1] - L.g_off[g]) / I.T);
+                U.inst = gi.x;
+                U.k = gi.y;
+                U.tile = (int)(local % I.T);
+                U.C = C;
+                U.chunk = C - 1 - (int)(local / I.T);
+                const int4 sc = I.sched[gi.y];
+                U.sc = sc;
+                const int n = sc.x + sc.y + (sc.w >= sc.z ? sc.w - sc.z + 1 : 0);
+                U.tau0 = U.chunk * I.R;
+                U.tau1 = min(n, U.tau0 + I.R);
+                // dependencies: rows read (newest row k - lag_min) and partial-buffer reuse
+                const int rel = gi.y - L.k0;
+                int need = 0;
+                if (U.tau1 > U.tau0) {
+                    int lag;
+                    TA c, c2;
+                    term_of<TA, ADJ>(I, sc, U.tau0, lag, c, c2);
+                    const int r_hi = gi.y - lag;
+                    if (r_hi >= L.k0) need = r_hi - L.k0 + 1;
+                }
+                if (C > 1 && rel - 1 > need) need = rel - 1;
+                if (need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
+            }
+            U.valid = ok;
+        }
+        __syncthreads();
+        if (!U.valid) break;
+
+        const int tile = U.tile, k = U.k, C = U.C;
+        const int tau0 = U.tau0, tau1 = U.tau1;
+        const int nterm = tau1 - tau0;
+        const int nst = (nterm + RS - 1) / RS;
+        const int j0 = tile * I.P + tid * V;  // first point of this thread's vector
+        long long tile_bytes = (long long)min(I.P, I.N - tile * I.P) * (long long)sizeof(TH);
+        tile_bytes = (tile_bytes + 15) & ~15ll;
+
+        TA acc[V], cmp[V], acc2[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = cmp[v] = acc2[v] = TA(0);
+
+        // ------------------------------------------------- stream the chunk
+        auto issue = [&](int s) {  // thread 0: stage s of this unit into ring slot n_issued % NS
+            const int b = (int)(n_issued % (uint32_t)NS);
+            const int t0 = tau0 + s * RS;
+            const int t1 = min(tau1, t0 + RS);
+            for (int t = t0; t < t1; ++t) {
+                int lag;
+                TA c, c2;
+                term_of<TA, ADJ>(I, U.sc, t, lag, c, c2);
+                const int slot = (k - lag) % I.cap;
+                if (I.hscale) c = c * (TA)__ldcg(I.hscale + (size_t)slot * I.T + tile);
+                coef[b * RS + (t - t0)] = c;
+                if (ADJ) coef2[b * RS + (t - t0)] = c2;
+            }
+            mbar_expect_tx(&bars[b], (uint32_t)(tile_bytes * (t1 - t0)));
+            for (int t = t0; t < t1; ++t) {
+                int lag;
+                TA c, c2;
+                term_of<TA, ADJ>(I, U.sc, t, lag, c, c2);
+                const int slot = (k - lag) % I.cap;
+                const char *src = I.hist + (size_t)slot * I.pitch + (size_t)tile * I.P * sizeof(TH);
+                bulk_g2s(stages + ((size_t)b * RS + (t - t0)) * row_bytes, src, (uint32_t)tile_bytes, &bars[b]);
+            }
+        };
+        if (tid == 0) {
+            fence_proxy_async_global();
+            const int pre = min(NS, nst);
+            for (int s = 0; s < pre; ++s) {
+                issue(s);
+                ++n_issued;
+            }
+        } else {
+            n_issued += (uint32_t)min(NS, nst);
+        }
+        for (int s = 0; s < nst; ++s) {
+            const int b = (int)(n_used % (uint32_t)NS);
+            const uint32_t par = (n_used / (uint32_t)NS) & 1u;
+            if (!mbar_try_wait(&bars[b], par)) {
+                const long long t0 = globaltimer();
+                while (!mbar_try_wait(&bars[b], par)) {
+                    if (globaltimer() - t0 > L.timeout_ns) {
+                        atomicCAS(L.err, ERR_NONE, ERR_PIPE);
+                        break;  // the copy is still owed to this slot; see below
+                    }
+                }
+            }
+            const int rows = min(RS, nterm - s * RS);
+            const unsigned char *base = stages + (size_t)b * RS * row_bytes + (size_t)tid * 16;
+            for (int r = 0; r < rows; ++r) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(base + (size_t)r * row_bytes);
+                TA x[V];
+                HVec<TH>::unpack(w, x);
+                const TA c = coef[b * RS + r];
+                if (KAHAN) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const TA y = c * x[v] - cmp[v];
+                        const TA t = acc[v] + y;
+                        cmp[v] = (t - acc[v]) - y;
+                        acc[v] = t;
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = fma(c, x[v], acc[v]);
+                }
+                if (ADJ) {
+                    const TA c2 = coef2[b * RS + r];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc2[v] = fma(c2, x[v], acc2[v]);
+                }
+            }
+            ++n_used;
+            __syncthreads();  // slot b fully read by every thread
+            if (s + NS < nst) {
+                if (tid == 0) issue(s + NS);
+                ++n_issued;
+            }
+        }
+        if (tid == 0) s_pipe = (ld_volatile(L.err) == ERR_PIPE);
+        __syncthreads();
+        if (s_pipe) {
+            // A stage never completed: drain what is owed (bounded) and stop.
+            if (tid == 0) {
+                const long long t0 = globaltimer();
+                while (n_used < n_issued && globaltimer() - t0 < L.timeout_ns) {
+                    const int b = (int)(n_used % (uint32_t)NS);
+                    if (mbar_try_wait(&bars[b], (n_used / (uint32_t)NS) & 1u)) ++n_used;
+                }
+            }
+            break;
+        }
+        if (KAHAN) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] -= cmp[v];
+        }
+
+        // ------------------------------------------- partials and arrival
+        const int par = k & 1;
+        auto prow = [&](int c, int plane) -> TA * {
+            return reinterpret_cast<TA *>(I.part + ((size_t)((par * I.maxC + c) * PLANES + plane)) * I.part_pitch);
+        };
+        if (C > 1) {
+            if (j0 < I.N) {
+                TA *p0 = prow(U.chunk, 0) + j0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) p0[v] = acc[v];
+                if (ADJ) {
+                    TA *p1 = prow(U.chunk, 1) + j0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) p1[v] = acc2[v];
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                unsigned *ar = &I.arrive[par * I.T + tile];
+                const unsigned old = atom_add_acq_rel(ar, 1u);
+                U.last = (old == (unsigned)(C - 1));
+                if (U.last) *ar = 0u;  // reset for step k+2 (published by the done release below)
+            }
+            __syncthreads();
+            if (!U.last) continue;
+        }
+
+        // ------------------------------------------------------- fixup
+        const int rel = k - L.k0;
+        if (tid == 0) {
+            int ok = 1;
+            const int h = (I.ndim == 2) ? I.nx : 1;
+            const int lo = max(0, tile * I.P - h) / I.P;
+            const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
+            for (int t = lo; t <= hi && ok; ++t)
+                if (rel > 0 && !wait_counter(&I.done[t], (unsigned)rel, L)) ok = 0;
+            if (ok && I.stall && rel == 0 && tile == 0) {
+                // fault injection: nothing ever raises this counter to 2^31
+                if (!wait_counter(&I.done[tile], 0x80000000u, L)) ok = 0;
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+
+        TA H[V], H2[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            H[v] = TA(0);
+            H2[v] = TA(0);
+        }
+        if (C > 1) {
+            if (j0 < I.N) {
+                for (int c = 0; c < C; ++c) {
+                    if (c == U.chunk) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            H[v] += acc[v];
+                            if (ADJ) H2[v] += acc2[v];
+                        }
+                    } else {
+                        const TA *p0 = prow(c, 0) + j0;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) H[v] += __ldcg(p0 + v);
+                        if (ADJ) {
+                            const TA *p1 = prow(c, 1) + j0;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) H2[v] += __ldcg(p1 + v);
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                H[v] = acc[v];
+                H2[v] = acc2[v];
+            }
+        }
+
+        // stencil on u^k (eq. deltasimp), ghosts: 0 (Dirichlet) or mirror (no-flux)
+        const TS *uk = reinterpret_cast<const TS *>(I.ubuf[k & 1]);
+        TS *un = reinterpret_cast<TS *>(I.ubuf[(k + 1) & 1]);
+        const bool mirror = (I.bc == 1);
+        TS d[V], uc[V];
+        float amax = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int j = j0 + v;
+            d[v] = TS(0);
+            uc[v] = TS(0);
+            if (j < I.N) {
+                const TS c = __ldcg(uk + j);
+                const TS g = mirror ? c : TS(0);
+                uc[v] = c;
+                if (I.ndim == 1) {
+                    const TS r = (j + 1 < I.N) ? __ldcg(uk + j + 1) : g;
+                    const TS l = (j > 0) ? __ldcg(uk + j - 1) : g;
+                    d[v] = r - TS(2) * c + l;
+                } else {
+                    const int x = j % I.nx, y = j / I.nx;
+                    const TS r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : g;
+                    const TS l = (x > 0) ? __ldcg(uk + j - 1) : g;
+                    const TS up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : g;
+                    const TS dn = (y > 0) ? __ldcg(uk + j - I.nx) : g;
+                    d[v] = r + l - TS(4) * c + up + dn;
+                }
+                amax = fmaxf(amax, fabsf((float)d[v]));
+            }
+        }
+
+        // history row k (FP16: per (row, tile) power-of-two scale)
+        float hs = 1.f;
+        const int slot = k % I.cap;
+        if (I.hist_write) {
+            if (I.hscale) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                if ((tid & 31) == 0) s_red[tid >> 5] = amax;
+                __syncthreads();
+                if (tid == 0) {
+                    float m = 0.f;
+                    for (int w = 0; w < (nthr + 31) / 32; ++w) m = fmaxf(m, s_red[w]);
+                    int e = 0;
+                    if (m > 0.f && isfinite(m)) {
+                        int ex;
+                        frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
+                        e = max(-100, min(100, 15 - ex));
+                    }
+                    s_red[0] = ldexpf(1.f, e);
+                    I.hscale[(size_t)slot * I.T + tile] = ldexpf(1.f, -e);
+                }
+                __syncthreads();
+                hs = s_red[0];
+            }
+            if (j0 < I.N) {
+                TS dz[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) dz[v] = (j0 + v < I.N) ? d[v] : TS(0);
+                *reinterpret_cast<uint4 *>(I.hist + (size_t)slot * I.pitch + (size_t)j0 * sizeof(TH)) =
+                    HVec<TH>::pack(dz, hs);
+            }
+        }
+
+        // update (eq. frac_final; adjoint: reverse-time recursion)
+        const TS S = (TS)I.S, dt = (TS)I.dt;
+        const TS r0 = (TS)I.react[0], r1 = (TS)I.react[1], r2 = (TS)I.react[2], r3 = (TS)I.react[3];
+        double dl[6] = {0, 0, 0, 0, 0, 0};
+        bool bad = false;
+        const TS *ua = nullptr;
+        if (ADJ) ua = reinterpret_cast<const TS *>(I.uadj) + (size_t)((I.adj_K - 1 - k) - I.uadj_r0) * I.N;
+        const bool tape_row = I.tape && (k + 1 - I.tape_k0) >= 0 && ((k + 1 - I.tape_k0) % I.tape_every) == 0 &&
+                              ((k + 1 - I.tape_k0) / I.tape_every) < I.tape_rows;
+        TS *tp = tape_row ? reinterpret_cast<TS *>(I.tape) + (size_t)((k + 1 - I.tape_k0) / I.tape_every) * I.N
+                          : nullptr;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int j = j0 + v;
+            if (j >= I.N) continue;
+            const TA G = (TA)d[v] + H[v];  // psi_0 delta^k + memory sum
+            TS nv;
+            if (!ADJ) {
+                const TS u = uc[v];
+                const TS f = r0 + u * (r1 + u * (r2 + u * r3));
+                nv = u + dt * f + S * (TS)G;
+            } else {
+                const TS lam = uc[v];
+                const TS ur = __ldcg(ua + j);
+                const TS fp = r1 + ur * (TS(2) * r2 + ur * TS(3) * r3);
+                nv = lam + dt * fp * lam + S * (TS)G;
+                dl[0] += (double)ur * (double)G;
+                dl[1] += (double)ur * (double)H2[v];
+                double pw = 1.0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    dl[2 + i] += (double)lam * pw;
+                    pw *= (double)ur;
+                }
+            }
+            bad |= !finite_(nv);
+            un[j] = nv;
+            if (tp) tp[j] = nv;
+        }
+        if (bad) atomicOr(L.nonfinite, 1u);
+        if (ADJ) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dl[i] += __shfl_xor_sync(0xffffffffu, dl[i], o);
+            if ((tid & 31) == 0)
+#pragma unroll
+                for (int i = 0; i < 6; ++i) s_dred[tid >> 5][i] = dl[i];
+        }
+        fence_proxy_async_global();
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            if (ADJ) {
+                double *dd = I.dots + (size_t)tile * 8;
+                for (int i = 0; i < 6; ++i) {
+                    double s = 0.0;
+                    for (int w = 0; w < (nthr + 31) / 32; ++w) s += s_dred[w][i];
+                    dd[i] += s;
+                }
+                __threadfence();
+            }
+            st_release(&I.done[tile], (unsigned)(rel + 1));
+        }
+    }
+}
+
+}  // namespace fdk

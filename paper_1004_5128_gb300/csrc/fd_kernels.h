@@ -1,0 +1,12 @@
+// fd_kernels.h -- registry of the engine's template instantiations (internal).
+#pragma once
+#include "fd_engine.cuh"
+
+namespace fdk {
+// Kernel for (state, history, accumulator) dtypes (FD_F64/FD_F32/FD_BF16/FD_F16 codes),
+// Kahan accumulation and adjoint mode; nullptr when the combination is not built.
+const void *kernel_for(int state, int hist, int acc, bool kahan, bool adj);
+const void *kernel_f64(bool kahan, bool adj);
+const void *kernel_f32(bool kahan, bool adj);
+const void *kernel_lowp(int hist, bool kahan, bool adj);
+}  // namespace fdk

@@ -1,0 +1,117 @@
+"""CPU tests of the C ABI's host side: symbols, weights, schedules, validation, workspace sizing.
+No kernel runs here (no GPU in this environment)."""
+import ctypes
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_5128_gb300 import _lib as L
+from paper_1004_5128_gb300 import build as B
+from paper_1004_5128_gb300 import make_problem, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    L.lib()
+
+
+def test_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "fd.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|int64_t|const char \*)\s*\**\s*(fd_\w+)\s*\(", hdr, re.M))
+    assert declared == set(L.EXPORTS)
+    lib = ctypes.CDLL(L.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_weights_match_oracle():
+    for g in (0.3, 0.5, 0.8, 1.0, 1.5):
+        a, da = L.fd_weights(g, 20001, with_derivative=True)
+        b, db = oracle.weights(g, 20001, with_derivative=True)
+        assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)) < 1e-13
+        m = np.abs(db) > 0
+        assert np.max(np.abs(da[m] - db[m]) / np.abs(db[m])) < 1e-12
+
+
+@pytest.mark.parametrize("mode,L_,a,rule", [(0, 0, 0, 0), (1, 1, 0, 0), (1, 7, 0, 0), (1, 500, 0, 0),
+                                            (2, 0, 2, 0), (2, 0, 3, 0), (2, 0, 10, 0), (2, 0, 50, 0),
+                                            (2, 0, 2, 1), (2, 0, 3, 1), (2, 0, 10, 1)])
+def test_schedule_matches_oracle(mode, L_, a, rule):
+    """The engine's integer schedule (prefix of medians + tail range) equals the oracle's
+    literal enumeration at every step, bit for bit."""
+    p = synth.with_mode(synth.config2(K=10), mode, L=L_, a=a, rule=rule)
+    fp = make_problem(p, max_steps=10)
+    for k in list(range(0, 200)) + [999, 4999, 7777, 10008, 10009, 12345]:
+        lag, mult = L.fd_schedule(fp, k)
+        olag, omult = oracle.schedule(mode, L_, a, rule, k)
+        assert np.array_equal(lag, olag) and np.array_equal(mult, omult), k
+
+
+def test_validation_codes():
+    p = synth.config2(K=10)
+    fp = make_problem(p, max_steps=10)
+    fp.gamma = 2.5
+    with pytest.raises(L.FdError) as e:
+        L.fd_workspace_bytes(fp)
+    assert e.value.code == L.FD_ERR_INVALID_ARG
+    fp = make_problem(p, max_steps=10)
+    fp.dt = p["dt"] * 100  # S far above 2^g / 8
+    with pytest.raises(L.FdError) as e:
+        L.fd_workspace_bytes(fp)
+    assert e.value.code == L.FD_ERR_UNSTABLE
+    fp.flags |= L.FD_FLAG_ALLOW_UNSTABLE
+    assert L.fd_workspace_bytes(fp) > 0
+    # adjoint supports full memory only
+    q = make_problem(synth.with_mode(p, synth.MEM_SHORT, L=5), max_steps=10, keep_tape=True)
+    with pytest.raises(L.FdError) as e:
+        L.fd_workspace_bytes(q)
+    assert e.value.code == L.FD_ERR_UNSUPPORTED
+    # bf16 history with an f64 state is not a built combination
+    q = make_problem(p, max_steps=10, state="f64", hist="bf16")
+    with pytest.raises(L.FdError) as e:
+        L.fd_workspace_bytes(q)
+    assert e.value.code == L.FD_ERR_UNSUPPORTED
+    for bad in (dict(mem_mode=synth.MEM_SHORT, mem_L=0), dict(mem_mode=synth.MEM_ADAPTIVE, mem_a=1)):
+        q = dict(p)
+        q.update(bad)
+        with pytest.raises(L.FdError):
+            L.fd_workspace_bytes(make_problem(q, max_steps=10))
+
+
+def test_init_rejects_small_or_misaligned_workspace():
+    p = make_problem(synth.config1(K=10), state="f64")
+    need = L.fd_workspace_bytes(p)
+    h = ctypes.c_void_p(0)
+    assert L.lib().fd_init(ctypes.byref(p), ctypes.c_void_p(1 << 20), need - 1, None, ctypes.byref(h)) \
+        == L.FD_ERR_WORKSPACE
+    assert L.lib().fd_init(ctypes.byref(p), ctypes.c_void_p((1 << 20) + 16), need, None,
+                           ctypes.byref(h)) == L.FD_ERR_WORKSPACE
+    assert L.lib().fd_init(ctypes.byref(p), None, need, None, ctypes.byref(h)) == L.FD_ERR_WORKSPACE
+
+
+def test_workspace_scales_with_history():
+    full = L.fd_workspace_bytes(make_problem(synth.config2(K=5000)))
+    short = L.fd_workspace_bytes(make_problem(synth.config2(synth.MEM_SHORT, K=5000)))
+    bf = L.fd_workspace_bytes(make_problem(synth.config2(K=5000), hist="bf16"))
+    assert 1.30e9 < full < 1.40e9          # 5000 rows x 256 KiB of FP32 delta history
+    assert short < 0.15e9                  # ring of L+1 = 501 rows
+    assert 0.6e9 < bf < 0.7e9
+    tape = L.fd_workspace_bytes(make_problem(synth.config5(K=4000), keep_tape=True))
+    assert tape > 2 * 4000 * 128 * 128 * 4  # forward + adjoint histories
+
+
+def test_batch_workspace():
+    probs = [make_problem(p) for p in synth.config4(count=8, steps_range=(100, 300),
+                                                    side_range=(16, 40), n1_range=(16, 300))]
+    assert L.fd_batch_workspace_bytes(probs) > 0
+
+
+def test_strerror():
+    assert "stability" in L.fd_strerror(L.FD_ERR_UNSTABLE)
+    assert L.fd_strerror(0) == "ok"
