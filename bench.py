@@ -97,7 +97,18 @@ class Clocks:
 
 # --------------------------------------------------------------------------- workloads
 
-def workload(name: str):
+def workload(name: str, K: int = 0, modes: str = ""):
+    runs = _workload(name)
+    if modes:
+        keep = modes.split(",")
+        runs = [r for r in runs if r[0] in keep]
+    if K:
+        for _, p, _ in runs:
+            p["K"] = K
+    return runs
+
+
+def _workload(name: str):
     from paper_1004_5128_gb300 import synth
     if name == "c2":
         return [("full", synth.config2(synth.MEM_FULL), {}),
@@ -134,7 +145,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     runs = []
-    for name, p, kw in workload(args.workload):
+    for name, p, kw in workload(args.workload, args.K, args.modes):
         s = FRD(p, device=dev, **kw)
         geo = s.geometry()
         runs.append(dict(name=name, p=p, kw=kw, solver=s, geo=geo,
@@ -244,7 +255,7 @@ def run_ours(args):
     launches = len(runs) * args.steps  # one persistent engine launch per run
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(args.workload, args.cpu_seconds)
+        cpu = cpu_baseline(args.workload, args.cpu_seconds, args.K, args.modes)
     if rank == 0:
         dtype = runs[0]["kw"].get("state", "f32")
         line = {
@@ -268,11 +279,11 @@ def run_ours(args):
 
 # ---------------------------------------------------------------------------- CPU oracle
 
-def _oracle_sample(name, seconds):
+def _oracle_sample(name, seconds, K=0, modes=""):
     """Run the oracle on the first K' steps of each run of the workload, K' grown until the
     whole sample takes about `seconds`.  Returns (terms, wall seconds, description)."""
     import oracle
-    runs = workload(name)
+    runs = workload(name, K, modes)
     threads = os.cpu_count() or 1
     kp = 8
     while True:
@@ -292,8 +303,8 @@ def _oracle_sample(name, seconds):
     return terms, t, threads, f"first {kp} steps of each run ({', '.join(r[0] for r in runs)})"
 
 
-def cpu_baseline(name, seconds):
-    terms, t, threads, desc = _oracle_sample(name, seconds)
+def cpu_baseline(name, seconds, K=0, modes=""):
+    terms, t, threads, desc = _oracle_sample(name, seconds, K, modes)
     return {"value": terms / t, "unit": "terms/s", "cores": threads, "kind": "oracle",
             "sample": desc + f"; {terms:.3e} terms in {t:.1f} s, OpenMP over grid points"}
 
@@ -306,7 +317,7 @@ def run_reference(args):
     desc = ""
     total_t = 0.0
     for i in range(args.warmup + args.steps):
-        terms, t, threads, desc = _oracle_sample(args.workload, args.cpu_seconds)
+        terms, t, threads, desc = _oracle_sample(args.workload, args.cpu_seconds, args.K, args.modes)
         if i >= args.warmup:
             vals.append((terms, t))
             total_t += t
@@ -335,6 +346,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--K", type=int, default=0, help="override the step count (profiling cases)")
+    ap.add_argument("--modes", default="", help="comma list of runs to keep, e.g. full")
     args = ap.parse_args()
     if args.impl == "reference":
         args.cpu_seconds = min(args.cpu_seconds, 8.0)

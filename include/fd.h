@@ -59,6 +59,7 @@ enum { FD_F64 = 0, FD_F32 = 1, FD_BF16 = 2, FD_F16 = 3 };
 #define FD_FLAG_KAHAN 1u           /* compensated FP32 accumulation of the memory sum */
 #define FD_FLAG_ALLOW_UNSTABLE 2u  /* skip the stability pre-check */
 #define FD_FLAG_KEEP_TAPE 4u       /* keep what fd_adjoint needs (u checkpoints, adjoint buffers) */
+#define FD_FLAG_PLAIN_STATE 16u   /* F32 state without the hi/lo compensation (see fd_problem) */
 #define FD_FLAG_INJECT_STALL 8u    /* fault injection: the first tile's first update waits on a
                                       counter nothing advances, so the wait times out and the
                                       launch ends with FD_ERR_TIMEOUT (GPU stays usable) */
@@ -75,7 +76,10 @@ typedef struct fd_problem {
     int mem_L;           /* short memory window in steps: lags 0..min(mem_L, k), mem_L >= 1 */
     int mem_a;           /* adaptive base interval [0, a], a >= 2 */
     int adaptive_rule;   /* FD_ADAPT_PAPER (literal Prop. 3.1) | FD_ADAPT_PARTITION */
-    int state_dtype;     /* FD_F64 | FD_F32 */
+    int state_dtype;     /* FD_F64 | FD_F32.  An F32 state is kept as a compensated hi + lo pair
+                            (TwoSum update), so per-step increments far below half an ulp of u
+                            still accumulate; FD_FLAG_PLAIN_STATE turns this off.  Values read
+                            and written through the ABI are the hi part. */
     int hist_dtype;      /* FD_F64 (with F64 state) | FD_F32 | FD_BF16 | FD_F16 (F32 state) */
     int accum_dtype;     /* FD_F64 (with F64 state) | FD_F32 */
     unsigned flags;      /* FD_FLAG_* */
@@ -88,6 +92,8 @@ typedef struct fd_problem {
     int stage_rows;      /* history rows per TMA stage */
     int stages;          /* stages in the shared-memory ring */
     int ctas_per_sm;     /* resident CTAs per SM for the persistent grid */
+    int head_lags;       /* lags 1..head_lags are summed by the per-tile update from rows kept in
+                            state precision (0 = 8 for F32/F64 history, 32 for BF16/F16) */
 } fd_problem;
 
 typedef struct fd_handle fd_handle;
@@ -152,6 +158,7 @@ int fd_destroy(fd_handle *h);
 /* Launch geometry the handle resolved (for tuning and reports). */
 typedef struct fd_geometry {
     int tile_threads, tile_points, tiles, chunk_terms, stage_rows, stages, ctas_per_sm, grid;
+    int head_lags;
     int64_t units_total;     /* work units for max_steps steps */
     int64_t hist_rows_total; /* sum_k n(k): history rows read over max_steps steps (lags >= 1) */
     int64_t terms_total;     /* sum_k N (n(k) + 1): GL terms over max_steps steps, lag 0 included */

@@ -31,6 +31,7 @@ FD_FLAG_KAHAN = 1
 FD_FLAG_ALLOW_UNSTABLE = 2
 FD_FLAG_KEEP_TAPE = 4
 FD_FLAG_INJECT_STALL = 8
+FD_FLAG_PLAIN_STATE = 16
 
 # every function include/fd.h declares
 EXPORTS = (
@@ -60,13 +61,14 @@ class FdProblem(ctypes.Structure):
         ("flags", ctypes.c_uint), ("max_steps", ctypes.c_int), ("ckpt_every", ctypes.c_int),
         ("timeout_ms", ctypes.c_int),
         ("tile_threads", ctypes.c_int), ("chunk_terms", ctypes.c_int), ("stage_rows", ctypes.c_int),
-        ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+        ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("head_lags", ctypes.c_int),
     ]
 
 
 class FdGeometry(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("tile_threads", "tile_points", "tiles", "chunk_terms",
-                                            "stage_rows", "stages", "ctas_per_sm", "grid")] + [
+                                            "stage_rows", "stages", "ctas_per_sm", "grid",
+                                            "head_lags")] + [
         ("units_total", ctypes.c_int64), ("hist_rows_total", ctypes.c_int64),
         ("terms_total", ctypes.c_int64)]
 

@@ -165,6 +165,7 @@ int validate(const fd_problem *p)
     if (p->chunk_terms < 0 || p->stage_rows < 0 || p->stages < 0 || p->ctas_per_sm < 0)
         return FD_ERR_INVALID_ARG;
     if (p->stage_rows > 64 || p->stages > 16 || p->ctas_per_sm > 8) return FD_ERR_INVALID_ARG;
+    if (p->head_lags < 0 || p->head_lags > 4096) return FD_ERR_INVALID_ARG;
     const bool kahan = p->flags & FD_FLAG_KAHAN;
     const bool adj = p->flags & FD_FLAG_KEEP_TAPE;
     if (!fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false))
@@ -185,12 +186,22 @@ int validate(const fd_problem *p)
 
 struct Geo {
     int threads, V, P, T, R, RS, NS, ctas, grid, maxC;
+    int head;        // lags summed by the fixup
+    int hring_sep;   // separate state-precision head ring
+    int hring_cap;
+    int64_t hring_pitch;
     int sh, ss, sa;  // element sizes: history, state, accumulator
     int cap;
     int64_t pitch, part_pitch;
     size_t smem;
     int planes;
 };
+
+// Dynamic shared memory: stage ring, per-unit term tables (R coefficients x2, R slots), barriers.
+inline size_t smem_bytes(const Geo &g, int rmax)
+{
+    return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)rmax * (2 * g.sa + 4) + 32 + 8 * (size_t)g.NS;
+}
 
 int device_sms()
 {
@@ -218,13 +229,19 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.P = th * g.V;
     g.T = (int)((N + g.P - 1) / g.P);
     g.RS = p.stage_rows ? p.stage_rows : 8;
-    g.NS = p.stages ? p.stages : 4;
-    g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 1;
+    g.NS = p.stages ? p.stages : 3;
+    g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 2;
     int sms = device_sms();
     if (sms <= 0) sms = 152;
     g.grid = sms * g.ctas;
+    g.cap = p.max_steps;
+    if (p.mem_mode == FD_MEM_SHORT) g.cap = (int)std::min<int64_t>((int64_t)p.mem_L + 1, p.max_steps);
+    g.cap = std::max(g.cap, 1);
+    g.hring_sep = (p.hist_dtype != p.state_dtype);
+    g.head = p.head_lags ? p.head_lags : (g.hring_sep ? 32 : 8);
+    if (!g.hring_sep && g.cap < g.head + 1) g.head = std::max(1, g.cap - 1);
     int64_t nmax = 0;
-    for (const int4 &e : s.step) nmax = std::max(nmax, n_terms(e));
+    for (const int4 &e : s.step) nmax = std::max(nmax, n_terms(e) - std::min<int64_t>(g.head, e.x));
     if (p.chunk_terms) {
         g.R = p.chunk_terms;
     } else {
@@ -235,25 +252,26 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         g.R = (int)r;
     }
     g.maxC = (int)std::max<int64_t>(1, (nmax + g.R - 1) / g.R);
-    g.cap = p.max_steps;
-    if (p.mem_mode == FD_MEM_SHORT) g.cap = (int)std::min<int64_t>((int64_t)p.mem_L + 1, p.max_steps);
-    g.cap = std::max(g.cap, 1);
     g.pitch = (int64_t)align_up((size_t)N * g.sh, kAlign);
+    g.hring_cap = g.hring_sep ? g.head + 1 : g.cap;
+    g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = (size_t)g.NS * g.RS * g.threads * 16 + 2 * (size_t)g.NS * g.RS * g.sa + 16 + 8 * g.NS;
+    g.smem = smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
 inline int64_t step_units(const Geo &g, const int4 &e)
 {
-    const int64_t n = n_terms(e);
+    const int64_t n = n_terms(e) - std::min<int64_t>(g.head, e.x);
     return (int64_t)g.T * std::max<int64_t>(1, (n + g.R - 1) / g.R);
 }
 
 // Device-side layout of one instance inside the workspace.
 struct Layout {
     char *ubuf[2];
+    char *ulo[2], *alo[2], *rlo[2];  // compensated-state low parts (forward, adjoint, recompute)
     char *hist;
+    char *hring;
     float *hscale;
     char *part;
     unsigned *arrive, *done;
@@ -273,7 +291,15 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     const size_t ubytes = align_up((size_t)N * g.ss, kAlign);
     L.ubuf[0] = c.take(ubytes);
     L.ubuf[1] = c.take(ubytes);
+    const bool comp = p.state_dtype == FD_F32 && !(p.flags & FD_FLAG_PLAIN_STATE);
+    const bool adj = p.flags & FD_FLAG_KEEP_TAPE;
+    for (int i = 0; i < 2; ++i) {
+        L.ulo[i] = comp ? c.take(ubytes) : nullptr;
+        L.alo[i] = (comp && adj) ? c.take(ubytes) : nullptr;
+        L.rlo[i] = (comp && adj) ? c.take(ubytes) : nullptr;
+    }
     L.hist = c.take((size_t)g.cap * g.pitch);
+    L.hring = g.hring_sep ? c.take((size_t)g.hring_cap * g.hring_pitch) : L.hist;
     L.hscale = (p.hist_dtype == FD_F16) ? (float *)c.take((size_t)g.cap * g.T * sizeof(float)) : nullptr;
     L.part = c.take((size_t)2 * g.maxC * g.planes * g.part_pitch);
     L.arrive = external_counters ? counters : (unsigned *)c.take(sizeof(unsigned) * 3 * (size_t)g.T);
@@ -398,9 +424,16 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.pitch = g.pitch;
     I.part_pitch = g.part_pitch;
     I.hist = adj ? L.ahist : L.hist;
+    I.head = g.head;
+    I.hring_sep = adj ? 0 : g.hring_sep;
+    I.hring = adj ? L.ahist : L.hring;
+    I.hring_cap = adj ? p.max_steps : g.hring_cap;
+    I.hring_pitch = adj ? g.pitch : g.hring_pitch;
     I.hscale = adj ? nullptr : L.hscale;
     I.ubuf[0] = adj ? L.abuf[0] : L.ubuf[0];
     I.ubuf[1] = adj ? L.abuf[1] : L.ubuf[1];
+    I.ulo[0] = adj ? L.alo[0] : L.ulo[0];
+    I.ulo[1] = adj ? L.alo[1] : L.ulo[1];
     I.part = L.part;
     I.arrive = L.arrive;
     I.done = L.done;
@@ -492,6 +525,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.k0 = k0;
     L.stage_rows = h->g.RS;
     L.stages = h->g.NS;
+    L.rmax = h->g.R;
     L.queue = h->ctrl.queue;
     L.err = h->ctrl.err;
     L.nonfinite = h->ctrl.nonfinite;
@@ -657,6 +691,7 @@ int fd_set_state(fd_handle *h, const void *u0)
     if (!h || !u0) return FD_ERR_INVALID_ARG;
     const size_t bytes = (size_t)h->p.nx * h->p.ny * h->g.ss;
     CK(cudaMemcpyAsync(h->L.ubuf[0], u0, bytes, cudaMemcpyDefault, h->st));
+    if (h->L.ulo[0]) CK(cudaMemsetAsync(h->L.ulo[0], 0, bytes, h->st));
     if (h->L.ckpt) CK(cudaMemcpyAsync(h->L.ckpt, u0, bytes, cudaMemcpyDefault, h->st));
     CK(cudaMemsetAsync(h->ctrl.err, 0, sizeof(int), h->st));
     CK(cudaMemsetAsync(h->ctrl.nonfinite, 0, sizeof(unsigned), h->st));
@@ -724,6 +759,7 @@ int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma
     cudaStream_t st = h->st;
     int rc = FD_OK;
     CK(cudaMemcpyAsync(h->L.abuf[0], dJ_duK, ub, cudaMemcpyDefault, st));
+    if (h->L.alo[0]) CK(cudaMemsetAsync(h->L.alo[0], 0, ub, st));
     CK(cudaMemsetAsync(h->L.dots, 0, sizeof(double) * 8 * (size_t)h->g.T, st));
     const int nseg = (K + C - 1) / C;
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
@@ -732,6 +768,9 @@ int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma
         Inst rec = h->inst_fwd;
         rec.ubuf[0] = h->L.rec[0];
         rec.ubuf[1] = h->L.rec[1];
+        rec.ulo[0] = h->L.rlo[0];
+        rec.ulo[1] = h->L.rlo[1];
+        if (rec.ulo[0]) CK(cudaMemsetAsync(h->L.rlo[c & 1], 0, ub, st));
         rec.hist_write = 0;
         rec.stall = 0;
         rec.tape = h->L.seg;
@@ -786,6 +825,7 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     g->stages = h->g.NS;
     g->ctas_per_sm = h->g.ctas;
     g->grid = h->g.grid;
+    g->head_lags = h->g.head;
     g->units_total = h->goff.back();
     int64_t rows = 0;
     for (const int4 &e : h->s.step) rows += n_terms(e);
@@ -838,7 +878,7 @@ struct fd_batch {
     std::vector<long long> goff;
     std::vector<int2> ginfo;
     const void *kfn;
-    int threads, RS, NS, grid;
+    int threads, RS, NS, grid, rmax;
     size_t smem;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -872,7 +912,9 @@ int batch_plan(const fd_problem *probs, int count, fd_batch &b, size_t *bytes, c
     b.threads = threads;
     b.RS = b.g[0].RS;
     b.NS = b.g[0].NS;
-    b.smem = b.g[0].smem;
+    b.rmax = 0;
+    for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].R);
+    b.smem = smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
     b.ctrl = carve_ctrl(c);
     b.counter_bytes = sizeof(unsigned) * 3 * (size_t)tiles;
@@ -974,6 +1016,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         L.k0 = 0;
         L.stage_rows = b->RS;
         L.stages = b->NS;
+        L.rmax = b->rmax;
         L.queue = b->ctrl.queue;
         L.err = b->ctrl.err;
         L.nonfinite = b->ctrl.nonfinite;
@@ -1020,6 +1063,7 @@ int fd_batch_set_state(fd_batch *b, int i, const void *u0)
     if (!b || !u0 || i < 0 || i >= (int)b->p.size()) return FD_ERR_INVALID_ARG;
     const size_t bytes = (size_t)b->p[i].nx * b->p[i].ny * b->g[i].ss;
     CK(cudaMemcpyAsync(b->L[i].ubuf[0], u0, bytes, cudaMemcpyDefault, b->st));
+    if (b->L[i].ulo[0]) CK(cudaMemsetAsync(b->L[i].ulo[0], 0, bytes, b->st));
     return FD_OK;
 }
 

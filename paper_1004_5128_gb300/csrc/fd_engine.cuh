@@ -52,15 +52,21 @@ struct Inst {
     int cap;                 // history ring rows
     int maxC;                // partial rows per parity
     int stall;               // fault injection: first fixup waits on a counter nothing advances
+    int head;                // lags 1..head are summed by the fixup from the head rows
+    int hring_cap;           // rows in the head ring (== cap when it is the history itself)
+    int hring_sep;           // 1: separate state-precision ring (low-precision history)
     int tape_k0, tape_every, tape_rows;
     int adj_K, uadj_r0;      // adjoint: u^r is row (adj_K-1-k) - uadj_r0 of uadj
     double S, dt;
     double react[4];
     long long pitch;         // history row pitch (bytes, multiple of 256)
     long long part_pitch;    // partial row pitch (bytes)
+    long long hring_pitch;   // head ring row pitch (bytes)
+    char *hring;             // head rows in state precision (the history itself when TH == TS)
     char *hist;
     float *hscale;           // [cap][T] row-tile scales (FP16 history) or null
     char *ubuf[2];           // state double buffer: u^k lives in ubuf[k & 1]
+    char *ulo[2];            // compensated state: low parts (null = plain state)
     char *part;              // [2][maxC][planes] partial rows
     unsigned *arrive;        // [2][T]
     unsigned *done;          // [T] steps completed by each tile in this launch
@@ -81,6 +87,7 @@ struct Launch {
     int g_begin, g_end;
     int k0;                  // first step of the launch: tile step counters count from it
     int stage_rows, stages;
+    int rmax;                // largest chunk (terms) over the launch's instances
     unsigned long long *queue;
     int *err;
     unsigned *nonfinite;
@@ -256,6 +263,41 @@ template <> struct HVec<__half> {
 
 template <class T> __device__ __forceinline__ bool finite_(T x) { return isfinite(x); }
 
+// V consecutive state values (16-byte aligned groups), loaded bypassing L1 / stored.
+template <class TS, int V> __device__ __forceinline__ void load_vec(const TS *p, TS *x)
+{
+    if constexpr (sizeof(TS) == 8) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+            const double2 w = __ldcg(reinterpret_cast<const double2 *>(p + i));
+            x[i] = (TS)w.x;
+            x[i + 1] = (TS)w.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; i += 4) {
+            const float4 w = __ldcg(reinterpret_cast<const float4 *>(p + i));
+            x[i] = (TS)w.x;
+            x[i + 1] = (TS)w.y;
+            x[i + 2] = (TS)w.z;
+            x[i + 3] = (TS)w.w;
+        }
+    }
+}
+template <class TS, int V> __device__ __forceinline__ void store_vec(TS *p, const TS *x)
+{
+    if constexpr (sizeof(TS) == 8) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2)
+            *reinterpret_cast<double2 *>(p + i) = make_double2((double)x[i], (double)x[i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; i += 4)
+            *reinterpret_cast<float4 *>(p + i) =
+                make_float4((float)x[i], (float)x[i + 1], (float)x[i + 2], (float)x[i + 3]);
+    }
+}
+
 // Unit descriptor broadcast from thread 0.
 struct Unit {
     int valid, inst, k, tile, chunk, C, tau0, tau1;
@@ -314,10 +356,11 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *stages = smem;
-    TA *coef = reinterpret_cast<TA *>(smem + (size_t)NS * RS * row_bytes);
-    TA *coef2 = coef + NS * RS;
+    TA *coef = reinterpret_cast<TA *>(smem + (size_t)NS * RS * row_bytes);  // per-unit term tables
+    TA *coef2 = coef + L.rmax;
+    int *toff = reinterpret_cast<int *>(coef2 + L.rmax);                   // history slot per term
     uint64_t *bars = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(coef2 + NS * RS) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(toff + L.rmax) + 15) & ~uintptr_t(15));
 
     __shared__ Inst I;
     __shared__ Unit U;
@@ -366,7 +409,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 const int4 sc = I.sched[gi.y];
                 U.sc = sc;
                 const int n = sc.x + sc.y + (sc.w >= sc.z ? sc.w - sc.z + 1 : 0);
-                U.tau0 = U.chunk * I.R;
+                U.tau0 = min(I.head, sc.x) + U.chunk * I.R;
                 U.tau1 = min(n, U.tau0 + I.R);
                 // dependencies: rows read (newest row k - lag_min) and partial-buffer reuse
                 const int rel = gi.y - L.k0;
@@ -378,7 +421,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     const int r_hi = gi.y - lag;
                     if (r_hi >= L.k0) need = r_hi - L.k0 + 1;
                 }
-                if (C > 1 && rel - 1 > need) need = rel - 1;
+                if (C > 1 && rel - 1 > need) need = rel - 1;  // partial rows of step k-2 consumed
                 if (need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
             }
             U.valid = ok;
@@ -399,28 +442,27 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         for (int v = 0; v < V; ++v) acc[v] = cmp[v] = acc2[v] = TA(0);
 
         // ------------------------------------------------- stream the chunk
+        // term tables of this unit, built by the whole CTA: coefficient(s) and history slot
+        for (int t = tid; t < nterm; t += nthr) {
+            int lag;
+            TA c, c2;
+            term_of<TA, ADJ>(I, U.sc, tau0 + t, lag, c, c2);
+            const int slot = (k - lag) % I.cap;
+            if (I.hscale) c = c * (TA)__ldcg(I.hscale + (size_t)slot * I.T + tile);
+            coef[t] = c;
+            if (ADJ) coef2[t] = c2;
+            toff[t] = slot;
+        }
+        __syncthreads();
         auto issue = [&](int s) {  // thread 0: stage s of this unit into ring slot n_issued % NS
             const int b = (int)(n_issued % (uint32_t)NS);
-            const int t0 = tau0 + s * RS;
-            const int t1 = min(tau1, t0 + RS);
-            for (int t = t0; t < t1; ++t) {
-                int lag;
-                TA c, c2;
-                term_of<TA, ADJ>(I, U.sc, t, lag, c, c2);
-                const int slot = (k - lag) % I.cap;
-                if (I.hscale) c = c * (TA)__ldcg(I.hscale + (size_t)slot * I.T + tile);
-                coef[b * RS + (t - t0)] = c;
-                if (ADJ) coef2[b * RS + (t - t0)] = c2;
-            }
+            const int t0 = s * RS;
+            const int t1 = min(nterm, t0 + RS);
             mbar_expect_tx(&bars[b], (uint32_t)(tile_bytes * (t1 - t0)));
-            for (int t = t0; t < t1; ++t) {
-                int lag;
-                TA c, c2;
-                term_of<TA, ADJ>(I, U.sc, t, lag, c, c2);
-                const int slot = (k - lag) % I.cap;
-                const char *src = I.hist + (size_t)slot * I.pitch + (size_t)tile * I.P * sizeof(TH);
-                bulk_g2s(stages + ((size_t)b * RS + (t - t0)) * row_bytes, src, (uint32_t)tile_bytes, &bars[b]);
-            }
+            const char *col = I.hist + (size_t)tile * I.P * sizeof(TH);
+            for (int t = t0; t < t1; ++t)
+                bulk_g2s(stages + ((size_t)b * RS + (t - t0)) * row_bytes, col + (size_t)toff[t] * I.pitch,
+                         (uint32_t)tile_bytes, &bars[b]);
         };
         if (tid == 0) {
             fence_proxy_async_global();
@@ -450,7 +492,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 const uint4 w = *reinterpret_cast<const uint4 *>(base + (size_t)r * row_bytes);
                 TA x[V];
                 HVec<TH>::unpack(w, x);
-                const TA c = coef[b * RS + r];
+                const TA c = coef[s * RS + r];
                 if (KAHAN) {
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
@@ -464,7 +506,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     for (int v = 0; v < V; ++v) acc[v] = fma(c, x[v], acc[v]);
                 }
                 if (ADJ) {
-                    const TA c2 = coef2[b * RS + r];
+                    const TA c2 = coef2[s * RS + r];
 #pragma unroll
                     for (int v = 0; v < V; ++v) acc2[v] = fma(c2, x[v], acc2[v]);
                 }
@@ -575,6 +617,47 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             }
         }
 
+        // head lags 1..h from the most recent rows (state precision), fixed order
+        {
+            const int h = min(I.head, U.sc.x);
+            const TA *psi = reinterpret_cast<const TA *>(I.psi);
+            const TA *dpsi = reinterpret_cast<const TA *>(I.dpsi);
+            TA hs[V], hc[V], hs2[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) hs[v] = hc[v] = hs2[v] = TA(0);
+            if (j0 < I.N) {
+                for (int m = h; m >= 1; --m) {
+                    const TS *row = reinterpret_cast<const TS *>(
+                        I.hring + (size_t)((k - m) % I.hring_cap) * I.hring_pitch) + j0;
+                    TS x[V];
+                    load_vec<TS, V>(row, x);
+                    const TA c = psi[m];
+                    if (KAHAN) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const TA y = c * (TA)x[v] - hc[v];
+                            const TA t = hs[v] + y;
+                            hc[v] = (t - hs[v]) - y;
+                            hs[v] = t;
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) hs[v] = fma(c, (TA)x[v], hs[v]);
+                    }
+                    if (ADJ) {
+                        const TA c2 = dpsi[m];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) hs2[v] = fma(c2, (TA)x[v], hs2[v]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                H[v] += KAHAN ? (hs[v] - hc[v]) : hs[v];
+                if (ADJ) H2[v] += hs2[v];
+            }
+        }
+
         // stencil on u^k (eq. deltasimp), ghosts: 0 (Dirichlet) or mirror (no-flux)
         const TS *uk = reinterpret_cast<const TS *>(I.ubuf[k & 1]);
         TS *un = reinterpret_cast<TS *>(I.ubuf[(k + 1) & 1]);
@@ -636,6 +719,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 for (int v = 0; v < V; ++v) dz[v] = (j0 + v < I.N) ? d[v] : TS(0);
                 *reinterpret_cast<uint4 *>(I.hist + (size_t)slot * I.pitch + (size_t)j0 * sizeof(TH)) =
                     HVec<TH>::pack(dz, hs);
+                if (I.hring_sep)
+                    store_vec<TS, V>(reinterpret_cast<TS *>(I.hring + (size_t)(k % I.hring_cap) * I.hring_pitch) + j0, dz);
             }
         }
 
@@ -646,6 +731,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         bool bad = false;
         const TS *ua = nullptr;
         if (ADJ) ua = reinterpret_cast<const TS *>(I.uadj) + (size_t)((I.adj_K - 1 - k) - I.uadj_r0) * I.N;
+        const TS *lo_k = I.ulo[0] ? reinterpret_cast<const TS *>(I.ulo[k & 1]) : nullptr;
+        TS *lo_n = I.ulo[0] ? reinterpret_cast<TS *>(I.ulo[(k + 1) & 1]) : nullptr;
         const bool tape_row = I.tape && (k + 1 - I.tape_k0) >= 0 && ((k + 1 - I.tape_k0) % I.tape_every) == 0 &&
                               ((k + 1 - I.tape_k0) / I.tape_every) < I.tape_rows;
         TS *tp = tape_row ? reinterpret_cast<TS *>(I.tape) + (size_t)((k + 1 - I.tape_k0) / I.tape_every) * I.N
@@ -655,16 +742,30 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             const int j = j0 + v;
             if (j >= I.N) continue;
             const TA G = (TA)d[v] + H[v];  // psi_0 delta^k + memory sum
-            TS nv;
+            TS nv, inc;
+            const TS x = uc[v];
             if (!ADJ) {
-                const TS u = uc[v];
-                const TS f = r0 + u * (r1 + u * (r2 + u * r3));
-                nv = u + dt * f + S * (TS)G;
+                const TS f = r0 + x * (r1 + x * (r2 + x * r3));
+                inc = dt * f + S * (TS)G;
             } else {
-                const TS lam = uc[v];
                 const TS ur = __ldcg(ua + j);
                 const TS fp = r1 + ur * (TS(2) * r2 + ur * TS(3) * r3);
-                nv = lam + dt * fp * lam + S * (TS)G;
+                inc = dt * fp * x + S * (TS)G;
+            }
+            if (lo_k) {
+                // state kept as hi + lo: TwoSum of hi and (increment + lo) (Knuth), so increments
+                // far below half an ulp of the state still accumulate
+                const TS y = inc + __ldcg(lo_k + j);
+                const TS sum = x + y;
+                const TS bb = sum - x;
+                lo_n[j] = (x - (sum - bb)) + (y - bb);
+                nv = sum;
+            } else {
+                nv = x + inc;
+            }
+            if (ADJ) {
+                const TS lam = x;
+                const TS ur = __ldcg(ua + j);
                 dl[0] += (double)ur * (double)G;
                 dl[1] += (double)ur * (double)H2[v];
                 double pw = 1.0;
