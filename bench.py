@@ -145,8 +145,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     runs = []
+    geo_over = {}
+    for item in filter(None, args.geom.split(",")):
+        k_, v_ = item.split("=")
+        geo_over[k_] = int(v_)
     for name, p, kw in workload(args.workload, args.K, args.modes):
-        s = FRD(p, device=dev, **kw)
+        s = FRD(p, device=dev, **kw, **geo_over)
         geo = s.geometry()
         runs.append(dict(name=name, p=p, kw=kw, solver=s, geo=geo,
                          u0=torch.from_numpy(p["u0"]).to(dev, s.dtype)))
@@ -348,6 +352,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--K", type=int, default=0, help="override the step count (profiling cases)")
     ap.add_argument("--modes", default="", help="comma list of runs to keep, e.g. full")
+    ap.add_argument("--geom", default="", help="launch geometry overrides, e.g. chunk_terms=256")
     args = ap.parse_args()
     if args.impl == "reference":
         args.cpu_seconds = min(args.cpu_seconds, 8.0)

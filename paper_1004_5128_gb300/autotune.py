@@ -1,0 +1,145 @@
+"""Launch-geometry autotuner for the engine.
+
+The engine's launch geometry (threads per CTA, memory terms per work unit, rows per
+TMA stage, ring stages, resident CTAs per SM, head lags) trades parallelism against
+per-unit overhead, and the best point depends on the grid size, the step count, the
+history dtype and the memory mode.  `tune` times candidates on the GPU (CUDA events
+around whole runs, so every step's work is included) by coordinate descent from the
+library's defaults and caches the winner in a JSON file keyed by
+(dtypes, memory mode, dimension, N bucket, K bucket).  `lookup` returns a cached
+geometry (or {} when none is known); `FRD(..., **lookup(p, ...))` applies it.
+
+Cache path: $FD_TUNE_CACHE, else ~/.cache/fd_tune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+import torch
+
+from . import _lib as L
+from .frd import FRD, FRDBatch
+
+PARAMS = {
+    "tile_threads": [128, 256, 512],
+    "chunk_terms": [32, 64, 128, 256, 512],
+    "stage_rows": [4, 8, 16],
+    "stages": [2, 3, 4, 6],
+    "ctas_per_sm": [1, 2, 3],
+}
+
+
+def cache_path() -> str:
+    return os.environ.get("FD_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
+                                                        "fd_tune.json"))
+
+
+def _bucket(x: int) -> int:
+    return 1 << max(0, int(math.ceil(math.log2(max(1, x)))))
+
+
+def key(p: dict, state: str = "f32", hist: str | None = None, kahan: bool = False) -> str:
+    N = p["nx"] * p["ny"]
+    return (f"{state}/{hist or state}/{'kahan' if kahan else 'plain'}/mode{p['mem_mode']}"
+            f"/d{p['ndim']}/N{_bucket(N)}/K{_bucket(p['K'])}")
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(k: str, geo: dict, rate: float):
+    d = _load()
+    d[k] = {"geometry": geo, "terms_per_s": rate}
+    os.makedirs(os.path.dirname(cache_path()), exist_ok=True)
+    tmp = cache_path() + f".{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path())
+
+
+def lookup(p: dict, state: str = "f32", hist: str | None = None, kahan: bool = False) -> dict:
+    e = _load().get(key(p, state, hist, kahan))
+    return dict(e["geometry"]) if e else {}
+
+
+def _time_single(p, geo, reps, **kw) -> float:
+    s = FRD(p, **kw, **geo)
+    terms = s.geometry()["terms_total"]
+    u0 = torch.from_numpy(p["u0"]).to(s.device, s.dtype)
+    st = s.stream
+    best = float("inf")
+    for i in range(reps + 1):
+        s.set_state(u0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        s.step(p["K"])
+        b.record(st)
+        if s.status() != 0:
+            raise RuntimeError("engine error while tuning")
+        if i:  # first run is a warm-up
+            best = min(best, a.elapsed_time(b))
+    s.close()
+    return terms / (best / 1e3)
+
+
+def _time_batch(probs, geo, reps, **kw) -> float:
+    b = FRDBatch(probs, **kw, **geo)
+    best = float("inf")
+    u0 = [torch.from_numpy(p["u0"]).to(b.device, b.dtype) for p in probs]
+    for i in range(reps + 1):
+        for j, u in enumerate(u0):
+            b.set_state(j, u)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.run()
+        e1.record(b.stream)
+        if b.status() != 0:
+            raise RuntimeError("engine error while tuning")
+        if i:
+            best = min(best, e0.elapsed_time(e1))
+    b.close()
+    return 1e3 / best  # runs per second
+
+
+def tune(p, state: str = "f32", hist: str | None = None, kahan: bool = False, reps: int = 2,
+         budget_s: float = 60.0, batch: list | None = None, verbose: bool = False) -> dict:
+    """Coordinate descent over PARAMS from the defaults; returns and caches the best geometry.
+
+    With `batch` (a list of problems) the whole batch launch is timed instead of `p` alone.
+    """
+    kw = dict(state=state, hist=hist, kahan=kahan)
+    cur: dict = {}
+    timer = (lambda g: _time_batch(batch, g, reps, **kw)) if batch else \
+        (lambda g: _time_single(p, g, reps, **kw))
+    best = timer(cur)
+    t_end = time.time() + budget_s
+    improved = True
+    while improved and time.time() < t_end:
+        improved = False
+        for name, values in PARAMS.items():
+            for v in values:
+                if time.time() > t_end:
+                    break
+                cand = dict(cur)
+                cand[name] = v
+                if cand == cur:
+                    continue
+                try:
+                    r = timer(cand)
+                except (L.FdError, RuntimeError):
+                    continue  # geometry not launchable (e.g. shared memory)
+                if verbose:
+                    print(f"  {cand} -> {r:.4g}")
+                if r > best * 1.01:
+                    best, cur, improved = r, cand, True
+    if not batch:
+        _store(key(p, state, hist, kahan), cur, best)
+    return cur

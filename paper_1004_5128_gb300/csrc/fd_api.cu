@@ -456,9 +456,18 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     return I;
 }
 
+// The attribute is per kernel and process-wide, while handles with different geometries share a
+// kernel: allow the device's opt-in maximum once, then check each handle's need against it.
 int set_smem_attr(const void *fn, size_t smem)
 {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FD_ERR_CUDA;
+    }
+    if (smem + 4096 > (size_t)optin) return FD_ERR_INVALID_ARG;  // static shared memory needs room too
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 4096) != cudaSuccess) {
         (void)cudaGetLastError();
         return FD_ERR_CUDA;
     }
