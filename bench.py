@@ -1,15 +1,19 @@
 """Benchmark: GL history terms/s of the GB300 engine (one JSON line on rank 0).
 
-Default workload: 2-D 256x256 no-flux fractional reaction-diffusion (gamma=0.8,
-alpha=0.5, f=-0.1u, S=0.1, eight seeded Gaussians), 5000 steps in each of the
-three memory modes (full, short window 500, adaptive a=10), FP32 state and
-history.  One benchmark step = the three 5000-step runs from u0.
+Default workload (c2): 2-D 256x256 no-flux fractional reaction-diffusion (gamma=0.8,
+alpha=0.5, f=-0.1u, S=0.1, eight seeded Gaussians), 5000 steps in each of the three
+memory modes (full, short window 500, adaptive a=10), FP32.  One benchmark step = the
+three 5000-step runs from u0.  Other workloads:
+  c1  1-D N=256, 1000 steps, full memory, FP64
+  c3  2-D 512x512, 20000 steps, BF16 / FP16 / FP32 history
+  c4  64 uneven instances in one persistent launch (full and adaptive memory)
+  c5  128x128, 4000 steps: forward + checkpointed adjoint, against a plain FP32 forward
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
-                  [--workload c2|c1|c3|c4|c5]
+                  [--workload c2|c1|c3|c4|c5] [--K k] [--modes a,b] [--geom k=v,...]
 
-`--impl reference` times the FP64 CPU oracle on bounded samples of the same
-workload (the oracle is the only reference this method has).
+`--impl reference` times the FP64 CPU oracle on bounded samples of the same workload (the
+oracle is the only reference this method has).
 """
 from __future__ import annotations
 
@@ -28,6 +32,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GL history terms/s and % of HBM roofline; fwd+adjoint steps/s vs plain FP32"
 L2_BYTES = 129 * 1024 * 1024
+HBYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+
+CONFIG_NAMES = {
+    "c2": "2-D 256x256 no-flux, gamma=0.8, alpha=0.5, f=-0.1u, S=0.1, 8 Gaussians, 5000 steps x "
+          "{full, short L=500, adaptive a=10}, FP32",
+    "c1": "1-D N=256 Dirichlet, gamma=0.5, S=0.2, 1000 steps, full memory, FP64",
+    "c3": "2-D 512x512 Dirichlet, gamma=0.6, f=u(1-u)-0.05u, 20000 steps, full memory, "
+          "{BF16, FP16, FP32} history, FP32 (Kahan) accumulation",
+    "c4": "64 instances (32 1-D N 64-4096, 32 2-D side 64-384), gamma~U[0.3,0.95], steps "
+          "U{1000..8000}, one persistent launch (CUDA graph), {full, adaptive a=10}, FP32",
+    "c5": "2-D 128x128 Dirichlet, gamma=0.7, alpha=0.8, f=-0.1u, 4000 steps, FP32: forward with "
+          "checkpoints every 200 + reverse-time adjoint (grad gamma, alpha, react, u0) vs plain "
+          "FP32 forward",
+}
 
 
 def peaks():
@@ -39,10 +57,8 @@ def peaks():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 class Clocks:
@@ -95,48 +111,197 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# --------------------------------------------------------------------------- workloads
+# ----------------------------------------------------------------------------- workloads
 
-def workload(name: str, K: int = 0, modes: str = ""):
-    runs = _workload(name)
+def problems(name: str, K: int = 0, modes: str = ""):
+    """[(run name, problem or list of problems, solver kwargs)] for a workload."""
+    from paper_1004_5128_gb300 import synth
+    if name == "c2":
+        runs = [("full", synth.config2(synth.MEM_FULL), {}),
+                ("short", synth.config2(synth.MEM_SHORT), {}),
+                ("adaptive", synth.config2(synth.MEM_ADAPTIVE), {})]
+    elif name == "c1":
+        runs = [("full", synth.config1(), {"state": "f64"})]
+    elif name == "c3":
+        runs = [("bf16", synth.config3(), {"hist": "bf16", "kahan": True}),
+                ("f16", synth.config3(), {"hist": "f16", "kahan": True}),
+                ("f32", synth.config3(), {})]
+    elif name == "c4":
+        runs = [("full", synth.config4(synth.MEM_FULL), {}),
+                ("adaptive", synth.config4(synth.MEM_ADAPTIVE), {})]
+    elif name == "c5":
+        runs = [("adjoint", synth.config5(), {})]
+    else:
+        raise SystemExit(f"unknown workload {name}")
     if modes:
-        keep = modes.split(",")
-        runs = [r for r in runs if r[0] in keep]
+        runs = [r for r in runs if r[0] in modes.split(",")]
     if K:
         for _, p, _ in runs:
-            p["K"] = K
+            for q in (p if isinstance(p, list) else [p]):
+                q["K"] = K
     return runs
 
 
-def _workload(name: str):
-    from paper_1004_5128_gb300 import synth
-    if name == "c2":
-        return [("full", synth.config2(synth.MEM_FULL), {}),
-                ("short", synth.config2(synth.MEM_SHORT), {}),
-                ("adaptive", synth.config2(synth.MEM_ADAPTIVE), {})]
-    if name == "c1":
-        return [("full", synth.config1(), {"state": "f64"})]
-    if name == "c3":
-        return [("bf16", synth.config3(), {"hist": "bf16", "kahan": True}),
-                ("f16", synth.config3(), {"hist": "f16", "kahan": True}),
-                ("f32", synth.config3(), {})]
-    raise SystemExit(f"unknown workload {name}")
+def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
+    """History rows read (lags >= 1) plus, per step, the u read/write and the delta write."""
+    N = p["nx"] * p["ny"]
+    sh = HBYTES[kw.get("hist", kw.get("state", "f32"))]
+    ss = 8 if kw.get("state") == "f64" else 4
+    return geo["hist_rows_total"] * N * sh + p["K"] * N * (2 * ss + sh)
 
 
-CONFIG_NAMES = {
-    "c2": "2-D 256x256 no-flux, gamma=0.8, alpha=0.5, f=-0.1u, S=0.1, 8 Gaussians, 5000 steps x "
-          "{full, short L=500, adaptive a=10}, FP32",
-    "c1": "1-D N=256 Dirichlet, gamma=0.5, S=0.2, 1000 steps, full memory, FP64",
-    "c3": "2-D 512x512 Dirichlet, gamma=0.6, f=u(1-u)-0.05u, 20000 steps, full memory, "
-          "{BF16, FP16, FP32} history, FP32 (Kahan) accumulation",
-}
+def _sample_terms(p, K):
+    import oracle
+    return sum(len(oracle.schedule(p["mem_mode"], p["mem_L"], p["mem_a"], p.get("adaptive_rule", 0),
+                                   k)[0]) for k in range(K)) * p["nx"] * p["ny"]
 
+
+class SingleRun:
+    def __init__(self, name, p, kw, geo, dev):
+        import torch
+        from paper_1004_5128_gb300 import FRD
+        self.name, self.p, self.kw = name, p, kw
+        self.s = FRD(p, device=dev, **kw, **geo)
+        self.geo = self.s.geometry()
+        self.terms = self.geo["terms_total"]
+        self.alg = alg_bytes(self.geo, p, kw)
+        self.u0 = torch.from_numpy(p["u0"]).to(dev, self.s.dtype)
+        self.launches = 1
+
+    def launch(self):
+        self.s.set_state(self.u0)
+        self.s.step(self.p["K"])
+
+    def status(self):
+        return self.s.status()
+
+    def e2e_prepare(self):
+        import torch
+        self.hin = torch.from_numpy(self.p["u0"]).to(self.s.dtype).pin_memory()
+        self.hout = torch.empty_like(self.hin).pin_memory()
+        return self.hin.numel() * self.hin.element_size(), self.hout.numel() * self.hout.element_size()
+
+    def e2e_run(self):
+        from paper_1004_5128_gb300 import _lib as L
+        L.fd_set_state(self.s.h, self.hin.data_ptr())
+        L.fd_run(self.s.h, self.p["K"], self.hout.data_ptr())
+
+
+class BatchRun:
+    def __init__(self, name, probs, kw, geo, dev):
+        import torch
+        from paper_1004_5128_gb300 import FRDBatch
+        self.name, self.probs, self.kw = name, probs, kw
+        self.b = FRDBatch(probs, device=dev, **kw, **geo)
+        geos = [self.b.geometry(i) for i in range(len(probs))]
+        self.geo = dict(geos[0])
+        self.terms = sum(g["terms_total"] for g in geos)
+        self.alg = sum(alg_bytes(g, p, kw) for g, p in zip(geos, probs))
+        self.u0 = [torch.from_numpy(p["u0"]).to(dev, self.b.dtype) for p in probs]
+        self.launches = 1
+
+    def launch(self):
+        for i, u in enumerate(self.u0):
+            self.b.set_state(i, u)
+        self.b.run()
+
+    def status(self):
+        return self.b.status()
+
+    def e2e_prepare(self):
+        import torch
+        self.hin = [torch.from_numpy(p["u0"]).to(self.b.dtype).pin_memory() for p in self.probs]
+        self.hout = [torch.empty_like(h).pin_memory() for h in self.hin]
+        nb = sum(h.numel() * h.element_size() for h in self.hin)
+        return nb, nb
+
+    def e2e_run(self):
+        from paper_1004_5128_gb300 import _lib as L
+        for i, h in enumerate(self.hin):
+            L.fd_batch_set_state(self.b.b, i, h.data_ptr())
+        L.fd_batch_run(self.b.b)
+        for i, h in enumerate(self.hout):
+            L.fd_batch_get_state(self.b.b, i, h.data_ptr())
+        if L.fd_batch_get_status(self.b.b) != 0:
+            raise SystemExit("batch status error")
+
+
+class AdjointRun:
+    """Forward with checkpoints + fd_adjoint; also times a plain FP32 forward of the same problem."""
+
+    def __init__(self, name, p, kw, geo, dev):
+        import torch
+        from paper_1004_5128_gb300 import FRD, synth
+        self.name, self.p, self.kw = name, p, kw
+        self.C = 200
+        self.s = FRD(p, device=dev, keep_tape=True, ckpt_every=self.C, **kw, **geo)
+        self.plain = FRD(p, device=dev, **kw, **geo)
+        tgt = FRD(synth.config5(K=p["K"], target=True), device=dev, **kw)
+        tgt.set_state(p["u0"])
+        self.target = tgt.run(p["K"])
+        tgt.close()
+        self.geo = self.s.geometry()
+        K, N = p["K"], p["nx"] * p["ny"]
+        fwd = self.geo["terms_total"]
+        recompute = fwd - sum((k + 1) * N for k in range(self.C - 1, K, self.C))
+        self.terms = fwd + recompute + fwd  # forward, segment recompute, adjoint (lags 0..q)
+        self.alg = alg_bytes(self.geo, p, kw)
+        self.u0 = torch.from_numpy(p["u0"]).to(dev, self.s.dtype)
+        self.launches = 1 + 2 * ((K + self.C - 1) // self.C)
+
+    def launch(self):
+        self.s.set_state(self.u0)
+        self.s.step(self.p["K"])
+        dJ = self.s.state() - self.target
+        self.grads = self.s.adjoint(dJ)
+
+    def status(self):
+        return self.s.status()
+
+    def time_plain(self, reps=3):
+        import torch
+        best = float("inf")
+        for _ in range(reps + 1):
+            self.plain.set_state(self.u0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.plain.stream)
+            self.plain.step(self.p["K"])
+            b.record(self.plain.stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    def e2e_prepare(self):
+        import torch
+        self.hin = torch.from_numpy(self.p["u0"]).to(self.s.dtype).pin_memory()
+        self.htgt = self.target.cpu().pin_memory()
+        self.hout = torch.empty_like(self.hin).pin_memory()
+        self.hdj = torch.empty_like(self.hin).pin_memory()
+        nb = self.hin.numel() * self.hin.element_size()
+        return 2 * nb, 2 * nb
+
+    def e2e_run(self):
+        from paper_1004_5128_gb300 import _lib as L
+        L.fd_set_state(self.s.h, self.hin.data_ptr())
+        L.fd_run(self.s.h, self.p["K"], self.hout.data_ptr())
+        self.hdj.copy_(self.hout - self.htgt)
+        L.fd_adjoint(self.s.h, self.hdj.data_ptr(), self.hout.data_ptr())
+
+
+def make_runs(args, dev):
+    geo = {}
+    for item in filter(None, args.geom.split(",")):
+        k_, v_ = item.split("=")
+        geo[k_] = int(v_)
+    cls = {"c4": BatchRun, "c5": AdjointRun}.get(args.workload, SingleRun)
+    return [cls(name, p, kw, geo, dev) for name, p, kw in problems(args.workload, args.K, args.modes)]
+
+
+# ------------------------------------------------------------------------------- our arm
 
 def run_ours(args):
     import torch
     import torch.distributed as dist
-
-    from paper_1004_5128_gb300 import FRD
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -144,45 +309,31 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    runs = []
-    geo_over = {}
-    for item in filter(None, args.geom.split(",")):
-        k_, v_ = item.split("=")
-        geo_over[k_] = int(v_)
-    for name, p, kw in workload(args.workload, args.K, args.modes):
-        s = FRD(p, device=dev, **kw, **geo_over)
-        geo = s.geometry()
-        runs.append(dict(name=name, p=p, kw=kw, solver=s, geo=geo,
-                         u0=torch.from_numpy(p["u0"]).to(dev, s.dtype)))
-    hist_bytes = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+    runs = make_runs(args, dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
     def one_step(events=None):
         for r in runs:
             flush.fill_(1)
-            s = r["solver"]
-            s.set_state(r["u0"])
             if events is not None:
-                events[r["name"]][0].record(stream)
-            s.step(r["p"]["K"])
+                events[r.name][0].record(stream)
+            r.launch()
             if events is not None:
-                events[r["name"]][1].record(stream)
+                events[r.name][1].record(stream)
 
     for _ in range(args.warmup):
         one_step()
     for r in runs:
-        st = r["solver"].status()
-        if st != 0:
-            raise SystemExit(f"engine status {st} in warm-up ({r['name']})")
+        if r.status() != 0:
+            raise SystemExit(f"engine status error in warm-up ({r.name})")
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    ev = {r["name"]: [[torch.cuda.Event(enable_timing=True) for _ in range(2)]
-                      for _ in range(args.steps)] for r in runs}
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    ev = {r.name: [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+          for r in runs}
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0.record(stream)
     for i in range(args.steps):
@@ -196,27 +347,33 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     for r in runs:
-        if r["solver"].status() != 0:
-            raise SystemExit(f"engine status error in timed region ({r['name']})")
-    terms_step = sum(r["geo"]["terms_total"] for r in runs)
+        if r.status() != 0:
+            raise SystemExit(f"engine status error in timed region ({r.name})")
+    terms_step = sum(r.terms for r in runs)
     value = ws * terms_step * args.steps / (ms / 1e3)
 
-    # per-mode breakdown and the roofline of the dominant launch
     modes = {}
     for r in runs:
-        per = [a.elapsed_time(b) for a, b in ev[r["name"]]]
-        g = r["geo"]
-        p = r["p"]
-        N = p["nx"] * p["ny"]
-        sh = hist_bytes[r["kw"].get("hist", r["kw"].get("state", "f32"))]
-        ss = 8 if r["kw"].get("state") == "f64" else 4
-        alg = g["hist_rows_total"] * N * sh + p["K"] * N * (2 * ss + sh)
-        modes[r["name"]] = dict(ms=float(np.mean(per)), terms=g["terms_total"],
-                                terms_per_s=g["terms_total"] / (np.mean(per) / 1e3),
-                                alg_bytes=alg, gbs=alg / (np.mean(per) / 1e3) / 1e9,
-                                geometry={k: g[k] for k in ("tile_threads", "tiles", "chunk_terms",
-                                                            "stage_rows", "stages", "ctas_per_sm",
-                                                            "grid")})
+        per = float(np.mean([a.elapsed_time(b) for a, b in ev[r.name]]))
+        g = r.geo
+        modes[r.name] = dict(ms=per, terms=r.terms, terms_per_s=r.terms / (per / 1e3),
+                             alg_bytes=r.alg, gbs=r.alg / (per / 1e3) / 1e9,
+                             geometry={k: g[k] for k in ("tile_threads", "tiles", "chunk_terms",
+                                                         "stage_rows", "stages", "ctas_per_sm",
+                                                         "grid", "head_lags")})
+    extra = {}
+    if args.workload == "c5":
+        r = runs[0]
+        plain_ms = r.time_plain()
+        K = r.p["K"]
+        fa_ms = modes[r.name]["ms"]
+        extra = {"fwd_adjoint_steps_per_s": K / (fa_ms / 1e3),
+                 "plain_fp32_fwd_steps_per_s": K / (plain_ms / 1e3),
+                 "fwd_adjoint_over_plain_fwd_time": fa_ms / plain_ms,
+                 "grads": {k: v for k, v in r.grads.items() if k != "du0"}}
+        # the roofline line is for the plain forward launch (one engine launch, timed alone)
+        modes[r.name]["gbs"] = r.alg / (plain_ms / 1e3) / 1e9
+        modes[r.name]["roofline_launch"] = "plain FP32 forward"
     dom = max(modes, key=lambda k: modes[k]["ms"])
     peak, which = peaks()
     ach = modes[dom]["gbs"]
@@ -229,52 +386,54 @@ def run_ours(args):
             traffic = None
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "traffic": traffic,
-            "kernel": f"engine_kernel ({dom} mode, one persistent launch per run)",
-            "peak_source": f"{which} hbm_gbs"}
+            "kernel": f"engine_kernel ({dom}, one persistent launch per run)",
+            "peak_source": f"{which} hbm_gbs (burst copy)"}
 
-    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        import ctypes  # noqa: F401
-        from paper_1004_5128_gb300 import _lib as L
-        host_in = [torch.from_numpy(r["p"]["u0"]).to(r["solver"].dtype).pin_memory() for r in runs]
-        host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+        h2d = d2h = 0
+        for r in runs:
+            a, b = r.e2e_prepare()
+            h2d += a
+            d2h += b
         torch.cuda.synchronize()
         k = max(1, args.steps)
         w0 = time.perf_counter()
         for _ in range(k):
-            for r, hi, ho in zip(runs, host_in, host_out):
-                L.fd_set_state(r["solver"].h, hi.data_ptr())
-                L.fd_run(r["solver"].h, r["p"]["K"], ho.data_ptr())
+            for r in runs:
+                r.e2e_run()
         torch.cuda.synchronize()
         we = time.perf_counter() - w0
         if ws > 1:
             t = torch.tensor([we], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             we = float(t.item())
-        e2e = {"value": ws * terms_step * k / we, "unit": "terms/s",
-               "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host_in)),
-               "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host_out))}
+        e2e = {"value": ws * terms_step * k / we, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
 
-    launches = len(runs) * args.steps  # one persistent engine launch per run
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(args.workload, args.cpu_seconds, args.K, args.modes)
+        cpu = cpu_baseline(args)
     if rank == 0:
-        dtype = runs[0]["kw"].get("state", "f32")
+        kw0 = runs[0].kw
+        dtype = "f64" if kw0.get("state") == "f64" else "f32"
+        if args.workload == "c3":
+            dtype = "f32 state, bf16/f16/f32 history"
         line = {
             "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f32": "f32", "f64": "f64"}[dtype] if args.workload != "c3" else "f32 (bf16/f16 history)",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (seeded SplitMix64 inputs)",
-            "config": {"workload": CONFIG_NAMES[args.workload],
-                       "l2": "inputs larger than L2 (1.3 GB history per full/adaptive run) and a "
-                             "258 MB L2 flush before every run",
+            "config": {"workload": CONFIG_NAMES[args.workload] +
+                       (f" [K={args.K}]" if args.K else "") + (f" [{args.modes}]" if args.modes else ""),
+                       "l2": "a 258 MB L2 flush before every run; histories of the full/adaptive "
+                             "runs exceed L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "modes": modes, "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+            "modes": modes, "roofline": roof, "e2e": e2e,
+            "gpu_launches": sum(r.launches for r in runs) * args.steps,
             "clocks": ck, "cpu_baseline": cpu,
         }
+        line.update(extra)
         print(json.dumps(line))
     if ws > 1:
         dist.barrier()
@@ -283,32 +442,48 @@ def run_ours(args):
 
 # ---------------------------------------------------------------------------- CPU oracle
 
-def _oracle_sample(name, seconds, K=0, modes=""):
-    """Run the oracle on the first K' steps of each run of the workload, K' grown until the
-    whole sample takes about `seconds`.  Returns (terms, wall seconds, description)."""
+def _oracle_sample(args, kp, threads):
+    """(terms, seconds) of the oracle on the first kp steps of every run of the workload."""
     import oracle
-    runs = workload(name, K, modes)
-    threads = os.cpu_count() or 1
-    kp = 8
-    while True:
-        terms, t = 0, 0.0
-        for rname, p, kw in runs:
+    from paper_1004_5128_gb300 import synth
+    terms, t = 0, 0.0
+    for name, p, kw in problems(args.workload, args.K, args.modes):
+        if args.workload == "c5":
             K = min(kp, p["K"])
             N = p["nx"] * p["ny"]
-            n = sum(len(oracle.schedule(p["mem_mode"], p["mem_L"], p["mem_a"],
-                                        p.get("adaptive_rule", 0), k)[0]) for k in range(K))
+            tgt = oracle.run(synth.config5(K=K, target=True), threads=threads)
             w = time.perf_counter()
-            oracle.run(p, K=K, threads=threads)
+            oracle.adjoint(p, tgt, K=K, threads=threads)
             t += time.perf_counter() - w
-            terms += n * N
-        if t > seconds / 4 or kp >= max(p["K"] for _, p, _ in runs):
+            terms += 2 * sum((k + 1) * N for k in range(K))
+            continue
+        for q in (p[:: max(1, len(p) // 8)] if isinstance(p, list) else [p]):
+            K = min(kp, q["K"])
+            n = _sample_terms(q, K)
+            w = time.perf_counter()
+            oracle.run(q, K=K, threads=threads)
+            t += time.perf_counter() - w
+            terms += n
+    return terms, t
+
+
+def _oracle_budget(args, seconds):
+    """Grow the sampled prefix until the oracle sample takes about `seconds`."""
+    threads = os.cpu_count() or 1
+    kmax = max(q["K"] for _, p, _ in problems(args.workload, args.K, args.modes)
+               for q in (p if isinstance(p, list) else [p]))
+    kp = 8
+    while True:
+        terms, t = _oracle_sample(args, kp, threads)
+        if t > seconds / 4 or kp >= kmax:
             break
         kp = int(kp * max(1.5, min(4.0, math.sqrt(seconds / 4 / max(t, 1e-3)))))
-    return terms, t, threads, f"first {kp} steps of each run ({', '.join(r[0] for r in runs)})"
+    what = "every 8th instance" if args.workload == "c4" else "each run"
+    return terms, t, threads, f"first {min(kp, kmax)} steps of {what}"
 
 
-def cpu_baseline(name, seconds, K=0, modes=""):
-    terms, t, threads, desc = _oracle_sample(name, seconds, K, modes)
+def cpu_baseline(args):
+    terms, t, threads, desc = _oracle_budget(args, args.cpu_seconds)
     return {"value": terms / t, "unit": "terms/s", "cores": threads, "kind": "oracle",
             "sample": desc + f"; {terms:.3e} terms in {t:.1f} s, OpenMP over grid points"}
 
@@ -317,16 +492,13 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    vals = []
-    desc = ""
-    total_t = 0.0
+    total_terms, total_t, desc, threads = 0, 0.0, "", 1
     for i in range(args.warmup + args.steps):
-        terms, t, threads, desc = _oracle_sample(args.workload, args.cpu_seconds, args.K, args.modes)
+        terms, t, threads, desc = _oracle_budget(args, args.cpu_seconds)
         if i >= args.warmup:
-            vals.append((terms, t))
+            total_terms += terms
             total_t += t
-    terms = sum(v[0] for v in vals)
-    value = terms / total_t
+    value = total_terms / total_t
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(1, args.steps),
@@ -346,7 +518,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -179,6 +179,7 @@ int fd_batch_set_state(fd_batch *b, int i, const void *u0);   /* device or host 
 int fd_batch_run(fd_batch *b);                                 /* enqueue all steps */
 int fd_batch_get_state(fd_batch *b, int i, void *u_out);       /* enqueue copy of u^{K_i} */
 int fd_batch_get_status(fd_batch *b);                          /* synchronises */
+int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g);  /* instance i's resolved geometry */
 int fd_batch_destroy(fd_batch *b);
 
 /* One-shot batch: init, set u_io[i] as u^0, run, write u^{K_i} back to u_io[i]
@@ -187,6 +188,7 @@ int fd_run_batch(const fd_problem *probs, int count, void *const *u_io, void *wo
                  size_t ws_bytes, void *cuda_stream);
 
 const char *fd_strerror(int code);
+
 
 #ifdef __cplusplus
 }

@@ -38,7 +38,8 @@ EXPORTS = (
     "fd_weights", "fd_schedule", "fd_workspace_bytes", "fd_init", "fd_set_state", "fd_step",
     "fd_run", "fd_get_state", "fd_current_step", "fd_adjoint", "fd_get_status", "fd_destroy",
     "fd_get_geometry", "fd_batch_workspace_bytes", "fd_batch_init", "fd_batch_set_state",
-    "fd_batch_run", "fd_batch_get_state", "fd_batch_get_status", "fd_batch_destroy",
+    "fd_batch_run", "fd_batch_get_state", "fd_batch_get_status", "fd_batch_get_geometry",
+    "fd_batch_destroy",
     "fd_run_batch", "fd_strerror",
 )
 
@@ -106,6 +107,7 @@ def lib():
             "fd_batch_run": [vp],
             "fd_batch_get_state": [vp, ctypes.c_int, vp],
             "fd_batch_get_status": [vp],
+            "fd_batch_get_geometry": [vp, ctypes.c_int, ctypes.POINTER(FdGeometry)],
             "fd_batch_destroy": [vp],
             "fd_run_batch": [P, ctypes.c_int, ctypes.POINTER(vp), vp, ctypes.c_size_t, vp],
             "fd_strerror": [ctypes.c_int],
@@ -240,6 +242,12 @@ def fd_batch_get_status(b: int) -> int:
     return int(lib().fd_batch_get_status(b))
 
 
+def fd_batch_get_geometry(b: int, i: int) -> dict:
+    g = FdGeometry()
+    check(lib().fd_batch_get_geometry(b, i, ctypes.byref(g)), "fd_batch_get_geometry")
+    return {n: getattr(g, n) for n, _ in FdGeometry._fields_}
+
+
 def fd_batch_destroy(b: int):
     lib().fd_batch_destroy(b)
 
@@ -252,3 +260,4 @@ def fd_run_batch(probs, ptrs, ws_ptr: int, ws_bytes: int, stream: int):
 
 def fd_strerror(code: int) -> str:
     return strerror(code)
+

@@ -1102,6 +1102,31 @@ int fd_batch_get_status(fd_batch *b)
     return status_from(err, nf);
 }
 
+int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g)
+{
+    if (!b || !g || i < 0 || i >= (int)b->p.size()) return FD_ERR_INVALID_ARG;
+    const Geo &q = b->g[i];
+    g->tile_threads = q.threads;
+    g->tile_points = q.P;
+    g->tiles = q.T;
+    g->chunk_terms = q.R;
+    g->stage_rows = b->RS;
+    g->stages = b->NS;
+    g->ctas_per_sm = b->grid / std::max(1, device_sms());
+    g->grid = b->grid;
+    g->head_lags = q.head;
+    int64_t units = 0, rows = 0;
+    for (const int4 &e : b->s[i].step) {
+        units += step_units(q, e);
+        rows += n_terms(e);
+    }
+    const int64_t N = (int64_t)b->p[i].nx * b->p[i].ny;
+    g->units_total = units;
+    g->hist_rows_total = rows;
+    g->terms_total = (rows + (int64_t)b->s[i].step.size()) * N;
+    return FD_OK;
+}
+
 int fd_batch_destroy(fd_batch *b)
 {
     if (!b) return FD_OK;

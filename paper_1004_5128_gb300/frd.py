@@ -153,6 +153,9 @@ class FRDBatch:
         L.fd_batch_get_state(self.b, i, out.data_ptr())
         return out
 
+    def geometry(self, i: int) -> dict:
+        return L.fd_batch_get_geometry(self.b, i)
+
     def status(self) -> int:
         s = L.fd_batch_get_status(self.b)
         self._keep = []
