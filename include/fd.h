@@ -189,6 +189,27 @@ int fd_run_batch(const fd_problem *probs, int count, void *const *u_io, void *wo
 
 const char *fd_strerror(int code);
 
+/* ---- allocation-free forward run ----
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory at all (a plugin inside a host application that owns the GPU's
+ * allocator and passes in only a stream, or a control loop that must not allocate after it
+ * starts).  fd_run_static advances nsteps steps from u0 (N values of state_dtype, device or
+ * host) and writes u^nsteps to u_out (device or host), using the same engine kernel as fd_run
+ * but with all scratch -- state buffers, delta history, partial sums, counters and the weight /
+ * schedule tables -- taken from one static device array of FD_STATIC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine, and uses no host heap.
+ *  - Problems needing more scratch than FD_STATIC_SCRATCH_BYTES are rejected with
+ *    FD_ERR_WORKSPACE before any device work.  p->max_steps is ignored (nsteps is the length);
+ *    FD_FLAG_KEEP_TAPE is rejected with FD_ERR_UNSUPPORTED (forward only).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device current); make that first call before any stream capture.
+ *  - Every call shares the one array and overwrites what the previous call left in it; calls
+ *    whose work overlaps on the GPU (other streams, other host threads) race and must be
+ *    serialised by the caller.
+ *  - Synchronises the stream; returns FD_OK or the device status (as fd_run). */
+#define FD_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+int fd_run_static(const fd_problem *p, const void *u0, int nsteps, void *u_out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

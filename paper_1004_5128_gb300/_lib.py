@@ -40,7 +40,7 @@ EXPORTS = (
     "fd_get_geometry", "fd_batch_workspace_bytes", "fd_batch_init", "fd_batch_set_state",
     "fd_batch_run", "fd_batch_get_state", "fd_batch_get_status", "fd_batch_get_geometry",
     "fd_batch_destroy",
-    "fd_run_batch", "fd_strerror",
+    "fd_run_batch", "fd_strerror", "fd_run_static",
 )
 
 
@@ -111,6 +111,7 @@ def lib():
             "fd_batch_destroy": [vp],
             "fd_run_batch": [P, ctypes.c_int, ctypes.POINTER(vp), vp, ctypes.c_size_t, vp],
             "fd_strerror": [ctypes.c_int],
+            "fd_run_static": [P, vp, ctypes.c_int, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -261,3 +262,7 @@ def fd_run_batch(probs, ptrs, ws_ptr: int, ws_bytes: int, stream: int):
 def fd_strerror(code: int) -> str:
     return strerror(code)
 
+
+def fd_run_static(p: FdProblem, u0_ptr: int, nsteps: int, out_ptr: int, stream: int):
+    """Allocation-free forward run (scratch in the library's static device array)."""
+    check(lib().fd_run_static(ctypes.byref(p), u0_ptr, nsteps, out_ptr, stream), "fd_run_static")
