@@ -121,30 +121,7 @@ class Clocks:
 def problems(name: str, K: int = 0, modes: str = ""):
     """[(run name, problem or list of problems, solver kwargs)] for a workload."""
     from paper_1004_5128_gb300 import synth
-    if name == "c2":
-        runs = [("full", synth.config2(synth.MEM_FULL), {}),
-                ("short", synth.config2(synth.MEM_SHORT), {}),
-                ("adaptive", synth.config2(synth.MEM_ADAPTIVE), {})]
-    elif name == "c1":
-        runs = [("full", synth.config1(), {"state": "f64"})]
-    elif name == "c3":
-        runs = [("bf16", synth.config3(), {"hist": "bf16", "kahan": True}),
-                ("f16", synth.config3(), {"hist": "f16", "kahan": True}),
-                ("f32", synth.config3(), {})]
-    elif name == "c4":
-        runs = [("full", synth.config4(synth.MEM_FULL), {}),
-                ("adaptive", synth.config4(synth.MEM_ADAPTIVE), {})]
-    elif name == "c5":
-        runs = [("adjoint", synth.config5(), {})]
-    else:
-        raise SystemExit(f"unknown workload {name}")
-    if modes:
-        runs = [r for r in runs if r[0] in modes.split(",")]
-    if K:
-        for _, p, _ in runs:
-            for q in (p if isinstance(p, list) else [p]):
-                q["K"] = K
-    return runs
+    return synth.workload_runs(name, K, modes)
 
 
 def alg_bytes(geo: dict, p: dict, kw: dict) -> int:

@@ -9,7 +9,11 @@ library's defaults and caches the winner in a JSON file keyed by
 (dtypes, memory mode, dimension, N bucket, K bucket).  `lookup` returns a cached
 geometry (or {} when none is known); `FRD(..., **lookup(p, ...))` applies it.
 
-Cache path: $FD_TUNE_CACHE, else ~/.cache/fd_tune.json.
+Cache path: $FD_TUNE_CACHE, else ~/.cache/fd_tune.json.  When the cache has no entry for a
+problem, `lookup` falls back to the table shipped with the package (tuned.json, measured on a
+GB300 with this tuner), first by exact key, then by the nearest step-count bucket.
+
+    python -m paper_1004_5128_gb300.autotune c2 c4 [--budget 60] [--out tuned.json]
 """
 from __future__ import annotations
 
@@ -65,13 +69,53 @@ def _store(k: str, geo: dict, rate: float):
     os.replace(tmp, cache_path())
 
 
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def _shipped() -> dict:
+    try:
+        with open(SHIPPED) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
 def lookup(p: dict, state: str = "f32", hist: str | None = None, kahan: bool = False) -> dict:
-    e = _load().get(key(p, state, hist, kahan))
-    return dict(e["geometry"]) if e else {}
+    """Tuned geometry for p: user cache, then the shipped table (nearest K bucket)."""
+    k = key(p, state, hist, kahan)
+    for table in (_load(), _shipped()):
+        if k in table:
+            return dict(table[k]["geometry"])
+    prefix, kb = k.rsplit("/K", 1)
+    best = None
+    for table in (_load(), _shipped()):
+        for kk, e in table.items():
+            pre, b = kk.rsplit("/K", 1)
+            if pre == prefix:
+                d = abs(math.log2(int(b)) - math.log2(int(kb)))
+                if best is None or d < best[0]:
+                    best = (d, e)
+        if best:
+            return dict(best[1]["geometry"])
+    return {}
+
+
+def batch_key(probs: list, state: str = "f32") -> str:
+    n = sum(p["nx"] * p["ny"] for p in probs)
+    k = max(p["K"] for p in probs)
+    return f"batch/{state}/mode{probs[0]['mem_mode']}/n{len(probs)}/N{_bucket(n)}/K{_bucket(k)}"
+
+
+def lookup_batch(probs: list, state: str = "f32") -> dict:
+    k = batch_key(probs, state)
+    for table in (_load(), _shipped()):
+        if k in table:
+            return dict(table[k]["geometry"])
+    return {}
 
 
 def _time_single(p, geo, reps, **kw) -> float:
-    s = FRD(p, **kw, **geo)
+    s = FRD(p, tuned=False, **kw, **geo)
     terms = s.geometry()["terms_total"]
     u0 = torch.from_numpy(p["u0"]).to(s.device, s.dtype)
     st = s.stream
@@ -91,7 +135,7 @@ def _time_single(p, geo, reps, **kw) -> float:
 
 
 def _time_batch(probs, geo, reps, **kw) -> float:
-    b = FRDBatch(probs, **kw, **geo)
+    b = FRDBatch(probs, tuned=False, **kw, **geo)
     best = float("inf")
     u0 = [torch.from_numpy(p["u0"]).to(b.device, b.dtype) for p in probs]
     for i in range(reps + 1):
@@ -140,6 +184,31 @@ def tune(p, state: str = "f32", hist: str | None = None, kahan: bool = False, re
                     print(f"  {cand} -> {r:.4g}")
                 if r > best * 1.01:
                     best, cur, improved = r, cand, True
-    if not batch:
-        _store(key(p, state, hist, kahan), cur, best)
+    _store(batch_key(batch, state) if batch else key(p, state, hist, kahan), cur, best)
     return cur
+
+
+def _main():
+    import argparse
+
+    from . import synth
+    ap = argparse.ArgumentParser(description="tune launch geometry for named workloads")
+    ap.add_argument("workloads", nargs="+")
+    ap.add_argument("--budget", type=float, default=60.0, help="seconds per run")
+    ap.add_argument("--K", type=int, default=0)
+    ap.add_argument("--out", default="", help="cache file (default: $FD_TUNE_CACHE or ~/.cache)")
+    args = ap.parse_args()
+    if args.out:
+        os.environ["FD_TUNE_CACHE"] = os.path.abspath(args.out)
+    for w in args.workloads:
+        for name, p, kw in synth.workload_runs(w, args.K):
+            t0 = time.time()
+            if isinstance(p, list):
+                g = tune(None, batch=p, budget_s=args.budget, **kw)
+            else:
+                g = tune(p, budget_s=args.budget, **kw)
+            print(f"{w}:{name} -> {g} ({time.time() - t0:.0f} s)", flush=True)
+
+
+if __name__ == "__main__":
+    _main()

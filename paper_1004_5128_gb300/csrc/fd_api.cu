@@ -23,6 +23,7 @@ using fdk::Launch;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kNpar = 4;  // partial-row parities: up to kNpar-1 steps of run-ahead per tile
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -301,9 +302,10 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     L.hist = c.take((size_t)g.cap * g.pitch);
     L.hring = g.hring_sep ? c.take((size_t)g.hring_cap * g.hring_pitch) : L.hist;
     L.hscale = (p.hist_dtype == FD_F16) ? (float *)c.take((size_t)g.cap * g.T * sizeof(float)) : nullptr;
-    L.part = c.take((size_t)2 * g.maxC * g.planes * g.part_pitch);
-    L.arrive = external_counters ? counters : (unsigned *)c.take(sizeof(unsigned) * 3 * (size_t)g.T);
-    L.done = L.arrive ? L.arrive + 2 * g.T : nullptr;
+    L.part = c.take((size_t)kNpar * g.maxC * g.planes * g.part_pitch);
+    L.arrive = external_counters ? counters
+                                 : (unsigned *)c.take(sizeof(unsigned) * (kNpar + 1) * (size_t)g.T);
+    L.done = L.arrive ? L.arrive + kNpar * g.T : nullptr;
     L.psi = c.take((size_t)(p.max_steps + 1) * g.sa);
     L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1) * g.sa) : nullptr;
     L.sched = (int4 *)c.take(sizeof(int4) * (size_t)p.max_steps);
@@ -416,6 +418,7 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.hist_write = 1;
     I.cap = adj ? p.max_steps : g.cap;
     I.maxC = g.maxC;
+    I.npar = kNpar;
     I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
     I.tape_every = 1;
     I.S = p.alpha * std::pow(p.dt, p.gamma) / (p.dx * p.dx);
@@ -642,7 +645,7 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
         h->d_ginfo = (int2 *)c.take(sizeof(int2) * (size_t)(p->max_steps + 1));
     }
     h->ctrl_zero_base = (char *)h->L.arrive;
-    h->ctrl_zero_bytes = sizeof(unsigned) * 3 * (size_t)h->g.T;
+    h->ctrl_zero_bytes = sizeof(unsigned) * (kNpar + 1) * (size_t)h->g.T;
     const bool kahan = p->flags & FD_FLAG_KAHAN;
     h->kfwd = fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
     h->kadj = (p->flags & FD_FLAG_KEEP_TAPE)
@@ -926,13 +929,13 @@ int batch_plan(const fd_problem *probs, int count, fd_batch &b, size_t *bytes, c
     b.smem = smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
     b.ctrl = carve_ctrl(c);
-    b.counter_bytes = sizeof(unsigned) * 3 * (size_t)tiles;
+    b.counter_bytes = sizeof(unsigned) * (kNpar + 1) * (size_t)tiles;
     b.counters = (unsigned *)c.take(b.counter_bytes);
     int64_t toff = 0;
     for (int i = 0; i < count; ++i) {
         unsigned *cnt = b.counters ? b.counters + toff : nullptr;
         carve_instance(c, probs[i], b.g[i], b.s[i], b.L[i], cnt, true);
-        toff += 3 * (int64_t)b.g[i].T;
+        toff += (kNpar + 1) * (int64_t)b.g[i].T;
     }
     // groups: step-major, then instance
     int maxK = 0;

@@ -51,6 +51,7 @@ struct Inst {
     int hist_write;          // 0: history rows already hold delta (adjoint recompute pass)
     int cap;                 // history ring rows
     int maxC;                // partial rows per parity
+    int npar;                // partial-row parities: steps k and k+npar share rows
     int stall;               // fault injection: first fixup waits on a counter nothing advances
     int head;                // lags 1..head are summed by the fixup from the head rows
     int hring_cap;           // rows in the head ring (== cap when it is the history itself)
@@ -67,8 +68,8 @@ struct Inst {
     float *hscale;           // [cap][T] row-tile scales (FP16 history) or null
     char *ubuf[2];           // state double buffer: u^k lives in ubuf[k & 1]
     char *ulo[2];            // compensated state: low parts (null = plain state)
-    char *part;              // [2][maxC][planes] partial rows
-    unsigned *arrive;        // [2][T]
+    char *part;              // [npar][maxC][planes] partial rows
+    unsigned *arrive;        // [npar][T]
     unsigned *done;          // [T] steps completed by each tile in this launch
     const char *psi;         // weights in accumulator type
     const char *dpsi;        // d psi / d gamma (adjoint)
@@ -421,7 +422,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     const int r_hi = gi.y - lag;
                     if (r_hi >= L.k0) need = r_hi - L.k0 + 1;
                 }
-                if (C > 1 && rel - 1 > need) need = rel - 1;  // partial rows of step k-2 consumed
+                // partial rows of step k-npar consumed by its fixup
+                if (C > 1 && rel - I.npar + 1 > need) need = rel - I.npar + 1;
                 if (need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
             }
             U.valid = ok;
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         }
 
         // ------------------------------------------- partials and arrival
-        const int par = k & 1;
+        const int par = k % I.npar;
         auto prow = [&](int c, int plane) -> TA * {
             return reinterpret_cast<TA *>(I.part + ((size_t)((par * I.maxC + c) * PLANES + plane)) * I.part_pitch);
         };
@@ -558,7 +560,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 unsigned *ar = &I.arrive[par * I.T + tile];
                 const unsigned old = atom_add_acq_rel(ar, 1u);
                 U.last = (old == (unsigned)(C - 1));
-                if (U.last) *ar = 0u;  // reset for step k+2 (published by the done release below)
+                if (U.last) *ar = 0u;  // reset for step k+npar (published by the done release below)
             }
             __syncthreads();
             if (!U.last) continue;

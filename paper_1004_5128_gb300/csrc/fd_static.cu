@@ -272,13 +272,14 @@ extern "C" int fd_run_static(const fd_problem *p, const void *u0, int nsteps, vo
     // carve the static scratch; a problem that does not fit is rejected
     Carve c{base, 0, FD_STATIC_SCRATCH_BYTES};
     char *ctrl = c.take(256);
-    unsigned *cnt = (unsigned *)c.take(sizeof(unsigned) * 3 * (size_t)T);
+    const int npar = 4;
+    unsigned *cnt = (unsigned *)c.take(sizeof(unsigned) * (npar + 1) * (size_t)T);
     char *ub0 = c.take(ubytes), *ub1 = c.take(ubytes);
     char *lo0 = comp ? c.take(ubytes) : base, *lo1 = comp ? c.take(ubytes) : base;
     char *hist = c.take((size_t)cap * pitch);
     char *hring = hsep ? c.take((size_t)(head + 1) * hpitch) : hist;
     float *hscale = (p->hist_dtype == FD_F16) ? (float *)c.take((size_t)cap * T * sizeof(float)) : nullptr;
-    char *part = c.take((size_t)2 * maxC * ppitch);
+    char *part = c.take((size_t)npar * maxC * ppitch);
     Tabs t;
     t.mode = p->mem_mode;
     t.L = p->mem_L;
@@ -315,6 +316,7 @@ extern "C" int fd_run_static(const fd_problem *p, const void *u0, int nsteps, vo
     I.hist_write = 1;
     I.cap = cap;
     I.maxC = maxC;
+    I.npar = npar;
     I.stall = (p->flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
     I.head = head;
     I.hring_cap = hsep ? head + 1 : cap;
@@ -335,7 +337,7 @@ extern "C" int fd_run_static(const fd_problem *p, const void *u0, int nsteps, vo
     I.ulo[1] = comp ? lo1 : nullptr;
     I.part = part;
     I.arrive = cnt;
-    I.done = cnt + 2 * T;
+    I.done = cnt + npar * T;
     I.psi = t.psi;
     I.sched = t.sched;
     I.g_lag = t.glag;
@@ -369,7 +371,7 @@ extern "C" int fd_run_static(const fd_problem *p, const void *u0, int nsteps, vo
 
     // the array keeps the previous call's contents: clear what must start at zero
     bool ok = cudaMemsetAsync(ctrl, 0, 256, st) == cudaSuccess &&
-              cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 3 * (size_t)T, st) == cudaSuccess &&
+              cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (npar + 1) * (size_t)T, st) == cudaSuccess &&
               (!comp || cudaMemsetAsync(lo0, 0, ubytes, st) == cudaSuccess) &&
               cudaMemcpyAsync(d_inst, &I, sizeof(I), cudaMemcpyHostToDevice, st) == cudaSuccess &&
               cudaMemcpyAsync(ub0, u0, ubytes, cudaMemcpyDefault, st) == cudaSuccess;

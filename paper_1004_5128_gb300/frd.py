@@ -50,11 +50,21 @@ def _require_cuda():
     L.lib()
 
 
-class FRD:
-    """One problem instance bound to a device workspace and a stream."""
+GEOMETRY_KEYS = ("tile_threads", "chunk_terms", "stage_rows", "stages", "ctas_per_sm", "head_lags")
 
-    def __init__(self, p: dict, device: str | torch.device = "cuda", stream=None, **kw):
+
+class FRD:
+    """One problem instance bound to a device workspace and a stream.
+
+    Without explicit launch-geometry options the autotuner's table is consulted (`tuned=False`
+    keeps the library's built-in heuristics)."""
+
+    def __init__(self, p: dict, device: str | torch.device = "cuda", stream=None, tuned: bool = True,
+                 **kw):
         _require_cuda()
+        if tuned and not any(k in kw for k in GEOMETRY_KEYS):
+            from .autotune import lookup
+            kw.update(lookup(p, kw.get("state", "f32"), kw.get("hist"), kw.get("kahan", False)))
         self.problem = p
         self.prob = make_problem(p, **kw)
         self.device = torch.device(device)
@@ -127,8 +137,12 @@ class FRD:
 class FRDBatch:
     """Many independent instances advanced by one persistent launch (replayed CUDA graph)."""
 
-    def __init__(self, problems: list, device: str | torch.device = "cuda", stream=None, **kw):
+    def __init__(self, problems: list, device: str | torch.device = "cuda", stream=None,
+                 tuned: bool = True, **kw):
         _require_cuda()
+        if tuned and not any(k in kw for k in GEOMETRY_KEYS):
+            from .autotune import lookup_batch
+            kw.update(lookup_batch(problems, kw.get("state", "f32")))
         self.problems = problems
         self.device = torch.device(device)
         self.probs = [make_problem(p, **kw) for p in problems]

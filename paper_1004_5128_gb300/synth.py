@@ -215,3 +215,33 @@ def eigenmode(p: dict, qx: int, qy: int = 1) -> np.ndarray:
         return ex
     ey = axis(p["ny"], qy)
     return np.outer(ey, ex).reshape(-1)
+
+
+def workload_runs(name: str, K: int = 0, modes: str = ""):
+    """Named workloads as [(run name, problem or list of problems, solver options)].
+
+    c1: config 1 (FP64); c2: config 2 in its three memory modes; c3: config 3 with BF16, FP16
+    and FP32 history; c4: the 64-instance batch, full and adaptive; c5: the adjoint problem.
+    K overrides every step count; modes keeps only the named runs.
+    """
+    if name == "c2":
+        runs = [("full", config2(MEM_FULL), {}), ("short", config2(MEM_SHORT), {}),
+                ("adaptive", config2(MEM_ADAPTIVE), {})]
+    elif name == "c1":
+        runs = [("full", config1(), {"state": "f64"})]
+    elif name == "c3":
+        runs = [("bf16", config3(), {"hist": "bf16", "kahan": True}),
+                ("f16", config3(), {"hist": "f16", "kahan": True}), ("f32", config3(), {})]
+    elif name == "c4":
+        runs = [("full", config4(MEM_FULL), {}), ("adaptive", config4(MEM_ADAPTIVE), {})]
+    elif name == "c5":
+        runs = [("adjoint", config5(), {})]
+    else:
+        raise ValueError(f"unknown workload {name}")
+    if modes:
+        runs = [r for r in runs if r[0] in modes.split(",")]
+    if K:
+        for _, p, _ in runs:
+            for q in (p if isinstance(p, list) else [p]):
+                q["K"] = K
+    return runs
