@@ -285,6 +285,8 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
+    from paper_1004_5128_gb300 import parallel
+
     ws, rank, local = dist_env()
     if ws > 1:
         dist.init_process_group("nccl")
@@ -323,11 +325,7 @@ def run_ours(args):
     t1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = parallel.max_over_ranks(t0.elapsed_time(t1))
     for r in runs:
         if r.status() != 0:
             raise SystemExit(f"engine status error in timed region ({r.name})")
@@ -385,11 +383,7 @@ def run_ours(args):
             for r in runs:
                 r.e2e_run()
         torch.cuda.synchronize()
-        we = time.perf_counter() - w0
-        if ws > 1:
-            t = torch.tensor([we], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            we = float(t.item())
+        we = parallel.max_over_ranks(time.perf_counter() - w0)
         e2e = {"value": ws * terms_step * k / we, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
