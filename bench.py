@@ -359,9 +359,13 @@ def run_ours(args):
     ach = modes[dom]["gbs"]
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
+    if os.path.exists(tfile) and not args.geom and not args.K:
         try:
-            traffic = json.load(open(tfile)).get(f"{args.workload}:{dom}")
+            import hashlib
+            t = json.load(open(tfile))
+            src = open(os.path.join(ROOT, t["kernel_source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest() == t["kernel_sha256"]:  # counters of this kernel only
+                traffic = t.get(f"{args.workload}:{dom}")
         except Exception:
             traffic = None
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
