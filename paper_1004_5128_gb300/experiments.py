@@ -23,6 +23,7 @@ FIG1_GAMMAS = (0.5, 0.75, 0.9, 1.0)
 FIG3_GAMMAS = (0.5, 0.75, 0.9, 0.95)
 FIG3_L = (10, 25, 50, 100, 200, 400, 800, 1200)
 FIG3_A = (2, 3, 5, 10, 20, 50)
+SUPER_GAMMAS = (1.25, 1.5, 1.75)  # superdiffusion: the Discussion expects larger errors there
 
 
 def fig1_problem(gamma: float) -> dict:
@@ -124,6 +125,9 @@ if __name__ == "__main__":
     import sys
     rows = fig3()
     print(fig3_table(rows))
+    if "--super" in sys.argv:
+        print()
+        print(fig3_table(fig3(gammas=SUPER_GAMMAS)))
     if "--fig1" in sys.argv:
         r = fig1()
         for g, v in r.items():

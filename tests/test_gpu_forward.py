@@ -161,3 +161,17 @@ def test_config2_gaussians_mass_balance(mode):
     M0 = p["u0"].sum()
     ref = M0 * (1.0 - 0.1 * p["dt"]) ** p["K"]
     assert abs(got.sum() - ref) / M0 < 2e-5
+
+
+@pytest.mark.parametrize("state", ["f32", "f64"])
+@pytest.mark.parametrize("mode,Lw,a", [(synth.MEM_FULL, 0, 0), (synth.MEM_SHORT, 40, 0),
+                                       (synth.MEM_ADAPTIVE, 0, 3)])
+def test_superdiffusion(state, mode, Lw, a):
+    """gamma = 1.5 (weights positive, partial sums growing like m^{1/2}), S at 60% of the bound."""
+    g = 1.5
+    dt = synth.dt_for_courant(0.6 * synth.stability_bound(g, 2), 1.0, 1.0, g)
+    p = synth.problem(2, 40, 33, g, 1.0, dt, 1.0, synth.BC_DIRICHLET0, react=(0, -0.05, 0, 0),
+                      mem_mode=mode, mem_L=Lw, mem_a=a, K=250,
+                      u0=synth.SplitMix64(17).uniform(40 * 33, 0, 1))
+    got, _ = run_gpu(p, state=state)
+    assert rel_inf(got, oracle.run(p)) < TOL[state]

@@ -89,10 +89,11 @@ def mittag_leffler(g, z):
     return float(mpmath.nsum(lambda k: (-z) ** k / mpmath.gamma(g * k + 1), [0, mpmath.inf]))
 
 
-@pytest.mark.parametrize("g", [0.5, 0.75, 0.9])
+@pytest.mark.parametrize("g", [0.5, 0.75, 0.9, 1.25, 1.5, 1.75])
 def test_relaxation_tracks_mittag_leffler(g):
     """N = 1, Dirichlet: delta = -2u, so the scheme discretises du/dt = -mu D^{1-g} u with
-    mu = 2 alpha / dx^2, whose solution is E_g(-mu t^g) u0; the GL error is first order."""
+    mu = 2 alpha / dx^2, whose solution is E_g(-mu t^g) u0 (for 1 < g < 2, D^{1-g} is a fractional
+    integral and the solution has zero initial velocity); the GL error is first order."""
     T, alpha, dx = 1.0, 0.5, 1.0  # mu = 1
     errs = []
     for K in (200, 400, 800):
@@ -168,3 +169,17 @@ def test_dense_linear_system(ndim, bc, nx, ny, mode, L, a):
     U = np.linalg.solve(A, b)
     got = oracle.run(p)
     assert rel_inf(got, U[-N:]) < 1e-12
+
+
+@pytest.mark.parametrize("g", [0.3, 0.5, 0.8, 1.0, 1.3, 1.5, 1.9])
+def test_stability_threshold_is_checkerboard_bound(g):
+    """Just below S = 2^g / (4 ndim) the highest mode (Lambda = 4 ndim) decays, just above it grows:
+    the bound the library enforces is the scheme's threshold for 0 < g < 2."""
+    bound = synth.stability_bound(g, 1)
+    amp = []
+    for f in (0.97, 1.03):
+        p = synth.problem(1, 5, 1, g, 1.0, 1.0, 1.0 / math.sqrt(f * bound), synth.BC_DIRICHLET0, K=3000)
+        A = oracle.scalar_mode(p, 4.0, K=3000)
+        amp.append(np.max(np.abs(A[-500:])))
+    assert amp[0] < 0.1
+    assert not np.isfinite(amp[1]) or amp[1] > 1e20
