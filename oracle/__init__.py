@@ -28,7 +28,7 @@ class OrProblem(ctypes.Structure):
         ("dt", ctypes.c_double), ("dx", ctypes.c_double),
         ("bc", ctypes.c_int), ("react", ctypes.c_double * 4),
         ("mem_mode", ctypes.c_int), ("mem_L", ctypes.c_int), ("mem_a", ctypes.c_int),
-        ("adaptive_rule", ctypes.c_int),
+        ("adaptive_rule", ctypes.c_int), ("nz", ctypes.c_int),
     ]
 
 
@@ -84,6 +84,7 @@ def _problem(p: dict) -> OrProblem:
         s.react[i] = p["react"][i]
     s.mem_mode, s.mem_L, s.mem_a = p["mem_mode"], p["mem_L"], p["mem_a"]
     s.adaptive_rule = p.get("adaptive_rule", ADAPT_PAPER)
+    s.nz = p.get("nz", 1)
     return s
 
 
@@ -109,7 +110,7 @@ def run(p: dict, K: int | None = None, u0=None, tape: bool = False, threads: int
     """u^K (and the (K+1, N) tape of u^0..u^K if tape=True)."""
     K = p["K"] if K is None else K
     u0 = np.ascontiguousarray(p["u0"] if u0 is None else u0, dtype=np.float64)
-    N = p["nx"] * p["ny"]
+    N = p["nx"] * p["ny"] * p.get("nz", 1)
     uK = np.empty(N)
     tp = np.empty((K + 1, N)) if tape else None
     s = _problem(p)
@@ -123,7 +124,7 @@ def run_cs(p: dict, K: int | None = None, gamma_im=0.0, alpha_im=0.0, react_im=N
            u0_im=None):
     """Complex-step forward: returns (Re u^K, Im u^K)."""
     K = p["K"] if K is None else K
-    N = p["nx"] * p["ny"]
+    N = p["nx"] * p["ny"] * p.get("nz", 1)
     u0 = np.ascontiguousarray(p["u0"], dtype=np.float64)
     ui = None if u0_im is None else np.ascontiguousarray(u0_im, dtype=np.float64)
     ri = None if react_im is None else np.ascontiguousarray(react_im, dtype=np.float64)
@@ -139,7 +140,7 @@ def run_cs(p: dict, K: int | None = None, gamma_im=0.0, alpha_im=0.0, react_im=N
 def adjoint(p: dict, target, K: int | None = None, threads: int = 0):
     """FP64 adjoint: dict with J, du0, dgamma, dalpha, dreact[4]."""
     K = p["K"] if K is None else K
-    N = p["nx"] * p["ny"]
+    N = p["nx"] * p["ny"] * p.get("nz", 1)
     u0 = np.ascontiguousarray(p["u0"], dtype=np.float64)
     tg = np.ascontiguousarray(target, dtype=np.float64)
     J, dg, da = np.zeros(1), np.zeros(1), np.zeros(1)

@@ -35,8 +35,9 @@ static inline void nadd(double *s, double *c, double x)
 static int check_problem(const or_problem *p, long K)
 {
     if (!p || K < 0) return -1;
-    if (p->ndim != 1 && p->ndim != 2) return -1;
-    if (p->nx < 1 || p->ny < 1 || (p->ndim == 1 && p->ny != 1)) return -1;
+    if (p->ndim < 1 || p->ndim > 3) return -1;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->ndim == 1 && p->ny != 1) || (p->ndim < 3 && p->nz != 1))
+        return -1;
     if (p->bc != OR_BC_DIRICHLET0 && p->bc != OR_BC_NOFLUX) return -1;
     if (!(p->dt > 0) || !(p->dx > 0)) return -1;
     if (p->mem_mode == OR_MEM_SHORT && p->mem_L < 0) return -1;
@@ -51,21 +52,31 @@ static int check_problem(const or_problem *p, long K)
  * or the boundary cell's own value (no-flux, cell-centred mirror). */
 static void apply_L(const or_problem *p, const double *u, double *out)
 {
-    const int nx = p->nx, ny = p->ny;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const long pl = (long)nx * ny; /* points per z-plane */
     const int mirror = (p->bc == OR_BC_NOFLUX);
-    for (int y = 0; y < ny; ++y) {
-        for (int x = 0; x < nx; ++x) {
-            const long i = (long)y * nx + x;
-            const double c = u[i];
-            const double g = mirror ? c : 0.0;
-            const double r = (x + 1 < nx) ? u[i + 1] : g;
-            const double l = (x > 0) ? u[i - 1] : g;
-            if (p->ndim == 1) {
-                out[i] = r - 2.0 * c + l;
-            } else {
-                const double up = (y + 1 < ny) ? u[i + nx] : g;
-                const double dn = (y > 0) ? u[i - nx] : g;
-                out[i] = r + l - 4.0 * c + up + dn;
+    for (int z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const long i = (long)z * pl + (long)y * nx + x;
+                const double c = u[i];
+                const double g = mirror ? c : 0.0;
+                const double r = (x + 1 < nx) ? u[i + 1] : g;
+                const double l = (x > 0) ? u[i - 1] : g;
+                if (p->ndim == 1) {
+                    out[i] = r - 2.0 * c + l;
+                } else if (p->ndim == 2) {
+                    const double up = (y + 1 < ny) ? u[i + nx] : g;
+                    const double dn = (y > 0) ? u[i - nx] : g;
+                    out[i] = r + l - 4.0 * c + up + dn;
+                } else {
+                    /* the 7-point analogue of eq. deltasimp: x pair, -6 u, y pair, z pair */
+                    const double up = (y + 1 < ny) ? u[i + nx] : g;
+                    const double dn = (y > 0) ? u[i - nx] : g;
+                    const double fw = (z + 1 < nz) ? u[i + pl] : g;
+                    const double bk = (z > 0) ? u[i - pl] : g;
+                    out[i] = r + l - 6.0 * c + up + dn + fw + bk;
+                }
             }
         }
     }
@@ -77,24 +88,28 @@ static void apply_L(const or_problem *p, const double *u, double *out)
  * L^T v sends v_i back to every column that row i read. */
 static void apply_LT(const or_problem *p, const double *v, double *out)
 {
-    const int nx = p->nx, ny = p->ny;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const long pl = (long)nx * ny;
     const int mirror = (p->bc == OR_BC_NOFLUX);
-    const long N = (long)nx * ny;
+    const long N = pl * nz;
     memset(out, 0, sizeof(double) * (size_t)N);
-    for (int y = 0; y < ny; ++y) {
-        for (int x = 0; x < nx; ++x) {
-            const long i = (long)y * nx + x;
-            const double vi = v[i];
-            const int ndir = 2 * p->ndim;
-            const long nb[4] = {x + 1 < nx ? i + 1 : -1, x > 0 ? i - 1 : -1,
-                                y + 1 < ny ? i + nx : -1, y > 0 ? i - nx : -1};
-            for (int d = 0; d < ndir; ++d) {
-                if (nb[d] >= 0)
-                    out[nb[d]] += vi;
-                else if (mirror)
-                    out[i] += vi;
+    for (int z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const long i = (long)z * pl + (long)y * nx + x;
+                const double vi = v[i];
+                const int ndir = 2 * p->ndim;
+                const long nb[6] = {x + 1 < nx ? i + 1 : -1, x > 0 ? i - 1 : -1,
+                                    y + 1 < ny ? i + nx : -1, y > 0 ? i - nx : -1,
+                                    z + 1 < nz ? i + pl : -1, z > 0 ? i - pl : -1};
+                for (int d = 0; d < ndir; ++d) {
+                    if (nb[d] >= 0)
+                        out[nb[d]] += vi;
+                    else if (mirror)
+                        out[i] += vi;
+                }
+                out[i] += -2.0 * p->ndim * vi;
             }
-            out[i] += -2.0 * p->ndim * vi;
         }
     }
 }
@@ -218,7 +233,7 @@ static long history_rows(const or_problem *p, long K)
 int or_run(const or_problem *p, const double *u0, long K, double *uK, double *tape, int threads)
 {
     if (check_problem(p, K) || !u0 || !uK) return -1;
-    const long N = (long)p->nx * p->ny;
+    const long N = (long)p->nx * p->ny * p->nz;
     const long cap = history_rows(p, K);
     const double S = p->alpha * pow(p->dt, p->gamma) / (p->dx * p->dx);
 
@@ -280,21 +295,30 @@ int or_run(const or_problem *p, const double *u0, long K, double *uK, double *ta
 
 static void apply_L_cs(const or_problem *p, const double complex *u, double complex *out)
 {
-    const int nx = p->nx, ny = p->ny;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const long pl = (long)nx * ny;
     const int mirror = (p->bc == OR_BC_NOFLUX);
-    for (int y = 0; y < ny; ++y) {
-        for (int x = 0; x < nx; ++x) {
-            const long i = (long)y * nx + x;
-            const double complex c = u[i];
-            const double complex g = mirror ? c : 0.0;
-            const double complex r = (x + 1 < nx) ? u[i + 1] : g;
-            const double complex l = (x > 0) ? u[i - 1] : g;
-            if (p->ndim == 1) {
-                out[i] = r - 2.0 * c + l;
-            } else {
-                const double complex up = (y + 1 < ny) ? u[i + nx] : g;
-                const double complex dn = (y > 0) ? u[i - nx] : g;
-                out[i] = r + l - 4.0 * c + up + dn;
+    for (int z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const long i = (long)z * pl + (long)y * nx + x;
+                const double complex c = u[i];
+                const double complex g = mirror ? c : 0.0;
+                const double complex r = (x + 1 < nx) ? u[i + 1] : g;
+                const double complex l = (x > 0) ? u[i - 1] : g;
+                if (p->ndim == 1) {
+                    out[i] = r - 2.0 * c + l;
+                } else if (p->ndim == 2) {
+                    const double complex up = (y + 1 < ny) ? u[i + nx] : g;
+                    const double complex dn = (y > 0) ? u[i - nx] : g;
+                    out[i] = r + l - 4.0 * c + up + dn;
+                } else {
+                    const double complex up = (y + 1 < ny) ? u[i + nx] : g;
+                    const double complex dn = (y > 0) ? u[i - nx] : g;
+                    const double complex fw = (z + 1 < nz) ? u[i + pl] : g;
+                    const double complex bk = (z > 0) ? u[i - pl] : g;
+                    out[i] = r + l - 6.0 * c + up + dn + fw + bk;
+                }
             }
         }
     }
@@ -304,7 +328,7 @@ int or_run_cs(const or_problem *p, double gamma_im, double alpha_im, const doubl
               const double *u0_re, const double *u0_im, long K, double *uK_re, double *uK_im)
 {
     if (check_problem(p, K) || !u0_re || !uK_re || !uK_im) return -1;
-    const long N = (long)p->nx * p->ny;
+    const long N = (long)p->nx * p->ny * p->nz;
     const long cap = history_rows(p, K);
     const double complex gam = p->gamma + I * gamma_im;
     const double complex alp = p->alpha + I * alpha_im;
@@ -350,7 +374,7 @@ int or_adjoint(const or_problem *p, const double *u0, long K, const double *targ
                double dJ_dreact[4], int threads)
 {
     if (check_problem(p, K) || p->mem_mode != OR_MEM_FULL || !u0 || !target || K < 1) return -1;
-    const long N = (long)p->nx * p->ny;
+    const long N = (long)p->nx * p->ny * p->nz;
     const double S = p->alpha * pow(p->dt, p->gamma) / (p->dx * p->dx);
     double *tape = malloc(sizeof(double) * (size_t)(K + 1) * (size_t)N);
     double *lam = malloc(sizeof(double) * (size_t)(K + 1) * (size_t)N); /* lambda^r at row r */

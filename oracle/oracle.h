@@ -34,8 +34,8 @@ enum { OR_MEM_FULL = 0, OR_MEM_SHORT = 1, OR_MEM_ADAPTIVE = 2 };
 enum { OR_ADAPT_PAPER = 0, OR_ADAPT_PARTITION = 1 };
 
 typedef struct {
-    int ndim;          /* 1 or 2 */
-    int nx, ny;        /* interior points per axis (ny = 1 in 1-D); point (x, y) at y*nx + x */
+    int ndim;          /* 1, 2 or 3 */
+    int nx, ny;        /* interior points per axis (ny = 1 in 1-D); point (x, y, z) at (z*ny + y)*nx + x */
     double gamma;      /* anomalous exponent */
     double alpha;      /* diffusivity */
     double dt, dx;     /* time step and grid spacing */
@@ -45,6 +45,7 @@ typedef struct {
     int mem_L;         /* short memory: lags 0..min(mem_L, k)  (eq. frac_shortmemory) */
     int mem_a;         /* adaptive memory: base interval [0, a], a >= 2 (Definition 3.1) */
     int adaptive_rule; /* OR_ADAPT_PAPER (literal Proposition 3.1) | OR_ADAPT_PARTITION */
+    int nz;            /* points along the third axis (3-D; 1 otherwise) */
 } or_problem;
 
 /* Grunwald-Letnikov weights psi(g, m), m = 0..n-1, by the recurrence of

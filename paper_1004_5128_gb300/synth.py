@@ -73,16 +73,17 @@ def stability_bound(gamma: float, ndim: int) -> float:
 
 
 def problem(ndim, nx, ny, gamma, alpha, dt, dx, bc, react=(0.0, 0.0, 0.0, 0.0),
-            mem_mode=MEM_FULL, mem_L=0, mem_a=0, adaptive_rule=ADAPT_PAPER, K=1, u0=None):
+            mem_mode=MEM_FULL, mem_L=0, mem_a=0, adaptive_rule=ADAPT_PAPER, K=1, u0=None, nz=1):
     ny = 1 if ndim == 1 else ny
-    p = dict(ndim=int(ndim), nx=int(nx), ny=int(ny), gamma=float(gamma), alpha=float(alpha),
-             dt=float(dt), dx=float(dx), bc=int(bc), react=[float(r) for r in react],
-             mem_mode=int(mem_mode), mem_L=int(mem_L), mem_a=int(mem_a),
-             adaptive_rule=int(adaptive_rule), K=int(K))
+    nz = nz if ndim == 3 else 1
+    p = dict(ndim=int(ndim), nx=int(nx), ny=int(ny), nz=int(nz), gamma=float(gamma),
+             alpha=float(alpha), dt=float(dt), dx=float(dx), bc=int(bc),
+             react=[float(r) for r in react], mem_mode=int(mem_mode), mem_L=int(mem_L),
+             mem_a=int(mem_a), adaptive_rule=int(adaptive_rule), K=int(K))
     if u0 is None:
-        u0 = np.zeros(nx * ny)
+        u0 = np.zeros(nx * ny * nz)
     p["u0"] = np.ascontiguousarray(np.asarray(u0, dtype=np.float64).reshape(-1))
-    assert p["u0"].size == nx * ny
+    assert p["u0"].size == nx * ny * nz
     return p
 
 
@@ -199,11 +200,11 @@ def with_mode(p: dict, mode: int, L: int = 0, a: int = 0, rule: int = ADAPT_PAPE
     return q
 
 
-def eigenmode(p: dict, qx: int, qy: int = 1) -> np.ndarray:
+def eigenmode(p: dict, qx: int, qy: int = 1, qz: int = 1) -> np.ndarray:
     """Discrete Laplacian eigenvector for p's grid and boundary condition.
 
     Dirichlet 0: sin(q pi (j+1)/(n+1)); no-flux (cell-centred mirror): cos(q pi (j+1/2)/n).
-    Product over the axes in 2-D, row-major (y, x) flat.
+    Product over the axes in 2-D / 3-D, row-major (z, y, x) flat.
     """
     def axis(n, q):
         j = np.arange(n, dtype=np.float64)
@@ -214,7 +215,10 @@ def eigenmode(p: dict, qx: int, qy: int = 1) -> np.ndarray:
     if p["ndim"] == 1:
         return ex
     ey = axis(p["ny"], qy)
-    return np.outer(ey, ex).reshape(-1)
+    if p["ndim"] == 2:
+        return np.outer(ey, ex).reshape(-1)
+    ez = axis(p["nz"], qz)
+    return np.einsum("z,y,x->zyx", ez, ey, ex).reshape(-1)
 
 
 def workload_runs(name: str, K: int = 0, modes: str = ""):

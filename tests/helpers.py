@@ -6,7 +6,7 @@ import numpy as np
 from paper_1004_5128_gb300 import synth
 
 
-def laplacian_eigenvalue(p: dict, qx: int, qy: int = 1) -> float:
+def laplacian_eigenvalue(p: dict, qx: int, qy: int = 1, qz: int = 1) -> float:
     """Lambda with L(phi) = -Lambda phi for the unnormalised 3/5-point stencil.
 
     For the Dirichlet sine mode sin(q pi (j+1)/(n+1)) and the cell-centred
@@ -17,8 +17,10 @@ def laplacian_eigenvalue(p: dict, qx: int, qy: int = 1) -> float:
         h = 1.0 / (n + 1.0) if p["bc"] == synth.BC_DIRICHLET0 else 1.0 / n
         return 4.0 * math.sin(q * math.pi * h / 2.0) ** 2
     v = lam(p["nx"], qx)
-    if p["ndim"] == 2:
+    if p["ndim"] >= 2:
         v += lam(p["ny"], qy)
+    if p["ndim"] == 3:
+        v += lam(p["nz"], qz)
     return v
 
 
@@ -31,20 +33,23 @@ def rel_inf(a, ref) -> float:
 
 def laplacian_matrix(p: dict) -> np.ndarray:
     """Dense L of eq. deltasimp with the ghost rule of p['bc'], built row by row."""
-    nx, ny = p["nx"], p["ny"]
-    N = nx * ny
+    nx, ny, nz = p["nx"], p["ny"], p.get("nz", 1)
+    N = nx * ny * nz
     L = np.zeros((N, N))
     mirror = p["bc"] == synth.BC_NOFLUX
-    for y in range(ny):
-        for x in range(nx):
-            i = y * nx + x
-            L[i, i] -= 2 * p["ndim"]
-            nbrs = [(x + 1, y), (x - 1, y)]
-            if p["ndim"] == 2:
-                nbrs += [(x, y + 1), (x, y - 1)]
-            for (xx, yy) in nbrs:
-                if 0 <= xx < nx and 0 <= yy < ny:
-                    L[i, yy * nx + xx] += 1.0
-                elif mirror:
-                    L[i, i] += 1.0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                i = (z * ny + y) * nx + x
+                L[i, i] -= 2 * p["ndim"]
+                nbrs = [(x + 1, y, z), (x - 1, y, z)]
+                if p["ndim"] >= 2:
+                    nbrs += [(x, y + 1, z), (x, y - 1, z)]
+                if p["ndim"] == 3:
+                    nbrs += [(x, y, z + 1), (x, y, z - 1)]
+                for (xx, yy, zz) in nbrs:
+                    if 0 <= xx < nx and 0 <= yy < ny and 0 <= zz < nz:
+                        L[i, (zz * ny + yy) * nx + xx] += 1.0
+                    elif mirror:
+                        L[i, i] += 1.0
     return L

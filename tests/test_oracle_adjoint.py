@@ -10,13 +10,13 @@ H_CS = 1e-30
 
 
 def adj_problem(bc, ndim=2):
-    nx, ny = (9, 7) if ndim == 2 else (23, 1)
+    nx, ny, nz = {1: (23, 1, 1), 2: (9, 7, 1), 3: (5, 4, 3)}[ndim]
     g = synth.SplitMix64(77)
-    u0 = g.uniform(nx * ny, 0.0, 1.0)
-    target = g.uniform(nx * ny, 0.0, 0.8)
+    u0 = g.uniform(nx * ny * nz, 0.0, 1.0)
+    target = g.uniform(nx * ny * nz, 0.0, 0.8)
     dt = 0.01
     p = synth.problem(ndim, nx, ny, 0.7, 0.8, dt, 1.0, bc, react=(0.05, -0.3, 0.2, -0.1), K=40,
-                      u0=u0)
+                      u0=u0, nz=nz)
     return p, target
 
 
@@ -35,7 +35,8 @@ def cs_grad(p, target, **im):
 
 
 @pytest.mark.parametrize("bc,ndim", [(synth.BC_DIRICHLET0, 2), (synth.BC_NOFLUX, 2),
-                                     (synth.BC_NOFLUX, 1)])
+                                     (synth.BC_NOFLUX, 1), (synth.BC_DIRICHLET0, 3),
+                                     (synth.BC_NOFLUX, 3)])
 def test_adjoint_matches_complex_step(bc, ndim):
     p, target = adj_problem(bc, ndim)
     a = oracle.adjoint(p, target)

@@ -14,29 +14,35 @@ MODES = [(oracle.MEM_FULL, 0, 0), (oracle.MEM_SHORT, 7, 0), (oracle.MEM_ADAPTIVE
          (oracle.MEM_ADAPTIVE, 0, 2)]
 
 
-def small_problem(ndim, bc, nx=13, ny=9, gamma=0.7, react=(0.0, -0.3, 0.0, 0.0), K=60, seed=11):
+def small_problem(ndim, bc, nx=13, ny=9, gamma=0.7, react=(0.0, -0.3, 0.0, 0.0), K=60, seed=11, nz=5):
     dx = 0.1
     dt = synth.dt_for_courant(0.12, 1.3, dx, gamma)
     ny = 1 if ndim == 1 else ny
-    u0 = synth.SplitMix64(seed).uniform(nx * ny, -1.0, 1.0)
-    return synth.problem(ndim, nx, ny, gamma, 1.3, dt, dx, bc, react=react, K=K, u0=u0)
+    nz = nz if ndim == 3 else 1
+    u0 = synth.SplitMix64(seed).uniform(nx * ny * nz, -1.0, 1.0)
+    return synth.problem(ndim, nx, ny, gamma, 1.3, dt, dx, bc, react=react, K=K, u0=u0, nz=nz)
 
 
 # P2 -------------------------------------------------------------------------
-@pytest.mark.parametrize("ndim,bc", [(1, 0), (1, 1), (2, 0), (2, 1)])
+@pytest.mark.parametrize("ndim,bc", [(1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1)])
 def test_gamma_one_is_ftcs_heat_bitwise(ndim, bc):
     """psi(1, m>=1) = 0 exactly, so eq. frac_final is the textbook FTCS heat update."""
     p = small_problem(ndim, bc, gamma=1.0, react=(0.05, -0.4, 0.1, -0.02), K=40)
     S = p["alpha"] * p["dt"] ** 1.0 / p["dx"] ** 2
     r = p["react"]
-    u = p["u0"].reshape(p["ny"], p["nx"]).copy()
+    u = p["u0"].reshape(p["nz"], p["ny"], p["nx"]).copy()
     for _ in range(p["K"]):
         pad = np.pad(u, 1, mode="edge" if bc == synth.BC_NOFLUX else "constant")
-        c = pad[1:-1, 1:-1]
+        c = pad[1:-1, 1:-1, 1:-1]
+        xp, xm = pad[1:-1, 1:-1, 2:], pad[1:-1, 1:-1, :-2]
+        yp, ym = pad[1:-1, 2:, 1:-1], pad[1:-1, :-2, 1:-1]
+        zp, zm = pad[2:, 1:-1, 1:-1], pad[:-2, 1:-1, 1:-1]
         if ndim == 1:
-            lap = pad[1:-1, 2:] - 2.0 * c + pad[1:-1, :-2]
+            lap = xp - 2.0 * c + xm
+        elif ndim == 2:
+            lap = xp + xm - 4.0 * c + yp + ym
         else:
-            lap = pad[1:-1, 2:] + pad[1:-1, :-2] - 4.0 * c + pad[2:, 1:-1] + pad[:-2, 1:-1]
+            lap = xp + xm - 6.0 * c + yp + ym + zp + zm
         f = r[0] + u * (r[1] + u * (r[2] + u * r[3]))
         u = u + p["dt"] * f + S * lap
     got = oracle.run(p)
@@ -44,13 +50,13 @@ def test_gamma_one_is_ftcs_heat_bitwise(ndim, bc):
 
 
 # P3 -------------------------------------------------------------------------
-@pytest.mark.parametrize("ndim,bc", [(1, 0), (1, 1), (2, 0), (2, 1)])
+@pytest.mark.parametrize("ndim,bc", [(1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1)])
 @pytest.mark.parametrize("mode,L,a", MODES)
 def test_eigenmode_reduces_to_scalar_recursion(ndim, bc, mode, L, a):
     p = synth.with_mode(small_problem(ndim, bc, K=80), mode, L=L, a=a)
-    qx, qy = 3, 2
-    phi = synth.eigenmode(p, qx, qy)
-    lam = laplacian_eigenvalue(p, qx, qy)
+    qx, qy, qz = 3, 2, 1
+    phi = synth.eigenmode(p, qx, qy, qz)
+    lam = laplacian_eigenvalue(p, qx, qy, qz)
     A = oracle.scalar_mode(p, lam)
     got = oracle.run(p, u0=phi)
     assert rel_inf(got, A[-1] * phi) < 1e-12
@@ -109,10 +115,11 @@ def test_relaxation_tracks_mittag_leffler(g):
 # P4 -------------------------------------------------------------------------
 @pytest.mark.parametrize("mode,L,a", MODES)
 @pytest.mark.parametrize("beta", [0.0, 0.8])
-def test_mass_balance_noflux(mode, L, a, beta):
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_mass_balance_noflux(mode, L, a, beta, ndim):
     """Mirror ghosts make every column of L sum to zero, so sum_j delta_j = 0 and
     with f = -beta u the mass obeys M^{k+1} = (1 - beta dt) M^k in every memory mode."""
-    p = synth.with_mode(small_problem(2, synth.BC_NOFLUX, nx=17, ny=11, react=(0, -beta, 0, 0),
+    p = synth.with_mode(small_problem(ndim, synth.BC_NOFLUX, nx=17, ny=11, react=(0, -beta, 0, 0),
                                       K=150), mode, L=L, a=a)
     p["u0"] = np.abs(p["u0"]) + 0.1
     _, tape = oracle.run(p, tape=True)
@@ -135,15 +142,16 @@ def test_modes_coincide_when_window_covers_history(ndim, bc):
 
 
 # P7 -------------------------------------------------------------------------
-@pytest.mark.parametrize("ndim,bc,nx,ny", [(1, 0, 4, 1), (1, 1, 5, 1), (2, 0, 3, 2), (2, 1, 2, 3)])
+@pytest.mark.parametrize("ndim,bc,nx,ny", [(1, 0, 4, 1), (1, 1, 5, 1), (2, 0, 3, 2), (2, 1, 2, 3),
+                                            (3, 0, 2, 2), (3, 1, 2, 1)])
 @pytest.mark.parametrize("mode,L,a", MODES)
 def test_dense_linear_system(ndim, bc, nx, ny, mode, L, a):
     """For linear f = r0 + r1 u the K steps form one block-lower-triangular linear system in
     (u^1 .. u^K); a dense library solve of it must equal the time stepping."""
     K = 14
-    p = synth.with_mode(small_problem(ndim, bc, nx=nx, ny=ny, react=(0.2, -0.5, 0, 0), K=K),
+    p = synth.with_mode(small_problem(ndim, bc, nx=nx, ny=ny, react=(0.2, -0.5, 0, 0), K=K, nz=2),
                         mode, L=L, a=a)
-    N = nx * ny
+    N = p["u0"].size
     Lm = laplacian_matrix(p)
     S = p["alpha"] * p["dt"] ** p["gamma"] / p["dx"] ** 2
     mpmath = pytest.importorskip("mpmath")
