@@ -126,7 +126,7 @@ def problems(name: str, K: int = 0, modes: str = ""):
 
 def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
     """History rows read (lags >= 1) plus, per step, the u read/write and the delta write."""
-    N = p["nx"] * p["ny"]
+    N = p["nx"] * p["ny"] * p.get("nz", 1)
     sh = HBYTES[kw.get("hist", kw.get("state", "f32"))]
     ss = 8 if kw.get("state") == "f64" else 4
     return geo["hist_rows_total"] * N * sh + p["K"] * N * (2 * ss + sh)
@@ -135,7 +135,7 @@ def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
 def _sample_terms(p, K):
     import oracle
     return sum(len(oracle.schedule(p["mem_mode"], p["mem_L"], p["mem_a"], p.get("adaptive_rule", 0),
-                                   k)[0]) for k in range(K)) * p["nx"] * p["ny"]
+                                   k)[0]) for k in range(K)) * p["nx"] * p["ny"] * p.get("nz", 1)
 
 
 class SingleRun:
@@ -223,7 +223,7 @@ class AdjointRun:
         self.target = tgt.run(p["K"])
         tgt.close()
         self.geo = self.s.geometry()
-        K, N = p["K"], p["nx"] * p["ny"]
+        K, N = p["K"], p["nx"] * p["ny"] * p.get("nz", 1)
         fwd = self.geo["terms_total"]
         recompute = fwd - sum((k + 1) * N for k in range(self.C - 1, K, self.C))
         self.terms = fwd + recompute + fwd  # forward, segment recompute, adjoint (lags 0..q)
@@ -430,7 +430,7 @@ def _oracle_sample(args, kp, threads):
     for name, p, kw in problems(args.workload, args.K, args.modes):
         if args.workload == "c5":
             K = min(kp, p["K"])
-            N = p["nx"] * p["ny"]
+            N = p["nx"] * p["ny"] * p.get("nz", 1)
             tgt = oracle.run(synth.config5(K=K, target=True), threads=threads)
             w = time.perf_counter()
             oracle.adjoint(p, tgt, K=K, threads=threads)

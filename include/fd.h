@@ -24,8 +24,8 @@
  *  - Streams: all device work is enqueued on the cudaStream_t passed to
  *    fd_init (NULL = legacy default stream).  Calls returning only after the
  *    stream drains say so.
- *  - Field layout: N = nx*ny points, row-major with x fastest
- *    (point (x, y) at index y*nx + x), in the problem's state_dtype.
+ *  - Field layout: N = nx*ny*nz points, row-major with x fastest
+ *    (point (x, y, z) at index (z*ny + y)*nx + x), in the problem's state_dtype.
  *  - State pointers may be device or host memory (cudaMemcpyDefault under
  *    unified addressing; pinned host memory keeps copies asynchronous).
  */
@@ -65,8 +65,8 @@ enum { FD_F64 = 0, FD_F32 = 1, FD_BF16 = 2, FD_F16 = 3 };
                                       launch ends with FD_ERR_TIMEOUT (GPU stays usable) */
 
 typedef struct fd_problem {
-    int ndim;            /* 1 or 2 */
-    int nx, ny;          /* interior points per axis (ny = 1 in 1-D), N = nx*ny >= 1 */
+    int ndim;            /* 1, 2 or 3 (3-D: the 7-point analogue of eq. deltasimp) */
+    int nx, ny;          /* interior points per axis (ny = 1 in 1-D), N = nx*ny*nz >= 1 */
     double gamma;        /* anomalous exponent, 0 < gamma < 2 */
     double alpha;        /* diffusivity > 0 */
     double dt, dx;       /* time step and grid spacing > 0 */
@@ -94,6 +94,7 @@ typedef struct fd_problem {
     int ctas_per_sm;     /* resident CTAs per SM for the persistent grid */
     int head_lags;       /* lags 1..head_lags are summed by the per-tile update from rows kept in
                             state precision (0 = 8 for F32/F64 history, 32 for BF16/F16) */
+    int nz;              /* points along the third axis when ndim == 3, else 1 */
 } fd_problem;
 
 typedef struct fd_handle fd_handle;

@@ -46,7 +46,7 @@ def _bucket(x: int) -> int:
 
 
 def key(p: dict, state: str = "f32", hist: str | None = None, kahan: bool = False) -> str:
-    N = p["nx"] * p["ny"]
+    N = p["nx"] * p["ny"] * p.get("nz", 1)
     return (f"{state}/{hist or state}/{'kahan' if kahan else 'plain'}/mode{p['mem_mode']}"
             f"/d{p['ndim']}/N{_bucket(N)}/K{_bucket(p['K'])}")
 
@@ -101,7 +101,7 @@ def lookup(p: dict, state: str = "f32", hist: str | None = None, kahan: bool = F
 
 
 def batch_key(probs: list, state: str = "f32") -> str:
-    n = sum(p["nx"] * p["ny"] for p in probs)
+    n = sum(p["nx"] * p["ny"] * p.get("nz", 1) for p in probs)
     k = max(p["K"] for p in probs)
     return f"batch/{state}/mode{probs[0]['mem_mode']}/n{len(probs)}/N{_bucket(n)}/K{_bucket(k)}"
 

@@ -145,9 +145,10 @@ inline int64_t n_terms(const int4 &e) { return (int64_t)e.x + e.y + (e.w >= e.z 
 int validate(const fd_problem *p)
 {
     if (!p) return FD_ERR_INVALID_ARG;
-    if (p->ndim != 1 && p->ndim != 2) return FD_ERR_INVALID_ARG;
-    if (p->nx < 1 || p->ny < 1 || (p->ndim == 1 && p->ny != 1)) return FD_ERR_INVALID_ARG;
-    if ((int64_t)p->nx * p->ny > (int64_t)1 << 30) return FD_ERR_INVALID_ARG;
+    if (p->ndim < 1 || p->ndim > 3) return FD_ERR_INVALID_ARG;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->ndim == 1 && p->ny != 1) || (p->ndim < 3 && p->nz != 1))
+        return FD_ERR_INVALID_ARG;
+    if ((int64_t)p->nx * p->ny * p->nz > (int64_t)1 << 30) return FD_ERR_INVALID_ARG;
     if (!(p->gamma > 0.0 && p->gamma < 2.0)) return FD_ERR_INVALID_ARG;
     if (!(p->alpha > 0.0) || !(p->dt > 0.0) || !(p->dx > 0.0)) return FD_ERR_INVALID_ARG;
     for (double r : p->react)
@@ -214,7 +215,7 @@ int device_sms()
 
 void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
 {
-    const int64_t N = (int64_t)p.nx * p.ny;
+    const int64_t N = (int64_t)p.nx * p.ny * p.nz;
     g.sh = dtype_size(p.hist_dtype);
     g.ss = dtype_size(p.state_dtype);
     g.sa = dtype_size(p.accum_dtype);
@@ -288,7 +289,7 @@ struct Layout {
 void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s, Layout &L,
                     unsigned *counters = nullptr, bool external_counters = false)
 {
-    const int64_t N = (int64_t)p.nx * p.ny;
+    const int64_t N = (int64_t)p.nx * p.ny * p.nz;
     const size_t ubytes = align_up((size_t)N * g.ss, kAlign);
     L.ubuf[0] = c.take(ubytes);
     L.ubuf[1] = c.take(ubytes);
@@ -411,7 +412,8 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.nx = p.nx;
     I.ny = p.ny;
     I.bc = p.bc;
-    I.N = p.nx * p.ny;
+    I.N = p.nx * p.ny * p.nz;
+    I.nz = p.nz;
     I.T = g.T;
     I.P = g.P;
     I.R = g.R;
@@ -551,6 +553,15 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     return FD_OK;
 }
 
+// A zero nz (structs initialised before the field existed) means a single plane.
+static const fd_problem *normalized(const fd_problem *p, fd_problem &q)
+{
+    if (!p) return p;
+    q = *p;
+    if (q.nz == 0) q.nz = 1;
+    return &q;
+}
+
 static int prepare(const fd_problem *p, Sched &s, Geo &g, size_t *bytes, Layout *Lout, char *ws,
                    Ctrl *ctrl)
 {
@@ -609,6 +620,8 @@ int fd_schedule(const fd_problem *p, int64_t k, int64_t *lags, int64_t *mult, in
 int fd_workspace_bytes(const fd_problem *p, size_t *bytes)
 {
     if (!bytes) return FD_ERR_INVALID_ARG;
+    fd_problem q;
+    p = normalized(p, q);
     Sched s;
     Geo g;
     return prepare(p, s, g, bytes, nullptr, nullptr, nullptr);
@@ -617,6 +630,8 @@ int fd_workspace_bytes(const fd_problem *p, size_t *bytes)
 int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_stream, fd_handle **out)
 {
     if (!out) return FD_ERR_INVALID_ARG;
+    fd_problem q;
+    p = normalized(p, q);
     *out = nullptr;
     fd_handle *h = new (std::nothrow) fd_handle();
     if (!h) return FD_ERR_INVALID_ARG;
@@ -701,7 +716,7 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
 int fd_set_state(fd_handle *h, const void *u0)
 {
     if (!h || !u0) return FD_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)h->p.nx * h->p.ny * h->g.ss;
+    const size_t bytes = (size_t)h->p.nx * h->p.ny * h->p.nz * h->g.ss;
     CK(cudaMemcpyAsync(h->L.ubuf[0], u0, bytes, cudaMemcpyDefault, h->st));
     if (h->L.ulo[0]) CK(cudaMemsetAsync(h->L.ulo[0], 0, bytes, h->st));
     if (h->L.ckpt) CK(cudaMemcpyAsync(h->L.ckpt, u0, bytes, cudaMemcpyDefault, h->st));
@@ -727,7 +742,7 @@ int fd_step(fd_handle *h, int nsteps)
 int fd_get_state(fd_handle *h, void *u_out)
 {
     if (!h || !u_out) return FD_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)h->p.nx * h->p.ny * h->g.ss;
+    const size_t bytes = (size_t)h->p.nx * h->p.ny * h->p.nz * h->g.ss;
     CK(cudaMemcpyAsync(u_out, h->L.ubuf[h->k & 1], bytes, cudaMemcpyDefault, h->st));
     return FD_OK;
 }
@@ -766,7 +781,7 @@ int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma
     const fd_problem &p = h->p;
     const int K = (int)h->k;
     const int C = p.ckpt_every ? p.ckpt_every : 200;
-    const int64_t N = (int64_t)p.nx * p.ny;
+    const int64_t N = (int64_t)p.nx * p.ny * p.nz;
     const size_t ub = (size_t)N * h->g.ss;
     cudaStream_t st = h->st;
     int rc = FD_OK;
@@ -841,7 +856,7 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     g->units_total = h->goff.back();
     int64_t rows = 0;
     for (const int4 &e : h->s.step) rows += n_terms(e);
-    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)h->s.step.size()) * N;
     return FD_OK;
@@ -898,9 +913,13 @@ struct fd_batch {
 
 namespace {
 
-int batch_plan(const fd_problem *probs, int count, fd_batch &b, size_t *bytes, char *ws)
+int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes, char *ws)
 {
-    if (!probs || count < 1) return FD_ERR_INVALID_ARG;
+    if (!probs_in || count < 1) return FD_ERR_INVALID_ARG;
+    std::vector<fd_problem> norm(probs_in, probs_in + count);
+    for (fd_problem &q : norm)
+        if (q.nz == 0) q.nz = 1;
+    const fd_problem *probs = norm.data();
     for (int i = 0; i < count; ++i) {
         const int rc = validate(&probs[i]);
         if (rc) return rc;
@@ -990,8 +1009,8 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
     }
     b->ws = (char *)workspace;
     b->st = (cudaStream_t)cuda_stream;
-    const bool kahan = probs[0].flags & FD_FLAG_KAHAN;
-    b->kfn = fdk::kernel_for(probs[0].state_dtype, probs[0].hist_dtype, probs[0].accum_dtype, kahan, false);
+    const bool kahan = b->p[0].flags & FD_FLAG_KAHAN;
+    b->kfn = fdk::kernel_for(b->p[0].state_dtype, b->p[0].hist_dtype, b->p[0].accum_dtype, kahan, false);
     Geo g0 = b->g[0];
     rc = set_smem_attr(b->kfn, b->smem);
     if (!rc) rc = resolve_grid(b->kfn, g0);
@@ -1002,9 +1021,9 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
     b->t.resize(count);
     std::vector<Inst> insts(count);
     for (int i = 0; i < count && !rc; ++i) {
-        build_tables(probs[i], b->s[i], b->g[i], b->t[i]);
-        rc = upload_tables(probs[i], b->s[i], b->t[i], b->L[i], st);
-        insts[i] = make_inst(probs[i], b->g[i], b->L[i], false);
+        build_tables(b->p[i], b->s[i], b->g[i], b->t[i]);
+        rc = upload_tables(b->p[i], b->s[i], b->t[i], b->L[i], st);
+        insts[i] = make_inst(b->p[i], b->g[i], b->L[i], false);
     }
     if (!rc && cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst) * insts.size(), cudaMemcpyHostToDevice,
                                st) != cudaSuccess)
@@ -1032,7 +1051,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         L.queue = b->ctrl.queue;
         L.err = b->ctrl.err;
         L.nonfinite = b->ctrl.nonfinite;
-        L.timeout_ns = (long long)(probs[0].timeout_ms ? probs[0].timeout_ms : 10000) * 1000000LL;
+        L.timeout_ns = (long long)(b->p[0].timeout_ms ? b->p[0].timeout_ms : 10000) * 1000000LL;
         cudaGraphNode_t m1, m2, kn;
         cudaMemsetParams mp;
         std::memset(&mp, 0, sizeof(mp));
@@ -1073,7 +1092,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
 int fd_batch_set_state(fd_batch *b, int i, const void *u0)
 {
     if (!b || !u0 || i < 0 || i >= (int)b->p.size()) return FD_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)b->p[i].nx * b->p[i].ny * b->g[i].ss;
+    const size_t bytes = (size_t)b->p[i].nx * b->p[i].ny * b->p[i].nz * b->g[i].ss;
     CK(cudaMemcpyAsync(b->L[i].ubuf[0], u0, bytes, cudaMemcpyDefault, b->st));
     if (b->L[i].ulo[0]) CK(cudaMemsetAsync(b->L[i].ulo[0], 0, bytes, b->st));
     return FD_OK;
@@ -1089,7 +1108,7 @@ int fd_batch_run(fd_batch *b)
 int fd_batch_get_state(fd_batch *b, int i, void *u_out)
 {
     if (!b || !u_out || i < 0 || i >= (int)b->p.size()) return FD_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)b->p[i].nx * b->p[i].ny * b->g[i].ss;
+    const size_t bytes = (size_t)b->p[i].nx * b->p[i].ny * b->p[i].nz * b->g[i].ss;
     CK(cudaMemcpyAsync(u_out, b->L[i].ubuf[b->p[i].max_steps & 1], bytes, cudaMemcpyDefault, b->st));
     return FD_OK;
 }
@@ -1123,7 +1142,7 @@ int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g)
         units += step_units(q, e);
         rows += n_terms(e);
     }
-    const int64_t N = (int64_t)b->p[i].nx * b->p[i].ny;
+    const int64_t N = (int64_t)b->p[i].nx * b->p[i].ny * b->p[i].nz;
     g->units_total = units;
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)b->s[i].step.size()) * N;

@@ -46,7 +46,7 @@ enum { ERR_NONE = 0, ERR_TIMEOUT = 1, ERR_PIPE = 2 };
 
 // One problem instance as the device sees it (copied to shared memory per unit).
 struct Inst {
-    int ndim, nx, ny, bc;
+    int ndim, nx, ny, nz, bc;
     int N, T, P, R;          // points, tiles, points per tile, terms per chunk
     int hist_write;          // 0: history rows already hold delta (adjoint recompute pass)
     int cap;                 // history ring rows
@@ -554,7 +554,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     for (int v = 0; v < V; ++v) p1[v] = acc2[v];
                 }
             }
-            __threadfence();
+            // CTA barrier, then one acq_rel atomic: its release half is cumulative over every
+            // thread's partial-row stores ordered before the barrier
             __syncthreads();
             if (tid == 0) {
                 unsigned *ar = &I.arrive[par * I.T + tile];
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         const int rel = k - L.k0;
         if (tid == 0) {
             int ok = 1;
-            const int h = (I.ndim == 2) ? I.nx : 1;
+            const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
             const int lo = max(0, tile * I.P - h) / I.P;
             const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
             for (int t = lo; t <= hi && ok; ++t)
@@ -679,13 +680,24 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     const TS r = (j + 1 < I.N) ? __ldcg(uk + j + 1) : g;
                     const TS l = (j > 0) ? __ldcg(uk + j - 1) : g;
                     d[v] = r - TS(2) * c + l;
-                } else {
+                } else if (I.ndim == 2) {
                     const int x = j % I.nx, y = j / I.nx;
                     const TS r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : g;
                     const TS l = (x > 0) ? __ldcg(uk + j - 1) : g;
                     const TS up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : g;
                     const TS dn = (y > 0) ? __ldcg(uk + j - I.nx) : g;
                     d[v] = r + l - TS(4) * c + up + dn;
+                } else {
+                    // 7-point analogue of eq. deltasimp for the N-dimensional x of eq. fracdiff
+                    const int pl = I.nx * I.ny;
+                    const int x = j % I.nx, y = (j / I.nx) % I.ny, z = j / pl;
+                    const TS r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : g;
+                    const TS l = (x > 0) ? __ldcg(uk + j - 1) : g;
+                    const TS up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : g;
+                    const TS dn = (y > 0) ? __ldcg(uk + j - I.nx) : g;
+                    const TS fw = (z + 1 < I.nz) ? __ldcg(uk + j + pl) : g;
+                    const TS bk = (z > 0) ? __ldcg(uk + j - pl) : g;
+                    d[v] = r + l - TS(6) * c + up + dn + fw + bk;
                 }
                 amax = fmaxf(amax, fabsf((float)d[v]));
             }
@@ -791,8 +803,10 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
 #pragma unroll
                 for (int i = 0; i < 6; ++i) s_dred[tid >> 5][i] = dl[i];
         }
+        // history rows are read later by bulk copies (async proxy): order this thread's generic
+        // stores before them, then publish the tile's step with one release store after the
+        // CTA barrier (cumulative over all threads' stores)
         fence_proxy_async_global();
-        __threadfence();
         __syncthreads();
         if (tid == 0) {
             if (ADJ) {
@@ -802,7 +816,6 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     for (int w = 0; w < (nthr + 31) / 32; ++w) s += s_dred[w][i];
                     dd[i] += s;
                 }
-                __threadfence();
             }
             st_release(&I.done[tile], (unsigned)(rel + 1));
         }

@@ -79,8 +79,9 @@ struct Carve {
 int check_problem(const fd_problem *p, int nsteps)
 {
     if (!p || nsteps < 0) return FD_ERR_INVALID_ARG;
-    if (p->ndim != 1 && p->ndim != 2) return FD_ERR_INVALID_ARG;
-    if (p->nx < 1 || p->ny < 1 || (p->ndim == 1 && p->ny != 1)) return FD_ERR_INVALID_ARG;
+    if (p->ndim < 1 || p->ndim > 3) return FD_ERR_INVALID_ARG;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->ndim == 1 && p->ny != 1) || (p->ndim < 3 && p->nz != 1))
+        return FD_ERR_INVALID_ARG;
     if (!(p->gamma > 0.0 && p->gamma < 2.0) || !(p->alpha > 0.0) || !(p->dt > 0.0) || !(p->dx > 0.0))
         return FD_ERR_INVALID_ARG;
     for (double r : p->react)
@@ -211,8 +212,14 @@ __global__ void static_tables_kernel(const Tabs t)
 
 }  // namespace
 
-extern "C" int fd_run_static(const fd_problem *p, const void *u0, int nsteps, void *u_out, void *cuda_stream)
+extern "C" int fd_run_static(const fd_problem *p_in, const void *u0, int nsteps, void *u_out, void *cuda_stream)
 {
+    fd_problem q;  // a zero nz (structs initialised before the field existed) means one plane
+    if (p_in) {
+        q = *p_in;
+        if (q.nz == 0) q.nz = 1;
+    }
+    const fd_problem *p = p_in ? &q : nullptr;
     int rc = check_problem(p, nsteps);
     if (rc) return rc;
     if (!u0 || !u_out) return FD_ERR_INVALID_ARG;
@@ -220,7 +227,7 @@ extern "C" int fd_run_static(const fd_problem *p, const void *u0, int nsteps, vo
     rc = scratch_address(&base);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int64_t N = (int64_t)p->nx * p->ny;
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
     const int sh = esize(p->hist_dtype), ss = esize(p->state_dtype), sa = esize(p->accum_dtype);
     const size_t ubytes = (size_t)N * ss;
     if (nsteps == 0) {
@@ -310,6 +317,7 @@ extern "C" int fd_run_static(const fd_problem *p, const void *u0, int nsteps, vo
     I.ny = p->ny;
     I.bc = p->bc;
     I.N = (int)N;
+    I.nz = p->nz;
     I.T = T;
     I.P = P;
     I.R = R;

@@ -41,6 +41,7 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
     s.ckpt_every, s.timeout_ms = ckpt_every, timeout_ms
     s.tile_threads, s.chunk_terms, s.stage_rows = tile_threads, chunk_terms, stage_rows
     s.stages, s.ctas_per_sm, s.head_lags = stages, ctas_per_sm, head_lags
+    s.nz = p.get("nz", 1)
     return s
 
 
@@ -68,7 +69,7 @@ class FRD:
         self.problem = p
         self.prob = make_problem(p, **kw)
         self.device = torch.device(device)
-        self.N = p["nx"] * p["ny"]
+        self.N = p["nx"] * p["ny"] * p.get("nz", 1)
         self.dtype = _TORCH[self.prob.state_dtype]
         self.ws_bytes = L.fd_workspace_bytes(self.prob)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
@@ -163,7 +164,7 @@ class FRDBatch:
 
     def state(self, i: int) -> torch.Tensor:
         p = self.problems[i]
-        out = torch.empty(p["nx"] * p["ny"], dtype=self.dtype, device=self.device)
+        out = torch.empty(p["nx"] * p["ny"] * p.get("nz", 1), dtype=self.dtype, device=self.device)
         L.fd_batch_get_state(self.b, i, out.data_ptr())
         return out
 

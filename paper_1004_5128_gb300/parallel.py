@@ -34,7 +34,7 @@ def schedule_terms(p: dict, samples: int = 64) -> float:
 
 def instance_cost(p: dict) -> float:
     """History elements streamed by one instance (rows read x points)."""
-    return schedule_terms(p) * p["nx"] * p["ny"]
+    return schedule_terms(p) * p["nx"] * p["ny"] * p.get("nz", 1)
 
 
 def shard(problems: list, world_size: int) -> list:

@@ -175,3 +175,35 @@ def test_superdiffusion(state, mode, Lw, a):
                       u0=synth.SplitMix64(17).uniform(40 * 33, 0, 1))
     got, _ = run_gpu(p, state=state)
     assert rel_inf(got, oracle.run(p)) < TOL[state]
+
+
+@pytest.mark.parametrize("state", ["f32", "f64"])
+@pytest.mark.parametrize("bc", [synth.BC_DIRICHLET0, synth.BC_NOFLUX])
+@pytest.mark.parametrize("mode,Lw,a", [(synth.MEM_FULL, 0, 0), (synth.MEM_SHORT, 30, 0),
+                                       (synth.MEM_ADAPTIVE, 0, 3)])
+def test_3d_ragged(state, bc, mode, Lw, a):
+    """3-D 20 x 17 x 13 (7-point stencil; tiles cut through z-planes), 200 steps."""
+    nx, ny, nz = 20, 17, 13
+    dt = synth.dt_for_courant(0.5 * synth.stability_bound(0.8, 3), 1.0, 1.0, 0.8)
+    p = synth.problem(3, nx, ny, 0.8, 1.0, dt, 1.0, bc, react=(0.02, -0.1, 0.1, -0.05),
+                      mem_mode=mode, mem_L=Lw, mem_a=a, K=200, nz=nz,
+                      u0=synth.SplitMix64(33).uniform(nx * ny * nz, 0, 1))
+    got, _ = run_gpu(p, state=state, chunk_terms=24)
+    assert rel_inf(got, oracle.run(p)) < TOL[state]
+
+
+def test_3d_64cube_eigenmodes():
+    """64^3 = 262144 points, 600 steps, no-flux, f = -0.05u: a sum of cosine modes evolves
+    through the oracle's scalar recursions (full memory)."""
+    n = 64
+    dt = synth.dt_for_courant(0.5 * synth.stability_bound(0.7, 3), 1.0, 1.0, 0.7)
+    p = synth.problem(3, n, n, 0.7, 1.0, dt, 1.0, synth.BC_NOFLUX, react=(0, -0.05, 0, 0), K=600,
+                      nz=n)
+    modes = [(0, 0, 0, 1.0), (1, 2, 3, 0.4), (9, 4, 17, 0.2), (40, 33, 60, 0.1)]
+    p["u0"] = sum(c * synth.eigenmode(p, qx, qy, qz) for qx, qy, qz, c in modes)
+    ref = np.zeros_like(p["u0"])
+    for qx, qy, qz, c in modes:
+        A = oracle.scalar_mode(p, laplacian_eigenvalue(p, qx, qy, qz))
+        ref += c * A[-1] * synth.eigenmode(p, qx, qy, qz)
+    got, _ = run_gpu(p)
+    assert rel_inf(got, ref) < 1e-5
