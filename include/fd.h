@@ -95,6 +95,12 @@ typedef struct fd_problem {
     int head_lags;       /* lags 1..head_lags are summed by the per-tile update from rows kept in
                             state precision (0 = 8 for F32/F64 history, 32 for BF16/F16) */
     int nz;              /* points along the third axis when ndim == 3, else 1 */
+    int time_block;      /* 0, or 4 / 8 / 16: temporally blocked sum (F32 state, history and
+                            accumulation, full or short memory, no Kahan, no tape).  Rows older
+                            than the current block of time_block steps are read once per block
+                            into time_block accumulators (the Toeplitz structure of eq.
+                            frac_norxn); the newest rows are summed per step.  Same terms,
+                            grouped differently; history traffic drops by about time_block. */
 } fd_problem;
 
 typedef struct fd_handle fd_handle;

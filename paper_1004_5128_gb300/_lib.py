@@ -63,7 +63,7 @@ class FdProblem(ctypes.Structure):
         ("timeout_ms", ctypes.c_int),
         ("tile_threads", ctypes.c_int), ("chunk_terms", ctypes.c_int), ("stage_rows", ctypes.c_int),
         ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("head_lags", ctypes.c_int),
-        ("nz", ctypes.c_int),
+        ("nz", ctypes.c_int), ("time_block", ctypes.c_int),
     ]
 
 

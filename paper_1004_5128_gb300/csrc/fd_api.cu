@@ -175,6 +175,12 @@ int validate(const fd_problem *p)
     if (adj && (p->mem_mode != FD_MEM_FULL ||
                 !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)))
         return FD_ERR_UNSUPPORTED;
+    if (p->time_block) {
+        if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16) return FD_ERR_INVALID_ARG;
+        if (p->state_dtype != FD_F32 || p->hist_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan || adj ||
+            (p->mem_mode != FD_MEM_FULL && p->mem_mode != FD_MEM_SHORT))
+            return FD_ERR_UNSUPPORTED;
+    }
     if (!(p->flags & FD_FLAG_ALLOW_UNSTABLE)) {
         // von Neumann bound of the full-memory scheme (checkerboard mode):
         // S * 4 ndim * sum_m psi_m (-1)^m = 2 with sum_m psi_m (-1)^m = 2^{1-g}
@@ -189,6 +195,8 @@ int validate(const fd_problem *p)
 struct Geo {
     int threads, V, P, T, R, RS, NS, ctas, grid, maxC;
     int head;        // lags summed by the fixup
+    int tb;          // temporal block (0: per-step kernel)
+    int nblocks;     // blocks of tb steps covering max_steps
     int hring_sep;   // separate state-precision head ring
     int hring_cap;
     int64_t hring_pitch;
@@ -211,6 +219,16 @@ int device_sms()
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     return sms;
+}
+
+// Far rows [rlo, rhi) of block b of the blocked kernel: rows older than the previous block,
+// limited to the short window.
+inline void block_rows(const fd_problem &p, int tb, int64_t b, int64_t &rlo, int64_t &rhi)
+{
+    const int64_t kb = b * tb;
+    rhi = std::max<int64_t>(0, kb - tb);
+    rlo = (p.mem_mode == FD_MEM_SHORT) ? std::max<int64_t>(0, kb - p.mem_L) : 0;
+    rlo = std::min(rlo, rhi);
 }
 
 void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
@@ -254,11 +272,28 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         g.R = (int)r;
     }
     g.maxC = (int)std::max<int64_t>(1, (nmax + g.R - 1) / g.R);
+    g.tb = p.time_block;
+    g.nblocks = g.tb ? (p.max_steps + g.tb - 1) / g.tb : 0;
+    if (g.tb) {
+        int64_t rmax = 0;
+        for (int64_t b = 0; b < g.nblocks; ++b) {
+            int64_t lo, hi;
+            block_rows(p, g.tb, b, lo, hi);
+            rmax = std::max(rmax, hi - lo);
+        }
+        if (!p.chunk_terms) {
+            int64_t r = (rmax * g.T + 4LL * g.grid - 1) / (4LL * g.grid);
+            r = std::min<int64_t>(std::max<int64_t>(r, 2 * g.RS), 512);
+            g.R = (int)((r + g.RS - 1) / g.RS * g.RS);
+        }
+        g.maxC = (int)std::max<int64_t>(1, (rmax + g.R - 1) / g.R);
+    }
     g.pitch = (int64_t)align_up((size_t)N * g.sh, kAlign);
     g.hring_cap = g.hring_sep ? g.head + 1 : g.cap;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = smem_bytes(g, g.R);
+    g.smem = g.tb ? (size_t)g.NS * g.RS * g.threads * 16 + (size_t)(g.R + g.tb) * 4 + 32 + 8 * (size_t)g.NS
+                  : smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -266,6 +301,14 @@ inline int64_t step_units(const Geo &g, const int4 &e)
 {
     const int64_t n = n_terms(e) - std::min<int64_t>(g.head, e.x);
     return (int64_t)g.T * std::max<int64_t>(1, (n + g.R - 1) / g.R);
+}
+
+// Units of block b of the blocked kernel: far chunks per tile plus one update unit per step.
+inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
+{
+    int64_t lo, hi;
+    block_rows(p, g.tb, b, lo, hi);
+    return (int64_t)g.T * (std::max<int64_t>(1, (hi - lo + g.R - 1) / g.R) + g.tb);
 }
 
 // Device-side layout of one instance inside the workspace.
@@ -303,11 +346,11 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     L.hist = c.take((size_t)g.cap * g.pitch);
     L.hring = g.hring_sep ? c.take((size_t)g.hring_cap * g.hring_pitch) : L.hist;
     L.hscale = (p.hist_dtype == FD_F16) ? (float *)c.take((size_t)g.cap * g.T * sizeof(float)) : nullptr;
-    L.part = c.take((size_t)kNpar * g.maxC * g.planes * g.part_pitch);
+    L.part = c.take((size_t)kNpar * g.maxC * g.planes * std::max(1, g.tb) * g.part_pitch);
     L.arrive = external_counters ? counters
                                  : (unsigned *)c.take(sizeof(unsigned) * (kNpar + 1) * (size_t)g.T);
     L.done = L.arrive ? L.arrive + kNpar * g.T : nullptr;
-    L.psi = c.take((size_t)(p.max_steps + 1) * g.sa);
+    L.psi = c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa);  // blocked: window reads to kb+tb-1
     L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1) * g.sa) : nullptr;
     L.sched = (int4 *)c.take(sizeof(int4) * (size_t)p.max_steps);
     const size_t ng = std::max<size_t>(1, s.G.size());
@@ -364,7 +407,7 @@ template <class TA> void to_acc(const std::vector<double> &x, std::vector<unsign
 
 void build_tables(const fd_problem &p, const Sched &s, const Geo &g, Tables &t)
 {
-    const int64_t n = (int64_t)p.max_steps + 1;
+    const int64_t n = (int64_t)p.max_steps + 1 + g.tb;
     t.psi.resize(n);
     t.dpsi.resize(n);
     gl_weights(p.gamma, n, t.psi.data(), t.dpsi.data());
@@ -420,6 +463,9 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.hist_write = 1;
     I.cap = adj ? p.max_steps : g.cap;
     I.maxC = g.maxC;
+    I.tb = g.tb;
+    I.mem_mode = p.mem_mode;
+    I.mem_L = p.mem_L;
     I.npar = kNpar;
     I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
     I.tape_every = 1;
@@ -527,7 +573,8 @@ struct fd_handle {
     int bad;                 // state invalid after a failed launch
 };
 
-static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin, int g_end, int k0)
+static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin, int g_end, int k0,
+                  int k_end = 0)
 {
     Launch L;
     std::memset(&L, 0, sizeof(L));
@@ -537,6 +584,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.g_begin = g_begin;
     L.g_end = g_end;
     L.k0 = k0;
+    L.k_end = k_end;
     L.stage_rows = h->g.RS;
     L.stages = h->g.NS;
     L.rmax = h->g.R;
@@ -662,7 +710,8 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     h->ctrl_zero_base = (char *)h->L.arrive;
     h->ctrl_zero_bytes = sizeof(unsigned) * (kNpar + 1) * (size_t)h->g.T;
     const bool kahan = p->flags & FD_FLAG_KAHAN;
-    h->kfwd = fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
+    h->kfwd = p->time_block ? fdk::kernel_tb(p->time_block)
+                            : fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
     h->kadj = (p->flags & FD_FLAG_KEEP_TAPE)
                   ? fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)
                   : nullptr;
@@ -674,16 +723,18 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
         return rc;
     }
     // group table: group k = step k of instance 0
-    h->goff.resize((size_t)p->max_steps + 1);
-    std::vector<int2> info((size_t)p->max_steps + 1);
+    // groups: step k (per-step kernel) or block b of time_block steps (blocked kernel)
+    const int ngroups = h->g.tb ? h->g.nblocks : p->max_steps;
+    h->goff.resize((size_t)ngroups + 1);
+    std::vector<int2> info((size_t)ngroups + 1);
     long long acc = 0;
-    for (int k = 0; k < p->max_steps; ++k) {
+    for (int k = 0; k < ngroups; ++k) {
         h->goff[k] = acc;
         info[k] = make_int2(0, k);
-        acc += step_units(h->g, h->s.step[k]);
+        acc += h->g.tb ? block_units(*p, h->g, k) : step_units(h->g, h->s.step[k]);
     }
-    h->goff[p->max_steps] = acc;
-    info[p->max_steps] = make_int2(0, p->max_steps);
+    h->goff[ngroups] = acc;
+    info[ngroups] = make_int2(0, ngroups);
     build_tables(*p, h->s, h->g, h->t);
     h->inst_fwd = make_inst(*p, h->g, h->L, false);
     h->inst_adj = (p->flags & FD_FLAG_KEEP_TAPE) ? make_inst(*p, h->g, h->L, true) : h->inst_fwd;
@@ -733,7 +784,14 @@ int fd_step(fd_handle *h, int nsteps)
     if (h->bad) return FD_ERR_STATE;
     if (h->k + nsteps > h->p.max_steps) return FD_ERR_STATE;
     if (nsteps == 0) return FD_OK;
-    const int rc = launch(h, h->kfwd, h->d_inst, (int)h->k, (int)(h->k + nsteps), (int)h->k);
+    int rc;
+    if (h->g.tb) {  // the blocks that intersect [k, k + nsteps)
+        const int tb = h->g.tb;
+        rc = launch(h, h->kfwd, h->d_inst, (int)(h->k / tb), (int)((h->k + nsteps + tb - 1) / tb), (int)h->k,
+                    (int)(h->k + nsteps));
+    } else {
+        rc = launch(h, h->kfwd, h->d_inst, (int)h->k, (int)(h->k + nsteps), (int)h->k, (int)(h->k + nsteps));
+    }
     if (rc) return rc;
     h->k += nsteps;
     return FD_OK;
@@ -927,7 +985,7 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
             probs[i].accum_dtype != probs[0].accum_dtype ||
             ((probs[i].flags ^ probs[0].flags) & (FD_FLAG_KAHAN | FD_FLAG_KEEP_TAPE)))
             return FD_ERR_INVALID_ARG;
-        if (probs[i].flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
+        if ((probs[i].flags & FD_FLAG_KEEP_TAPE) || probs[i].time_block) return FD_ERR_UNSUPPORTED;
     }
     b.p.assign(probs, probs + count);
     b.s.resize(count);

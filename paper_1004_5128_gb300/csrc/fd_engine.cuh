@@ -56,6 +56,8 @@ struct Inst {
     int head;                // lags 1..head are summed by the fixup from the head rows
     int hring_cap;           // rows in the head ring (== cap when it is the history itself)
     int hring_sep;           // 1: separate state-precision ring (low-precision history)
+    int tb;                  // temporal block (steps per block) of the blocked kernel, else 0
+    int mem_mode, mem_L;     // memory mode and short window (blocked kernel)
     int tape_k0, tape_every, tape_rows;
     int adj_K, uadj_r0;      // adjoint: u^r is row (adj_K-1-k) - uadj_r0 of uadj
     double S, dt;
@@ -87,6 +89,7 @@ struct Launch {
     const int2 *g_info;      // (instance, step) of each group
     int g_begin, g_end;
     int k0;                  // first step of the launch: tile step counters count from it
+    int k_end;               // one past the last step of the launch (blocked kernel)
     int stage_rows, stages;
     int rmax;                // largest chunk (terms) over the launch's instances
     unsigned long long *queue;

@@ -1,0 +1,340 @@
+// fd_engine_tb.cuh -- temporally blocked variant of the engine (FP32, full and short memory).
+//
+// The full-memory sum is a Toeplitz product: row delta^r enters step k with weight
+// psi_{k-r} (eq. frac_norxn), so the steps k = kb .. kb+T-1 of one block all use the same old
+// rows.  For block b (kb = bT) this kernel splits each step's sum into
+//   far:  rows r <= kb-T-1, read ONCE per block and multiplied into T accumulators with the
+//         sliding coefficient window psi_{kb-r} .. psi_{kb+T-1-r};
+//   head: lags 1 .. min(k-kb+T, n_base(k)), the at most 2T-1 newest rows, summed step by step
+//         in the per-tile update (these rows are written during the block itself).
+// Far rows of block b are complete once block b-2 has been updated, so the far streaming of
+// block b+1 overlaps the T sequential updates of block b.  History traffic drops by about T
+// while the multiply-adds stay the same: the sum is the paper's, only grouped differently.
+// Short memory (eq. frac_shortmemory) is the same product with psi_m set to 0 for m > L.
+//
+// Work units of block b, in claim order: first T_tiles x C far units (tile, chunk of R far
+// rows), each writing T partial rows and counting itself in the tile's arrival counter; then
+// T x T_tiles update units, step-major (step kb+t, tile), each waiting for its tile's far
+// count and for its halo tiles' previous step.  Every wait therefore targets units with
+// smaller numbers, so the persistent grid cannot deadlock whatever the residency (an update
+// never waits on work that sits behind it in the queue).  Determinism, bounded waits, status
+// words and the memory-ordering protocol are those of engine_kernel.
+#pragma once
+
+#include "fd_engine.cuh"
+
+namespace fdk {
+
+struct UnitTB {
+    int valid, inst, b, tile, chunk, C, r0, r1;
+    int fix;  // 0: far unit; 1: update unit of step k
+    int k;
+};
+
+template <int TB>
+__global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
+{
+    constexpr int V = 4;  // FP32: one float4 column per thread
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    const int RS = L.stage_rows, NS = L.stages;
+    const int row_bytes = nthr * 16;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *stages = smem;
+    float *psw = reinterpret_cast<float *>(smem + (size_t)NS * RS * row_bytes);  // coefficient window
+    uint64_t *bars = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(psw + L.rmax + TB) + 15) & ~uintptr_t(15));
+
+    __shared__ Inst I;
+    __shared__ UnitTB U;
+    __shared__ int s_cur_inst, s_ok, s_pipe;
+
+    if (tid == 0) {
+        for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        s_cur_inst = -1;
+    }
+    __syncthreads();
+
+    uint32_t n_issued = 0, n_used = 0;
+    int ghint = L.g_begin;
+    const long long u_base = L.g_off[L.g_begin];
+    const long long u_end = L.g_off[L.g_end];
+    unsigned long long next = 0;
+    if (tid == 0) next = atomicAdd(L.queue, 1ull);
+
+    for (;;) {
+        // ---------------------------------------------------------------- claim
+        if (tid == 0) {
+            const long long u = u_base + (long long)next;
+            int ok = (u < u_end) && (ld_volatile(L.err) == ERR_NONE);
+            if (ok) {
+                next = atomicAdd(L.queue, 1ull);
+                const int g = find_group(L.g_off, ghint, L.g_end, u);
+                ghint = g;
+                const int2 gi = L.g_info[g];
+                if (gi.x != s_cur_inst) {
+                    I = L.inst[gi.x];
+                    s_cur_inst = gi.x;
+                }
+                const long long local = u - L.g_off[g];
+                const int C = (int)((L.g_off[g + 1] - L.g_off[g]) / I.T) - TB;  // far chunks per tile
+                const int kb = gi.y * TB;
+                const int rhi = max(0, kb - TB);
+                const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
+                U.inst = gi.x;
+                U.b = gi.y;
+                U.C = C;
+                if (local < (long long)C * I.T) {  // far unit
+                    U.fix = 0;
+                    U.tile = (int)(local % I.T);
+                    U.chunk = (int)(local / I.T);
+                    U.r0 = min(rhi, rlo + U.chunk * I.R);
+                    U.r1 = min(rhi, U.r0 + I.R);
+                    // far rows up to r1-1 written; partial rows of block b-npar consumed
+                    int need = (U.r1 > U.r0) ? U.r1 - L.k0 : 0;
+                    need = max(need, kb - (I.npar - 1) * TB - L.k0);
+                    if (need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
+                } else {  // update unit
+                    const int idx = (int)(local - (long long)C * I.T);
+                    U.fix = 1;
+                    U.tile = idx % I.T;
+                    U.k = kb + idx / I.T;
+                    U.chunk = 0;
+                    U.r0 = U.r1 = 0;
+                }
+            }
+            U.valid = ok;
+        }
+        __syncthreads();
+        if (!U.valid) break;
+
+        const int tile = U.tile, C = U.C, b = U.b, kb = b * TB;
+        const int par = b % I.npar;
+        const int j0 = tile * I.P + tid * V;
+        auto prow = [&](int c, int t) -> float * {
+            return reinterpret_cast<float *>(I.part + ((size_t)((par * I.maxC + c) * TB + t)) * I.part_pitch);
+        };
+
+        if (!U.fix) {
+            // ================================================================ far unit
+            const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;
+            const int nst = (nrow + RS - 1) / RS;
+            long long tile_bytes = (long long)min(I.P, I.N - tile * I.P) * 4ll;
+            tile_bytes = (tile_bytes + 15) & ~15ll;
+
+            // coefficient window: row r, step kb+t uses psw[(r1-1-r) + t] = psi_{kb+t-r}
+            {
+                const float *psi = reinterpret_cast<const float *>(I.psi);
+                const int lag0 = kb - (r1 - 1);
+                for (int i = tid; i < nrow + TB - 1; i += nthr) {
+                    const int lag = lag0 + i;
+                    psw[i] = (I.mem_mode == 1 && lag > I.mem_L) ? 0.f : psi[lag];
+                }
+            }
+            __syncthreads();
+
+            float acc[TB][V];
+#pragma unroll
+            for (int t = 0; t < TB; ++t)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[t][v] = 0.f;
+
+            auto issue = [&](int s) {
+                const int bb = (int)(n_issued % (uint32_t)NS);
+                const int a0 = s * RS, a1 = min(nrow, a0 + RS);
+                mbar_expect_tx(&bars[bb], (uint32_t)(tile_bytes * (a1 - a0)));
+                const char *col = I.hist + (size_t)tile * I.P * 4;
+                for (int a = a0; a < a1; ++a)
+                    bulk_g2s(stages + ((size_t)bb * RS + (a - a0)) * row_bytes,
+                             col + (size_t)((r0 + a) % I.cap) * I.pitch, (uint32_t)tile_bytes, &bars[bb]);
+            };
+            if (tid == 0) {
+                fence_proxy_async_global();
+                const int pre = min(NS, nst);
+                for (int s = 0; s < pre; ++s) {
+                    issue(s);
+                    ++n_issued;
+                }
+            } else {
+                n_issued += (uint32_t)min(NS, nst);
+            }
+            for (int s = 0; s < nst; ++s) {
+                const int bb = (int)(n_used % (uint32_t)NS);
+                const uint32_t ph = (n_used / (uint32_t)NS) & 1u;
+                if (!mbar_try_wait(&bars[bb], ph)) {
+                    const long long t0 = globaltimer();
+                    while (!mbar_try_wait(&bars[bb], ph)) {
+                        if (globaltimer() - t0 > L.timeout_ns) {
+                            atomicCAS(L.err, ERR_NONE, ERR_PIPE);
+                            break;
+                        }
+                    }
+                }
+                const int rows = min(RS, nrow - s * RS);
+                const unsigned char *base = stages + (size_t)bb * RS * row_bytes + (size_t)tid * 16;
+                for (int r = 0; r < rows; ++r) {
+                    const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)r * row_bytes);
+                    const float x[4] = {x4.x, x4.y, x4.z, x4.w};
+                    const float *cw = psw + (r1 - 1 - (r0 + s * RS + r));
+#pragma unroll
+                    for (int t = 0; t < TB; ++t) {
+                        const float c = cw[t];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[t][v] = fmaf(c, x[v], acc[t][v]);
+                    }
+                }
+                ++n_used;
+                __syncthreads();
+                if (s + NS < nst) {
+                    if (tid == 0) issue(s + NS);
+                    ++n_issued;
+                }
+            }
+            if (tid == 0) s_pipe = (ld_volatile(L.err) == ERR_PIPE);
+            __syncthreads();
+            if (s_pipe) {
+                if (tid == 0) {
+                    const long long t0 = globaltimer();
+                    while (n_used < n_issued && globaltimer() - t0 < L.timeout_ns) {
+                        const int bb = (int)(n_used % (uint32_t)NS);
+                        if (mbar_try_wait(&bars[bb], (n_used / (uint32_t)NS) & 1u)) ++n_used;
+                    }
+                }
+                break;
+            }
+            if (j0 < I.N) {
+#pragma unroll
+                for (int t = 0; t < TB; ++t)
+                    *reinterpret_cast<float4 *>(prow(U.chunk, t) + j0) =
+                        make_float4(acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+            }
+            // CTA barrier, then one release add: cumulative over every thread's partial stores
+            __syncthreads();
+            if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
+            continue;
+        }
+
+        // ================================================== update unit: step k, this tile
+        const int k = U.k, t = k - kb;
+        if (k < L.k0 || k >= L.k_end) continue;  // block edge outside this launch
+        const int rel = k - L.k0;
+        const bool last_of_block = (k == min(kb + TB, L.k_end) - 1);
+        if (tid == 0) {
+            int ok = wait_counter(&I.arrive[par * I.T + tile], (unsigned)C, L) ? 1 : 0;
+            const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
+            const int lo = max(0, tile * I.P - h) / I.P;
+            const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
+            for (int tt = lo; tt <= hi && ok; ++tt)
+                if (rel > 0 && !wait_counter(&I.done[tt], (unsigned)rel, L)) ok = 0;
+            if (ok && I.stall && rel == 0 && tile == 0)
+                if (!wait_counter(&I.done[tile], 0x80000000u, L)) ok = 0;
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+
+        const float S = (float)I.S, dt = (float)I.dt;
+        const float q0 = (float)I.react[0], q1 = (float)I.react[1], q2 = (float)I.react[2],
+                    q3 = (float)I.react[3];
+        const float *psi = reinterpret_cast<const float *>(I.psi);
+        const bool mirror = (I.bc == 1);
+        float H[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) H[v] = 0.f;
+        if (j0 < I.N) {
+            // far part: chunk partials in fixed order
+            for (int c = 0; c < C; ++c) {
+                const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t) + j0));
+                H[0] += w.x;
+                H[1] += w.y;
+                H[2] += w.z;
+                H[3] += w.w;
+            }
+            // head: lags 1 .. min(k-kb+T, n_base(k)), descending lag
+            const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
+            const int hk = min(t + TB, nb);
+            for (int m = hk; m >= 1; --m) {
+                float x[V];
+                load_vec<float, V>(reinterpret_cast<const float *>(I.hist + (size_t)((k - m) % I.cap) * I.pitch) + j0,
+                                   x);
+                const float c = psi[m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) H[v] = fmaf(c, x[v], H[v]);
+            }
+        }
+        const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
+        float *un = reinterpret_cast<float *>(I.ubuf[(k + 1) & 1]);
+        const float *lo_k = I.ulo[0] ? reinterpret_cast<const float *>(I.ulo[k & 1]) : nullptr;
+        float *lo_n = I.ulo[0] ? reinterpret_cast<float *>(I.ulo[(k + 1) & 1]) : nullptr;
+        const bool tape_row = I.tape && (k + 1 - I.tape_k0) >= 0 && ((k + 1 - I.tape_k0) % I.tape_every) == 0 &&
+                              ((k + 1 - I.tape_k0) / I.tape_every) < I.tape_rows;
+        float *tp = tape_row ? reinterpret_cast<float *>(I.tape) + (size_t)((k + 1 - I.tape_k0) / I.tape_every) * I.N
+                             : nullptr;
+        float d[V];
+        bool bad = false;
+        if (j0 < I.N) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int j = j0 + v;
+                d[v] = 0.f;
+                if (j >= I.N) continue;
+                const float c = __ldcg(uk + j);
+                const float gh = mirror ? c : 0.f;
+                if (I.ndim == 1) {
+                    const float r = (j + 1 < I.N) ? __ldcg(uk + j + 1) : gh;
+                    const float l = (j > 0) ? __ldcg(uk + j - 1) : gh;
+                    d[v] = r - 2.f * c + l;
+                } else if (I.ndim == 2) {
+                    const int x = j % I.nx, y = j / I.nx;
+                    const float r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : gh;
+                    const float l = (x > 0) ? __ldcg(uk + j - 1) : gh;
+                    const float up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : gh;
+                    const float dn = (y > 0) ? __ldcg(uk + j - I.nx) : gh;
+                    d[v] = r + l - 4.f * c + up + dn;
+                } else {
+                    const int pl = I.nx * I.ny;
+                    const int x = j % I.nx, y = (j / I.nx) % I.ny, z = j / pl;
+                    const float r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : gh;
+                    const float l = (x > 0) ? __ldcg(uk + j - 1) : gh;
+                    const float up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : gh;
+                    const float dn = (y > 0) ? __ldcg(uk + j - I.nx) : gh;
+                    const float fw = (z + 1 < I.nz) ? __ldcg(uk + j + pl) : gh;
+                    const float bk = (z > 0) ? __ldcg(uk + j - pl) : gh;
+                    d[v] = r + l - 6.f * c + up + dn + fw + bk;
+                }
+                const float f = q0 + c * (q1 + c * (q2 + c * q3));
+                const float inc = dt * f + S * (d[v] + H[v]);
+                float nv;
+                if (lo_k) {
+                    const float y2 = inc + __ldcg(lo_k + j);
+                    const float sum = c + y2;
+                    const float bb = sum - c;
+                    lo_n[j] = (c - (sum - bb)) + (y2 - bb);
+                    nv = sum;
+                } else {
+                    nv = c + inc;
+                }
+                bad |= !isfinite(nv);
+                un[j] = nv;
+                if (tp) tp[j] = nv;
+            }
+            if (I.hist_write)
+                *reinterpret_cast<float4 *>(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * 4) =
+                    make_float4(d[0], d[1], d[2], d[3]);
+        }
+        if (bad) atomicOr(L.nonfinite, 1u);
+        fence_proxy_async_global();
+        __syncthreads();
+        if (tid == 0) {
+            // the block's last update for this tile resets the far count for block b+npar,
+            // whose far units wait for this step before they count
+            if (last_of_block) I.arrive[par * I.T + tile] = 0u;
+            st_release(&I.done[tile], (unsigned)(rel + 1));
+        }
+    }
+}
+
+}  // namespace fdk

@@ -1,6 +1,6 @@
 // fd_kernels.h -- registry of the engine's template instantiations (internal).
 #pragma once
-#include "fd_engine.cuh"
+#include "fd_engine_tb.cuh"
 
 namespace fdk {
 // Kernel for (state, history, accumulator) dtypes (FD_F64/FD_F32/FD_BF16/FD_F16 codes),
@@ -9,4 +9,6 @@ const void *kernel_for(int state, int hist, int acc, bool kahan, bool adj);
 const void *kernel_f64(bool kahan, bool adj);
 const void *kernel_f32(bool kahan, bool adj);
 const void *kernel_lowp(int hist, bool kahan, bool adj);
+// Temporally blocked FP32 kernel for a block of tb steps (4, 8 or 16), else nullptr.
+const void *kernel_tb(int tb);
 }  // namespace fdk

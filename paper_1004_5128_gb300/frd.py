@@ -20,7 +20,7 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
                  allow_unstable: bool = False, ckpt_every: int = 0, timeout_ms: int = 0,
                  inject_stall: bool = False, tile_threads: int = 0, chunk_terms: int = 0,
                  stage_rows: int = 0, stages: int = 0, ctas_per_sm: int = 0,
-                 head_lags: int = 0, plain_state: bool = False) -> L.FdProblem:
+                 head_lags: int = 0, plain_state: bool = False, time_block: int = 0) -> L.FdProblem:
     """fd_problem for a synth-style problem dict."""
     s = L.FdProblem()
     s.ndim, s.nx, s.ny = p["ndim"], p["nx"], p["ny"]
@@ -42,6 +42,7 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
     s.tile_threads, s.chunk_terms, s.stage_rows = tile_threads, chunk_terms, stage_rows
     s.stages, s.ctas_per_sm, s.head_lags = stages, ctas_per_sm, head_lags
     s.nz = p.get("nz", 1)
+    s.time_block = time_block
     return s
 
 
@@ -51,7 +52,8 @@ def _require_cuda():
     L.lib()
 
 
-GEOMETRY_KEYS = ("tile_threads", "chunk_terms", "stage_rows", "stages", "ctas_per_sm", "head_lags")
+GEOMETRY_KEYS = ("tile_threads", "chunk_terms", "stage_rows", "stages", "ctas_per_sm", "head_lags",
+                 "time_block")
 
 
 class FRD:

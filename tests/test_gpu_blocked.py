@@ -1,0 +1,68 @@
+"""Temporally blocked engine (time_block = 4 / 8 / 16; FP32, full and short memory) against the
+FP64 oracle and against properties that hold at full size."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_5128_gb300 import FRD, synth
+from tests.helpers import laplacian_eigenvalue, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+def ragged(bc, mode, L=0, K=300):
+    return synth.problem(2, 45, 37, 0.75, 0.7, synth.dt_for_courant(0.15, 0.7, 1.0, 0.75), 1.0, bc,
+                         react=(0.01, -0.2, 0.3, -0.4), mem_mode=mode, mem_L=L, K=K,
+                         u0=synth.SplitMix64(21).uniform(45 * 37, 0, 1))
+
+
+@pytest.mark.parametrize("tb", [4, 8, 16])
+@pytest.mark.parametrize("bc", [synth.BC_DIRICHLET0, synth.BC_NOFLUX])
+@pytest.mark.parametrize("mode,L", [(synth.MEM_FULL, 0), (synth.MEM_SHORT, 50), (synth.MEM_SHORT, 7)])
+def test_blocked_matches_oracle(tb, bc, mode, L):
+    """Several far chunks per block (chunk 16 rows), short windows longer and shorter than 2T."""
+    p = ragged(bc, mode, L)
+    s = FRD(p, time_block=tb, chunk_terms=16)
+    s.set_state(p["u0"])
+    assert rel_inf(s.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5
+
+
+def test_blocked_1d_many_tiles():
+    p = synth.problem(1, 3001, 1, 0.55, 1.0, synth.dt_for_courant(0.2, 1.0, 1.0, 0.55), 1.0,
+                      synth.BC_DIRICHLET0, react=(0, -0.05, 0, 0), K=400,
+                      u0=synth.SplitMix64(8).uniform(3001, -1, 1))
+    s = FRD(p, time_block=8, tile_threads=64, chunk_terms=24)
+    s.set_state(p["u0"])
+    assert rel_inf(s.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5
+
+
+def test_blocked_launch_split_is_bitwise_invariant():
+    """Blocks are aligned to absolute steps, so any split into launches gives the same bits."""
+    p = ragged(synth.BC_NOFLUX, synth.MEM_FULL, K=400)
+    a = FRD(p, time_block=8, chunk_terms=32)
+    a.set_state(p["u0"])
+    one = a.run(400).cpu().numpy()
+    b = FRD(p, time_block=8, chunk_terms=32)
+    b.set_state(p["u0"])
+    for n in (57, 3, 100, 1, 139, 100):
+        b.step(n)
+    assert np.array_equal(one, b.run(0).cpu().numpy())
+
+
+@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_SHORT])
+def test_blocked_config2_full_size(mode):
+    """256^2, 5000 steps: eigenmode superposition against the oracle's scalar recursions, and
+    the Gaussian input's mass balance."""
+    p = synth.config2(mode)
+    modes = [(0, 0, 1.0), (1, 0, 0.5), (3, 2, 0.25), (17, 5, 0.125), (64, 64, 0.0625), (200, 31, 0.03)]
+    q = dict(p)
+    q["u0"] = sum(c * synth.eigenmode(p, qx, qy) for qx, qy, c in modes)
+    ref = sum(c * oracle.scalar_mode(p, laplacian_eigenvalue(p, qx, qy))[-1] * synth.eigenmode(p, qx, qy)
+              for qx, qy, c in modes)
+    s = FRD(q, time_block=8)
+    s.set_state(q["u0"])
+    assert rel_inf(s.run(q["K"]).cpu().double().numpy(), ref) < 1e-5
+    s = FRD(p, time_block=8)
+    s.set_state(p["u0"])
+    M0 = p["u0"].sum()
+    assert abs(s.run(p["K"]).cpu().double().numpy().sum() - M0 * (1 - 0.1 * p["dt"]) ** p["K"]) / M0 < 2e-5

@@ -115,3 +115,18 @@ def test_batch_workspace():
 def test_strerror():
     assert "stability" in L.fd_strerror(L.FD_ERR_UNSTABLE)
     assert L.fd_strerror(0) == "ok"
+
+
+def test_time_block_validation():
+    p = synth.config2(K=100)
+    assert L.fd_workspace_bytes(make_problem(p, time_block=8)) > 0
+    for bad, code in ((dict(time_block=5), L.FD_ERR_INVALID_ARG),
+                      (dict(time_block=8, hist="bf16"), L.FD_ERR_UNSUPPORTED),
+                      (dict(time_block=8, kahan=True), L.FD_ERR_UNSUPPORTED),
+                      (dict(time_block=8, keep_tape=True), L.FD_ERR_UNSUPPORTED)):
+        with pytest.raises(L.FdError) as e:
+            L.fd_workspace_bytes(make_problem(p, **bad))
+        assert e.value.code == code
+    with pytest.raises(L.FdError) as e:
+        L.fd_workspace_bytes(make_problem(synth.with_mode(p, synth.MEM_ADAPTIVE, a=10), time_block=8))
+    assert e.value.code == L.FD_ERR_UNSUPPORTED
