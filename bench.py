@@ -125,11 +125,14 @@ def problems(name: str, K: int = 0, modes: str = ""):
 
 
 def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
-    """History rows read (lags >= 1) plus, per step, the u read/write and the delta write."""
+    """History rows the launch's kernel must read plus, per step, the u read/write and the delta
+    write.  Per-step kernel: every lag >= 1 of every step.  Temporally blocked kernel: the far rows
+    once per block plus each step's newest rows."""
     N = p["nx"] * p["ny"] * p.get("nz", 1)
     sh = HBYTES[kw.get("hist", kw.get("state", "f32"))]
     ss = 8 if kw.get("state") == "f64" else 4
-    return geo["hist_rows_total"] * N * sh + p["K"] * N * (2 * ss + sh)
+    rows = geo.get("stream_rows_total", geo["hist_rows_total"])
+    return rows * N * sh + p["K"] * N * (2 * ss + sh)
 
 
 def _sample_terms(p, K):
@@ -338,9 +341,9 @@ def run_ours(args):
         g = r.geo
         modes[r.name] = dict(ms=per, terms=r.terms, terms_per_s=r.terms / (per / 1e3),
                              alg_bytes=r.alg, gbs=r.alg / (per / 1e3) / 1e9,
-                             geometry={k: g[k] for k in ("tile_threads", "tiles", "chunk_terms",
-                                                         "stage_rows", "stages", "ctas_per_sm",
-                                                         "grid", "head_lags")})
+                             geometry={k: g.get(k) for k in ("tile_threads", "tiles", "chunk_terms",
+                                                             "stage_rows", "stages", "ctas_per_sm",
+                                                             "grid", "head_lags", "time_block")})
     extra = {}
     if args.workload == "c5":
         r = runs[0]

@@ -169,6 +169,10 @@ typedef struct fd_geometry {
     int64_t units_total;     /* work units for max_steps steps */
     int64_t hist_rows_total; /* sum_k n(k): history rows read over max_steps steps (lags >= 1) */
     int64_t terms_total;     /* sum_k N (n(k) + 1): GL terms over max_steps steps, lag 0 included */
+    int64_t stream_rows_total; /* history rows the chosen kernel reads over max_steps steps: equal
+                                  to hist_rows_total per step; with time_block, far rows once per
+                                  block plus every step's newest (head) rows */
+    int time_block;
 } fd_geometry;
 int fd_get_geometry(fd_handle *h, fd_geometry *g);
 

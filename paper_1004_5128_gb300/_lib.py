@@ -72,7 +72,8 @@ class FdGeometry(ctypes.Structure):
                                             "stage_rows", "stages", "ctas_per_sm", "grid",
                                             "head_lags")] + [
         ("units_total", ctypes.c_int64), ("hist_rows_total", ctypes.c_int64),
-        ("terms_total", ctypes.c_int64)]
+        ("terms_total", ctypes.c_int64), ("stream_rows_total", ctypes.c_int64),
+        ("time_block", ctypes.c_int)]
 
 
 _lib = None

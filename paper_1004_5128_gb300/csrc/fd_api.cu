@@ -303,12 +303,17 @@ inline int64_t step_units(const Geo &g, const int4 &e)
     return (int64_t)g.T * std::max<int64_t>(1, (n + g.R - 1) / g.R);
 }
 
-// Units of block b of the blocked kernel: far chunks per tile plus one update unit per step.
+// Units of group b of the blocked kernel: the far chunks of block b (none past the last block)
+// plus the update units (one per step and tile) of block b-1.
 inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
 {
-    int64_t lo, hi;
-    block_rows(p, g.tb, b, lo, hi);
-    return (int64_t)g.T * (std::max<int64_t>(1, (hi - lo + g.R - 1) / g.R) + g.tb);
+    int64_t far = 0;
+    if (b < g.nblocks) {
+        int64_t lo, hi;
+        block_rows(p, g.tb, b, lo, hi);
+        far = (int64_t)g.T * std::max<int64_t>(1, (hi - lo + g.R - 1) / g.R);
+    }
+    return far + (b >= 1 ? (int64_t)g.T * g.tb : 0);
 }
 
 // Device-side layout of one instance inside the workspace.
@@ -622,8 +627,8 @@ static int prepare(const fd_problem *p, Sched &s, Geo &g, size_t *bytes, Layout 
     Layout L;
     carve_instance(c, *p, g, s, L);
     c.take(sizeof(Inst) * 2);                                     // device instance descriptors
-    c.take(sizeof(long long) * (size_t)(p->max_steps + 1));       // group offsets
-    c.take(sizeof(int2) * (size_t)(p->max_steps + 1));            // group info
+    c.take(sizeof(long long) * (size_t)(p->max_steps + 2));       // group offsets
+    c.take(sizeof(int2) * (size_t)(p->max_steps + 2));            // group info
     if (bytes) *bytes = c.off;
     if (Lout) *Lout = L;
     if (ctrl) *ctrl = cc;
@@ -704,8 +709,8 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
         Layout tmp;
         carve_instance(c, *p, h->g, h->s, tmp);
         h->d_inst = (Inst *)c.take(sizeof(Inst) * 2);
-        h->d_goff = (long long *)c.take(sizeof(long long) * (size_t)(p->max_steps + 1));
-        h->d_ginfo = (int2 *)c.take(sizeof(int2) * (size_t)(p->max_steps + 1));
+        h->d_goff = (long long *)c.take(sizeof(long long) * (size_t)(p->max_steps + 2));
+        h->d_ginfo = (int2 *)c.take(sizeof(int2) * (size_t)(p->max_steps + 2));
     }
     h->ctrl_zero_base = (char *)h->L.arrive;
     h->ctrl_zero_bytes = sizeof(unsigned) * (kNpar + 1) * (size_t)h->g.T;
@@ -724,7 +729,7 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     }
     // group table: group k = step k of instance 0
     // groups: step k (per-step kernel) or block b of time_block steps (blocked kernel)
-    const int ngroups = h->g.tb ? h->g.nblocks : p->max_steps;
+    const int ngroups = h->g.tb ? h->g.nblocks + 1 : p->max_steps;
     h->goff.resize((size_t)ngroups + 1);
     std::vector<int2> info((size_t)ngroups + 1);
     long long acc = 0;
@@ -787,7 +792,7 @@ int fd_step(fd_handle *h, int nsteps)
     int rc;
     if (h->g.tb) {  // the blocks that intersect [k, k + nsteps)
         const int tb = h->g.tb;
-        rc = launch(h, h->kfwd, h->d_inst, (int)(h->k / tb), (int)((h->k + nsteps + tb - 1) / tb), (int)h->k,
+        rc = launch(h, h->kfwd, h->d_inst, (int)(h->k / tb), (int)((h->k + nsteps + tb - 1) / tb) + 1, (int)h->k,
                     (int)(h->k + nsteps));
     } else {
         rc = launch(h, h->kfwd, h->d_inst, (int)h->k, (int)(h->k + nsteps), (int)h->k, (int)(h->k + nsteps));
@@ -917,6 +922,22 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)h->s.step.size()) * N;
+    g->time_block = h->g.tb;
+    g->stream_rows_total = rows;
+    if (h->g.tb) {
+        const int tb = h->g.tb;
+        int64_t st = 0;
+        for (int64_t b = 0; b < h->g.nblocks; ++b) {
+            int64_t lo, hi;
+            block_rows(h->p, tb, b, lo, hi);
+            st += hi - lo;
+        }
+        for (int64_t k = 0; k < h->p.max_steps; ++k) {
+            const int64_t nb = (h->p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(h->p.mem_L, k) : k;
+            st += std::min<int64_t>(k - (k / tb) * tb + tb, nb);
+        }
+        g->stream_rows_total = st;
+    }
     return FD_OK;
 }
 
@@ -1204,6 +1225,8 @@ int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g)
     g->units_total = units;
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)b->s[i].step.size()) * N;
+    g->stream_rows_total = rows;
+    g->time_block = 0;
     return FD_OK;
 }
 

@@ -12,13 +12,16 @@
 // while the multiply-adds stay the same: the sum is the paper's, only grouped differently.
 // Short memory (eq. frac_shortmemory) is the same product with psi_m set to 0 for m > L.
 //
-// Work units of block b, in claim order: first T_tiles x C far units (tile, chunk of R far
-// rows), each writing T partial rows and counting itself in the tile's arrival counter; then
-// T x T_tiles update units, step-major (step kb+t, tile), each waiting for its tile's far
-// count and for its halo tiles' previous step.  Every wait therefore targets units with
-// smaller numbers, so the persistent grid cannot deadlock whatever the residency (an update
-// never waits on work that sits behind it in the queue).  Determinism, bounded waits, status
-// words and the memory-ordering protocol are those of engine_kernel.
+// Work units.  Group g holds the far units of block g (T_tiles x C: tile, chunk of R far rows;
+// each writes T partial rows and counts itself in the tile's arrival counter) interleaved with
+// the update units of block g-1 (one per step and tile, step-major): step s of block g-1's
+// updates is followed by the s-th slice of block g's far units, so CTAs that would otherwise
+// wait on the update chain find streaming work next in the queue.  An update waits for its
+// tile's far count (group g-1) and its halo tiles' previous step (earlier in group g or in g-1);
+// a far unit of block g waits for block g-2's updates (group g-1).  Every wait therefore
+// targets units with smaller numbers, so the persistent grid cannot deadlock whatever the
+// residency.  Determinism, bounded waits, status words and the memory-ordering protocol are
+// those of engine_kernel.
 #pragma once
 
 #include "fd_engine.cuh"
@@ -80,30 +83,38 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     s_cur_inst = gi.x;
                 }
                 const long long local = u - L.g_off[g];
-                const int C = (int)((L.g_off[g + 1] - L.g_off[g]) / I.T) - TB;  // far chunks per tile
-                const int kb = gi.y * TB;
-                const int rhi = max(0, kb - TB);
-                const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
+                const int gb = gi.y;  // group: far units of block gb, updates of block gb-1
+                const int Tu = (gb >= 1) ? I.T : 0;
+                const long long F = (L.g_off[g + 1] - L.g_off[g]) - (long long)TB * Tu;
+                int sseg = 0;  // segment s: Tu update units of step s, then far slice s
+                while (sseg + 1 < TB && (long long)(sseg + 1) * Tu + (long long)(sseg + 1) * F / TB <= local) ++sseg;
+                const long long off = local - ((long long)sseg * Tu + (long long)sseg * F / TB);
                 U.inst = gi.x;
-                U.b = gi.y;
-                U.C = C;
-                if (local < (long long)C * I.T) {  // far unit
+                if (off < Tu) {  // update unit: block gb-1, step s
+                    U.fix = 1;
+                    U.b = gb - 1;
+                    U.tile = (int)off;
+                    U.k = U.b * TB + sseg;
+                    U.C = (int)(((L.g_off[g] - L.g_off[g - 1]) - (long long)TB * (gb >= 2 ? I.T : 0)) / I.T);
+                    U.chunk = 0;
+                    U.r0 = U.r1 = 0;
+                } else {  // far unit of block gb
+                    const long long f = (long long)sseg * F / TB + (off - Tu);
+                    const int kb = gb * TB;
+                    const int rhi = max(0, kb - TB);
+                    const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
                     U.fix = 0;
-                    U.tile = (int)(local % I.T);
-                    U.chunk = (int)(local / I.T);
+                    U.b = gb;
+                    U.C = (int)(F / I.T);
+                    U.tile = (int)(f % I.T);
+                    U.chunk = (int)(f / I.T);
                     U.r0 = min(rhi, rlo + U.chunk * I.R);
                     U.r1 = min(rhi, U.r0 + I.R);
+                    U.k = (kb < L.k_end) ? 1 : 0;  // 0: block beyond the launch, nothing to do
                     // far rows up to r1-1 written; partial rows of block b-npar consumed
                     int need = (U.r1 > U.r0) ? U.r1 - L.k0 : 0;
                     need = max(need, kb - (I.npar - 1) * TB - L.k0);
-                    if (need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
-                } else {  // update unit
-                    const int idx = (int)(local - (long long)C * I.T);
-                    U.fix = 1;
-                    U.tile = idx % I.T;
-                    U.k = kb + idx / I.T;
-                    U.chunk = 0;
-                    U.r0 = U.r1 = 0;
+                    if (U.k && need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
                 }
             }
             U.valid = ok;
@@ -120,6 +131,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
         if (!U.fix) {
             // ================================================================ far unit
+            if (!U.k) continue;  // block starts at or after the launch's end
             const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;
             const int nst = (nrow + RS - 1) / RS;
             long long tile_bytes = (long long)min(I.P, I.N - tile * I.P) * 4ll;
