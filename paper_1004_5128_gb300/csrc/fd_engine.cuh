@@ -596,23 +596,32 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         }
         if (C > 1) {
             if (j0 < I.N) {
-                for (int c = 0; c < C; ++c) {
-                    if (c == U.chunk) {
+                // partial rows in fixed chunk order (this unit's own row holds the same bits as
+                // its registers); loads issued 4 rows at a time so the L2 round trips overlap
+                constexpr int B = 4;
+                for (int c0 = 0; c0 < C; c0 += B) {
+                    TA w[B][V], w2[B][V];
 #pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            H[v] += acc[v];
-                            if (ADJ) H2[v] += acc2[v];
+                    for (int i = 0; i < B; ++i)
+                        if (c0 + i < C) {
+                            const TA *p0 = prow(c0 + i, 0) + j0;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) w[i][v] = __ldcg(p0 + v);
+                            if (ADJ) {
+                                const TA *p1 = prow(c0 + i, 1) + j0;
+#pragma unroll
+                                for (int v = 0; v < V; ++v) w2[i][v] = __ldcg(p1 + v);
+                            }
                         }
-                    } else {
-                        const TA *p0 = prow(c, 0) + j0;
 #pragma unroll
-                        for (int v = 0; v < V; ++v) H[v] += __ldcg(p0 + v);
-                        if (ADJ) {
-                            const TA *p1 = prow(c, 1) + j0;
+                    for (int i = 0; i < B; ++i)
+                        if (c0 + i < C) {
 #pragma unroll
-                            for (int v = 0; v < V; ++v) H2[v] += __ldcg(p1 + v);
+                            for (int v = 0; v < V; ++v) {
+                                H[v] += w[i][v];
+                                if (ADJ) H2[v] += w2[i][v];
+                            }
                         }
-                    }
                 }
             }
         } else {

@@ -257,24 +257,42 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
         for (int v = 0; v < V; ++v) H[v] = 0.f;
         if (j0 < I.N) {
-            // far part: chunk partials in fixed order
-            for (int c = 0; c < C; ++c) {
-                const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t) + j0));
-                H[0] += w.x;
-                H[1] += w.y;
-                H[2] += w.z;
-                H[3] += w.w;
+            // far part: chunk partials in fixed order; loads issued B at a time so the L2
+            // round trips overlap (the additions keep their order)
+            constexpr int B = 4;
+            for (int c0 = 0; c0 < C; c0 += B) {
+                float4 w[B];
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (c0 + i < C) w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c0 + i, t) + j0));
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (c0 + i < C) {
+                        H[0] += w[i].x;
+                        H[1] += w[i].y;
+                        H[2] += w[i].z;
+                        H[3] += w[i].w;
+                    }
             }
-            // head: lags 1 .. min(k-kb+T, n_base(k)), descending lag
+            // head: lags 1 .. min(k-kb+T, n_base(k)), descending lag, batched loads
             const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
             const int hk = min(t + TB, nb);
-            for (int m = hk; m >= 1; --m) {
-                float x[V];
-                load_vec<float, V>(reinterpret_cast<const float *>(I.hist + (size_t)((k - m) % I.cap) * I.pitch) + j0,
-                                   x);
-                const float c = psi[m];
+            for (int m0 = hk; m0 >= 1; m0 -= B) {
+                float4 w[B];
 #pragma unroll
-                for (int v = 0; v < V; ++v) H[v] = fmaf(c, x[v], H[v]);
+                for (int i = 0; i < B; ++i)
+                    if (m0 - i >= 1)
+                        w[i] = __ldcg(reinterpret_cast<const float4 *>(
+                            reinterpret_cast<const float *>(I.hist + (size_t)((k - (m0 - i)) % I.cap) * I.pitch) + j0));
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (m0 - i >= 1) {
+                        const float c = psi[m0 - i];
+                        H[0] = fmaf(c, w[i].x, H[0]);
+                        H[1] = fmaf(c, w[i].y, H[1]);
+                        H[2] = fmaf(c, w[i].z, H[2]);
+                        H[3] = fmaf(c, w[i].w, H[3]);
+                    }
             }
         }
         const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
