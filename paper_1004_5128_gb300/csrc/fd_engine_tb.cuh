@@ -14,9 +14,9 @@
 //
 // Work units.  Group g holds the far units of block g (T_tiles x C: tile, chunk of R far rows;
 // each writes T partial rows and counts itself in the tile's arrival counter) interleaved with
-// the update units of block g-1 (one per step and tile, step-major): step s of block g-1's
-// updates is followed by the s-th slice of block g's far units, so CTAs that would otherwise
-// wait on the update chain find streaming work next in the queue.  An update waits for its
+// the update units of block g-1 (one per step and tile, step-major): the s-th slice of block
+// g's far units precedes the updates of step s, so an update is claimed only after a slice of
+// streaming work, by which time its previous step is usually done.  An update waits for its
 // tile's far count (group g-1) and its halo tiles' previous step (earlier in group g or in g-1);
 // a far unit of block g waits for block g-2's updates (group g-1).  Every wait therefore
 // targets units with smaller numbers, so the persistent grid cannot deadlock whatever the
@@ -86,20 +86,22 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const int gb = gi.y;  // group: far units of block gb, updates of block gb-1
                 const int Tu = (gb >= 1) ? I.T : 0;
                 const long long F = (L.g_off[g + 1] - L.g_off[g]) - (long long)TB * Tu;
-                int sseg = 0;  // segment s: Tu update units of step s, then far slice s
+                int sseg = 0;  // segment s: far slice s, then the Tu update units of step s
                 while (sseg + 1 < TB && (long long)(sseg + 1) * Tu + (long long)(sseg + 1) * F / TB <= local) ++sseg;
-                const long long off = local - ((long long)sseg * Tu + (long long)sseg * F / TB);
+                const long long fs0 = (long long)sseg * F / TB;
+                const long long fsn = (long long)(sseg + 1) * F / TB - fs0;  // far units in slice s
+                const long long off = local - ((long long)sseg * Tu + fs0);
                 U.inst = gi.x;
-                if (off < Tu) {  // update unit: block gb-1, step s
+                if (off >= fsn) {  // update unit: block gb-1, step s
                     U.fix = 1;
                     U.b = gb - 1;
-                    U.tile = (int)off;
+                    U.tile = (int)(off - fsn);
                     U.k = U.b * TB + sseg;
                     U.C = (int)(((L.g_off[g] - L.g_off[g - 1]) - (long long)TB * (gb >= 2 ? I.T : 0)) / I.T);
                     U.chunk = 0;
                     U.r0 = U.r1 = 0;
                 } else {  // far unit of block gb
-                    const long long f = (long long)sseg * F / TB + (off - Tu);
+                    const long long f = fs0 + off;
                     const int kb = gb * TB;
                     const int rhi = max(0, kb - TB);
                     const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
@@ -257,42 +259,24 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
         for (int v = 0; v < V; ++v) H[v] = 0.f;
         if (j0 < I.N) {
-            // far part: chunk partials in fixed order; loads issued B at a time so the L2
-            // round trips overlap (the additions keep their order)
-            constexpr int B = 4;
-            for (int c0 = 0; c0 < C; c0 += B) {
-                float4 w[B];
-#pragma unroll
-                for (int i = 0; i < B; ++i)
-                    if (c0 + i < C) w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c0 + i, t) + j0));
-#pragma unroll
-                for (int i = 0; i < B; ++i)
-                    if (c0 + i < C) {
-                        H[0] += w[i].x;
-                        H[1] += w[i].y;
-                        H[2] += w[i].z;
-                        H[3] += w[i].w;
-                    }
+            // far part: chunk partials in fixed order
+            for (int c = 0; c < C; ++c) {
+                const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t) + j0));
+                H[0] += w.x;
+                H[1] += w.y;
+                H[2] += w.z;
+                H[3] += w.w;
             }
-            // head: lags 1 .. min(k-kb+T, n_base(k)), descending lag, batched loads
+            // head: lags 1 .. min(k-kb+T, n_base(k)), descending lag
             const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
             const int hk = min(t + TB, nb);
-            for (int m0 = hk; m0 >= 1; m0 -= B) {
-                float4 w[B];
+            for (int m = hk; m >= 1; --m) {
+                float x[V];
+                load_vec<float, V>(reinterpret_cast<const float *>(I.hist + (size_t)((k - m) % I.cap) * I.pitch) + j0,
+                                   x);
+                const float c = psi[m];
 #pragma unroll
-                for (int i = 0; i < B; ++i)
-                    if (m0 - i >= 1)
-                        w[i] = __ldcg(reinterpret_cast<const float4 *>(
-                            reinterpret_cast<const float *>(I.hist + (size_t)((k - (m0 - i)) % I.cap) * I.pitch) + j0));
-#pragma unroll
-                for (int i = 0; i < B; ++i)
-                    if (m0 - i >= 1) {
-                        const float c = psi[m0 - i];
-                        H[0] = fmaf(c, w[i].x, H[0]);
-                        H[1] = fmaf(c, w[i].y, H[1]);
-                        H[2] = fmaf(c, w[i].z, H[2]);
-                        H[3] = fmaf(c, w[i].w, H[3]);
-                    }
+                for (int v = 0; v < V; ++v) H[v] = fmaf(c, x[v], H[v]);
             }
         }
         const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
