@@ -67,7 +67,10 @@ class FRD:
         _require_cuda()
         if tuned and not any(k in kw for k in GEOMETRY_KEYS):
             from .autotune import lookup
-            kw.update(lookup(p, kw.get("state", "f32"), kw.get("hist"), kw.get("kahan", False)))
+            geo = lookup(p, kw.get("state", "f32"), kw.get("hist"), kw.get("kahan", False))
+            if kw.get("keep_tape"):
+                geo.pop("time_block", None)  # the adjoint's tape runs with the per-step kernel
+            kw.update(geo)
         self.problem = p
         self.prob = make_problem(p, **kw)
         self.device = torch.device(device)
