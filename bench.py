@@ -135,6 +135,27 @@ def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
     return rows * N * sh + p["K"] * N * (2 * ss + sh)
 
 
+def measured_traffic(key: str, geometry: dict):
+    """DRAM bytes (read + write) of one launch from an ncu capture stored in profiles/traffic.json,
+    or None when there is none for this run, or when the kernel sources or the launch geometry
+    have changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            entries = json.load(f)["entries"]
+        for e in entries:
+            if e["key"] != key:
+                continue
+            if any(geometry.get(k) != v for k, v in e["geometry"].items()):
+                continue
+            if all(hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest() == h
+                   for src, h in e["sources"].items()):
+                return e["bytes"]
+    except (OSError, KeyError, ValueError):
+        return None
+    return None
+
+
 def _sample_terms(p, K):
     import oracle
     return sum(len(oracle.schedule(p["mem_mode"], p["mem_L"], p["mem_a"], p.get("adaptive_rule", 0),
@@ -360,20 +381,13 @@ def run_ours(args):
     dom = max(modes, key=lambda k: modes[k]["ms"])
     peak, which = peaks()
     ach = modes[dom]["gbs"]
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile) and not args.geom and not args.K:
-        try:
-            import hashlib
-            t = json.load(open(tfile))
-            src = open(os.path.join(ROOT, t["kernel_source"]), "rb").read()
-            if hashlib.sha256(src).hexdigest() == t["kernel_sha256"]:  # counters of this kernel only
-                traffic = t.get(f"{args.workload}:{dom}")
-        except Exception:
-            traffic = None
+    kname = f"engine_tb_kernel<{modes[dom]['geometry']['time_block']}>" \
+        if modes[dom]["geometry"].get("time_block") else "engine_kernel"
+    traffic = None if (args.geom or args.K) else measured_traffic(f"{args.workload}:{dom}",
+                                                                  modes[dom]["geometry"])
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "traffic": traffic,
-            "kernel": f"engine_kernel ({dom}, one persistent launch per run)",
+            "kernel": f"{kname} ({dom}, one persistent launch per run)",
             "peak_source": f"{which} hbm_gbs (burst copy)"}
 
     e2e = None

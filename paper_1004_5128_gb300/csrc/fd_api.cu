@@ -177,9 +177,10 @@ int validate(const fd_problem *p)
         return FD_ERR_UNSUPPORTED;
     if (p->time_block) {
         if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16) return FD_ERR_INVALID_ARG;
-        if (p->state_dtype != FD_F32 || p->hist_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan || adj ||
+        if (p->state_dtype != FD_F32 || p->hist_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan ||
             (p->mem_mode != FD_MEM_FULL && p->mem_mode != FD_MEM_SHORT))
             return FD_ERR_UNSUPPORTED;
+        if (adj && !fdk::kernel_tb(p->time_block, true)) return FD_ERR_UNSUPPORTED;  // adjoint blocks: 4, 8
     }
     if (!(p->flags & FD_FLAG_ALLOW_UNSTABLE)) {
         // von Neumann bound of the full-memory scheme (checkerboard mode):
@@ -292,7 +293,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = g.hring_sep ? g.head + 1 : g.cap;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = g.tb ? (size_t)g.NS * g.RS * g.threads * 16 + (size_t)(g.R + g.tb) * 4 + 32 + 8 * (size_t)g.NS
+    g.smem = g.tb ? (size_t)g.NS * g.RS * g.threads * 16 + (size_t)g.planes * (g.R + g.tb) * 4 + 32 + 8 * (size_t)g.NS
                   : smem_bytes(g, g.R);
 }
 
@@ -356,7 +357,7 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
                                  : (unsigned *)c.take(sizeof(unsigned) * (kNpar + 1) * (size_t)g.T);
     L.done = L.arrive ? L.arrive + kNpar * g.T : nullptr;
     L.psi = c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa);  // blocked: window reads to kb+tb-1
-    L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1) * g.sa) : nullptr;
+    L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa) : nullptr;
     L.sched = (int4 *)c.take(sizeof(int4) * (size_t)p.max_steps);
     const size_t ng = std::max<size_t>(1, s.G.size());
     L.glag = (int *)c.take(sizeof(int) * ng);
@@ -606,6 +607,15 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     return FD_OK;
 }
 
+// Steps [k0, k1) with fn: the per-step kernel's groups are steps; the blocked kernel's are the
+// blocks that intersect the span, plus the group holding the last block's updates.
+static int launch_steps(fd_handle *h, const void *fn, const Inst *d_inst, int k0, int k1)
+{
+    const int tb = h->g.tb;
+    if (tb) return launch(h, fn, d_inst, k0 / tb, (k1 + tb - 1) / tb + 1, k0, k1);
+    return launch(h, fn, d_inst, k0, k1, k0, k1);
+}
+
 // A zero nz (structs initialised before the field existed) means a single plane.
 static const fd_problem *normalized(const fd_problem *p, fd_problem &q)
 {
@@ -717,9 +727,9 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     const bool kahan = p->flags & FD_FLAG_KAHAN;
     h->kfwd = p->time_block ? fdk::kernel_tb(p->time_block)
                             : fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
-    h->kadj = (p->flags & FD_FLAG_KEEP_TAPE)
-                  ? fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)
-                  : nullptr;
+    h->kadj = !(p->flags & FD_FLAG_KEEP_TAPE) ? nullptr
+              : p->time_block ? fdk::kernel_tb(p->time_block, true)
+                              : fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true);
     rc = set_smem_attr(h->kfwd, h->g.smem);
     if (!rc && h->kadj) rc = set_smem_attr(h->kadj, h->g.smem);
     if (!rc) rc = resolve_grid(h->kfwd, h->g);
@@ -789,14 +799,7 @@ int fd_step(fd_handle *h, int nsteps)
     if (h->bad) return FD_ERR_STATE;
     if (h->k + nsteps > h->p.max_steps) return FD_ERR_STATE;
     if (nsteps == 0) return FD_OK;
-    int rc;
-    if (h->g.tb) {  // the blocks that intersect [k, k + nsteps)
-        const int tb = h->g.tb;
-        rc = launch(h, h->kfwd, h->d_inst, (int)(h->k / tb), (int)((h->k + nsteps + tb - 1) / tb) + 1, (int)h->k,
-                    (int)(h->k + nsteps));
-    } else {
-        rc = launch(h, h->kfwd, h->d_inst, (int)h->k, (int)(h->k + nsteps), (int)h->k, (int)(h->k + nsteps));
-    }
+    const int rc = launch_steps(h, h->kfwd, h->d_inst, (int)h->k, (int)(h->k + nsteps));
     if (rc) return rc;
     h->k += nsteps;
     return FD_OK;
@@ -876,11 +879,11 @@ int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma
         CK(cudaMemcpyAsync(h->L.rec[c & 1], uc, ub, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(h->L.seg, uc, ub, cudaMemcpyDeviceToDevice, st));
         if (ce - c > 1) {
-            rc = launch(h, h->kfwd, &h->d_inst[0], c, ce - 1, c);
+            rc = launch_steps(h, h->kfwd, &h->d_inst[0], c, ce - 1);
             if (rc) break;
         }
         // adjoint steps q = K-ce .. K-1-c  (r = K-1-q from ce-1 down to c)
-        rc = launch(h, h->kadj, &h->d_inst[1], K - ce, K - c, K - ce);
+        rc = launch_steps(h, h->kadj, &h->d_inst[1], K - ce, K - c);
         if (rc) break;
     }
     // restore the forward descriptor

@@ -183,6 +183,23 @@ __device__ __forceinline__ bool wait_counter(const unsigned *p, unsigned need, c
     }
 }
 
+// The same wait with a short sleep cap, for waits on the step-to-step chain, where a long
+// back-off would add directly to every step.
+__device__ __forceinline__ bool wait_counter_fast(const unsigned *p, unsigned need, const Launch &L)
+{
+    if (ld_acquire(p) >= need) return true;
+    const long long t0 = globaltimer();
+    for (;;) {
+        __nanosleep(32);
+        if (ld_acquire(p) >= need) return true;
+        if (ld_volatile(L.err) != ERR_NONE) return false;
+        if (globaltimer() - t0 > L.timeout_ns) {
+            atomicCAS(L.err, ERR_NONE, ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
 // ------------------------------------------------------- history vector traits
 template <class TH> struct HVec;
 template <> struct HVec<double> {

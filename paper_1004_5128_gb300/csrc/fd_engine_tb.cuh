@@ -11,6 +11,8 @@
 // block b+1 overlaps the T sequential updates of block b.  History traffic drops by about T
 // while the multiply-adds stay the same: the sum is the paper's, only grouped differently.
 // Short memory (eq. frac_shortmemory) is the same product with psi_m set to 0 for m > L.
+// The reverse-time adjoint (ADJ) has the same structure in adjoint steps over the rows
+// mu = L lambda, with a second accumulator for psi' = d psi / d gamma (see engine_kernel).
 //
 // Work units.  Group g holds the far units of block g (T_tiles x C: tile, chunk of R far rows;
 // each writes T partial rows and counts itself in the tile's arrival counter) interleaved with
@@ -34,9 +36,10 @@ struct UnitTB {
     int k;
 };
 
-template <int TB>
+template <int TB, bool ADJ>
 __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 {
+    constexpr int PLANES = ADJ ? 2 : 1;
     constexpr int V = 4;  // FP32: one float4 column per thread
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -46,12 +49,14 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *stages = smem;
     float *psw = reinterpret_cast<float *>(smem + (size_t)NS * RS * row_bytes);  // coefficient window
+    float *psw2 = psw + L.rmax + TB;                                               // psi' window (ADJ)
     uint64_t *bars = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(psw + L.rmax + TB) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(psw + PLANES * (L.rmax + TB)) + 15) & ~uintptr_t(15));
 
     __shared__ Inst I;
     __shared__ UnitTB U;
-    __shared__ int s_cur_inst, s_ok, s_pipe;
+    __shared__ int s_cur_inst, s_ok, s_ok2, s_pipe;
+    __shared__ double s_dred[ADJ ? 16 : 1][6];
 
     if (tid == 0) {
         for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
@@ -127,8 +132,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         const int tile = U.tile, C = U.C, b = U.b, kb = b * TB;
         const int par = b % I.npar;
         const int j0 = tile * I.P + tid * V;
-        auto prow = [&](int c, int t) -> float * {
-            return reinterpret_cast<float *>(I.part + ((size_t)((par * I.maxC + c) * TB + t)) * I.part_pitch);
+        auto prow = [&](int c, int t, int plane) -> float * {
+            return reinterpret_cast<float *>(I.part +
+                                             ((size_t)(((par * I.maxC + c) * TB + t) * PLANES + plane)) * I.part_pitch);
         };
 
         if (!U.fix) {
@@ -145,16 +151,22 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const int lag0 = kb - (r1 - 1);
                 for (int i = tid; i < nrow + TB - 1; i += nthr) {
                     const int lag = lag0 + i;
-                    psw[i] = (I.mem_mode == 1 && lag > I.mem_L) ? 0.f : psi[lag];
+                    const bool cut = (I.mem_mode == 1 && lag > I.mem_L);
+                    psw[i] = cut ? 0.f : psi[lag];
+                    if (ADJ) psw2[i] = cut ? 0.f : reinterpret_cast<const float *>(I.dpsi)[lag];
                 }
             }
             __syncthreads();
 
-            float acc[TB][V];
+            float acc[TB][V], acc2[ADJ ? TB : 1][V];
 #pragma unroll
             for (int t = 0; t < TB; ++t)
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[t][v] = 0.f;
+#pragma unroll
+            for (int t = 0; t < (ADJ ? TB : 1); ++t)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc2[t][v] = 0.f;
 
             auto issue = [&](int s) {
                 const int bb = (int)(n_issued % (uint32_t)NS);
@@ -192,12 +204,20 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 for (int r = 0; r < rows; ++r) {
                     const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)r * row_bytes);
                     const float x[4] = {x4.x, x4.y, x4.z, x4.w};
-                    const float *cw = psw + (r1 - 1 - (r0 + s * RS + r));
+                    const int wo = r1 - 1 - (r0 + s * RS + r);
 #pragma unroll
                     for (int t = 0; t < TB; ++t) {
-                        const float c = cw[t];
+                        const float c = psw[wo + t];
 #pragma unroll
                         for (int v = 0; v < V; ++v) acc[t][v] = fmaf(c, x[v], acc[t][v]);
+                    }
+                    if (ADJ) {
+#pragma unroll
+                        for (int t = 0; t < (ADJ ? TB : 1); ++t) {
+                            const float c2 = psw2[wo + t];
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc2[t][v] = fmaf(c2, x[v], acc2[t][v]);
+                        }
                     }
                 }
                 ++n_used;
@@ -222,8 +242,14 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             if (j0 < I.N) {
 #pragma unroll
                 for (int t = 0; t < TB; ++t)
-                    *reinterpret_cast<float4 *>(prow(U.chunk, t) + j0) =
+                    *reinterpret_cast<float4 *>(prow(U.chunk, t, 0) + j0) =
                         make_float4(acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+                if (ADJ) {
+#pragma unroll
+                    for (int t = 0; t < (ADJ ? TB : 1); ++t)
+                        *reinterpret_cast<float4 *>(prow(U.chunk, t, 1) + j0) =
+                            make_float4(acc2[t][0], acc2[t][1], acc2[t][2], acc2[t][3]);
+                }
             }
             // CTA barrier, then one release add: cumulative over every thread's partial stores
             __syncthreads();
@@ -236,15 +262,14 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         if (k < L.k0 || k >= L.k_end) continue;  // block edge outside this launch
         const int rel = k - L.k0;
         const bool last_of_block = (k == min(kb + TB, L.k_end) - 1);
+        // Two phases keep the partial and head sums off the step-to-step chain.  Phase A needs
+        // only the tile's far count and this tile's rows up to k-2 (its own step k-2), so it
+        // runs while step k-1 is still being updated; phase B waits for u^k on the halo tiles
+        // and row k-1, then adds lag 1 and updates.  The summation order is unchanged:
+        // partials by chunk, then lags hk .. 1.
         if (tid == 0) {
             int ok = wait_counter(&I.arrive[par * I.T + tile], (unsigned)C, L) ? 1 : 0;
-            const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
-            const int lo = max(0, tile * I.P - h) / I.P;
-            const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
-            for (int tt = lo; tt <= hi && ok; ++tt)
-                if (rel > 0 && !wait_counter(&I.done[tt], (unsigned)rel, L)) ok = 0;
-            if (ok && I.stall && rel == 0 && tile == 0)
-                if (!wait_counter(&I.done[tile], 0x80000000u, L)) ok = 0;
+            if (ok && rel > 1 && !wait_counter(&I.done[tile], (unsigned)(rel - 1), L)) ok = 0;
             s_ok = ok;
         }
         __syncthreads();
@@ -254,29 +279,119 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         const float q0 = (float)I.react[0], q1 = (float)I.react[1], q2 = (float)I.react[2],
                     q3 = (float)I.react[3];
         const float *psi = reinterpret_cast<const float *>(I.psi);
+        const float *dpsi = reinterpret_cast<const float *>(I.dpsi);
         const bool mirror = (I.bc == 1);
-        float H[V];
+        const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
+        const int hk = min(t + TB, nb);  // head: lags 1 .. min(k-kb+T, n_base(k)), descending
+        auto hrow = [&](int m) -> const float * {
+            return reinterpret_cast<const float *>(I.hist + (size_t)((k - m) % I.cap) * I.pitch) + j0;
+        };
+        float H[V], H2[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) H[v] = 0.f;
+        for (int v = 0; v < V; ++v) H[v] = H2[v] = 0.f;
         if (j0 < I.N) {
-            // far part: chunk partials in fixed order
-            for (int c = 0; c < C; ++c) {
-                const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t) + j0));
+            // far part: chunk partials in fixed order, four loads in flight
+            int c = 0;
+            for (; c + 4 <= C; c += 4) {
+                float4 w[4], w2[ADJ ? 4 : 1];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 0) + j0));
+                    if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 1) + j0));
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    H[0] += w[i].x;
+                    H[1] += w[i].y;
+                    H[2] += w[i].z;
+                    H[3] += w[i].w;
+                    if (ADJ) {
+                        H2[0] += w2[ADJ ? i : 0].x;
+                        H2[1] += w2[ADJ ? i : 0].y;
+                        H2[2] += w2[ADJ ? i : 0].z;
+                        H2[3] += w2[ADJ ? i : 0].w;
+                    }
+                }
+            }
+            for (; c < C; ++c) {
+                const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 0) + j0));
                 H[0] += w.x;
                 H[1] += w.y;
                 H[2] += w.z;
                 H[3] += w.w;
+                if (ADJ) {
+                    const float4 w2 = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 1) + j0));
+                    H2[0] += w2.x;
+                    H2[1] += w2.y;
+                    H2[2] += w2.z;
+                    H2[3] += w2.w;
+                }
             }
-            // head: lags 1 .. min(k-kb+T, n_base(k)), descending lag
-            const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
-            const int hk = min(t + TB, nb);
-            for (int m = hk; m >= 1; --m) {
-                float x[V];
-                load_vec<float, V>(reinterpret_cast<const float *>(I.hist + (size_t)((k - m) % I.cap) * I.pitch) + j0,
-                                   x);
-                const float c = psi[m];
+            // head lags hk .. 2: rows this tile wrote at steps up to k-2, four loads in flight
+            int m = hk;
+            for (; m - 3 >= 2; m -= 4) {
+                float4 x[4];
 #pragma unroll
-                for (int v = 0; v < V; ++v) H[v] = fmaf(c, x[v], H[v]);
+                for (int i = 0; i < 4; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(m - i)));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float cc = psi[m - i];
+                    H[0] = fmaf(cc, x[i].x, H[0]);
+                    H[1] = fmaf(cc, x[i].y, H[1]);
+                    H[2] = fmaf(cc, x[i].z, H[2]);
+                    H[3] = fmaf(cc, x[i].w, H[3]);
+                    if (ADJ) {
+                        const float c2 = dpsi[m - i];
+                        H2[0] = fmaf(c2, x[i].x, H2[0]);
+                        H2[1] = fmaf(c2, x[i].y, H2[1]);
+                        H2[2] = fmaf(c2, x[i].z, H2[2]);
+                        H2[3] = fmaf(c2, x[i].w, H2[3]);
+                    }
+                }
+            }
+            for (; m >= 2; --m) {
+                const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow(m)));
+                const float cc = psi[m];
+                H[0] = fmaf(cc, x.x, H[0]);
+                H[1] = fmaf(cc, x.y, H[1]);
+                H[2] = fmaf(cc, x.z, H[2]);
+                H[3] = fmaf(cc, x.w, H[3]);
+                if (ADJ) {
+                    const float c2 = dpsi[m];
+                    H2[0] = fmaf(c2, x.x, H2[0]);
+                    H2[1] = fmaf(c2, x.y, H2[1]);
+                    H2[2] = fmaf(c2, x.z, H2[2]);
+                    H2[3] = fmaf(c2, x.w, H2[3]);
+                }
+            }
+        }
+        // phase B: u^k on this tile and its halo tiles, and row k-1
+        if (tid == 0) {
+            int ok = 1;
+            const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
+            const int lo = max(0, tile * I.P - h) / I.P;
+            const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
+            for (int tt = lo; tt <= hi && ok; ++tt)
+                if (rel > 0 && !wait_counter_fast(&I.done[tt], (unsigned)rel, L)) ok = 0;
+            if (ok && I.stall && rel == 0 && tile == 0)
+                if (!wait_counter(&I.done[tile], 0x80000000u, L)) ok = 0;
+            s_ok2 = ok;
+        }
+        __syncthreads();
+        if (!s_ok2) break;
+        if (j0 < I.N && hk >= 1) {
+            const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow(1)));
+            const float cc = psi[1];
+            H[0] = fmaf(cc, x.x, H[0]);
+            H[1] = fmaf(cc, x.y, H[1]);
+            H[2] = fmaf(cc, x.z, H[2]);
+            H[3] = fmaf(cc, x.w, H[3]);
+            if (ADJ) {
+                const float c2 = dpsi[1];
+                H2[0] = fmaf(c2, x.x, H2[0]);
+                H2[1] = fmaf(c2, x.y, H2[1]);
+                H2[2] = fmaf(c2, x.z, H2[2]);
+                H2[3] = fmaf(c2, x.w, H2[3]);
             }
         }
         const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
@@ -289,6 +404,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                              : nullptr;
         float d[V];
         bool bad = false;
+        double dl[6] = {0, 0, 0, 0, 0, 0};
+        const float *ua = nullptr;
+        if (ADJ) ua = reinterpret_cast<const float *>(I.uadj) + (size_t)((I.adj_K - 1 - k) - I.uadj_r0) * I.N;
         if (j0 < I.N) {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -319,8 +437,25 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     const float bk = (z > 0) ? __ldcg(uk + j - pl) : gh;
                     d[v] = r + l - 6.f * c + up + dn + fw + bk;
                 }
-                const float f = q0 + c * (q1 + c * (q2 + c * q3));
-                const float inc = dt * f + S * (d[v] + H[v]);
+                const float G = d[v] + H[v];  // psi_0 times the fresh row plus the memory sum
+                float inc;
+                if (!ADJ) {
+                    const float f = q0 + c * (q1 + c * (q2 + c * q3));
+                    inc = dt * f + S * G;
+                } else {
+                    // reverse-time recursion: lambda^r = lambda^{r+1} + dt f'(u^r) lambda^{r+1} + S G
+                    const float ur = __ldcg(ua + j);
+                    const float fp = q1 + ur * (2.f * q2 + ur * 3.f * q3);
+                    inc = dt * fp * c + S * G;
+                    dl[0] += (double)ur * (double)G;
+                    dl[1] += (double)ur * (double)H2[v];
+                    double pw = 1.0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        dl[2 + i] += (double)c * pw;
+                        pw *= (double)ur;
+                    }
+                }
                 float nv;
                 if (lo_k) {
                     const float y2 = inc + __ldcg(lo_k + j);
@@ -340,9 +475,26 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     make_float4(d[0], d[1], d[2], d[3]);
         }
         if (bad) atomicOr(L.nonfinite, 1u);
+        if (ADJ) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dl[i] += __shfl_xor_sync(0xffffffffu, dl[i], o);
+            if ((tid & 31) == 0)
+#pragma unroll
+                for (int i = 0; i < 6; ++i) s_dred[tid >> 5][i] = dl[i];
+        }
         fence_proxy_async_global();
         __syncthreads();
         if (tid == 0) {
+            if (ADJ) {  // per-tile gradient partials, one writer per tile, in step order
+                double *dd = I.dots + (size_t)tile * 8;
+                for (int i = 0; i < 6; ++i) {
+                    double sacc = 0.0;
+                    for (int w = 0; w < (nthr + 31) / 32; ++w) sacc += s_dred[w][i];
+                    dd[i] += sacc;
+                }
+            }
             // the block's last update for this tile resets the far count for block b+npar,
             // whose far units wait for this step before they count
             if (last_of_block) I.arrive[par * I.T + tile] = 0u;

@@ -9,6 +9,6 @@ const void *kernel_for(int state, int hist, int acc, bool kahan, bool adj);
 const void *kernel_f64(bool kahan, bool adj);
 const void *kernel_f32(bool kahan, bool adj);
 const void *kernel_lowp(int hist, bool kahan, bool adj);
-// Temporally blocked FP32 kernel for a block of tb steps (4, 8 or 16), else nullptr.
-const void *kernel_tb(int tb);
+// Temporally blocked FP32 kernel for a block of tb steps (forward 4/8/16, adjoint 4/8), else nullptr.
+const void *kernel_tb(int tb, bool adj = false);
 }  // namespace fdk

@@ -68,8 +68,8 @@ class FRD:
         if tuned and not any(k in kw for k in GEOMETRY_KEYS):
             from .autotune import lookup
             geo = lookup(p, kw.get("state", "f32"), kw.get("hist"), kw.get("kahan", False))
-            if kw.get("keep_tape"):
-                geo.pop("time_block", None)  # the adjoint's tape runs with the per-step kernel
+            if kw.get("keep_tape") and geo.get("time_block", 0) > 8:
+                geo["time_block"] = 8  # blocked adjoint: blocks of at most 8 steps
             kw.update(geo)
         self.problem = p
         self.prob = make_problem(p, **kw)

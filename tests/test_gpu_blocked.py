@@ -1,7 +1,9 @@
 """Temporally blocked engine (time_block = 4 / 8 / 16; FP32, full and short memory) against the
-FP64 oracle and against properties that hold at full size."""
+FP64 oracle and against properties that hold at full size; the blocked reverse-time adjoint
+(time_block = 4 / 8) against the oracle's adjoint."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_1004_5128_gb300 import FRD, synth
@@ -66,3 +68,45 @@ def test_blocked_config2_full_size(mode):
     s.set_state(p["u0"])
     M0 = p["u0"].sum()
     assert abs(s.run(p["K"]).cpu().double().numpy().sum() - M0 * (1 - 0.1 * p["dt"]) ** p["K"]) / M0 < 2e-5
+
+
+def blocked_adjoint(p, tgt, tb, ckpt, **kw):
+    s = FRD(p, keep_tape=True, ckpt_every=ckpt, time_block=tb, **kw)
+    assert s.geometry()["time_block"] == tb
+    s.set_state(p["u0"])
+    uK = s.run(p["K"])
+    r = s.adjoint(uK - torch.as_tensor(tgt, device=uK.device, dtype=uK.dtype))
+    r["du0"] = r["du0"].cpu().double().numpy()
+    return r
+
+
+def compare_grads(r, ref, tol):
+    assert rel_inf(r["du0"], ref["du0"]) < tol
+    for key in ("dgamma", "dalpha"):
+        assert abs(r[key] - ref[key]) <= tol * abs(ref[key]), (key, r[key], ref[key])
+    assert np.max(np.abs(np.array(r["dreact"]) - ref["dreact"])) <= tol * np.max(np.abs(ref["dreact"]))
+
+
+@pytest.mark.parametrize("tb", [4, 8])
+@pytest.mark.parametrize("bc", [synth.BC_DIRICHLET0, synth.BC_NOFLUX])
+def test_blocked_adjoint_matches_oracle(tb, bc):
+    """Checkpoint segments of 50 steps (not a multiple of the block: recompute and adjoint
+    launches start inside a block) and a ragged last segment; several far chunks per block."""
+    p = ragged(bc, synth.MEM_FULL, K=230)
+    tgt = synth.SplitMix64(3).uniform(p["nx"] * p["ny"], 0, 0.8)
+    compare_grads(blocked_adjoint(p, tgt, tb, ckpt=50, chunk_terms=16), oracle.adjoint(p, tgt), 2e-4)
+
+
+def test_blocked_adjoint_config5_reduced():
+    """Config-5 physics (128^2, gamma=0.7, alpha=0.8, f=-0.1u, dt=0.005) at 600 steps, the
+    config's checkpoint spacing of 200 steps."""
+    p = synth.config5(K=600)
+    tgt = oracle.run(synth.config5(K=600, target=True))
+    compare_grads(blocked_adjoint(p, tgt, 8, ckpt=200), oracle.adjoint(p, tgt), 2e-4)
+
+
+def test_blocked_adjoint_rejects_blocks_of_16():
+    from paper_1004_5128_gb300 import _lib as L
+    with pytest.raises(L.FdError) as e:
+        FRD(ragged(synth.BC_NOFLUX, synth.MEM_FULL), keep_tape=True, time_block=16)
+    assert e.value.code == L.FD_ERR_UNSUPPORTED

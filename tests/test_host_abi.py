@@ -120,10 +120,13 @@ def test_strerror():
 def test_time_block_validation():
     p = synth.config2(K=100)
     assert L.fd_workspace_bytes(make_problem(p, time_block=8)) > 0
+    # the blocked adjoint keeps two accumulator sets: blocks of 4 and 8 steps only
+    taped = L.fd_workspace_bytes(make_problem(p, time_block=8, keep_tape=True))
+    assert taped > L.fd_workspace_bytes(make_problem(p, keep_tape=True)) > 0
     for bad, code in ((dict(time_block=5), L.FD_ERR_INVALID_ARG),
                       (dict(time_block=8, hist="bf16"), L.FD_ERR_UNSUPPORTED),
                       (dict(time_block=8, kahan=True), L.FD_ERR_UNSUPPORTED),
-                      (dict(time_block=8, keep_tape=True), L.FD_ERR_UNSUPPORTED)):
+                      (dict(time_block=16, keep_tape=True), L.FD_ERR_UNSUPPORTED)):
         with pytest.raises(L.FdError) as e:
             L.fd_workspace_bytes(make_problem(p, **bad))
         assert e.value.code == code
