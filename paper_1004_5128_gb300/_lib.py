@@ -37,6 +37,7 @@ FD_FLAG_PLAIN_STATE = 16
 EXPORTS = (
     "fd_weights", "fd_schedule", "fd_workspace_bytes", "fd_init", "fd_set_state", "fd_step",
     "fd_run", "fd_get_state", "fd_current_step", "fd_adjoint", "fd_get_status", "fd_destroy",
+    "fd_get_error_info",
     "fd_get_geometry", "fd_batch_workspace_bytes", "fd_batch_init", "fd_batch_set_state",
     "fd_batch_run", "fd_batch_get_state", "fd_batch_get_status", "fd_batch_get_geometry",
     "fd_batch_destroy",
@@ -101,6 +102,7 @@ def lib():
             "fd_current_step": [vp],
             "fd_adjoint": [vp, vp, vp, dp, dp, dp],
             "fd_get_status": [vp],
+            "fd_get_error_info": [vp, ctypes.POINTER(ctypes.c_int64)],
             "fd_destroy": [vp],
             "fd_get_geometry": [vp, ctypes.POINTER(FdGeometry)],
             "fd_batch_workspace_bytes": [P, ctypes.c_int, sz],
@@ -195,6 +197,20 @@ def fd_current_step(h: int) -> int:
 
 def fd_get_status(h: int) -> int:
     return int(lib().fd_get_status(h))
+
+
+ERROR_SITES = {0: "none", 1: "blocked far unit: history rows", 2: "blocked far unit: bulk copy",
+               3: "blocked update: far count", 4: "blocked update: own rows",
+               5: "blocked update: halo tile", 6: "chunk: history rows", 7: "chunk: bulk copy",
+               8: "fixup: halo tile"}
+
+
+def fd_get_error_info(h: int) -> dict:
+    """Where a device wait gave up: site name and its eight raw words."""
+    v = (ctypes.c_int64 * 8)()
+    check(lib().fd_get_error_info(h, v), "fd_get_error_info")
+    words = [int(x) for x in v]
+    return {"site": ERROR_SITES.get(words[0], str(words[0])), "words": words}
 
 
 def fd_adjoint(h: int, dj_duk_ptr: int, dj_du0_ptr: int | None):

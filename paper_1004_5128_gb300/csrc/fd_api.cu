@@ -181,6 +181,8 @@ int validate(const fd_problem *p)
             (p->mem_mode != FD_MEM_FULL && p->mem_mode != FD_MEM_SHORT))
             return FD_ERR_UNSUPPORTED;
         if (adj && !fdk::kernel_tb(p->time_block, true)) return FD_ERR_UNSUPPORTED;  // adjoint blocks: 4, 8
+        // arrival words hold a block generation (blocks / 4) and a chunk count in 16 bits each
+        if ((int64_t)p->max_steps / p->time_block / 4 >= 65535) return FD_ERR_INVALID_ARG;
     }
     if (!(p->flags & FD_FLAG_ALLOW_UNSTABLE)) {
         // von Neumann bound of the full-memory scheme (checkerboard mode):
@@ -293,7 +295,9 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = g.hring_sep ? g.head + 1 : g.cap;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = g.tb ? (size_t)g.NS * g.RS * g.threads * 16 + (size_t)g.planes * (g.R + g.tb) * 4 + 32 + 8 * (size_t)g.NS
+    // blocked: stage ring, four shifted copies of each coefficient window, barriers
+    g.smem = g.tb ? (size_t)g.NS * g.RS * g.threads * 16 + (size_t)g.planes * 4 * ((g.R + g.tb + 7) & ~3) * 4 + 32 +
+                        8 * (size_t)g.NS
                   : smem_bytes(g, g.R);
 }
 
@@ -385,6 +389,7 @@ struct Ctrl {
     unsigned long long *queue;
     int *err;
     unsigned *nonfinite;
+    long long *err_info;  // 8 words: the first wait that gave up (site, operands, CTA)
 };
 
 Ctrl carve_ctrl(Carve &c)
@@ -394,6 +399,7 @@ Ctrl carve_ctrl(Carve &c)
     r.queue = (unsigned long long *)b;
     r.err = b ? (int *)(b + 64) : nullptr;
     r.nonfinite = b ? (unsigned *)(b + 128) : nullptr;
+    r.err_info = b ? (long long *)(b + 192) : nullptr;
     return r;
 }
 
@@ -597,6 +603,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.queue = h->ctrl.queue;
     L.err = h->ctrl.err;
     L.nonfinite = h->ctrl.nonfinite;
+    L.err_info = h->ctrl.err_info;
     L.timeout_ns = (long long)(h->p.timeout_ms ? h->p.timeout_ms : 10000) * 1000000LL;
     CK(cudaMemsetAsync(h->ctrl.queue, 0, sizeof(unsigned long long), h->st));
     CK(cudaMemsetAsync(h->ctrl_zero_base, 0, h->ctrl_zero_bytes, h->st));
@@ -788,6 +795,7 @@ int fd_set_state(fd_handle *h, const void *u0)
     if (h->L.ckpt) CK(cudaMemcpyAsync(h->L.ckpt, u0, bytes, cudaMemcpyDefault, h->st));
     CK(cudaMemsetAsync(h->ctrl.err, 0, sizeof(int), h->st));
     CK(cudaMemsetAsync(h->ctrl.nonfinite, 0, sizeof(unsigned), h->st));
+    CK(cudaMemsetAsync(h->ctrl.err_info, 0, 8 * sizeof(long long), h->st));
     h->k = 0;
     h->bad = 0;
     return FD_OK;
@@ -826,6 +834,16 @@ int fd_get_status(fd_handle *h)
     const int s = status_from(err, nf);
     if (s == FD_ERR_TIMEOUT) h->bad = 1;
     return s;
+}
+
+int fd_get_error_info(fd_handle *h, int64_t info[8])
+{
+    if (!h || !info) return FD_ERR_INVALID_ARG;
+    long long v[8];
+    CK(cudaMemcpyAsync(v, h->ctrl.err_info, sizeof(v), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int i = 0; i < 8; ++i) info[i] = v[i];
+    return FD_OK;
 }
 
 int fd_run(fd_handle *h, int nsteps, void *u_out)
@@ -1133,6 +1151,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         L.queue = b->ctrl.queue;
         L.err = b->ctrl.err;
         L.nonfinite = b->ctrl.nonfinite;
+        L.err_info = b->ctrl.err_info;
         L.timeout_ns = (long long)(b->p[0].timeout_ms ? b->p[0].timeout_ms : 10000) * 1000000LL;
         cudaGraphNode_t m1, m2, kn;
         cudaMemsetParams mp;

@@ -96,6 +96,7 @@ struct Launch {
     int *err;
     unsigned *nonfinite;
     long long timeout_ns;
+    long long *err_info;     // first wait that gave up: site code, operands, CTA (8 words) or null
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -164,40 +165,47 @@ __device__ __forceinline__ int ld_volatile(const int *p)
     return *reinterpret_cast<const volatile int *>(p);
 }
 
-// Bounded wait until *p >= need (thread 0 only).  Returns false on timeout or
-// when another CTA has already recorded an error.
-__device__ __forceinline__ bool wait_counter(const unsigned *p, unsigned need, const Launch &L)
+// Bounded wait until *p >= need, with a sleep between polls that doubles up to max_sleep ns.
+// Returns 1 when satisfied, 0 when another wait has already recorded an error, and -1 when
+// this wait ran out of time (it then records FD_ERR_TIMEOUT).
+__device__ __forceinline__ int wait_until(const unsigned *p, unsigned need, const Launch &L, unsigned max_sleep)
 {
-    if (ld_acquire(p) >= need) return true;
+    if (ld_acquire(p) >= need) return 1;
     const long long t0 = globaltimer();
     unsigned ns = 32;
     for (;;) {
         __nanosleep(ns);
-        if (ns < 512) ns <<= 1;
-        if (ld_acquire(p) >= need) return true;
-        if (ld_volatile(L.err) != ERR_NONE) return false;
+        if (ns < max_sleep) ns <<= 1;
+        if (ld_acquire(p) >= need) return 1;
+        if (ld_volatile(L.err) != ERR_NONE) return 0;
         if (globaltimer() - t0 > L.timeout_ns) {
             atomicCAS(L.err, ERR_NONE, ERR_TIMEOUT);
-            return false;
+            return -1;
         }
     }
 }
 
-// The same wait with a short sleep cap, for waits on the step-to-step chain, where a long
-// back-off would add directly to every step.
-__device__ __forceinline__ bool wait_counter_fast(const unsigned *p, unsigned need, const Launch &L)
+__device__ __forceinline__ bool wait_counter(const unsigned *p, unsigned need, const Launch &L)
 {
-    if (ld_acquire(p) >= need) return true;
-    const long long t0 = globaltimer();
-    for (;;) {
-        __nanosleep(32);
-        if (ld_acquire(p) >= need) return true;
-        if (ld_volatile(L.err) != ERR_NONE) return false;
-        if (globaltimer() - t0 > L.timeout_ns) {
-            atomicCAS(L.err, ERR_NONE, ERR_TIMEOUT);
-            return false;
-        }
-    }
+    return wait_until(p, need, L, 512) > 0;
+}
+
+// Records the first wait that gave up: a site code, six operands and the CTA, for the host's
+// error report.  Later failures (usually consequences of the first) leave it unchanged.
+__device__ __forceinline__ void note_failure(const Launch &L, long long site, long long a, long long b, long long c,
+                                             long long d, long long e, long long f)
+{
+    if (!L.err_info) return;
+    if (atomicCAS(reinterpret_cast<unsigned long long *>(L.err_info), 0ull, (unsigned long long)site) != 0ull)
+        return;
+    L.err_info[1] = a;
+    L.err_info[2] = b;
+    L.err_info[3] = c;
+    L.err_info[4] = d;
+    L.err_info[5] = e;
+    L.err_info[6] = f;
+    L.err_info[7] = blockIdx.x;
+    __threadfence();
 }
 
 // ------------------------------------------------------- history vector traits
@@ -444,7 +452,11 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 }
                 // partial rows of step k-npar consumed by its fixup
                 if (C > 1 && rel - I.npar + 1 > need) need = rel - I.npar + 1;
-                if (need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
+                if (need > 0) {
+                    const int w = wait_until(&I.done[U.tile], (unsigned)need, L, 512);
+                    if (w < 0) note_failure(L, 6, gi.y, U.tile, need, ld_acquire(&I.done[U.tile]), L.k0, 0);
+                    if (w <= 0) ok = 0;
+                }
             }
             U.valid = ok;
         }
@@ -503,7 +515,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 const long long t0 = globaltimer();
                 while (!mbar_try_wait(&bars[b], par)) {
                     if (globaltimer() - t0 > L.timeout_ns) {
-                        atomicCAS(L.err, ERR_NONE, ERR_PIPE);
+                        if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE) note_failure(L, 7, U.k, U.tile, 0, 0, 0, 0);
                         break;  // the copy is still owed to this slot; see below
                     }
                 }
@@ -595,7 +607,11 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             const int lo = max(0, tile * I.P - h) / I.P;
             const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
             for (int t = lo; t <= hi && ok; ++t)
-                if (rel > 0 && !wait_counter(&I.done[t], (unsigned)rel, L)) ok = 0;
+                if (rel > 0) {
+                    const int w = wait_until(&I.done[t], (unsigned)rel, L, 512);
+                    if (w < 0) note_failure(L, 8, k, tile, t, rel, ld_acquire(&I.done[t]), L.k0);
+                    if (w <= 0) ok = 0;
+                }
             if (ok && I.stall && rel == 0 && tile == 0) {
                 // fault injection: nothing ever raises this counter to 2^31
                 if (!wait_counter(&I.done[tile], 0x80000000u, L)) ok = 0;

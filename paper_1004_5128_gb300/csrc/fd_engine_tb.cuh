@@ -48,10 +48,13 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *stages = smem;
-    float *psw = reinterpret_cast<float *>(smem + (size_t)NS * RS * row_bytes);  // coefficient window
-    float *psw2 = psw + L.rmax + TB;                                               // psi' window (ADJ)
+    // Coefficient window in four copies shifted by 0..3 elements, so that the TB coefficients
+    // of any row are TB/4 aligned 16-byte loads: copy q holds w[i + q] at index i.
+    const int WS = (L.rmax + TB + 7) & ~3;                                          // copy stride
+    float *psw = reinterpret_cast<float *>(smem + (size_t)NS * RS * row_bytes);  // psi window
+    float *psw2 = psw + 4 * WS;                                                    // psi' window (ADJ)
     uint64_t *bars = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(psw + PLANES * (L.rmax + TB)) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(psw + PLANES * 4 * WS) + 15) & ~uintptr_t(15));
 
     __shared__ Inst I;
     __shared__ UnitTB U;
@@ -75,10 +78,16 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
     for (;;) {
         // ---------------------------------------------------------------- claim
+        // Thread 0 passes over units with nothing to do in this launch (far units of a block
+        // that starts at or after the launch's end, updates of steps outside it) without
+        // publishing them: every published unit ends with a CTA barrier, so the shared
+        // descriptor is never rewritten while another thread may still read it.
         if (tid == 0) {
-            const long long u = u_base + (long long)next;
-            int ok = (u < u_end) && (ld_volatile(L.err) == ERR_NONE);
-            if (ok) {
+            int ok = 0;
+            for (;;) {
+                const long long u = u_base + (long long)next;
+                ok = (u < u_end) && (ld_volatile(L.err) == ERR_NONE);
+                if (!ok) break;
                 next = atomicAdd(L.queue, 1ull);
                 const int g = find_group(L.g_off, ghint, L.g_end, u);
                 ghint = g;
@@ -98,16 +107,19 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const long long off = local - ((long long)sseg * Tu + fs0);
                 U.inst = gi.x;
                 if (off >= fsn) {  // update unit: block gb-1, step s
+                    const int k = (gb - 1) * TB + sseg;
+                    if (k < L.k0 || k >= L.k_end) continue;  // block edge outside this launch
                     U.fix = 1;
                     U.b = gb - 1;
                     U.tile = (int)(off - fsn);
-                    U.k = U.b * TB + sseg;
+                    U.k = k;
                     U.C = (int)(((L.g_off[g] - L.g_off[g - 1]) - (long long)TB * (gb >= 2 ? I.T : 0)) / I.T);
                     U.chunk = 0;
                     U.r0 = U.r1 = 0;
                 } else {  // far unit of block gb
-                    const long long f = fs0 + off;
                     const int kb = gb * TB;
+                    if (kb >= L.k_end) continue;  // block starts at or after the launch's end
+                    const long long f = fs0 + off;
                     const int rhi = max(0, kb - TB);
                     const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
                     U.fix = 0;
@@ -117,12 +129,17 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     U.chunk = (int)(f / I.T);
                     U.r0 = min(rhi, rlo + U.chunk * I.R);
                     U.r1 = min(rhi, U.r0 + I.R);
-                    U.k = (kb < L.k_end) ? 1 : 0;  // 0: block beyond the launch, nothing to do
+                    U.k = 0;
                     // far rows up to r1-1 written; partial rows of block b-npar consumed
                     int need = (U.r1 > U.r0) ? U.r1 - L.k0 : 0;
                     need = max(need, kb - (I.npar - 1) * TB - L.k0);
-                    if (U.k && need > 0 && !wait_counter(&I.done[U.tile], (unsigned)need, L)) ok = 0;
+                    if (need > 0) {
+                        const int w = wait_until(&I.done[U.tile], (unsigned)need, L, 512);
+                        if (w < 0) note_failure(L, 1, gb, U.tile, need, ld_acquire(&I.done[U.tile]), L.k0, 0);
+                        if (w <= 0) ok = 0;
+                    }
                 }
+                break;
             }
             U.valid = ok;
         }
@@ -131,6 +148,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
         const int tile = U.tile, C = U.C, b = U.b, kb = b * TB;
         const int par = b % I.npar;
+        // Arrival counters carry the block's generation within its parity in the high half
+        // ((b - first block of the launch) / npar), so a count left by block b - npar can never
+        // satisfy block b's wait; the last update of block b sets the word for block b + npar.
+        auto arrive_target = [&](int bb, int count) -> unsigned {
+            return ((unsigned)((bb - L.g_begin) / I.npar) << 16) + (unsigned)count;
+        };
         const int j0 = tile * I.P + tid * V;
         auto prow = [&](int c, int t, int plane) -> float * {
             return reinterpret_cast<float *>(I.part +
@@ -139,21 +162,22 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
         if (!U.fix) {
             // ================================================================ far unit
-            if (!U.k) continue;  // block starts at or after the launch's end
             const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;
             const int nst = (nrow + RS - 1) / RS;
             long long tile_bytes = (long long)min(I.P, I.N - tile * I.P) * 4ll;
             tile_bytes = (tile_bytes + 15) & ~15ll;
 
-            // coefficient window: row r, step kb+t uses psw[(r1-1-r) + t] = psi_{kb+t-r}
+            // coefficient window w[i] = psi_{lag0 + i}: row r, step kb+t uses w[(r1-1-r) + t]
             {
                 const float *psi = reinterpret_cast<const float *>(I.psi);
                 const int lag0 = kb - (r1 - 1);
-                for (int i = tid; i < nrow + TB - 1; i += nthr) {
-                    const int lag = lag0 + i;
-                    const bool cut = (I.mem_mode == 1 && lag > I.mem_L);
-                    psw[i] = cut ? 0.f : psi[lag];
-                    if (ADJ) psw2[i] = cut ? 0.f : reinterpret_cast<const float *>(I.dpsi)[lag];
+                const int nw = nrow + TB - 1;
+                for (int e = tid; e < 4 * WS; e += nthr) {
+                    const int q = e / WS, i = e - q * WS, w = i + q;
+                    const int lag = lag0 + w;
+                    const bool cut = (w >= nw) || (I.mem_mode == 1 && lag > I.mem_L);
+                    psw[q * WS + i] = cut ? 0.f : psi[lag];
+                    if (ADJ) psw2[q * WS + i] = cut ? 0.f : reinterpret_cast<const float *>(I.dpsi)[lag];
                 }
             }
             __syncthreads();
@@ -194,29 +218,70 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     const long long t0 = globaltimer();
                     while (!mbar_try_wait(&bars[bb], ph)) {
                         if (globaltimer() - t0 > L.timeout_ns) {
-                            atomicCAS(L.err, ERR_NONE, ERR_PIPE);
+                            if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE)
+                                note_failure(L, 2, ((long long)b << 32) | tile, ((long long)s << 32) | nst,
+                                             ((long long)n_issued << 32) | n_used,
+                                             (long long)*reinterpret_cast<volatile unsigned long long *>(&bars[bb]),
+                                             ((long long)L.k0 << 32) | L.k_end, ((long long)r0 << 32) | r1);
                             break;
                         }
                     }
                 }
                 const int rows = min(RS, nrow - s * RS);
                 const unsigned char *base = stages + (size_t)bb * RS * row_bytes + (size_t)tid * 16;
-                for (int r = 0; r < rows; ++r) {
+                int r = 0;
+                // Four rows at a time.  Row a = s*RS + r + i uses w[wo - i + t], wo = nrow-1-(s*RS+r):
+                // the TB+3 coefficients w[wo-3 .. wo+TB-1] come in aligned 16-byte loads from the
+                // copy shifted by (wo-3) & 3 and serve all four rows from registers.
+                for (; r + 4 <= rows; r += 4) {
+                    const int lo = nrow - 1 - (s * RS + r) - 3;
+                    const int cq = (lo & 3) * WS + (lo & ~3);
+                    float c[TB + 4], c2[ADJ ? TB + 4 : 1];
+#pragma unroll
+                    for (int j = 0; j < TB + 4; j += 4) {
+                        const float4 c4 = *reinterpret_cast<const float4 *>(psw + cq + j);
+                        c[j] = c4.x;
+                        c[j + 1] = c4.y;
+                        c[j + 2] = c4.z;
+                        c[j + 3] = c4.w;
+                        if (ADJ) {
+                            const float4 d4 = *reinterpret_cast<const float4 *>(psw2 + cq + j);
+                            c2[ADJ ? j : 0] = d4.x;
+                            c2[ADJ ? j + 1 : 0] = d4.y;
+                            c2[ADJ ? j + 2 : 0] = d4.z;
+                            c2[ADJ ? j + 3 : 0] = d4.w;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)(r + i) * row_bytes);
+                        const float x[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                        for (int t = 0; t < TB; ++t)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc[t][v] = fmaf(c[3 - i + t], x[v], acc[t][v]);
+                        if (ADJ) {
+#pragma unroll
+                            for (int t = 0; t < (ADJ ? TB : 1); ++t)
+#pragma unroll
+                                for (int v = 0; v < V; ++v)
+                                    acc2[t][v] = fmaf(c2[ADJ ? 3 - i + t : 0], x[v], acc2[t][v]);
+                        }
+                    }
+                }
+                for (; r < rows; ++r) {  // remaining rows one at a time (unshifted copy)
                     const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)r * row_bytes);
                     const float x[4] = {x4.x, x4.y, x4.z, x4.w};
-                    const int wo = r1 - 1 - (r0 + s * RS + r);
+                    const int wo = nrow - 1 - (s * RS + r);
 #pragma unroll
                     for (int t = 0; t < TB; ++t) {
-                        const float c = psw[wo + t];
+                        const float cc = psw[wo + t];
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[t][v] = fmaf(c, x[v], acc[t][v]);
-                    }
-                    if (ADJ) {
+                        for (int v = 0; v < V; ++v) acc[t][v] = fmaf(cc, x[v], acc[t][v]);
+                        if (ADJ) {
+                            const float cd = psw2[wo + t];
 #pragma unroll
-                        for (int t = 0; t < (ADJ ? TB : 1); ++t) {
-                            const float c2 = psw2[wo + t];
-#pragma unroll
-                            for (int v = 0; v < V; ++v) acc2[t][v] = fmaf(c2, x[v], acc2[t][v]);
+                            for (int v = 0; v < V; ++v) acc2[ADJ ? t : 0][v] = fmaf(cd, x[v], acc2[ADJ ? t : 0][v]);
                         }
                     }
                 }
@@ -259,7 +324,6 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
         // ================================================== update unit: step k, this tile
         const int k = U.k, t = k - kb;
-        if (k < L.k0 || k >= L.k_end) continue;  // block edge outside this launch
         const int rel = k - L.k0;
         const bool last_of_block = (k == min(kb + TB, L.k_end) - 1);
         // Two phases keep the partial and head sums off the step-to-step chain.  Phase A needs
@@ -267,10 +331,20 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         // runs while step k-1 is still being updated; phase B waits for u^k on the halo tiles
         // and row k-1, then adds lag 1 and updates.  The summation order is unchanged:
         // partials by chunk, then lags hk .. 1.
-        if (tid == 0) {
-            int ok = wait_counter(&I.arrive[par * I.T + tile], (unsigned)C, L) ? 1 : 0;
-            if (ok && rel > 1 && !wait_counter(&I.done[tile], (unsigned)(rel - 1), L)) ok = 0;
-            s_ok = ok;
+        if (tid < 32) {  // the two waits run in parallel lanes
+            int ok = 1;
+            if (tid == 0) {
+                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C), L, 512);
+                if (w < 0) note_failure(L, 3, k, tile, arrive_target(b, C), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
+                ok = w > 0;
+            }
+            if (tid == 1 && rel > 1) {
+                const int w = wait_until(&I.done[tile], (unsigned)(rel - 1), L, 512);
+                if (w < 0) note_failure(L, 4, k, tile, rel - 1, ld_acquire(&I.done[tile]), L.k0, 0);
+                ok = w > 0;
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            if (tid == 0) s_ok = ok;
         }
         __syncthreads();
         if (!s_ok) break;
@@ -366,34 +440,24 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             }
         }
         // phase B: u^k on this tile and its halo tiles, and row k-1
-        if (tid == 0) {
+        if (tid < 32) {  // one lane per halo tile
             int ok = 1;
             const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
             const int lo = max(0, tile * I.P - h) / I.P;
             const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
-            for (int tt = lo; tt <= hi && ok; ++tt)
-                if (rel > 0 && !wait_counter_fast(&I.done[tt], (unsigned)rel, L)) ok = 0;
-            if (ok && I.stall && rel == 0 && tile == 0)
+            for (int tt = lo + tid; tt <= hi && ok; tt += 32)
+                if (rel > 0) {
+                    const int w = wait_until(&I.done[tt], (unsigned)rel, L, 32);
+                    if (w < 0) note_failure(L, 5, k, tile, tt, rel, ld_acquire(&I.done[tt]), L.k0);
+                    if (w <= 0) ok = 0;
+                }
+            if (tid == 0 && ok && I.stall && rel == 0 && tile == 0)
                 if (!wait_counter(&I.done[tile], 0x80000000u, L)) ok = 0;
-            s_ok2 = ok;
+            ok = __all_sync(0xffffffffu, ok);
+            if (tid == 0) s_ok2 = ok;
         }
         __syncthreads();
         if (!s_ok2) break;
-        if (j0 < I.N && hk >= 1) {
-            const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow(1)));
-            const float cc = psi[1];
-            H[0] = fmaf(cc, x.x, H[0]);
-            H[1] = fmaf(cc, x.y, H[1]);
-            H[2] = fmaf(cc, x.z, H[2]);
-            H[3] = fmaf(cc, x.w, H[3]);
-            if (ADJ) {
-                const float c2 = dpsi[1];
-                H2[0] = fmaf(c2, x.x, H2[0]);
-                H2[1] = fmaf(c2, x.y, H2[1]);
-                H2[2] = fmaf(c2, x.z, H2[2]);
-                H2[3] = fmaf(c2, x.w, H2[3]);
-            }
-        }
         const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
         float *un = reinterpret_cast<float *>(I.ubuf[(k + 1) & 1]);
         const float *lo_k = I.ulo[0] ? reinterpret_cast<const float *>(I.ulo[k & 1]) : nullptr;
@@ -408,34 +472,69 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         const float *ua = nullptr;
         if (ADJ) ua = reinterpret_cast<const float *>(I.uadj) + (size_t)((I.adj_K - 1 - k) - I.uadj_r0) * I.N;
         if (j0 < I.N) {
+            // Every operand of the update is loaded before any is used, so that the loads of
+            // this step's critical path are in flight together: row k-1, u^k and its
+            // neighbours, the state's low part and (adjoint) u^r.
+            const float4 x1 = (hk >= 1) ? __ldcg(reinterpret_cast<const float4 *>(hrow(1))) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int pl = I.nx * I.ny;
+            float cu[V], nb[V][6], lw[V], ur[V];
+            unsigned inb[V];  // bit e: neighbour e inside the grid (r, l, up, dn, fw, bk)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int j = j0 + v;
+                const bool in = j < I.N;
+                const int x = j % I.nx, y = (I.ndim >= 2) ? (j / I.nx) % I.ny : 0, z = (I.ndim == 3) ? j / pl : 0;
+                unsigned m = 0;
+                if (in && x + 1 < I.nx) m |= 1u;
+                if (in && x > 0) m |= 2u;
+                if (in && I.ndim >= 2 && y + 1 < I.ny) m |= 4u;
+                if (in && I.ndim >= 2 && y > 0) m |= 8u;
+                if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
+                if (in && I.ndim == 3 && z > 0) m |= 32u;
+                inb[v] = m;
+                cu[v] = in ? __ldcg(uk + j) : 0.f;
+                nb[v][0] = (m & 1u) ? __ldcg(uk + j + 1) : 0.f;
+                nb[v][1] = (m & 2u) ? __ldcg(uk + j - 1) : 0.f;
+                nb[v][2] = (m & 4u) ? __ldcg(uk + j + I.nx) : 0.f;
+                nb[v][3] = (m & 8u) ? __ldcg(uk + j - I.nx) : 0.f;
+                nb[v][4] = (m & 16u) ? __ldcg(uk + j + pl) : 0.f;
+                nb[v][5] = (m & 32u) ? __ldcg(uk + j - pl) : 0.f;
+                lw[v] = (in && lo_k) ? __ldcg(lo_k + j) : 0.f;
+                ur[v] = (ADJ && in) ? __ldcg(ua + j) : 0.f;
+            }
+            if (hk >= 1) {  // lag 1 completes the memory sum
+                const float cc = psi[1];
+                H[0] = fmaf(cc, x1.x, H[0]);
+                H[1] = fmaf(cc, x1.y, H[1]);
+                H[2] = fmaf(cc, x1.z, H[2]);
+                H[3] = fmaf(cc, x1.w, H[3]);
+                if (ADJ) {
+                    const float c2 = dpsi[1];
+                    H2[0] = fmaf(c2, x1.x, H2[0]);
+                    H2[1] = fmaf(c2, x1.y, H2[1]);
+                    H2[2] = fmaf(c2, x1.z, H2[2]);
+                    H2[3] = fmaf(c2, x1.w, H2[3]);
+                }
+            }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const int j = j0 + v;
                 d[v] = 0.f;
                 if (j >= I.N) continue;
-                const float c = __ldcg(uk + j);
+                const float c = cu[v];
                 const float gh = mirror ? c : 0.f;
+                const unsigned m = inb[v];
+                const float r = (m & 1u) ? nb[v][0] : gh, l = (m & 2u) ? nb[v][1] : gh;
                 if (I.ndim == 1) {
-                    const float r = (j + 1 < I.N) ? __ldcg(uk + j + 1) : gh;
-                    const float l = (j > 0) ? __ldcg(uk + j - 1) : gh;
                     d[v] = r - 2.f * c + l;
-                } else if (I.ndim == 2) {
-                    const int x = j % I.nx, y = j / I.nx;
-                    const float r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : gh;
-                    const float l = (x > 0) ? __ldcg(uk + j - 1) : gh;
-                    const float up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : gh;
-                    const float dn = (y > 0) ? __ldcg(uk + j - I.nx) : gh;
-                    d[v] = r + l - 4.f * c + up + dn;
                 } else {
-                    const int pl = I.nx * I.ny;
-                    const int x = j % I.nx, y = (j / I.nx) % I.ny, z = j / pl;
-                    const float r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : gh;
-                    const float l = (x > 0) ? __ldcg(uk + j - 1) : gh;
-                    const float up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : gh;
-                    const float dn = (y > 0) ? __ldcg(uk + j - I.nx) : gh;
-                    const float fw = (z + 1 < I.nz) ? __ldcg(uk + j + pl) : gh;
-                    const float bk = (z > 0) ? __ldcg(uk + j - pl) : gh;
-                    d[v] = r + l - 6.f * c + up + dn + fw + bk;
+                    const float up = (m & 4u) ? nb[v][2] : gh, dn = (m & 8u) ? nb[v][3] : gh;
+                    if (I.ndim == 2) {
+                        d[v] = r + l - 4.f * c + up + dn;
+                    } else {
+                        const float fw = (m & 16u) ? nb[v][4] : gh, bk = (m & 32u) ? nb[v][5] : gh;
+                        d[v] = r + l - 6.f * c + up + dn + fw + bk;
+                    }
                 }
                 const float G = d[v] + H[v];  // psi_0 times the fresh row plus the memory sum
                 float inc;
@@ -444,21 +543,21 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     inc = dt * f + S * G;
                 } else {
                     // reverse-time recursion: lambda^r = lambda^{r+1} + dt f'(u^r) lambda^{r+1} + S G
-                    const float ur = __ldcg(ua + j);
-                    const float fp = q1 + ur * (2.f * q2 + ur * 3.f * q3);
+                    const float u_r = ur[v];
+                    const float fp = q1 + u_r * (2.f * q2 + u_r * 3.f * q3);
                     inc = dt * fp * c + S * G;
-                    dl[0] += (double)ur * (double)G;
-                    dl[1] += (double)ur * (double)H2[v];
+                    dl[0] += (double)u_r * (double)G;
+                    dl[1] += (double)u_r * (double)H2[v];
                     double pw = 1.0;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         dl[2 + i] += (double)c * pw;
-                        pw *= (double)ur;
+                        pw *= (double)u_r;
                     }
                 }
                 float nv;
                 if (lo_k) {
-                    const float y2 = inc + __ldcg(lo_k + j);
+                    const float y2 = inc + lw[v];
                     const float sum = c + y2;
                     const float bb = sum - c;
                     lo_n[j] = (c - (sum - bb)) + (y2 - bb);
@@ -497,7 +596,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             }
             // the block's last update for this tile resets the far count for block b+npar,
             // whose far units wait for this step before they count
-            if (last_of_block) I.arrive[par * I.T + tile] = 0u;
+            if (last_of_block) I.arrive[par * I.T + tile] = arrive_target(b + I.npar, 0);
             st_release(&I.done[tile], (unsigned)(rel + 1));
         }
     }

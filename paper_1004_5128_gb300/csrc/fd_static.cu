@@ -376,6 +376,7 @@ extern "C" int fd_run_static(const fd_problem *p_in, const void *u0, int nsteps,
     L.queue = (unsigned long long *)ctrl;
     L.err = (int *)(ctrl + 64);
     L.nonfinite = (unsigned *)(ctrl + 128);
+    L.err_info = (long long *)(ctrl + 192);
     L.timeout_ns = (long long)(p->timeout_ms ? p->timeout_ms : 10000) * 1000000LL;
 
     // the array keeps the previous call's contents: clear what must start at zero

@@ -116,6 +116,10 @@ class FRD:
     def status(self) -> int:
         return L.fd_get_status(self.h)
 
+    def error_info(self) -> dict:
+        """Where a device wait gave up after a timeout (site and raw words)."""
+        return L.fd_get_error_info(self.h)
+
     def geometry(self) -> dict:
         return L.fd_get_geometry(self.h)
 

@@ -110,3 +110,22 @@ def test_blocked_adjoint_rejects_blocks_of_16():
     with pytest.raises(L.FdError) as e:
         FRD(ragged(synth.BC_NOFLUX, synth.MEM_FULL), keep_tape=True, time_block=16)
     assert e.value.code == L.FD_ERR_UNSUPPORTED
+
+
+def test_blocked_adjoint_repeats_bitwise_at_config5_size():
+    """128^2, 4000 steps, checkpoints every 200 with the shipped adjoint geometry (blocks of 8,
+    128-thread tiles, 16-row stages, 128-row chunks): 40 launches per adjoint, each with
+    boundary units that the kernel passes over.  Five repetitions must all finish and agree
+    to the bit (fixed summation order)."""
+    p = synth.config5(K=4000)
+    geo = dict(time_block=8, tile_threads=128, stage_rows=16, chunk_terms=128)
+    runs = []
+    for _ in range(5):
+        s = FRD(p, keep_tape=True, ckpt_every=200, timeout_ms=5000, **geo)
+        s.set_state(p["u0"])
+        uK = s.run(p["K"])
+        r = s.adjoint(uK * 0.01)
+        runs.append((r["dgamma"], r["dalpha"], r["du0"].cpu().numpy()))
+        s.close()
+    for dg, da, du in runs[1:]:
+        assert dg == runs[0][0] and da == runs[0][1] and np.array_equal(du, runs[0][2])
