@@ -452,7 +452,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     if (w <= 0) ok = 0;
                 }
             if (tid == 0 && ok && I.stall && rel == 0 && tile == 0)
-                if (!wait_counter(&I.done[tile], 0x80000000u, L)) ok = 0;
+                {  // fault injection: nothing ever raises a step counter to 2^31
+                    const int w = wait_until(&I.done[tile], 0x80000000u, L, 512);
+                    if (w < 0) note_failure(L, 9, k, tile, 0x80000000ll, ld_acquire(&I.done[tile]), L.k0, 0);
+                    if (w <= 0) ok = 0;
+                }
             ok = __all_sync(0xffffffffu, ok);
             if (tid == 0) s_ok2 = ok;
         }

@@ -129,3 +129,20 @@ def test_blocked_adjoint_repeats_bitwise_at_config5_size():
         s.close()
     for dg, da, du in runs[1:]:
         assert dg == runs[0][0] and da == runs[0][1] and np.array_equal(du, runs[0][2])
+
+
+def test_blocked_stall_injection_reports_its_site():
+    """A wait nothing will satisfy ends the blocked launch with FD_ERR_TIMEOUT, the error record
+    names the wait, and the next handle runs normally."""
+    from paper_1004_5128_gb300 import _lib as L
+    p = ragged(synth.BC_NOFLUX, synth.MEM_FULL, K=40)
+    s = FRD(p, time_block=8, inject_stall=True, timeout_ms=200)
+    s.set_state(p["u0"])
+    with pytest.raises(L.FdError) as e:
+        s.run(p["K"])
+    assert e.value.code == L.FD_ERR_TIMEOUT
+    assert s.error_info()["site"] == "injected stall"
+    s.close()
+    t = FRD(p, time_block=8)
+    t.set_state(p["u0"])
+    assert rel_inf(t.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5

@@ -124,6 +124,8 @@ def test_stall_injection_times_out_and_gpu_stays_usable():
     with pytest.raises(FdError) as e:
         s.run(20)
     assert e.value.code == L.FD_ERR_TIMEOUT
+    info = s.error_info()
+    assert info["site"] == "injected stall" and info["words"][2] == 0  # tile 0
     with pytest.raises(FdError) as e:
         s.step(1)
     assert e.value.code == L.FD_ERR_STATE
