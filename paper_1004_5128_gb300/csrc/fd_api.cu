@@ -216,6 +216,14 @@ inline size_t smem_bytes(const Geo &g, int rmax)
     return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)rmax * (2 * g.sa + 4) + 32 + 8 * (size_t)g.NS;
 }
 
+// Blocked kernel: stage ring, four shifted copies of each coefficient window (psi, and psi'
+// for the adjoint), barriers.
+inline size_t smem_bytes_tb(const Geo &g, int rmax)
+{
+    return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)g.planes * 4 * ((rmax + g.tb + 7) & ~3) * 4 + 32 +
+           8 * (size_t)g.NS;
+}
+
 int device_sms()
 {
     int dev = 0, sms = 0;
@@ -295,10 +303,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = g.hring_sep ? g.head + 1 : g.cap;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    // blocked: stage ring, four shifted copies of each coefficient window, barriers
-    g.smem = g.tb ? (size_t)g.NS * g.RS * g.threads * 16 + (size_t)g.planes * 4 * ((g.R + g.tb + 7) & ~3) * 4 + 32 +
-                        8 * (size_t)g.NS
-                  : smem_bytes(g, g.R);
+    g.smem = g.tb ? smem_bytes_tb(g, g.R) : smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -319,6 +324,24 @@ inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
         far = (int64_t)g.T * std::max<int64_t>(1, (hi - lo + g.R - 1) / g.R);
     }
     return far + (b >= 1 ? (int64_t)g.T * g.tb : 0);
+}
+
+// History rows the blocked kernel reads over max_steps steps: the far rows once per block, then
+// every step's head rows (lags 1 .. min(k - kb + tb, n(k))).
+int64_t blocked_stream_rows(const fd_problem &p, const Geo &g)
+{
+    const int tb = g.tb;
+    int64_t st = 0;
+    for (int64_t b = 0; b < g.nblocks; ++b) {
+        int64_t lo, hi;
+        block_rows(p, tb, b, lo, hi);
+        st += hi - lo;
+    }
+    for (int64_t k = 0; k < p.max_steps; ++k) {
+        const int64_t nb = (p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(p.mem_L, k) : k;
+        st += std::min<int64_t>(k - (k / tb) * tb + tb, nb);
+    }
+    return st;
 }
 
 // Device-side layout of one instance inside the workspace.
@@ -478,6 +501,7 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.tb = g.tb;
     I.mem_mode = p.mem_mode;
     I.mem_L = p.mem_L;
+    I.ksteps = p.max_steps;
     I.npar = kNpar;
     I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
     I.tape_every = 1;
@@ -944,21 +968,7 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)h->s.step.size()) * N;
     g->time_block = h->g.tb;
-    g->stream_rows_total = rows;
-    if (h->g.tb) {
-        const int tb = h->g.tb;
-        int64_t st = 0;
-        for (int64_t b = 0; b < h->g.nblocks; ++b) {
-            int64_t lo, hi;
-            block_rows(h->p, tb, b, lo, hi);
-            st += hi - lo;
-        }
-        for (int64_t k = 0; k < h->p.max_steps; ++k) {
-            const int64_t nb = (h->p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(h->p.mem_L, k) : k;
-            st += std::min<int64_t>(k - (k / tb) * tb + tb, nb);
-        }
-        g->stream_rows_total = st;
-    }
+    g->stream_rows_total = h->g.tb ? blocked_stream_rows(h->p, h->g) : rows;
     return FD_OK;
 }
 
@@ -1005,7 +1015,7 @@ struct fd_batch {
     std::vector<long long> goff;
     std::vector<int2> ginfo;
     const void *kfn;
-    int threads, RS, NS, grid, rmax;
+    int threads, RS, NS, grid, rmax, tb;
     size_t smem;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -1027,7 +1037,8 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
             probs[i].accum_dtype != probs[0].accum_dtype ||
             ((probs[i].flags ^ probs[0].flags) & (FD_FLAG_KAHAN | FD_FLAG_KEEP_TAPE)))
             return FD_ERR_INVALID_ARG;
-        if ((probs[i].flags & FD_FLAG_KEEP_TAPE) || probs[i].time_block) return FD_ERR_UNSUPPORTED;
+        if (probs[i].flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
+        if (probs[i].time_block != probs[0].time_block) return FD_ERR_INVALID_ARG;  // one kernel per batch
     }
     b.p.assign(probs, probs + count);
     b.s.resize(count);
@@ -1045,7 +1056,8 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     b.NS = b.g[0].NS;
     b.rmax = 0;
     for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].R);
-    b.smem = smem_bytes(b.g[0], b.rmax);
+    b.tb = probs[0].time_block;
+    b.smem = b.tb ? smem_bytes_tb(b.g[0], b.rmax) : smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
     b.ctrl = carve_ctrl(c);
     b.counter_bytes = sizeof(unsigned) * (kNpar + 1) * (size_t)tiles;
@@ -1056,19 +1068,33 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
         carve_instance(c, probs[i], b.g[i], b.s[i], b.L[i], cnt, true);
         toff += (kNpar + 1) * (int64_t)b.g[i].T;
     }
-    // groups: step-major, then instance
-    int maxK = 0;
-    for (int i = 0; i < count; ++i) maxK = std::max(maxK, probs[i].max_steps);
+    // groups: step-major (per-step kernel) or block-major (blocked kernel: group b of an
+    // instance holds its block b's far units and block b-1's updates), then instance
+    int maxK = 0, maxB = 0;
+    for (int i = 0; i < count; ++i) {
+        maxK = std::max(maxK, probs[i].max_steps);
+        maxB = std::max(maxB, b.g[i].nblocks);
+    }
     b.goff.clear();
     b.ginfo.clear();
     long long acc = 0;
-    for (int k = 0; k < maxK; ++k)
-        for (int i = 0; i < count; ++i) {
-            if (k >= probs[i].max_steps) continue;
-            b.goff.push_back(acc);
-            b.ginfo.push_back(make_int2(i, k));
-            acc += step_units(b.g[i], b.s[i].step[k]);
-        }
+    if (b.tb) {
+        for (int k = 0; k <= maxB; ++k)
+            for (int i = 0; i < count; ++i) {
+                if (k > b.g[i].nblocks) continue;
+                b.goff.push_back(acc);
+                b.ginfo.push_back(make_int2(i, k));
+                acc += block_units(probs[i], b.g[i], k);
+            }
+    } else {
+        for (int k = 0; k < maxK; ++k)
+            for (int i = 0; i < count; ++i) {
+                if (k >= probs[i].max_steps) continue;
+                b.goff.push_back(acc);
+                b.ginfo.push_back(make_int2(i, k));
+                acc += step_units(b.g[i], b.s[i].step[k]);
+            }
+    }
     b.goff.push_back(acc);
     b.ginfo.push_back(make_int2(0, 0));
     b.d_inst = (Inst *)c.take(sizeof(Inst) * (size_t)count);
@@ -1110,8 +1136,10 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
     b->ws = (char *)workspace;
     b->st = (cudaStream_t)cuda_stream;
     const bool kahan = b->p[0].flags & FD_FLAG_KAHAN;
-    b->kfn = fdk::kernel_for(b->p[0].state_dtype, b->p[0].hist_dtype, b->p[0].accum_dtype, kahan, false);
+    b->kfn = b->tb ? fdk::kernel_tb(b->tb)
+                   : fdk::kernel_for(b->p[0].state_dtype, b->p[0].hist_dtype, b->p[0].accum_dtype, kahan, false);
     Geo g0 = b->g[0];
+    g0.smem = b->smem;  // the launch's shared memory: the largest chunk over the instances
     rc = set_smem_attr(b->kfn, b->smem);
     if (!rc) rc = resolve_grid(b->kfn, g0);
     b->grid = g0.grid;
@@ -1145,6 +1173,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         L.g_begin = 0;
         L.g_end = (int)b->goff.size() - 1;
         L.k0 = 0;
+        L.k_end = 0x7fffffff;  // blocked kernel: each instance stops at its own step count
         L.stage_rows = b->RS;
         L.stages = b->NS;
         L.rmax = b->rmax;
@@ -1243,12 +1272,16 @@ int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g)
         units += step_units(q, e);
         rows += n_terms(e);
     }
+    if (q.tb) {
+        units = 0;
+        for (int64_t k = 0; k <= q.nblocks; ++k) units += block_units(b->p[i], q, k);
+    }
     const int64_t N = (int64_t)b->p[i].nx * b->p[i].ny * b->p[i].nz;
     g->units_total = units;
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)b->s[i].step.size()) * N;
-    g->stream_rows_total = rows;
-    g->time_block = 0;
+    g->stream_rows_total = q.tb ? blocked_stream_rows(b->p[i], q) : rows;
+    g->time_block = q.tb;
     return FD_OK;
 }
 

@@ -36,6 +36,15 @@ struct UnitTB {
     int k;
 };
 
+// Far chunks of block b of an instance: its far rows [rlo, rhi), in chunks of R, at least one.
+template <int TB> __device__ __forceinline__ int far_chunks(const Inst &I, int b)
+{
+    const int kb = b * TB;
+    const int rhi = max(0, kb - TB);
+    const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
+    return max(1, (rhi - rlo + I.R - 1) / I.R);
+}
+
 template <int TB, bool ADJ>
 __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 {
@@ -98,6 +107,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 }
                 const long long local = u - L.g_off[g];
                 const int gb = gi.y;  // group: far units of block gb, updates of block gb-1
+                const int k_end = min(L.k_end, I.ksteps);  // a batch runs each instance to its end
                 const int Tu = (gb >= 1) ? I.T : 0;
                 const long long F = (L.g_off[g + 1] - L.g_off[g]) - (long long)TB * Tu;
                 int sseg = 0;  // segment s: far slice s, then the Tu update units of step s
@@ -108,23 +118,23 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 U.inst = gi.x;
                 if (off >= fsn) {  // update unit: block gb-1, step s
                     const int k = (gb - 1) * TB + sseg;
-                    if (k < L.k0 || k >= L.k_end) continue;  // block edge outside this launch
+                    if (k < L.k0 || k >= k_end) continue;  // block edge outside this launch
                     U.fix = 1;
                     U.b = gb - 1;
                     U.tile = (int)(off - fsn);
                     U.k = k;
-                    U.C = (int)(((L.g_off[g] - L.g_off[g - 1]) - (long long)TB * (gb >= 2 ? I.T : 0)) / I.T);
+                    U.C = far_chunks<TB>(I, gb - 1);
                     U.chunk = 0;
                     U.r0 = U.r1 = 0;
                 } else {  // far unit of block gb
                     const int kb = gb * TB;
-                    if (kb >= L.k_end) continue;  // block starts at or after the launch's end
+                    if (kb >= k_end) continue;  // block starts at or after the launch's end
                     const long long f = fs0 + off;
                     const int rhi = max(0, kb - TB);
                     const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
                     U.fix = 0;
                     U.b = gb;
-                    U.C = (int)(F / I.T);
+                    U.C = far_chunks<TB>(I, gb);
                     U.tile = (int)(f % I.T);
                     U.chunk = (int)(f / I.T);
                     U.r0 = min(rhi, rlo + U.chunk * I.R);
@@ -149,10 +159,10 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         const int tile = U.tile, C = U.C, b = U.b, kb = b * TB;
         const int par = b % I.npar;
         // Arrival counters carry the block's generation within its parity in the high half
-        // ((b - first block of the launch) / npar), so a count left by block b - npar can never
+        // ((b - the launch's first block k0/TB) / npar), so a count left by block b - npar can never
         // satisfy block b's wait; the last update of block b sets the word for block b + npar.
         auto arrive_target = [&](int bb, int count) -> unsigned {
-            return ((unsigned)((bb - L.g_begin) / I.npar) << 16) + (unsigned)count;
+            return ((unsigned)((bb - L.k0 / TB) / I.npar) << 16) + (unsigned)count;
         };
         const int j0 = tile * I.P + tid * V;
         auto prow = [&](int c, int t, int plane) -> float * {
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         // ================================================== update unit: step k, this tile
         const int k = U.k, t = k - kb;
         const int rel = k - L.k0;
-        const bool last_of_block = (k == min(kb + TB, L.k_end) - 1);
+        const bool last_of_block = (k == min(kb + TB, min(L.k_end, I.ksteps)) - 1);
         // Two phases keep the partial and head sums off the step-to-step chain.  Phase A needs
         // only the tile's far count and this tile's rows up to k-2 (its own step k-2), so it
         // runs while step k-1 is still being updated; phase B waits for u^k on the halo tiles

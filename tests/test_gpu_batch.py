@@ -75,3 +75,36 @@ def test_config4_full_batch_sampled_vs_oracle(mode):
     for i in np.argsort(cost)[:3]:
         assert rel_inf(out[i], oracle.run(probs[i])) < 1e-5
     assert all(np.all(np.isfinite(o)) for o in out)
+
+
+@pytest.mark.parametrize("tb", [4, 8, 16])
+@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_SHORT])
+def test_small_uneven_blocked_batch_vs_oracle(tb, mode):
+    """The temporally blocked kernel over a batch of uneven 1-D/2-D instances with their own
+    step counts (not multiples of the block), chunk sizes and short windows."""
+    probs = synth.config4(count=10, steps_range=(50, 300), side_range=(9, 60), n1_range=(5, 2000))
+    if mode == synth.MEM_SHORT:
+        probs = [synth.with_mode(p, synth.MEM_SHORT, L=7 + 13 * i) for i, p in enumerate(probs)]
+    out, b = run_batch(probs, chunk_terms=24, time_block=tb)
+    assert b.geometry(0)["time_block"] == tb
+    for p, got in zip(probs, out):
+        assert rel_inf(got, oracle.run(p)) < 1e-5
+
+
+def test_blocked_batch_equals_single_blocked_runs_bitwise():
+    """Same blocks, chunks and summation order as one instance per launch."""
+    probs = synth.config4(count=6, steps_range=(100, 300), side_range=(20, 50), n1_range=(40, 900))
+    b = FRDBatch(probs, chunk_terms=32, time_block=8)
+    res = []
+    for _ in range(2):
+        for i, p in enumerate(probs):
+            b.set_state(i, p["u0"])
+        b.run()
+        res.append([b.state(i).cpu().numpy() for i in range(len(probs))])
+        assert b.status() == 0
+    for x, y in zip(*res):
+        assert np.array_equal(x, y)
+    for p, x in zip(probs, res[0]):
+        s = FRD(p, chunk_terms=32, tile_threads=256, time_block=8)
+        s.set_state(p["u0"])
+        assert np.array_equal(s.run(p["K"]).cpu().numpy(), x)

@@ -133,3 +133,17 @@ def test_time_block_validation():
     with pytest.raises(L.FdError) as e:
         L.fd_workspace_bytes(make_problem(synth.with_mode(p, synth.MEM_ADAPTIVE, a=10), time_block=8))
     assert e.value.code == L.FD_ERR_UNSUPPORTED
+
+
+def test_blocked_batch_validation():
+    """A batch runs one kernel: every instance takes the same time_block."""
+    probs = synth.config4(count=4, steps_range=(50, 90), side_range=(9, 20), n1_range=(5, 50))
+    same = [make_problem(p, time_block=8) for p in probs]
+    assert L.fd_batch_workspace_bytes(same) > L.fd_batch_workspace_bytes([make_problem(p) for p in probs])
+    mixed = [make_problem(p, time_block=8 if i else 4) for i, p in enumerate(probs)]
+    with pytest.raises(L.FdError) as e:
+        L.fd_batch_workspace_bytes(mixed)
+    assert e.value.code == L.FD_ERR_INVALID_ARG
+    with pytest.raises(L.FdError) as e:
+        L.fd_batch_workspace_bytes([make_problem(p, time_block=8, keep_tape=True) for p in probs])
+    assert e.value.code == L.FD_ERR_UNSUPPORTED
