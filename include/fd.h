@@ -63,6 +63,8 @@ enum { FD_F64 = 0, FD_F32 = 1, FD_BF16 = 2, FD_F16 = 3 };
 #define FD_FLAG_INJECT_STALL 8u    /* fault injection: the first tile's first update waits on a
                                       counter nothing advances, so the wait times out and the
                                       launch ends with FD_ERR_TIMEOUT (GPU stays usable) */
+#define FD_FLAG_STEP_UPDATES 32u   /* time_block: one update unit per step and tile even where
+                                      block-long update units would fit (see time_block) */
 
 typedef struct fd_problem {
     int ndim;            /* 1, 2 or 3 (3-D: the 7-point analogue of eq. deltasimp) */
@@ -96,11 +98,15 @@ typedef struct fd_problem {
                             state precision (0 = 8 for F32/F64 history, 32 for BF16/F16) */
     int nz;              /* points along the third axis when ndim == 3, else 1 */
     int time_block;      /* 0, or 4 / 8 / 16: temporally blocked sum (F32 state, history and
-                            accumulation, full or short memory, no Kahan, no tape).  Rows older
-                            than the current block of time_block steps are read once per block
-                            into time_block accumulators (the Toeplitz structure of eq.
-                            frac_norxn); the newest rows are summed per step.  Same terms,
-                            grouped differently; history traffic drops by about time_block. */
+                            accumulation, full or short memory, no Kahan; with FD_FLAG_KEEP_TAPE
+                            4 or 8).  Rows older than the current block of time_block steps are
+                            read once per block into time_block accumulators (the Toeplitz
+                            structure of eq. frac_norxn); the newest rows are summed per step.
+                            Same terms, grouped differently; history traffic drops by about
+                            time_block.  When the tiles are few against the grid (at most a
+                            quarter of its CTAs), one unit per tile carries a whole block's
+                            updates and keeps the block's newest rows in on-chip memory, unless
+                            FD_FLAG_STEP_UPDATES is set. */
 } fd_problem;
 
 typedef struct fd_handle fd_handle;
@@ -184,6 +190,7 @@ typedef struct fd_geometry {
                                   to hist_rows_total per step; with time_block, far rows once per
                                   block plus every step's newest (head) rows */
     int time_block;
+    int block_updates;       /* time_block: 1 when one unit per tile carries a whole block's updates */
 } fd_geometry;
 int fd_get_geometry(fd_handle *h, fd_geometry *g);
 

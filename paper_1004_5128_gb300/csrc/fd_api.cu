@@ -199,6 +199,9 @@ struct Geo {
     int threads, V, P, T, R, RS, NS, ctas, grid, maxC;
     int head;        // lags summed by the fixup
     int tb;          // temporal block (0: per-step kernel)
+    int ub;          // blocked: one update unit per (block, tile)
+    int cmax;        // blocked: most far chunks per block (0: chunks of R rows)
+    int rwin;        // blocked: largest far chunk (rows), the coefficient window's length
     int nblocks;     // blocks of tb steps covering max_steps
     int hring_sep;   // separate state-precision head ring
     int hring_cap;
@@ -216,11 +219,13 @@ inline size_t smem_bytes(const Geo &g, int rmax)
     return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)rmax * (2 * g.sa + 4) + 32 + 8 * (size_t)g.NS;
 }
 
-// Blocked kernel: stage ring, four shifted copies of each coefficient window (psi, and psi'
-// for the adjoint), barriers.
-inline size_t smem_bytes_tb(const Geo &g, int rmax)
+// Blocked kernel: stage ring (block-long update units keep their steps' memory sums there, so it
+// holds at least tb x planes rows, as the kernel assumes), four shifted copies of each coefficient window (psi, and
+// psi' for the adjoint), barriers.
+inline size_t smem_bytes_tb(const Geo &g, int rwin)
 {
-    return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)g.planes * 4 * ((rmax + g.tb + 7) & ~3) * 4 + 32 +
+    const int ring = std::max(g.NS * g.RS, g.tb * g.planes);
+    return (size_t)ring * g.threads * 16 + (size_t)g.planes * 4 * ((rwin + g.tb + 7) & ~3) * 4 + 32 +
            8 * (size_t)g.NS;
 }
 
@@ -240,6 +245,18 @@ inline void block_rows(const fd_problem &p, int tb, int64_t b, int64_t &rlo, int
     rhi = std::max<int64_t>(0, kb - tb);
     rlo = (p.mem_mode == FD_MEM_SHORT) ? std::max<int64_t>(0, kb - p.mem_L) : 0;
     rlo = std::min(rlo, rhi);
+}
+
+// Far chunking of block b: chunks of R rows, or, with cmax, of max(R, ceil(rows / cmax)) rows,
+// so that a block-long update unit sums at most cmax partial rows per step.
+inline void block_chunks(const fd_problem &p, const Geo &g, int64_t b, int64_t &Rb, int64_t &Cb)
+{
+    int64_t lo, hi;
+    block_rows(p, g.tb, b, lo, hi);
+    const int64_t rows = hi - lo;
+    Rb = g.R;
+    if (g.cmax) Rb = std::max<int64_t>(Rb, (rows + g.cmax - 1) / g.cmax);
+    Cb = std::max<int64_t>(1, (rows + Rb - 1) / Rb);
 }
 
 void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
@@ -285,6 +302,9 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.maxC = (int)std::max<int64_t>(1, (nmax + g.R - 1) / g.R);
     g.tb = p.time_block;
     g.nblocks = g.tb ? (p.max_steps + g.tb - 1) / g.tb : 0;
+    g.ub = 0;
+    g.cmax = 0;
+    g.rwin = g.R;
     if (g.tb) {
         int64_t rmax = 0;
         for (int64_t b = 0; b < g.nblocks; ++b) {
@@ -297,13 +317,25 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
             r = std::min<int64_t>(std::max<int64_t>(r, 2 * g.RS), 512);
             g.R = (int)((r + g.RS - 1) / g.RS * g.RS);
         }
-        g.maxC = (int)std::max<int64_t>(1, (rmax + g.R - 1) / g.R);
+        // Block-long update units need every tile's unit resident at once: allow them when the
+        // tiles are at most a quarter of the SMs, so at least three quarters keep streaming.
+        g.ub = !(p.flags & FD_FLAG_STEP_UPDATES) && (int64_t)g.T * 4 <= sms;
+        g.cmax = g.ub ? std::max(1, 128 / g.tb) : 0;
+        int64_t cmaxb = 1, rwin = g.R;
+        for (int64_t b = 0; b < g.nblocks; ++b) {
+            int64_t Rb, Cb;
+            block_chunks(p, g, b, Rb, Cb);
+            cmaxb = std::max(cmaxb, Cb);
+            rwin = std::max(rwin, Rb);
+        }
+        g.maxC = (int)cmaxb;
+        g.rwin = (int)rwin;
     }
     g.pitch = (int64_t)align_up((size_t)N * g.sh, kAlign);
     g.hring_cap = g.hring_sep ? g.head + 1 : g.cap;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = g.tb ? smem_bytes_tb(g, g.R) : smem_bytes(g, g.R);
+    g.smem = g.tb ? smem_bytes_tb(g, g.rwin) : smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -314,20 +346,21 @@ inline int64_t step_units(const Geo &g, const int4 &e)
 }
 
 // Units of group b of the blocked kernel: the far chunks of block b (none past the last block)
-// plus the update units (one per step and tile) of block b-1.
+// plus block b-1's update units (one per step and tile, or one per tile for the whole block).
 inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
 {
     int64_t far = 0;
     if (b < g.nblocks) {
-        int64_t lo, hi;
-        block_rows(p, g.tb, b, lo, hi);
-        far = (int64_t)g.T * std::max<int64_t>(1, (hi - lo + g.R - 1) / g.R);
+        int64_t Rb, Cb;
+        block_chunks(p, g, b, Rb, Cb);
+        far = (int64_t)g.T * Cb;
     }
-    return far + (b >= 1 ? (int64_t)g.T * g.tb : 0);
+    return far + (b >= 1 ? (int64_t)g.T * (g.ub ? 1 : g.tb) : 0);
 }
 
 // History rows the blocked kernel reads over max_steps steps: the far rows once per block, then
-// every step's head rows (lags 1 .. min(k - kb + tb, n(k))).
+// every step's head rows (lags 1 .. min(k - kb + tb, n(k))), or, with block-long update units,
+// the previous block's rows once per block.
 int64_t blocked_stream_rows(const fd_problem &p, const Geo &g)
 {
     const int tb = g.tb;
@@ -336,7 +369,10 @@ int64_t blocked_stream_rows(const fd_problem &p, const Geo &g)
         int64_t lo, hi;
         block_rows(p, tb, b, lo, hi);
         st += hi - lo;
+        // block-long update units read the previous block's rows once; later rows stay on chip
+        if (g.ub) st += std::min<int64_t>(tb, b * tb);
     }
+    if (g.ub) return st;
     for (int64_t k = 0; k < p.max_steps; ++k) {
         const int64_t nb = (p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(p.mem_L, k) : k;
         st += std::min<int64_t>(k - (k / tb) * tb + tb, nb);
@@ -502,6 +538,8 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.mem_mode = p.mem_mode;
     I.mem_L = p.mem_L;
     I.ksteps = p.max_steps;
+    I.ub = g.ub;
+    I.cmax = g.cmax;
     I.npar = kNpar;
     I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
     I.tape_every = 1;
@@ -623,7 +661,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.k_end = k_end;
     L.stage_rows = h->g.RS;
     L.stages = h->g.NS;
-    L.rmax = h->g.R;
+    L.rmax = h->g.tb ? h->g.rwin : h->g.R;
     L.queue = h->ctrl.queue;
     L.err = h->ctrl.err;
     L.nonfinite = h->ctrl.nonfinite;
@@ -968,6 +1006,7 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)h->s.step.size()) * N;
     g->time_block = h->g.tb;
+    g->block_updates = h->g.ub;
     g->stream_rows_total = h->g.tb ? blocked_stream_rows(h->p, h->g) : rows;
     return FD_OK;
 }
@@ -1055,7 +1094,7 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     b.RS = b.g[0].RS;
     b.NS = b.g[0].NS;
     b.rmax = 0;
-    for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].R);
+    for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].tb ? b.g[i].rwin : b.g[i].R);
     b.tb = probs[0].time_block;
     b.smem = b.tb ? smem_bytes_tb(b.g[0], b.rmax) : smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
@@ -1282,6 +1321,7 @@ int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g)
     g->terms_total = (rows + (int64_t)b->s[i].step.size()) * N;
     g->stream_rows_total = q.tb ? blocked_stream_rows(b->p[i], q) : rows;
     g->time_block = q.tb;
+    g->block_updates = q.ub;
     return FD_OK;
 }
 

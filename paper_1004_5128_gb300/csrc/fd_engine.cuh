@@ -59,6 +59,8 @@ struct Inst {
     int tb;                  // temporal block (steps per block) of the blocked kernel, else 0
     int mem_mode, mem_L;     // memory mode and short window (blocked kernel)
     int ksteps;              // steps the instance runs (its max_steps); bounds a batch launch
+    int ub;                  // blocked kernel: 1 = one update unit per (block, tile)
+    int cmax;                // blocked kernel: most far chunks per block (0 = no limit)
     int tape_k0, tape_every, tape_rows;
     int adj_K, uadj_r0;      // adjoint: u^r is row (adj_K-1-k) - uadj_r0 of uadj
     double S, dt;

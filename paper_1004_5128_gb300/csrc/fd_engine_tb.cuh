@@ -36,13 +36,29 @@ struct UnitTB {
     int k;
 };
 
-// Far chunks of block b of an instance: its far rows [rlo, rhi), in chunks of R, at least one.
-template <int TB> __device__ __forceinline__ int far_chunks(const Inst &I, int b)
+// Far rows [rlo, rhi) of block b: rows older than the previous block, within the short window.
+template <int TB> __device__ __forceinline__ void far_rows(const Inst &I, int b, int &rlo, int &rhi)
 {
     const int kb = b * TB;
-    const int rhi = max(0, kb - TB);
-    const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
-    return max(1, (rhi - rlo + I.R - 1) / I.R);
+    rhi = max(0, kb - TB);
+    rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
+}
+
+// Rows per far chunk of block b: R, or enough that the block has at most cmax chunks.
+template <int TB> __device__ __forceinline__ int block_R(const Inst &I, int b)
+{
+    int rlo, rhi;
+    far_rows<TB>(I, b, rlo, rhi);
+    return I.cmax ? max(I.R, (rhi - rlo + I.cmax - 1) / I.cmax) : I.R;
+}
+
+// Far chunks of block b (at least one).
+template <int TB> __device__ __forceinline__ int far_chunks(const Inst &I, int b)
+{
+    int rlo, rhi;
+    far_rows<TB>(I, b, rlo, rhi);
+    const int Rb = block_R<TB>(I, b);
+    return max(1, (rhi - rlo + Rb - 1) / Rb);
 }
 
 template <int TB, bool ADJ>
@@ -60,7 +76,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // Coefficient window in four copies shifted by 0..3 elements, so that the TB coefficients
     // of any row are TB/4 aligned 16-byte loads: copy q holds w[i + q] at index i.
     const int WS = (L.rmax + TB + 7) & ~3;                                          // copy stride
-    float *psw = reinterpret_cast<float *>(smem + (size_t)NS * RS * row_bytes);  // psi window
+    // the stage ring also holds a block-long update unit's sums: at least TB x PLANES rows
+    const int ring_rows = max(NS * RS, TB * PLANES);
+    float *psw = reinterpret_cast<float *>(smem + (size_t)ring_rows * row_bytes);  // psi window
     float *psw2 = psw + 4 * WS;                                                    // psi' window (ADJ)
     uint64_t *bars = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(psw + PLANES * 4 * WS) + 15) & ~uintptr_t(15));
@@ -82,8 +100,6 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     int ghint = L.g_begin;
     const long long u_base = L.g_off[L.g_begin];
     const long long u_end = L.g_off[L.g_end];
-    unsigned long long next = 0;
-    if (tid == 0) next = atomicAdd(L.queue, 1ull);
 
     for (;;) {
         // ---------------------------------------------------------------- claim
@@ -94,10 +110,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         if (tid == 0) {
             int ok = 0;
             for (;;) {
-                const long long u = u_base + (long long)next;
+                // claimed when needed, never ahead: a CTA waiting inside a block-long update unit
+                // must not hold an unstarted unit that its neighbours' units wait for
+                const long long u = u_base + (long long)atomicAdd(L.queue, 1ull);
                 ok = (u < u_end) && (ld_volatile(L.err) == ERR_NONE);
                 if (!ok) break;
-                next = atomicAdd(L.queue, 1ull);
                 const int g = find_group(L.g_off, ghint, L.g_end, u);
                 ghint = g;
                 const int2 gi = L.g_info[g];
@@ -108,37 +125,60 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const long long local = u - L.g_off[g];
                 const int gb = gi.y;  // group: far units of block gb, updates of block gb-1
                 const int k_end = min(L.k_end, I.ksteps);  // a batch runs each instance to its end
-                const int Tu = (gb >= 1) ? I.T : 0;
-                const long long F = (L.g_off[g + 1] - L.g_off[g]) - (long long)TB * Tu;
-                int sseg = 0;  // segment s: far slice s, then the Tu update units of step s
-                while (sseg + 1 < TB && (long long)(sseg + 1) * Tu + (long long)(sseg + 1) * F / TB <= local) ++sseg;
-                const long long fs0 = (long long)sseg * F / TB;
-                const long long fsn = (long long)(sseg + 1) * F / TB - fs0;  // far units in slice s
-                const long long off = local - ((long long)sseg * Tu + fs0);
+                const int Tu = (gb >= 1) ? I.T * (I.ub ? 1 : TB) : 0;  // block gb-1's update units
+                const long long F = (L.g_off[g + 1] - L.g_off[g]) - (long long)Tu;  // block gb's far units
+                long long f = -1;  // far unit index within block gb, or -1 for an update unit
                 U.inst = gi.x;
-                if (off >= fsn) {  // update unit: block gb-1, step s
-                    const int k = (gb - 1) * TB + sseg;
-                    if (k < L.k0 || k >= k_end) continue;  // block edge outside this launch
-                    U.fix = 1;
-                    U.b = gb - 1;
-                    U.tile = (int)(off - fsn);
-                    U.k = k;
-                    U.C = far_chunks<TB>(I, gb - 1);
-                    U.chunk = 0;
-                    U.r0 = U.r1 = 0;
-                } else {  // far unit of block gb
+                if (I.ub) {
+                    // block-long update units first, so block gb-1's steps start as soon as its
+                    // far units have all arrived; then block gb's far units
+                    if (local < Tu) {
+                        const int kb1 = (gb - 1) * TB;
+                        if (max(kb1, L.k0) >= min(kb1 + TB, k_end)) continue;  // no step in this launch
+                        U.fix = 2;
+                        U.b = gb - 1;
+                        U.tile = (int)local;
+                        U.k = 0;
+                        U.C = far_chunks<TB>(I, gb - 1);
+                        U.chunk = 0;
+                        U.r0 = U.r1 = 0;
+                    } else {
+                        f = local - Tu;
+                    }
+                } else {
+                    int sseg = 0;  // segment s: far slice s, then the T update units of step s
+                    const int Ts = Tu / TB;
+                    while (sseg + 1 < TB && (long long)(sseg + 1) * Ts + (long long)(sseg + 1) * F / TB <= local) ++sseg;
+                    const long long fs0 = (long long)sseg * F / TB;
+                    const long long fsn = (long long)(sseg + 1) * F / TB - fs0;  // far units in slice s
+                    const long long off = local - ((long long)sseg * Ts + fs0);
+                    if (off >= fsn) {  // update unit: block gb-1, step s
+                        const int k = (gb - 1) * TB + sseg;
+                        if (k < L.k0 || k >= k_end) continue;  // block edge outside this launch
+                        U.fix = 1;
+                        U.b = gb - 1;
+                        U.tile = (int)(off - fsn);
+                        U.k = k;
+                        U.C = far_chunks<TB>(I, gb - 1);
+                        U.chunk = 0;
+                        U.r0 = U.r1 = 0;
+                    } else {
+                        f = fs0 + off;
+                    }
+                }
+                if (f >= 0) {  // far unit of block gb
                     const int kb = gb * TB;
                     if (kb >= k_end) continue;  // block starts at or after the launch's end
-                    const long long f = fs0 + off;
-                    const int rhi = max(0, kb - TB);
-                    const int rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
+                    int rlo, rhi;
+                    far_rows<TB>(I, gb, rlo, rhi);
+                    const int Rb = block_R<TB>(I, gb);
                     U.fix = 0;
                     U.b = gb;
                     U.C = far_chunks<TB>(I, gb);
                     U.tile = (int)(f % I.T);
                     U.chunk = (int)(f / I.T);
-                    U.r0 = min(rhi, rlo + U.chunk * I.R);
-                    U.r1 = min(rhi, U.r0 + I.R);
+                    U.r0 = min(rhi, rlo + U.chunk * Rb);
+                    U.r1 = min(rhi, U.r0 + Rb);
                     U.k = 0;
                     // far rows up to r1-1 written; partial rows of block b-npar consumed
                     int need = (U.r1 > U.r0) ? U.r1 - L.k0 : 0;
@@ -332,10 +372,342 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             continue;
         }
 
+        const float S = (float)I.S, dt = (float)I.dt;
+        const float q0 = (float)I.react[0], q1 = (float)I.react[1], q2 = (float)I.react[2],
+                    q3 = (float)I.react[3];
+        const float *psi = reinterpret_cast<const float *>(I.psi);
+        const float *dpsi = reinterpret_cast<const float *>(I.dpsi);
+        const bool mirror = (I.bc == 1);
+        const int kend = min(L.k_end, I.ksteps);
+        auto hrow_at = [&](int r) -> const float * {
+            return reinterpret_cast<const float *>(I.hist + (size_t)(r % I.cap) * I.pitch) + j0;
+        };
+
+        // Phase B of step k on this tile: wait for u^k on the halo tiles, optionally add lag 1
+        // (row k-1), apply the stencil, the reaction and the update (eq. frac_final; adjoint: the
+        // reverse-time recursion), append delta^k and publish the tile's step.  H/H2 hold the rest
+        // of the memory sum; d receives delta^k.  False when a wait gave up.
+        auto phase_b = [&](int k, bool add_lag1, float *H, float *H2, float *d, bool last) -> bool {
+            const int rel = k - L.k0;
+            if (tid < 32) {  // one lane per halo tile
+                int ok = 1;
+                const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
+                const int lo = max(0, tile * I.P - h) / I.P;
+                const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
+                for (int tt = lo + tid; tt <= hi && ok; tt += 32)
+                    if (rel > 0) {
+                        const int w = wait_until(&I.done[tt], (unsigned)rel, L, 32);
+                        if (w < 0) note_failure(L, 5, k, tile, tt, rel, ld_acquire(&I.done[tt]), L.k0);
+                        if (w <= 0) ok = 0;
+                    }
+                if (tid == 0 && ok && I.stall && rel == 0 && tile == 0) {
+                    // fault injection: nothing ever raises a step counter to 2^31
+                    const int w = wait_until(&I.done[tile], 0x80000000u, L, 512);
+                    if (w < 0) note_failure(L, 9, k, tile, 0x80000000ll, ld_acquire(&I.done[tile]), L.k0, 0);
+                    if (w <= 0) ok = 0;
+                }
+                ok = __all_sync(0xffffffffu, ok);
+                if (tid == 0) s_ok2 = ok;
+            }
+            __syncthreads();
+            if (!s_ok2) return false;
+            const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
+            float *un = reinterpret_cast<float *>(I.ubuf[(k + 1) & 1]);
+            const float *lo_k = I.ulo[0] ? reinterpret_cast<const float *>(I.ulo[k & 1]) : nullptr;
+            float *lo_n = I.ulo[0] ? reinterpret_cast<float *>(I.ulo[(k + 1) & 1]) : nullptr;
+            const bool tape_row = I.tape && (k + 1 - I.tape_k0) >= 0 && ((k + 1 - I.tape_k0) % I.tape_every) == 0 &&
+                                  ((k + 1 - I.tape_k0) / I.tape_every) < I.tape_rows;
+            float *tp = tape_row ? reinterpret_cast<float *>(I.tape) + (size_t)((k + 1 - I.tape_k0) / I.tape_every) * I.N
+                                 : nullptr;
+            bool bad = false;
+            double dl[6] = {0, 0, 0, 0, 0, 0};
+            const float *ua = nullptr;
+            if (ADJ) ua = reinterpret_cast<const float *>(I.uadj) + (size_t)((I.adj_K - 1 - k) - I.uadj_r0) * I.N;
+#pragma unroll
+            for (int v = 0; v < V; ++v) d[v] = 0.f;
+            if (j0 < I.N) {
+                // Every operand of the update is loaded before any is used, so that the loads of
+                // this step's critical path are in flight together: row k-1, u^k and its
+                // neighbours, the state's low part and (adjoint) u^r.
+                const float4 x1 = add_lag1 ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(k - 1)))
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int pl = I.nx * I.ny;
+                float cu[V], nb[V][6], lw[V], ur[V];
+                unsigned inb[V];  // bit e: neighbour e inside the grid (r, l, up, dn, fw, bk)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int j = j0 + v;
+                    const bool in = j < I.N;
+                    const int x = j % I.nx, y = (I.ndim >= 2) ? (j / I.nx) % I.ny : 0, z = (I.ndim == 3) ? j / pl : 0;
+                    unsigned m = 0;
+                    if (in && x + 1 < I.nx) m |= 1u;
+                    if (in && x > 0) m |= 2u;
+                    if (in && I.ndim >= 2 && y + 1 < I.ny) m |= 4u;
+                    if (in && I.ndim >= 2 && y > 0) m |= 8u;
+                    if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
+                    if (in && I.ndim == 3 && z > 0) m |= 32u;
+                    inb[v] = m;
+                    cu[v] = in ? __ldcg(uk + j) : 0.f;
+                    nb[v][0] = (m & 1u) ? __ldcg(uk + j + 1) : 0.f;
+                    nb[v][1] = (m & 2u) ? __ldcg(uk + j - 1) : 0.f;
+                    nb[v][2] = (m & 4u) ? __ldcg(uk + j + I.nx) : 0.f;
+                    nb[v][3] = (m & 8u) ? __ldcg(uk + j - I.nx) : 0.f;
+                    nb[v][4] = (m & 16u) ? __ldcg(uk + j + pl) : 0.f;
+                    nb[v][5] = (m & 32u) ? __ldcg(uk + j - pl) : 0.f;
+                    lw[v] = (in && lo_k) ? __ldcg(lo_k + j) : 0.f;
+                    ur[v] = (ADJ && in) ? __ldcg(ua + j) : 0.f;
+                }
+                if (add_lag1) {  // lag 1 completes the memory sum
+                    const float cc = psi[1];
+                    H[0] = fmaf(cc, x1.x, H[0]);
+                    H[1] = fmaf(cc, x1.y, H[1]);
+                    H[2] = fmaf(cc, x1.z, H[2]);
+                    H[3] = fmaf(cc, x1.w, H[3]);
+                    if (ADJ) {
+                        const float c2 = dpsi[1];
+                        H2[0] = fmaf(c2, x1.x, H2[0]);
+                        H2[1] = fmaf(c2, x1.y, H2[1]);
+                        H2[2] = fmaf(c2, x1.z, H2[2]);
+                        H2[3] = fmaf(c2, x1.w, H2[3]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int j = j0 + v;
+                    if (j >= I.N) continue;
+                    const float c = cu[v];
+                    const float gh = mirror ? c : 0.f;
+                    const unsigned m = inb[v];
+                    const float r = (m & 1u) ? nb[v][0] : gh, l = (m & 2u) ? nb[v][1] : gh;
+                    if (I.ndim == 1) {
+                        d[v] = r - 2.f * c + l;
+                    } else {
+                        const float up = (m & 4u) ? nb[v][2] : gh, dn = (m & 8u) ? nb[v][3] : gh;
+                        if (I.ndim == 2) {
+                            d[v] = r + l - 4.f * c + up + dn;
+                        } else {
+                            const float fw = (m & 16u) ? nb[v][4] : gh, bk = (m & 32u) ? nb[v][5] : gh;
+                            d[v] = r + l - 6.f * c + up + dn + fw + bk;
+                        }
+                    }
+                    const float G = d[v] + H[v];  // psi_0 times the fresh row plus the memory sum
+                    float inc;
+                    if (!ADJ) {
+                        const float f = q0 + c * (q1 + c * (q2 + c * q3));
+                        inc = dt * f + S * G;
+                    } else {
+                        // reverse-time recursion: lambda^r = lambda^{r+1} + dt f'(u^r) lambda^{r+1} + S G
+                        const float u_r = ur[v];
+                        const float fp = q1 + u_r * (2.f * q2 + u_r * 3.f * q3);
+                        inc = dt * fp * c + S * G;
+                        dl[0] += (double)u_r * (double)G;
+                        dl[1] += (double)u_r * (double)H2[v];
+                        double pw = 1.0;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            dl[2 + i] += (double)c * pw;
+                            pw *= (double)u_r;
+                        }
+                    }
+                    float nv;
+                    if (lo_k) {
+                        const float y2 = inc + lw[v];
+                        const float sum = c + y2;
+                        const float bb = sum - c;
+                        lo_n[j] = (c - (sum - bb)) + (y2 - bb);
+                        nv = sum;
+                    } else {
+                        nv = c + inc;
+                    }
+                    bad |= !isfinite(nv);
+                    un[j] = nv;
+                    if (tp) tp[j] = nv;
+                }
+                if (I.hist_write)
+                    *reinterpret_cast<float4 *>(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * 4) =
+                        make_float4(d[0], d[1], d[2], d[3]);
+            }
+            if (bad) atomicOr(L.nonfinite, 1u);
+            if (ADJ) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) dl[i] += __shfl_xor_sync(0xffffffffu, dl[i], o);
+                if ((tid & 31) == 0)
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) s_dred[tid >> 5][i] = dl[i];
+            }
+            // history rows are read later by bulk copies (async proxy): order this thread's
+            // generic stores before them, then publish with one release after the CTA barrier
+            fence_proxy_async_global();
+            __syncthreads();
+            if (tid == 0) {
+                if (ADJ) {  // per-tile gradient partials, one writer per tile, in step order
+                    double *dd = I.dots + (size_t)tile * 8;
+                    for (int i = 0; i < 6; ++i) {
+                        double sacc = 0.0;
+                        for (int w = 0; w < (nthr + 31) / 32; ++w) sacc += s_dred[w][i];
+                        dd[i] += sacc;
+                    }
+                }
+                // the block's last update for this tile sets the far count word for block
+                // b+npar, whose far units wait for this step before they count
+                if (last) I.arrive[par * I.T + tile] = arrive_target(b + I.npar, 0);
+                st_release(&I.done[tile], (unsigned)(rel + 1));
+            }
+            return true;
+        };
+
+        if (U.fix == 2) {
+            // ============================ block-long update unit: every step of block b, this tile
+            // The block's steps run in order on this CTA.  The memory sum of step kb+t is the
+            // block's far partials, then the rows before the block (read once, oldest first),
+            // then the rows of the block's earlier steps, which this unit produced itself: each
+            // new delta^k is folded into the sums of the later steps right after its update.
+            // The summation order per step is that of the per-step units (partials by chunk,
+            // then rows by increasing row index), so results agree with them to the bit when
+            // the chunks agree.  The sums live in the stage ring, idle during this unit.
+            const int kf = max(kb, L.k0), kl = min(kb + TB, kend);
+            if (tid < 32) {
+                int ok = 1;
+                if (tid == 0) {
+                    const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C), L, 512);
+                    if (w < 0) note_failure(L, 3, kf, tile, arrive_target(b, C), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
+                    ok = w > 0;
+                }
+                if (tid == 1 && kf - L.k0 > 0) {  // this tile's rows up to kf-1
+                    const int w = wait_until(&I.done[tile], (unsigned)(kf - L.k0), L, 512);
+                    if (w < 0) note_failure(L, 4, kf, tile, kf - L.k0, ld_acquire(&I.done[tile]), L.k0, 0);
+                    ok = w > 0;
+                }
+                ok = __all_sync(0xffffffffu, ok);
+                if (tid == 0) s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) break;
+            float4 *Hs = reinterpret_cast<float4 *>(stages);  // [TB][nthr] sums of the block's steps
+            float4 *Hs2 = Hs + TB * nthr;                      // psi' sums (adjoint)
+            const int t0 = kf - kb, t1 = kl - kb;
+            auto window = [&](int k) { return (I.mem_mode == 1) ? min(I.mem_L, k) : k; };
+            if (j0 < I.N) {
+                // far part of every step: the block's partial rows in fixed chunk order
+                for (int t = t0; t < t1; ++t) {
+                    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), h2 = h;
+                    int c = 0;
+                    for (; c + 4 <= C; c += 4) {
+                        float4 w[4], w2[ADJ ? 4 : 1];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 0) + j0));
+                            if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 1) + j0));
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            h.x += w[i].x;
+                            h.y += w[i].y;
+                            h.z += w[i].z;
+                            h.w += w[i].w;
+                            if (ADJ) {
+                                h2.x += w2[ADJ ? i : 0].x;
+                                h2.y += w2[ADJ ? i : 0].y;
+                                h2.z += w2[ADJ ? i : 0].z;
+                                h2.w += w2[ADJ ? i : 0].w;
+                            }
+                        }
+                    }
+                    for (; c < C; ++c) {
+                        const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 0) + j0));
+                        h.x += w.x;
+                        h.y += w.y;
+                        h.z += w.z;
+                        h.w += w.w;
+                        if (ADJ) {
+                            const float4 w2 = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 1) + j0));
+                            h2.x += w2.x;
+                            h2.y += w2.y;
+                            h2.z += w2.z;
+                            h2.w += w2.w;
+                        }
+                    }
+                    Hs[t * nthr + tid] = h;
+                    if (ADJ) Hs2[t * nthr + tid] = h2;
+                }
+                // rows before kf: the previous block's and, when this launch starts inside the
+                // block, the block's earlier ones; oldest first
+                for (int r = max(0, kb - TB); r < kf; ++r) {
+                    const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow_at(r)));
+                    for (int t = t0; t < t1; ++t) {
+                        const int lag = kb + t - r;
+                        if (lag > window(kb + t)) continue;
+                        const float cc = psi[lag];
+                        float4 h = Hs[t * nthr + tid];
+                        h.x = fmaf(cc, x.x, h.x);
+                        h.y = fmaf(cc, x.y, h.y);
+                        h.z = fmaf(cc, x.z, h.z);
+                        h.w = fmaf(cc, x.w, h.w);
+                        Hs[t * nthr + tid] = h;
+                        if (ADJ) {
+                            const float c2 = dpsi[lag];
+                            float4 h2 = Hs2[t * nthr + tid];
+                            h2.x = fmaf(c2, x.x, h2.x);
+                            h2.y = fmaf(c2, x.y, h2.y);
+                            h2.z = fmaf(c2, x.z, h2.z);
+                            h2.w = fmaf(c2, x.w, h2.w);
+                            Hs2[t * nthr + tid] = h2;
+                        }
+                    }
+                }
+            }
+            bool stop = false;
+            for (int t = t0; t < t1; ++t) {
+                const int k = kb + t;
+                float H[V], H2[V], d[V];
+                const float4 h = (j0 < I.N) ? Hs[t * nthr + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 h2 = (ADJ && j0 < I.N) ? Hs2[t * nthr + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+                H[0] = h.x;
+                H[1] = h.y;
+                H[2] = h.z;
+                H[3] = h.w;
+                H2[0] = h2.x;
+                H2[1] = h2.y;
+                H2[2] = h2.z;
+                H2[3] = h2.w;
+                if (!phase_b(k, false, H, H2, d, k == kl - 1)) {
+                    stop = true;
+                    break;
+                }
+                if (j0 < I.N) {  // delta^k enters the later steps of the block
+                    for (int t2 = t + 1; t2 < t1; ++t2) {
+                        const int lag = t2 - t;
+                        if (lag > window(kb + t2)) continue;
+                        const float cc = psi[lag];
+                        float4 a = Hs[t2 * nthr + tid];
+                        a.x = fmaf(cc, d[0], a.x);
+                        a.y = fmaf(cc, d[1], a.y);
+                        a.z = fmaf(cc, d[2], a.z);
+                        a.w = fmaf(cc, d[3], a.w);
+                        Hs[t2 * nthr + tid] = a;
+                        if (ADJ) {
+                            const float c2 = dpsi[lag];
+                            float4 a2 = Hs2[t2 * nthr + tid];
+                            a2.x = fmaf(c2, d[0], a2.x);
+                            a2.y = fmaf(c2, d[1], a2.y);
+                            a2.z = fmaf(c2, d[2], a2.z);
+                            a2.w = fmaf(c2, d[3], a2.w);
+                            Hs2[t2 * nthr + tid] = a2;
+                        }
+                    }
+                }
+            }
+            if (stop) break;
+            // the ring is filled by bulk copies again: order this thread's accesses before them
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            continue;
+        }
+
         // ================================================== update unit: step k, this tile
         const int k = U.k, t = k - kb;
         const int rel = k - L.k0;
-        const bool last_of_block = (k == min(kb + TB, min(L.k_end, I.ksteps)) - 1);
         // Two phases keep the partial and head sums off the step-to-step chain.  Phase A needs
         // only the tile's far count and this tile's rows up to k-2 (its own step k-2), so it
         // runs while step k-1 is still being updated; phase B waits for u^k on the halo tiles
@@ -359,18 +731,10 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         __syncthreads();
         if (!s_ok) break;
 
-        const float S = (float)I.S, dt = (float)I.dt;
-        const float q0 = (float)I.react[0], q1 = (float)I.react[1], q2 = (float)I.react[2],
-                    q3 = (float)I.react[3];
-        const float *psi = reinterpret_cast<const float *>(I.psi);
-        const float *dpsi = reinterpret_cast<const float *>(I.dpsi);
-        const bool mirror = (I.bc == 1);
         const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
         const int hk = min(t + TB, nb);  // head: lags 1 .. min(k-kb+T, n_base(k)), descending
-        auto hrow = [&](int m) -> const float * {
-            return reinterpret_cast<const float *>(I.hist + (size_t)((k - m) % I.cap) * I.pitch) + j0;
-        };
-        float H[V], H2[V];
+        auto hrow = [&](int m) -> const float * { return hrow_at(k - m); };
+        float H[V], H2[V], d[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) H[v] = H2[v] = 0.f;
         if (j0 < I.N) {
@@ -449,170 +813,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 }
             }
         }
-        // phase B: u^k on this tile and its halo tiles, and row k-1
-        if (tid < 32) {  // one lane per halo tile
-            int ok = 1;
-            const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
-            const int lo = max(0, tile * I.P - h) / I.P;
-            const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
-            for (int tt = lo + tid; tt <= hi && ok; tt += 32)
-                if (rel > 0) {
-                    const int w = wait_until(&I.done[tt], (unsigned)rel, L, 32);
-                    if (w < 0) note_failure(L, 5, k, tile, tt, rel, ld_acquire(&I.done[tt]), L.k0);
-                    if (w <= 0) ok = 0;
-                }
-            if (tid == 0 && ok && I.stall && rel == 0 && tile == 0)
-                {  // fault injection: nothing ever raises a step counter to 2^31
-                    const int w = wait_until(&I.done[tile], 0x80000000u, L, 512);
-                    if (w < 0) note_failure(L, 9, k, tile, 0x80000000ll, ld_acquire(&I.done[tile]), L.k0, 0);
-                    if (w <= 0) ok = 0;
-                }
-            ok = __all_sync(0xffffffffu, ok);
-            if (tid == 0) s_ok2 = ok;
-        }
-        __syncthreads();
-        if (!s_ok2) break;
-        const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
-        float *un = reinterpret_cast<float *>(I.ubuf[(k + 1) & 1]);
-        const float *lo_k = I.ulo[0] ? reinterpret_cast<const float *>(I.ulo[k & 1]) : nullptr;
-        float *lo_n = I.ulo[0] ? reinterpret_cast<float *>(I.ulo[(k + 1) & 1]) : nullptr;
-        const bool tape_row = I.tape && (k + 1 - I.tape_k0) >= 0 && ((k + 1 - I.tape_k0) % I.tape_every) == 0 &&
-                              ((k + 1 - I.tape_k0) / I.tape_every) < I.tape_rows;
-        float *tp = tape_row ? reinterpret_cast<float *>(I.tape) + (size_t)((k + 1 - I.tape_k0) / I.tape_every) * I.N
-                             : nullptr;
-        float d[V];
-        bool bad = false;
-        double dl[6] = {0, 0, 0, 0, 0, 0};
-        const float *ua = nullptr;
-        if (ADJ) ua = reinterpret_cast<const float *>(I.uadj) + (size_t)((I.adj_K - 1 - k) - I.uadj_r0) * I.N;
-        if (j0 < I.N) {
-            // Every operand of the update is loaded before any is used, so that the loads of
-            // this step's critical path are in flight together: row k-1, u^k and its
-            // neighbours, the state's low part and (adjoint) u^r.
-            const float4 x1 = (hk >= 1) ? __ldcg(reinterpret_cast<const float4 *>(hrow(1))) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int pl = I.nx * I.ny;
-            float cu[V], nb[V][6], lw[V], ur[V];
-            unsigned inb[V];  // bit e: neighbour e inside the grid (r, l, up, dn, fw, bk)
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const int j = j0 + v;
-                const bool in = j < I.N;
-                const int x = j % I.nx, y = (I.ndim >= 2) ? (j / I.nx) % I.ny : 0, z = (I.ndim == 3) ? j / pl : 0;
-                unsigned m = 0;
-                if (in && x + 1 < I.nx) m |= 1u;
-                if (in && x > 0) m |= 2u;
-                if (in && I.ndim >= 2 && y + 1 < I.ny) m |= 4u;
-                if (in && I.ndim >= 2 && y > 0) m |= 8u;
-                if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
-                if (in && I.ndim == 3 && z > 0) m |= 32u;
-                inb[v] = m;
-                cu[v] = in ? __ldcg(uk + j) : 0.f;
-                nb[v][0] = (m & 1u) ? __ldcg(uk + j + 1) : 0.f;
-                nb[v][1] = (m & 2u) ? __ldcg(uk + j - 1) : 0.f;
-                nb[v][2] = (m & 4u) ? __ldcg(uk + j + I.nx) : 0.f;
-                nb[v][3] = (m & 8u) ? __ldcg(uk + j - I.nx) : 0.f;
-                nb[v][4] = (m & 16u) ? __ldcg(uk + j + pl) : 0.f;
-                nb[v][5] = (m & 32u) ? __ldcg(uk + j - pl) : 0.f;
-                lw[v] = (in && lo_k) ? __ldcg(lo_k + j) : 0.f;
-                ur[v] = (ADJ && in) ? __ldcg(ua + j) : 0.f;
-            }
-            if (hk >= 1) {  // lag 1 completes the memory sum
-                const float cc = psi[1];
-                H[0] = fmaf(cc, x1.x, H[0]);
-                H[1] = fmaf(cc, x1.y, H[1]);
-                H[2] = fmaf(cc, x1.z, H[2]);
-                H[3] = fmaf(cc, x1.w, H[3]);
-                if (ADJ) {
-                    const float c2 = dpsi[1];
-                    H2[0] = fmaf(c2, x1.x, H2[0]);
-                    H2[1] = fmaf(c2, x1.y, H2[1]);
-                    H2[2] = fmaf(c2, x1.z, H2[2]);
-                    H2[3] = fmaf(c2, x1.w, H2[3]);
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const int j = j0 + v;
-                d[v] = 0.f;
-                if (j >= I.N) continue;
-                const float c = cu[v];
-                const float gh = mirror ? c : 0.f;
-                const unsigned m = inb[v];
-                const float r = (m & 1u) ? nb[v][0] : gh, l = (m & 2u) ? nb[v][1] : gh;
-                if (I.ndim == 1) {
-                    d[v] = r - 2.f * c + l;
-                } else {
-                    const float up = (m & 4u) ? nb[v][2] : gh, dn = (m & 8u) ? nb[v][3] : gh;
-                    if (I.ndim == 2) {
-                        d[v] = r + l - 4.f * c + up + dn;
-                    } else {
-                        const float fw = (m & 16u) ? nb[v][4] : gh, bk = (m & 32u) ? nb[v][5] : gh;
-                        d[v] = r + l - 6.f * c + up + dn + fw + bk;
-                    }
-                }
-                const float G = d[v] + H[v];  // psi_0 times the fresh row plus the memory sum
-                float inc;
-                if (!ADJ) {
-                    const float f = q0 + c * (q1 + c * (q2 + c * q3));
-                    inc = dt * f + S * G;
-                } else {
-                    // reverse-time recursion: lambda^r = lambda^{r+1} + dt f'(u^r) lambda^{r+1} + S G
-                    const float u_r = ur[v];
-                    const float fp = q1 + u_r * (2.f * q2 + u_r * 3.f * q3);
-                    inc = dt * fp * c + S * G;
-                    dl[0] += (double)u_r * (double)G;
-                    dl[1] += (double)u_r * (double)H2[v];
-                    double pw = 1.0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        dl[2 + i] += (double)c * pw;
-                        pw *= (double)u_r;
-                    }
-                }
-                float nv;
-                if (lo_k) {
-                    const float y2 = inc + lw[v];
-                    const float sum = c + y2;
-                    const float bb = sum - c;
-                    lo_n[j] = (c - (sum - bb)) + (y2 - bb);
-                    nv = sum;
-                } else {
-                    nv = c + inc;
-                }
-                bad |= !isfinite(nv);
-                un[j] = nv;
-                if (tp) tp[j] = nv;
-            }
-            if (I.hist_write)
-                *reinterpret_cast<float4 *>(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * 4) =
-                    make_float4(d[0], d[1], d[2], d[3]);
-        }
-        if (bad) atomicOr(L.nonfinite, 1u);
-        if (ADJ) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) dl[i] += __shfl_xor_sync(0xffffffffu, dl[i], o);
-            if ((tid & 31) == 0)
-#pragma unroll
-                for (int i = 0; i < 6; ++i) s_dred[tid >> 5][i] = dl[i];
-        }
-        fence_proxy_async_global();
-        __syncthreads();
-        if (tid == 0) {
-            if (ADJ) {  // per-tile gradient partials, one writer per tile, in step order
-                double *dd = I.dots + (size_t)tile * 8;
-                for (int i = 0; i < 6; ++i) {
-                    double sacc = 0.0;
-                    for (int w = 0; w < (nthr + 31) / 32; ++w) sacc += s_dred[w][i];
-                    dd[i] += sacc;
-                }
-            }
-            // the block's last update for this tile resets the far count for block b+npar,
-            // whose far units wait for this step before they count
-            if (last_of_block) I.arrive[par * I.T + tile] = arrive_target(b + I.npar, 0);
-            st_release(&I.done[tile], (unsigned)(rel + 1));
-        }
+        if (!phase_b(k, hk >= 1, H, H2, d, k == min(kb + TB, kend) - 1)) break;
     }
 }
 

@@ -20,7 +20,8 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
                  allow_unstable: bool = False, ckpt_every: int = 0, timeout_ms: int = 0,
                  inject_stall: bool = False, tile_threads: int = 0, chunk_terms: int = 0,
                  stage_rows: int = 0, stages: int = 0, ctas_per_sm: int = 0,
-                 head_lags: int = 0, plain_state: bool = False, time_block: int = 0) -> L.FdProblem:
+                 head_lags: int = 0, plain_state: bool = False, time_block: int = 0,
+                 step_updates: bool = False) -> L.FdProblem:
     """fd_problem for a synth-style problem dict."""
     s = L.FdProblem()
     s.ndim, s.nx, s.ny = p["ndim"], p["nx"], p["ny"]
@@ -36,7 +37,8 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
     s.flags = ((L.FD_FLAG_KAHAN if kahan else 0) | (L.FD_FLAG_KEEP_TAPE if keep_tape else 0) |
                (L.FD_FLAG_ALLOW_UNSTABLE if allow_unstable else 0) |
                (L.FD_FLAG_INJECT_STALL if inject_stall else 0) |
-               (L.FD_FLAG_PLAIN_STATE if plain_state else 0))
+               (L.FD_FLAG_PLAIN_STATE if plain_state else 0) |
+               (L.FD_FLAG_STEP_UPDATES if step_updates else 0))
     s.max_steps = int(max_steps if max_steps is not None else p["K"])
     s.ckpt_every, s.timeout_ms = ckpt_every, timeout_ms
     s.tile_threads, s.chunk_terms, s.stage_rows = tile_threads, chunk_terms, stage_rows
@@ -53,7 +55,7 @@ def _require_cuda():
 
 
 GEOMETRY_KEYS = ("tile_threads", "chunk_terms", "stage_rows", "stages", "ctas_per_sm", "head_lags",
-                 "time_block")
+                 "time_block", "step_updates")
 
 
 class FRD:

@@ -1,6 +1,7 @@
 """Temporally blocked engine (time_block = 4 / 8 / 16; FP32, full and short memory) against the
-FP64 oracle and against properties that hold at full size; the blocked reverse-time adjoint
-(time_block = 4 / 8) against the oracle's adjoint."""
+FP64 oracle and against properties that hold at full size, with block-long update units (the
+default where the tiles are few) and with one update unit per step (step_updates); the blocked
+reverse-time adjoint (time_block = 4 / 8) against the oracle's adjoint."""
 import numpy as np
 import pytest
 import torch
@@ -18,15 +19,37 @@ def ragged(bc, mode, L=0, K=300):
                          u0=synth.SplitMix64(21).uniform(45 * 37, 0, 1))
 
 
+@pytest.mark.parametrize("step_updates", [False, True])
 @pytest.mark.parametrize("tb", [4, 8, 16])
 @pytest.mark.parametrize("bc", [synth.BC_DIRICHLET0, synth.BC_NOFLUX])
 @pytest.mark.parametrize("mode,L", [(synth.MEM_FULL, 0), (synth.MEM_SHORT, 50), (synth.MEM_SHORT, 7)])
-def test_blocked_matches_oracle(tb, bc, mode, L):
+def test_blocked_matches_oracle(tb, bc, mode, L, step_updates):
     """Several far chunks per block (chunk 16 rows), short windows longer and shorter than 2T."""
     p = ragged(bc, mode, L)
-    s = FRD(p, time_block=tb, chunk_terms=16)
+    s = FRD(p, time_block=tb, chunk_terms=16, step_updates=step_updates)
+    assert s.geometry()["block_updates"] == (0 if step_updates else 1)
     s.set_state(p["u0"])
     assert rel_inf(s.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5
+
+
+@pytest.mark.parametrize("tb,chunk", [(4, 16), (8, 24), (16, 40)])
+@pytest.mark.parametrize("mode,L", [(synth.MEM_FULL, 0), (synth.MEM_SHORT, 37)])
+def test_block_updates_equal_step_updates_bitwise(tb, chunk, mode, L):
+    """With the same far chunks (chunk rows at least the block's rows over its chunk limit), the
+    block-long units sum each step's terms in the per-step units' order: identical bits, in
+    one launch and in launches that start inside blocks."""
+    p = ragged(synth.BC_NOFLUX, mode, L)
+    outs = []
+    for su in (False, True):
+        s = FRD(p, time_block=tb, chunk_terms=chunk, step_updates=su)
+        s.set_state(p["u0"])
+        outs.append(s.run(p["K"]).cpu().numpy())
+        s.set_state(p["u0"])
+        for n in (37, 5, 101, 1, 156):
+            s.step(n)
+        outs.append(s.run(0).cpu().numpy())
+    for x in outs[1:]:
+        assert np.array_equal(outs[0], x)
 
 
 def test_blocked_1d_many_tiles():
@@ -38,21 +61,23 @@ def test_blocked_1d_many_tiles():
     assert rel_inf(s.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5
 
 
-def test_blocked_launch_split_is_bitwise_invariant():
+@pytest.mark.parametrize("step_updates", [False, True])
+def test_blocked_launch_split_is_bitwise_invariant(step_updates):
     """Blocks are aligned to absolute steps, so any split into launches gives the same bits."""
     p = ragged(synth.BC_NOFLUX, synth.MEM_FULL, K=400)
-    a = FRD(p, time_block=8, chunk_terms=32)
+    a = FRD(p, time_block=8, chunk_terms=32, step_updates=step_updates)
     a.set_state(p["u0"])
     one = a.run(400).cpu().numpy()
-    b = FRD(p, time_block=8, chunk_terms=32)
+    b = FRD(p, time_block=8, chunk_terms=32, step_updates=step_updates)
     b.set_state(p["u0"])
     for n in (57, 3, 100, 1, 139, 100):
         b.step(n)
     assert np.array_equal(one, b.run(0).cpu().numpy())
 
 
+@pytest.mark.parametrize("step_updates", [False, True])
 @pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_SHORT])
-def test_blocked_config2_full_size(mode):
+def test_blocked_config2_full_size(mode, step_updates):
     """256^2, 5000 steps: eigenmode superposition against the oracle's scalar recursions, and
     the Gaussian input's mass balance."""
     p = synth.config2(mode)
@@ -61,10 +86,11 @@ def test_blocked_config2_full_size(mode):
     q["u0"] = sum(c * synth.eigenmode(p, qx, qy) for qx, qy, c in modes)
     ref = sum(c * oracle.scalar_mode(p, laplacian_eigenvalue(p, qx, qy))[-1] * synth.eigenmode(p, qx, qy)
               for qx, qy, c in modes)
-    s = FRD(q, time_block=8)
+    s = FRD(q, time_block=8, tile_threads=512, step_updates=step_updates)
+    assert s.geometry()["block_updates"] == (0 if step_updates else 1)
     s.set_state(q["u0"])
     assert rel_inf(s.run(q["K"]).cpu().double().numpy(), ref) < 1e-5
-    s = FRD(p, time_block=8)
+    s = FRD(p, time_block=8, tile_threads=512, step_updates=step_updates)
     s.set_state(p["u0"])
     M0 = p["u0"].sum()
     assert abs(s.run(p["K"]).cpu().double().numpy().sum() - M0 * (1 - 0.1 * p["dt"]) ** p["K"]) / M0 < 2e-5
@@ -87,14 +113,16 @@ def compare_grads(r, ref, tol):
     assert np.max(np.abs(np.array(r["dreact"]) - ref["dreact"])) <= tol * np.max(np.abs(ref["dreact"]))
 
 
+@pytest.mark.parametrize("step_updates", [False, True])
 @pytest.mark.parametrize("tb", [4, 8])
 @pytest.mark.parametrize("bc", [synth.BC_DIRICHLET0, synth.BC_NOFLUX])
-def test_blocked_adjoint_matches_oracle(tb, bc):
+def test_blocked_adjoint_matches_oracle(tb, bc, step_updates):
     """Checkpoint segments of 50 steps (not a multiple of the block: recompute and adjoint
     launches start inside a block) and a ragged last segment; several far chunks per block."""
     p = ragged(bc, synth.MEM_FULL, K=230)
     tgt = synth.SplitMix64(3).uniform(p["nx"] * p["ny"], 0, 0.8)
-    compare_grads(blocked_adjoint(p, tgt, tb, ckpt=50, chunk_terms=16), oracle.adjoint(p, tgt), 2e-4)
+    compare_grads(blocked_adjoint(p, tgt, tb, ckpt=50, chunk_terms=16, step_updates=step_updates),
+                  oracle.adjoint(p, tgt), 2e-4)
 
 
 def test_blocked_adjoint_config5_reduced():
@@ -112,13 +140,14 @@ def test_blocked_adjoint_rejects_blocks_of_16():
     assert e.value.code == L.FD_ERR_UNSUPPORTED
 
 
-def test_blocked_adjoint_repeats_bitwise_at_config5_size():
+@pytest.mark.parametrize("step_updates", [False, True])
+def test_blocked_adjoint_repeats_bitwise_at_config5_size(step_updates):
     """128^2, 4000 steps, checkpoints every 200 with the shipped adjoint geometry (blocks of 8,
     128-thread tiles, 16-row stages, 128-row chunks): 40 launches per adjoint, each with
     boundary units that the kernel passes over.  Five repetitions must all finish and agree
     to the bit (fixed summation order)."""
     p = synth.config5(K=4000)
-    geo = dict(time_block=8, tile_threads=128, stage_rows=16, chunk_terms=128)
+    geo = dict(time_block=8, tile_threads=128, stage_rows=16, chunk_terms=128, step_updates=step_updates)
     runs = []
     for _ in range(5):
         s = FRD(p, keep_tape=True, ckpt_every=200, timeout_ms=5000, **geo)
