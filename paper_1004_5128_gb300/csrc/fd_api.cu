@@ -219,12 +219,12 @@ inline size_t smem_bytes(const Geo &g, int rmax)
     return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)rmax * (2 * g.sa + 4) + 32 + 8 * (size_t)g.NS;
 }
 
-// Blocked kernel: stage ring (block-long update units keep their steps' memory sums there, so it
-// holds at least tb x planes rows, as the kernel assumes), four shifted copies of each coefficient window (psi, and
+// Blocked kernel: stage ring (block-long update units keep their steps' memory sums and their
+// tile's state there, so it holds at least tb x planes + 2 rows, as the kernel assumes), four shifted copies of each coefficient window (psi, and
 // psi' for the adjoint), barriers.
 inline size_t smem_bytes_tb(const Geo &g, int rwin)
 {
-    const int ring = std::max(g.NS * g.RS, g.tb * g.planes);
+    const int ring = std::max(g.NS * g.RS, g.tb * g.planes + 2);
     return (size_t)ring * g.threads * 16 + (size_t)g.planes * 4 * ((rwin + g.tb + 7) & ~3) * 4 + 32 +
            8 * (size_t)g.NS;
 }

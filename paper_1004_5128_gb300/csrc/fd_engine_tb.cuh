@@ -76,8 +76,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // Coefficient window in four copies shifted by 0..3 elements, so that the TB coefficients
     // of any row are TB/4 aligned 16-byte loads: copy q holds w[i + q] at index i.
     const int WS = (L.rmax + TB + 7) & ~3;                                          // copy stride
-    // the stage ring also holds a block-long update unit's sums: at least TB x PLANES rows
-    const int ring_rows = max(NS * RS, TB * PLANES);
+    // the stage ring also holds a block-long update unit's sums and its tile's u^k, u^{k+1}:
+    // at least TB x PLANES + 2 rows
+    const int ring_rows = max(NS * RS, TB * PLANES + 2);
     float *psw = reinterpret_cast<float *>(smem + (size_t)ring_rows * row_bytes);  // psi window
     float *psw2 = psw + 4 * WS;                                                    // psi' window (ADJ)
     uint64_t *bars = reinterpret_cast<uint64_t *>(
@@ -387,7 +388,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         // (row k-1), apply the stencil, the reaction and the update (eq. frac_final; adjoint: the
         // reverse-time recursion), append delta^k and publish the tile's step.  H/H2 hold the rest
         // of the memory sum; d receives delta^k.  False when a wait gave up.
-        auto phase_b = [&](int k, bool add_lag1, float *H, float *H2, float *d, bool last) -> bool {
+        // With own != null (block-long units) the tile's own u^k and low parts come from the
+        // unit itself: own[0..V) and own[V..2V) in registers, and us[P] in shared memory for the
+        // stencil's in-tile neighbours (us_next receives u^{k+1}); only halo points are loaded.
+        const int t0p = tile * I.P;  // first point of the tile
+        auto phase_b = [&](int k, bool add_lag1, float *H, float *H2, float *d, bool last, float *own,
+                           const float *us, float *us_next) -> bool {
             const int rel = k - L.k0;
             if (tid < 32) {  // one lane per halo tile
                 int ok = 1;
@@ -447,14 +453,20 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
                     if (in && I.ndim == 3 && z > 0) m |= 32u;
                     inb[v] = m;
-                    cu[v] = in ? __ldcg(uk + j) : 0.f;
-                    nb[v][0] = (m & 1u) ? __ldcg(uk + j + 1) : 0.f;
-                    nb[v][1] = (m & 2u) ? __ldcg(uk + j - 1) : 0.f;
-                    nb[v][2] = (m & 4u) ? __ldcg(uk + j + I.nx) : 0.f;
-                    nb[v][3] = (m & 8u) ? __ldcg(uk + j - I.nx) : 0.f;
-                    nb[v][4] = (m & 16u) ? __ldcg(uk + j + pl) : 0.f;
-                    nb[v][5] = (m & 32u) ? __ldcg(uk + j - pl) : 0.f;
-                    lw[v] = (in && lo_k) ? __ldcg(lo_k + j) : 0.f;
+                    // a neighbour inside this tile comes from shared memory when the unit keeps it
+                    auto nbr = [&](unsigned bit, int jn) -> float {
+                        if (!(m & bit)) return 0.f;
+                        if (own && jn >= t0p && jn < t0p + I.P) return us[jn - t0p];
+                        return __ldcg(uk + jn);
+                    };
+                    cu[v] = !in ? 0.f : own ? own[v] : __ldcg(uk + j);
+                    nb[v][0] = nbr(1u, j + 1);
+                    nb[v][1] = nbr(2u, j - 1);
+                    nb[v][2] = nbr(4u, j + I.nx);
+                    nb[v][3] = nbr(8u, j - I.nx);
+                    nb[v][4] = nbr(16u, j + pl);
+                    nb[v][5] = nbr(32u, j - pl);
+                    lw[v] = (!in || !lo_k) ? 0.f : own ? own[V + v] : __ldcg(lo_k + j);
                     ur[v] = (ADJ && in) ? __ldcg(ua + j) : 0.f;
                 }
                 if (add_lag1) {  // lag 1 completes the memory sum
@@ -509,12 +521,13 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             pw *= (double)u_r;
                         }
                     }
-                    float nv;
+                    float nv, nl = 0.f;
                     if (lo_k) {
                         const float y2 = inc + lw[v];
                         const float sum = c + y2;
                         const float bb = sum - c;
-                        lo_n[j] = (c - (sum - bb)) + (y2 - bb);
+                        nl = (c - (sum - bb)) + (y2 - bb);
+                        lo_n[j] = nl;
                         nv = sum;
                     } else {
                         nv = c + inc;
@@ -522,6 +535,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     bad |= !isfinite(nv);
                     un[j] = nv;
                     if (tp) tp[j] = nv;
+                    if (own) {
+                        own[v] = nv;
+                        own[V + v] = nl;
+                        us_next[j - t0p] = nv;
+                    }
                 }
                 if (I.hist_write)
                     *reinterpret_cast<float4 *>(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * 4) =
@@ -658,6 +676,21 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     }
                 }
             }
+            // the tile's own u^kf and low parts: registers, and u in shared memory for the stencil
+            float own[2 * V];
+            float *us = reinterpret_cast<float *>(Hs + TB * PLANES * nthr);  // [2][P]: u^k by k parity
+            {
+                const float *u0 = reinterpret_cast<const float *>(I.ubuf[kf & 1]);
+                const float *l0 = I.ulo[0] ? reinterpret_cast<const float *>(I.ulo[kf & 1]) : nullptr;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int j = j0 + v;
+                    own[v] = (j < I.N) ? __ldcg(u0 + j) : 0.f;
+                    own[V + v] = (j < I.N && l0) ? __ldcg(l0 + j) : 0.f;
+                    if (j < I.N) us[(kf & 1) * I.P + (j - t0p)] = own[v];
+                }
+            }
+            __syncthreads();
             bool stop = false;
             for (int t = t0; t < t1; ++t) {
                 const int k = kb + t;
@@ -672,7 +705,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 H2[1] = h2.y;
                 H2[2] = h2.z;
                 H2[3] = h2.w;
-                if (!phase_b(k, false, H, H2, d, k == kl - 1)) {
+                if (!phase_b(k, false, H, H2, d, k == kl - 1, own, us + (k & 1) * I.P, us + ((k + 1) & 1) * I.P)) {
                     stop = true;
                     break;
                 }
@@ -813,7 +846,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 }
             }
         }
-        if (!phase_b(k, hk >= 1, H, H2, d, k == min(kb + TB, kend) - 1)) break;
+        if (!phase_b(k, hk >= 1, H, H2, d, k == min(kb + TB, kend) - 1, nullptr, nullptr, nullptr)) break;
     }
 }
 
