@@ -181,8 +181,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     U.r0 = min(rhi, rlo + U.chunk * Rb);
                     U.r1 = min(rhi, U.r0 + Rb);
                     U.k = 0;
-                    // far rows up to r1-1 written; partial rows of block b-npar consumed
-                    int need = (U.r1 > U.r0) ? U.r1 - L.k0 : 0;
+                    // far rows up to r1-1 written (block-long units: their whole block, whose
+                    // last step fences the block's rows for bulk copies); partial rows of block
+                    // b-npar consumed
+                    int need = 0;
+                    if (U.r1 > U.r0) need = (I.ub ? (U.r1 + TB - 1) / TB * TB : U.r1) - L.k0;
                     need = max(need, kb - (I.npar - 1) * TB - L.k0);
                     if (need > 0) {
                         const int w = wait_until(&I.done[U.tile], (unsigned)need, L, 512);
@@ -440,6 +443,22 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const int pl = I.nx * I.ny;
                 float cu[V], nb[V][6], lw[V], ur[V];
                 unsigned inb[V];  // bit e: neighbour e inside the grid (r, l, up, dn, fw, bk)
+                // a point inside this tile comes from shared memory when the unit keeps it
+                auto get1 = [&](int jn) -> float {
+                    return (own && jn >= t0p && jn < t0p + I.P) ? us[jn - t0p] : __ldcg(uk + jn);
+                };
+                // four consecutive points from jn (a multiple of 4), in one 16-byte load
+                auto get4 = [&](int jn, float *o) {
+                    float4 w;
+                    if (own && jn >= t0p && jn + 3 < t0p + I.P)
+                        w = *reinterpret_cast<const float4 *>(us + (jn - t0p));
+                    else
+                        w = __ldcg(reinterpret_cast<const float4 *>(uk + jn));
+                    o[0] = w.x;
+                    o[1] = w.y;
+                    o[2] = w.z;
+                    o[3] = w.w;
+                };
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const int j = j0 + v;
@@ -453,21 +472,61 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
                     if (in && I.ndim == 3 && z > 0) m |= 32u;
                     inb[v] = m;
-                    // a neighbour inside this tile comes from shared memory when the unit keeps it
-                    auto nbr = [&](unsigned bit, int jn) -> float {
-                        if (!(m & bit)) return 0.f;
-                        if (own && jn >= t0p && jn < t0p + I.P) return us[jn - t0p];
-                        return __ldcg(uk + jn);
-                    };
-                    cu[v] = !in ? 0.f : own ? own[v] : __ldcg(uk + j);
-                    nb[v][0] = nbr(1u, j + 1);
-                    nb[v][1] = nbr(2u, j - 1);
-                    nb[v][2] = nbr(4u, j + I.nx);
-                    nb[v][3] = nbr(8u, j - I.nx);
-                    nb[v][4] = nbr(16u, j + pl);
-                    nb[v][5] = nbr(32u, j - pl);
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) nb[v][e] = 0.f;
                     lw[v] = (!in || !lo_k) ? 0.f : own ? own[V + v] : __ldcg(lo_k + j);
                     ur[v] = (ADJ && in) ? __ldcg(ua + j) : 0.f;
+                }
+                if (j0 + V <= I.N) {
+                    // all four points in the grid: the centre in one load, x-neighbours inside
+                    // the vector from it (a set mask bit means the same row), y/z-neighbours in
+                    // one load each where the row (plane) length keeps them aligned
+                    if (own) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) cu[v] = own[v];
+                    } else {
+                        get4(j0, cu);
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        if (inb[v] & 1u) nb[v][0] = (v + 1 < V) ? cu[v + 1] : get1(j0 + V);
+                        if (inb[v] & 2u) nb[v][1] = (v > 0) ? cu[v - 1] : get1(j0 - 1);
+                    }
+                    auto vert = [&](int e, unsigned bit, int off, int len) {
+                        if ((len & 3) == 0) {  // the four share a row (plane): one mask for all
+                            if (inb[0] & bit) {
+                                float o[V];
+                                get4(j0 + off, o);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) nb[v][e] = o[v];
+                            }
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < V; ++v)
+                                if (inb[v] & bit) nb[v][e] = get1(j0 + v + off);
+                        }
+                    };
+                    if (I.ndim >= 2) {
+                        vert(2, 4u, I.nx, I.nx);
+                        vert(3, 8u, -I.nx, I.nx);
+                    }
+                    if (I.ndim == 3) {
+                        vert(4, 16u, pl, pl);
+                        vert(5, 32u, -pl, pl);
+                    }
+                } else {  // the grid's ragged end: point by point
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int j = j0 + v;
+                        const unsigned m = inb[v];
+                        cu[v] = (j >= I.N) ? 0.f : own ? own[v] : __ldcg(uk + j);
+                        if (m & 1u) nb[v][0] = get1(j + 1);
+                        if (m & 2u) nb[v][1] = get1(j - 1);
+                        if (m & 4u) nb[v][2] = get1(j + I.nx);
+                        if (m & 8u) nb[v][3] = get1(j - I.nx);
+                        if (m & 16u) nb[v][4] = get1(j + pl);
+                        if (m & 32u) nb[v][5] = get1(j - pl);
+                    }
                 }
                 if (add_lag1) {  // lag 1 completes the memory sum
                     const float cc = psi[1];
@@ -483,9 +542,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         H2[3] = fmaf(c2, x1.w, H2[3]);
                     }
                 }
+                float nvv[V], nlv[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const int j = j0 + v;
+                    nvv[v] = cu[v];
+                    nlv[v] = 0.f;
                     if (j >= I.N) continue;
                     const float c = cu[v];
                     const float gh = mirror ? c : 0.f;
@@ -521,24 +583,44 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             pw *= (double)u_r;
                         }
                     }
-                    float nv, nl = 0.f;
+                    float nl = 0.f;
                     if (lo_k) {
                         const float y2 = inc + lw[v];
                         const float sum = c + y2;
                         const float bb = sum - c;
                         nl = (c - (sum - bb)) + (y2 - bb);
-                        lo_n[j] = nl;
-                        nv = sum;
+                        nvv[v] = sum;
                     } else {
-                        nv = c + inc;
+                        nvv[v] = c + inc;
                     }
-                    bad |= !isfinite(nv);
-                    un[j] = nv;
-                    if (tp) tp[j] = nv;
-                    if (own) {
-                        own[v] = nv;
-                        own[V + v] = nl;
-                        us_next[j - t0p] = nv;
+                    nlv[v] = nl;
+                    bad |= !isfinite(nvv[v]);
+                }
+                // stores: 16-byte vectors where all four points exist
+                if (j0 + V <= I.N) {
+                    *reinterpret_cast<float4 *>(un + j0) = make_float4(nvv[0], nvv[1], nvv[2], nvv[3]);
+                    if (lo_n) *reinterpret_cast<float4 *>(lo_n + j0) = make_float4(nlv[0], nlv[1], nlv[2], nlv[3]);
+                    if (own)
+                        *reinterpret_cast<float4 *>(us_next + (j0 - t0p)) = make_float4(nvv[0], nvv[1], nvv[2], nvv[3]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (j0 + v < I.N) {
+                            un[j0 + v] = nvv[v];
+                            if (lo_n) lo_n[j0 + v] = nlv[v];
+                            if (own) us_next[j0 + v - t0p] = nvv[v];
+                        }
+                }
+                if (tp) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (j0 + v < I.N) tp[j0 + v] = nvv[v];
+                }
+                if (own) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        own[v] = nvv[v];
+                        own[V + v] = nlv[v];
                     }
                 }
                 if (I.hist_write)
@@ -555,9 +637,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
                     for (int i = 0; i < 6; ++i) s_dred[tid >> 5][i] = dl[i];
             }
-            // history rows are read later by bulk copies (async proxy): order this thread's
-            // generic stores before them, then publish with one release after the CTA barrier
-            fence_proxy_async_global();
+            // History rows are read later by bulk copies (async proxy): order this thread's
+            // generic stores before them, then publish with one release after the CTA barrier.
+            // A block-long unit fences once, at its last step: bulk copies read a block's rows
+            // only after that step's release, and the fence covers all of the thread's earlier
+            // stores.
+            if (!own || last) fence_proxy_async_global();
             __syncthreads();
             if (tid == 0) {
                 if (ADJ) {  // per-tile gradient partials, one writer per tile, in step order
