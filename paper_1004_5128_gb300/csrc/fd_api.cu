@@ -23,7 +23,11 @@ using fdk::Launch;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kNpar = 4;  // partial-row parities: up to kNpar-1 steps of run-ahead per tile
+// Partial-row parities: a tile's chunks may run up to npar-1 steps (blocks) ahead of its
+// update.  The per-step kernel takes 8 (its chunks need rows at least head+1 steps old, so 8
+// parities let them overlap every step the history allows); the blocked kernel 4 (its far units
+// run one block ahead of the updates, and partials are T rows per chunk).
+inline int npar_for(int tb) { return tb ? 4 : 8; }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -211,6 +215,7 @@ struct Geo {
     int64_t pitch, part_pitch;
     size_t smem;
     int planes;
+    int npar;        // partial-row parities
 };
 
 // Dynamic shared memory: stage ring, per-unit term tables (R coefficients x2, R slots), barriers.
@@ -301,6 +306,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     }
     g.maxC = (int)std::max<int64_t>(1, (nmax + g.R - 1) / g.R);
     g.tb = p.time_block;
+    g.npar = npar_for(g.tb);
     g.nblocks = g.tb ? (p.max_steps + g.tb - 1) / g.tb : 0;
     g.ub = 0;
     g.cmax = 0;
@@ -415,10 +421,10 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     L.hist = c.take((size_t)g.cap * g.pitch);
     L.hring = g.hring_sep ? c.take((size_t)g.hring_cap * g.hring_pitch) : L.hist;
     L.hscale = (p.hist_dtype == FD_F16) ? (float *)c.take((size_t)g.cap * g.T * sizeof(float)) : nullptr;
-    L.part = c.take((size_t)kNpar * g.maxC * g.planes * std::max(1, g.tb) * g.part_pitch);
+    L.part = c.take((size_t)g.npar * g.maxC * g.planes * std::max(1, g.tb) * g.part_pitch);
     L.arrive = external_counters ? counters
-                                 : (unsigned *)c.take(sizeof(unsigned) * (kNpar + 1) * (size_t)g.T);
-    L.done = L.arrive ? L.arrive + kNpar * g.T : nullptr;
+                                 : (unsigned *)c.take(sizeof(unsigned) * (g.npar + 1) * (size_t)g.T);
+    L.done = L.arrive ? L.arrive + g.npar * g.T : nullptr;
     L.psi = c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa);  // blocked: window reads to kb+tb-1
     L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa) : nullptr;
     L.sched = (int4 *)c.take(sizeof(int4) * (size_t)p.max_steps);
@@ -540,7 +546,7 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.ksteps = p.max_steps;
     I.ub = g.ub;
     I.cmax = g.cmax;
-    I.npar = kNpar;
+    I.npar = g.npar;
     I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
     I.tape_every = 1;
     I.S = p.alpha * std::pow(p.dt, p.gamma) / (p.dx * p.dx);
@@ -792,7 +798,7 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
         h->d_ginfo = (int2 *)c.take(sizeof(int2) * (size_t)(p->max_steps + 2));
     }
     h->ctrl_zero_base = (char *)h->L.arrive;
-    h->ctrl_zero_bytes = sizeof(unsigned) * (kNpar + 1) * (size_t)h->g.T;
+    h->ctrl_zero_bytes = sizeof(unsigned) * (h->g.npar + 1) * (size_t)h->g.T;
     const bool kahan = p->flags & FD_FLAG_KAHAN;
     h->kfwd = p->time_block ? fdk::kernel_tb(p->time_block)
                             : fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
@@ -1099,13 +1105,15 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     b.smem = b.tb ? smem_bytes_tb(b.g[0], b.rmax) : smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
     b.ctrl = carve_ctrl(c);
-    b.counter_bytes = sizeof(unsigned) * (kNpar + 1) * (size_t)tiles;
+    int64_t counters = 0;
+    for (int i = 0; i < count; ++i) counters += (int64_t)(b.g[i].npar + 1) * b.g[i].T;
+    b.counter_bytes = sizeof(unsigned) * (size_t)counters;
     b.counters = (unsigned *)c.take(b.counter_bytes);
     int64_t toff = 0;
     for (int i = 0; i < count; ++i) {
         unsigned *cnt = b.counters ? b.counters + toff : nullptr;
         carve_instance(c, probs[i], b.g[i], b.s[i], b.L[i], cnt, true);
-        toff += (kNpar + 1) * (int64_t)b.g[i].T;
+        toff += (b.g[i].npar + 1) * (int64_t)b.g[i].T;
     }
     // groups: step-major (per-step kernel) or block-major (blocked kernel: group b of an
     // instance holds its block b's far units and block b-1's updates), then instance

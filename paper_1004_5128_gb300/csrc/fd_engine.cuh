@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
     __shared__ Inst I;
     __shared__ Unit U;
     __shared__ int s_cur_inst;
-    __shared__ int s_ok;
+    __shared__ int s_ok, s_ok2;
     __shared__ int s_pipe;
     __shared__ float s_red[32];
     __shared__ double s_dred[32][6];
@@ -603,26 +603,20 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         }
 
         // ------------------------------------------------------- fixup
+        // Phase A, before the halo is needed: the partial rows (this unit is the step's last
+        // arrival, so they are complete) and head lags h..2 (this tile's rows up to k-2, i.e. its
+        // own step k-2).  Phase B waits for u^k on the halo tiles, adds lag 1 and updates.  The
+        // summation order is that of one pass: partials by chunk, then lags h..1.
         const int rel = k - L.k0;
-        if (tid == 0) {
+        if (tid < 32) {
             int ok = 1;
-            const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
-            const int lo = max(0, tile * I.P - h) / I.P;
-            const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
-            for (int t = lo; t <= hi && ok; ++t)
-                if (rel > 0) {
-                    const int w = wait_until(&I.done[t], (unsigned)rel, L, 512);
-                    if (w < 0) note_failure(L, 8, k, tile, t, rel, ld_acquire(&I.done[t]), L.k0);
-                    if (w <= 0) ok = 0;
-                }
-            if (ok && I.stall && rel == 0 && tile == 0) {
-                {  // fault injection: nothing ever raises a step counter to 2^31
-                    const int w = wait_until(&I.done[tile], 0x80000000u, L, 512);
-                    if (w < 0) note_failure(L, 9, k, tile, 0x80000000ll, ld_acquire(&I.done[tile]), L.k0, 0);
-                    if (w <= 0) ok = 0;
-                }
+            if (tid == 0 && rel > 1) {
+                const int w = wait_until(&I.done[tile], (unsigned)(rel - 1), L, 32);
+                if (w < 0) note_failure(L, 8, k, tile, tile, rel - 1, ld_acquire(&I.done[tile]), L.k0);
+                ok = w > 0;
             }
-            s_ok = ok;
+            ok = __all_sync(0xffffffffu, ok);
+            if (tid == 0) s_ok = ok;
         }
         __syncthreads();
         if (!s_ok) break;
@@ -636,21 +630,15 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         if (C > 1) {
             if (j0 < I.N) {
                 // partial rows in fixed chunk order (this unit's own row holds the same bits as
-                // its registers); loads issued 4 rows at a time so the L2 round trips overlap
+                // its registers); 16-byte loads, 4 rows at a time so the L2 round trips overlap
                 constexpr int B = 4;
                 for (int c0 = 0; c0 < C; c0 += B) {
                     TA w[B][V], w2[B][V];
 #pragma unroll
                     for (int i = 0; i < B; ++i)
                         if (c0 + i < C) {
-                            const TA *p0 = prow(c0 + i, 0) + j0;
-#pragma unroll
-                            for (int v = 0; v < V; ++v) w[i][v] = __ldcg(p0 + v);
-                            if (ADJ) {
-                                const TA *p1 = prow(c0 + i, 1) + j0;
-#pragma unroll
-                                for (int v = 0; v < V; ++v) w2[i][v] = __ldcg(p1 + v);
-                            }
+                            load_vec<TA, V>(prow(c0 + i, 0) + j0, w[i]);
+                            if (ADJ) load_vec<TA, V>(prow(c0 + i, 1) + j0, w2[i]);
                         }
 #pragma unroll
                     for (int i = 0; i < B; ++i)
@@ -671,91 +659,168 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             }
         }
 
-        // head lags 1..h from the most recent rows (state precision), fixed order
-        {
-            const int h = min(I.head, U.sc.x);
-            const TA *psi = reinterpret_cast<const TA *>(I.psi);
-            const TA *dpsi = reinterpret_cast<const TA *>(I.dpsi);
-            TA hs[V], hc[V], hs2[V];
+        // head lags h..1 from the most recent rows (state precision), fixed order
+        const int hh = min(I.head, U.sc.x);
+        const TA *psi = reinterpret_cast<const TA *>(I.psi);
+        const TA *dpsi = reinterpret_cast<const TA *>(I.dpsi);
+        TA hs[V], hc[V], hs2[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) hs[v] = hc[v] = hs2[v] = TA(0);
-            if (j0 < I.N) {
-                for (int m = h; m >= 1; --m) {
-                    const TS *row = reinterpret_cast<const TS *>(
-                        I.hring + (size_t)((k - m) % I.hring_cap) * I.hring_pitch) + j0;
-                    TS x[V];
-                    load_vec<TS, V>(row, x);
-                    const TA c = psi[m];
-                    if (KAHAN) {
+        for (int v = 0; v < V; ++v) hs[v] = hc[v] = hs2[v] = TA(0);
+        auto head_row = [&](int m) -> const TS * {
+            return reinterpret_cast<const TS *>(I.hring + (size_t)((k - m) % I.hring_cap) * I.hring_pitch) + j0;
+        };
+        auto head_add = [&](int m, const TS *x) {
+            const TA c = psi[m];
+            if (KAHAN) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            const TA y = c * (TA)x[v] - hc[v];
-                            const TA t = hs[v] + y;
-                            hc[v] = (t - hs[v]) - y;
-                            hs[v] = t;
-                        }
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) hs[v] = fma(c, (TA)x[v], hs[v]);
-                    }
-                    if (ADJ) {
-                        const TA c2 = dpsi[m];
-#pragma unroll
-                        for (int v = 0; v < V; ++v) hs2[v] = fma(c2, (TA)x[v], hs2[v]);
-                    }
+                for (int v = 0; v < V; ++v) {
+                    const TA y = c * (TA)x[v] - hc[v];
+                    const TA t = hs[v] + y;
+                    hc[v] = (t - hs[v]) - y;
+                    hs[v] = t;
                 }
-            }
+            } else {
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                H[v] += KAHAN ? (hs[v] - hc[v]) : hs[v];
-                if (ADJ) H2[v] += hs2[v];
+                for (int v = 0; v < V; ++v) hs[v] = fma(c, (TA)x[v], hs[v]);
+            }
+            if (ADJ) {
+                const TA c2 = dpsi[m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) hs2[v] = fma(c2, (TA)x[v], hs2[v]);
+            }
+        };
+        if (j0 < I.N) {  // lags h..2, several rows in flight
+            constexpr int HB = (V > 4) ? 2 : 4;
+            int m = hh;
+            for (; m - (HB - 1) >= 2; m -= HB) {
+                TS x[HB][V];
+#pragma unroll
+                for (int i = 0; i < HB; ++i) load_vec<TS, V>(head_row(m - i), x[i]);
+#pragma unroll
+                for (int i = 0; i < HB; ++i) head_add(m - i, x[i]);
+            }
+            for (; m >= 2; --m) {
+                TS x[V];
+                load_vec<TS, V>(head_row(m), x);
+                head_add(m, x);
             }
         }
 
-        // stencil on u^k (eq. deltasimp), ghosts: 0 (Dirichlet) or mirror (no-flux)
+        // Phase B: u^k on this tile and its halo tiles (one lane per tile), and row k-1
+        if (tid < 32) {
+            int ok = 1;
+            const int h = (I.ndim == 3) ? I.nx * I.ny : (I.ndim == 2) ? I.nx : 1;
+            const int lo = max(0, tile * I.P - h) / I.P;
+            const int hi = min(I.N - 1, tile * I.P + I.P - 1 + h) / I.P;
+            for (int t = lo + tid; t <= hi && ok; t += 32)
+                if (rel > 0) {
+                    const int w = wait_until(&I.done[t], (unsigned)rel, L, 32);
+                    if (w < 0) note_failure(L, 8, k, tile, t, rel, ld_acquire(&I.done[t]), L.k0);
+                    if (w <= 0) ok = 0;
+                }
+            if (tid == 0 && ok && I.stall && rel == 0 && tile == 0) {
+                // fault injection: nothing ever raises a step counter to 2^31
+                const int w = wait_until(&I.done[tile], 0x80000000u, L, 512);
+                if (w < 0) note_failure(L, 9, k, tile, 0x80000000ll, ld_acquire(&I.done[tile]), L.k0, 0);
+                if (w <= 0) ok = 0;
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            if (tid == 0) s_ok2 = ok;
+        }
+        __syncthreads();
+        if (!s_ok2) break;
+
+        // stencil on u^k (eq. deltasimp), ghosts: 0 (Dirichlet) or mirror (no-flux).  Every
+        // operand is loaded before any is used: the centre as one vector, x-neighbours inside
+        // the vector from it, y/z-neighbours as one vector where the row (plane) length keeps
+        // the points in one row (plane) and the vector aligned.
         const TS *uk = reinterpret_cast<const TS *>(I.ubuf[k & 1]);
         TS *un = reinterpret_cast<TS *>(I.ubuf[(k + 1) & 1]);
         const bool mirror = (I.bc == 1);
-        TS d[V], uc[V];
-        float amax = 0.f;
+        const int pl = I.nx * I.ny;
+        TS d[V], uc[V], up[V], dn[V], fw[V], bk[V];
+        TS xr = TS(0), xl = TS(0);  // x-neighbours of the vector's last and first point
+        unsigned inb[V];
+        TS x1[V];
+        const bool lag1 = (hh >= 1) && (j0 < I.N);
+        if (lag1) load_vec<TS, V>(head_row(1), x1);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int j = j0 + v;
-            d[v] = TS(0);
-            uc[v] = TS(0);
-            if (j < I.N) {
-                const TS c = __ldcg(uk + j);
-                const TS g = mirror ? c : TS(0);
-                uc[v] = c;
-                if (I.ndim == 1) {
-                    const TS r = (j + 1 < I.N) ? __ldcg(uk + j + 1) : g;
-                    const TS l = (j > 0) ? __ldcg(uk + j - 1) : g;
-                    d[v] = r - TS(2) * c + l;
-                } else if (I.ndim == 2) {
-                    const int x = j % I.nx, y = j / I.nx;
-                    const TS r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : g;
-                    const TS l = (x > 0) ? __ldcg(uk + j - 1) : g;
-                    const TS up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : g;
-                    const TS dn = (y > 0) ? __ldcg(uk + j - I.nx) : g;
-                    d[v] = r + l - TS(4) * c + up + dn;
+            const bool in = j < I.N;
+            const int x = j % I.nx, y = (I.ndim >= 2) ? (j / I.nx) % I.ny : 0, z = (I.ndim == 3) ? j / pl : 0;
+            unsigned m = 0;
+            if (in && x + 1 < I.nx) m |= 1u;
+            if (in && x > 0) m |= 2u;
+            if (in && I.ndim >= 2 && y + 1 < I.ny) m |= 4u;
+            if (in && I.ndim >= 2 && y > 0) m |= 8u;
+            if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
+            if (in && I.ndim == 3 && z > 0) m |= 32u;
+            inb[v] = m;
+            d[v] = uc[v] = up[v] = dn[v] = fw[v] = bk[v] = TS(0);
+        }
+        if (j0 < I.N) {
+            const bool full = (j0 + V <= I.N);
+            if (full) {
+                load_vec<TS, V>(uk + j0, uc);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (j0 + v < I.N) uc[v] = __ldcg(uk + j0 + v);
+            }
+            // x-neighbours inside the vector come from uc (a set mask bit means the same row)
+            if (inb[V - 1] & 1u) xr = __ldcg(uk + j0 + V);
+            if (inb[0] & 2u) xl = __ldcg(uk + j0 - 1);
+            auto vert = [&](TS *o, unsigned bit, int off, int len) {
+                if (full && len % V == 0) {  // the V points share a row (plane): one mask, one vector
+                    if (inb[0] & bit) load_vec<TS, V>(uk + j0 + off, o);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (inb[v] & bit) o[v] = __ldcg(uk + j0 + v + off);
+                }
+            };
+            if (I.ndim >= 2) {
+                vert(up, 4u, I.nx, I.nx);
+                vert(dn, 8u, -I.nx, I.nx);
+            }
+            if (I.ndim == 3) {
+                vert(fw, 16u, pl, pl);
+                vert(bk, 32u, -pl, pl);
+            }
+        }
+        if (lag1) head_add(1, x1);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            H[v] += KAHAN ? (hs[v] - hc[v]) : hs[v];
+            if (ADJ) H2[v] += hs2[v];
+        }
+        float amax = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (j0 + v >= I.N) continue;
+            const TS c = uc[v];
+            const TS g = mirror ? c : TS(0);
+            const unsigned m = inb[v];
+            const TS r = (m & 1u) ? ((v + 1 < V) ? uc[(v + 1) % V] : xr) : g;
+            const TS l = (m & 2u) ? ((v > 0) ? uc[(v + V - 1) % V] : xl) : g;
+            if (I.ndim == 1) {
+                d[v] = r - TS(2) * c + l;
+            } else {
+                const TS u_ = (m & 4u) ? up[v] : g, dn_ = (m & 8u) ? dn[v] : g;
+                if (I.ndim == 2) {
+                    d[v] = r + l - TS(4) * c + u_ + dn_;
                 } else {
                     // 7-point analogue of eq. deltasimp for the N-dimensional x of eq. fracdiff
-                    const int pl = I.nx * I.ny;
-                    const int x = j % I.nx, y = (j / I.nx) % I.ny, z = j / pl;
-                    const TS r = (x + 1 < I.nx) ? __ldcg(uk + j + 1) : g;
-                    const TS l = (x > 0) ? __ldcg(uk + j - 1) : g;
-                    const TS up = (y + 1 < I.ny) ? __ldcg(uk + j + I.nx) : g;
-                    const TS dn = (y > 0) ? __ldcg(uk + j - I.nx) : g;
-                    const TS fw = (z + 1 < I.nz) ? __ldcg(uk + j + pl) : g;
-                    const TS bk = (z > 0) ? __ldcg(uk + j - pl) : g;
-                    d[v] = r + l - TS(6) * c + up + dn + fw + bk;
+                    const TS f_ = (m & 16u) ? fw[v] : g, b_ = (m & 32u) ? bk[v] : g;
+                    d[v] = r + l - TS(6) * c + u_ + dn_ + f_ + b_;
                 }
-                amax = fmaxf(amax, fabsf((float)d[v]));
             }
+            amax = fmaxf(amax, fabsf((float)d[v]));
         }
 
         // history row k (FP16: per (row, tile) power-of-two scale)
-        float hs = 1.f;
+        float hsc = 1.f;
         const int slot = k % I.cap;
         if (I.hist_write) {
             if (I.hscale) {
@@ -776,14 +841,14 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     I.hscale[(size_t)slot * I.T + tile] = ldexpf(1.f, -e);
                 }
                 __syncthreads();
-                hs = s_red[0];
+                hsc = s_red[0];
             }
             if (j0 < I.N) {
                 TS dz[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) dz[v] = (j0 + v < I.N) ? d[v] : TS(0);
                 *reinterpret_cast<uint4 *>(I.hist + (size_t)slot * I.pitch + (size_t)j0 * sizeof(TH)) =
-                    HVec<TH>::pack(dz, hs);
+                    HVec<TH>::pack(dz, hsc);
                 if (I.hring_sep)
                     store_vec<TS, V>(reinterpret_cast<TS *>(I.hring + (size_t)(k % I.hring_cap) * I.hring_pitch) + j0, dz);
             }
@@ -802,9 +867,11 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                               ((k + 1 - I.tape_k0) / I.tape_every) < I.tape_rows;
         TS *tp = tape_row ? reinterpret_cast<TS *>(I.tape) + (size_t)((k + 1 - I.tape_k0) / I.tape_every) * I.N
                           : nullptr;
+        TS nvv[V], nlv[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int j = j0 + v;
+            nvv[v] = nlv[v] = TS(0);
             if (j >= I.N) continue;
             const TA G = (TA)d[v] + H[v];  // psi_0 delta^k + memory sum
             TS nv, inc;
@@ -823,7 +890,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 const TS y = inc + __ldcg(lo_k + j);
                 const TS sum = x + y;
                 const TS bb = sum - x;
-                lo_n[j] = (x - (sum - bb)) + (y - bb);
+                nlv[v] = (x - (sum - bb)) + (y - bb);
                 nv = sum;
             } else {
                 nv = x + inc;
@@ -841,8 +908,23 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 }
             }
             bad |= !finite_(nv);
-            un[j] = nv;
-            if (tp) tp[j] = nv;
+            nvv[v] = nv;
+        }
+        if (j0 + V <= I.N) {  // 16-byte stores where all V points exist
+            store_vec<TS, V>(un + j0, nvv);
+            if (lo_n) store_vec<TS, V>(lo_n + j0, nlv);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (j0 + v < I.N) {
+                    un[j0 + v] = nvv[v];
+                    if (lo_n) lo_n[j0 + v] = nlv[v];
+                }
+        }
+        if (tp) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (j0 + v < I.N) tp[j0 + v] = nvv[v];
         }
         if (bad) atomicOr(L.nonfinite, 1u);
         if (ADJ) {

@@ -100,7 +100,7 @@ def test_workspace_scales_with_history():
     short = L.fd_workspace_bytes(make_problem(synth.config2(synth.MEM_SHORT, K=5000)))
     bf = L.fd_workspace_bytes(make_problem(synth.config2(K=5000), hist="bf16"))
     assert 1.30e9 < full < 1.40e9          # 5000 rows x 256 KiB of FP32 delta history
-    assert short < 0.15e9                  # ring of L+1 = 501 rows
+    assert short < 0.2e9                   # ring of L+1 = 501 rows (131 MB) plus partial rows
     assert 0.6e9 < bf < 0.75e9            # BF16 rows plus FP32 partial rows and head ring
     tape = L.fd_workspace_bytes(make_problem(synth.config5(K=4000), keep_tape=True))
     assert tape > 2 * 4000 * 128 * 128 * 4  # forward + adjoint histories
