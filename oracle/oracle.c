@@ -373,7 +373,9 @@ int or_adjoint(const or_problem *p, const double *u0, long K, const double *targ
                double *J, double *dJ_du0, double *dJ_dgamma, double *dJ_dalpha,
                double dJ_dreact[4], int threads)
 {
-    if (check_problem(p, K) || p->mem_mode != OR_MEM_FULL || !u0 || !target || K < 1) return -1;
+    if (check_problem(p, K) || (p->mem_mode != OR_MEM_FULL && p->mem_mode != OR_MEM_SHORT) || !u0 ||
+        !target || K < 1)
+        return -1;
     const long N = (long)p->nx * p->ny * p->nz;
     const double S = p->alpha * pow(p->dt, p->gamma) / (p->dx * p->dx);
     double *tape = malloc(sizeof(double) * (size_t)(K + 1) * (size_t)N);
@@ -406,7 +408,8 @@ int or_adjoint(const or_problem *p, const double *u0, long K, const double *targ
     const int nthr = threads > 0 ? threads : omp_get_max_threads();
 #endif
     for (long r = K - 1; r >= 0; --r) {
-        const long nm = K - 1 - r; /* m = 0 .. K-1-r */
+        /* m = 0 .. K-1-r, within the short window m <= L */
+        const long nm = (p->mem_mode == OR_MEM_SHORT && p->mem_L < K - 1 - r) ? p->mem_L : K - 1 - r;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(nthr)
 #endif

@@ -83,3 +83,28 @@ def test_complex_step_forward_matches_real_forward():
     p, _ = adj_problem(synth.BC_NOFLUX)
     re, im = oracle.run_cs(p)
     assert np.max(np.abs(re - oracle.run(p))) < 1e-13 and np.all(im == 0)
+
+
+@pytest.mark.parametrize("bc,L", [(synth.BC_DIRICHLET0, 6), (synth.BC_NOFLUX, 13), (synth.BC_NOFLUX, 25)])
+def test_short_memory_adjoint_matches_complex_step(bc, L):
+    """Short memory (eq. frac_shortmemory): the transposed window M(r) = min(L, K-1-r); a
+    dropped window bound (full-memory sums) or an off-by-one in it fails these."""
+    p, target = adj_problem(bc)
+    p = synth.with_mode(p, synth.MEM_SHORT, L=L)
+    a = oracle.adjoint(p, target)
+    assert abs(a["J"] - J_of(p, target)) < 1e-14 * a["J"]
+    dg = cs_grad(p, target, gamma_im=H_CS)
+    da = cs_grad(p, target, alpha_im=H_CS)
+    assert abs(a["dgamma"] - dg) < 1e-11 * abs(dg)
+    assert abs(a["dalpha"] - da) < 1e-11 * abs(da)
+    for i in range(4):
+        e = np.zeros(4)
+        e[i] = H_CS
+        dr = cs_grad(p, target, react_im=e)
+        assert abs(a["dreact"][i] - dr) < 1e-11 * abs(dr), i
+    v = synth.SplitMix64(6).uniform(p["u0"].size, -1.0, 1.0)
+    dv = cs_grad(p, target, u0_im=H_CS * v)
+    assert abs(float(a["du0"] @ v) - dv) < 1e-11 * abs(dv)
+    # the short-memory gradient differs from the full-memory one (the window matters)
+    full = oracle.adjoint(synth.with_mode(p, synth.MEM_FULL), target)
+    assert abs(full["dgamma"] - a["dgamma"]) > 1e-6 * abs(a["dgamma"])
