@@ -154,7 +154,8 @@ int fd_get_state(fd_handle *h, void *u_out);
 int64_t fd_current_step(fd_handle *h);
 
 /* Reverse-time adjoint of J(u^K) for the K steps taken since fd_set_state
- * (full memory, F32 or F64 state/history, FD_FLAG_KEEP_TAPE required).
+ * (full or short memory, F32 or F64 state/history, FD_FLAG_KEEP_TAPE required; short memory
+ * transposes its window: delta^r reaches the steps r+m with m <= L, eq. frac_shortmemory).
  * dJ_duK: N values (state dtype, device or host) = dJ/du^K.  Outputs dJ/du^0
  * (N values, device or host; may be NULL) and the scalar gradients with respect
  * to gamma (through psi and dt^g), alpha and react[0..3] (each may be NULL).

@@ -1,7 +1,8 @@
 """Launch-geometry autotuner for the engine.
 
-The engine's launch geometry (temporal block, threads per CTA, memory terms per work unit,
-rows per TMA stage, ring stages, resident CTAs per SM) trades parallelism against
+The engine's launch geometry (temporal block and its kind of update unit, threads per CTA,
+memory terms per work unit, rows per TMA stage, ring stages, resident CTAs per SM) trades
+parallelism against
 per-unit overhead, and the best point depends on the grid size, the step count, the
 history dtype and the memory mode.  `tune` times candidates on the GPU (CUDA events
 around whole runs, so every step's work is included) by coordinate descent from the
@@ -29,6 +30,7 @@ from .frd import FRD, FRDBatch
 
 PARAMS = {
     "time_block": [0, 8, 16],
+    "step_updates": [0, 1],
     "tile_threads": [128, 256, 512],
     "chunk_terms": [32, 64, 128, 256, 512],
     "stage_rows": [4, 8, 16],

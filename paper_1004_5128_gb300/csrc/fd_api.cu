@@ -176,7 +176,7 @@ int validate(const fd_problem *p)
     const bool adj = p->flags & FD_FLAG_KEEP_TAPE;
     if (!fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false))
         return FD_ERR_UNSUPPORTED;
-    if (adj && (p->mem_mode != FD_MEM_FULL ||
+    if (adj && ((p->mem_mode != FD_MEM_FULL && p->mem_mode != FD_MEM_SHORT) ||
                 !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)))
         return FD_ERR_UNSUPPORTED;
     if (p->time_block) {
@@ -288,7 +288,9 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     if (sms <= 0) sms = 152;
     g.grid = sms * g.ctas;
     g.cap = p.max_steps;
-    if (p.mem_mode == FD_MEM_SHORT) g.cap = (int)std::min<int64_t>((int64_t)p.mem_L + 1, p.max_steps);
+    // short memory keeps a ring of L+1 rows, unless the adjoint's recompute will read old rows
+    if (p.mem_mode == FD_MEM_SHORT && !(p.flags & FD_FLAG_KEEP_TAPE))
+        g.cap = (int)std::min<int64_t>((int64_t)p.mem_L + 1, p.max_steps);
     g.cap = std::max(g.cap, 1);
     g.hring_sep = (p.hist_dtype != p.state_dtype);
     g.head = p.head_lags ? p.head_lags : (g.hring_sep ? 32 : 8);

@@ -138,3 +138,14 @@ def test_autograd_function():
     assert abs(gam.grad.item() - ref["dgamma"]) < 1e-10 * abs(ref["dgamma"])
     assert abs(alp.grad.item() - ref["dalpha"]) < 1e-10 * abs(ref["dalpha"])
     assert np.max(np.abs(react.grad.numpy() - ref["dreact"])) < 1e-10 * np.max(np.abs(ref["dreact"]))
+
+
+@pytest.mark.parametrize("state,tol", [("f64", 1e-10), ("f32", 2e-4)])
+@pytest.mark.parametrize("L", [9, 40])
+def test_short_memory_adjoint_vs_oracle(state, tol, L):
+    """Short memory: the adjoint sums each row over the transposed window (lags m <= L), with
+    checkpoint segments of 40 steps over 150."""
+    p, tgt = small(synth.BC_NOFLUX)
+    p = synth.with_mode(p, synth.MEM_SHORT, L=L)
+    r = gpu_adjoint(p, tgt, state, ckpt=40)
+    compare(r, oracle.adjoint(p, tgt), tol)

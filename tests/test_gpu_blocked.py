@@ -177,3 +177,13 @@ def test_blocked_stall_injection_reports_its_site():
     t = FRD(p, time_block=8)
     t.set_state(p["u0"])
     assert rel_inf(t.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5
+
+
+@pytest.mark.parametrize("step_updates", [False, True])
+@pytest.mark.parametrize("tb,L", [(4, 9), (8, 37)])
+def test_blocked_short_memory_adjoint_matches_oracle(tb, L, step_updates):
+    """Blocked adjoint of short memory: the far window and the head both stop at lag L."""
+    p = ragged(synth.BC_DIRICHLET0, synth.MEM_SHORT, L=L, K=230)
+    tgt = synth.SplitMix64(4).uniform(p["nx"] * p["ny"], 0, 0.8)
+    compare_grads(blocked_adjoint(p, tgt, tb, ckpt=50, chunk_terms=16, step_updates=step_updates),
+                  oracle.adjoint(p, tgt), 2e-4)

@@ -67,8 +67,11 @@ def test_validation_codes():
     assert e.value.code == L.FD_ERR_UNSTABLE
     fp.flags |= L.FD_FLAG_ALLOW_UNSTABLE
     assert L.fd_workspace_bytes(fp) > 0
-    # adjoint supports full memory only
+    # adjoint: full and short memory (the short run then keeps every row for the recompute);
+    # the adaptive schedule has no adjoint
     q = make_problem(synth.with_mode(p, synth.MEM_SHORT, L=5), max_steps=10, keep_tape=True)
+    assert L.fd_workspace_bytes(q) > 0
+    q = make_problem(synth.with_mode(p, synth.MEM_ADAPTIVE, a=3), max_steps=10, keep_tape=True)
     with pytest.raises(L.FdError) as e:
         L.fd_workspace_bytes(q)
     assert e.value.code == L.FD_ERR_UNSUPPORTED
