@@ -364,7 +364,7 @@ def run_ours(args):
                              alg_bytes=r.alg, gbs=r.alg / (per / 1e3) / 1e9,
                              geometry={k: g.get(k) for k in ("tile_threads", "tiles", "chunk_terms",
                                                              "stage_rows", "stages", "ctas_per_sm",
-                                                             "grid", "head_lags", "time_block")})
+                                                             "grid", "head_lags", "time_block", "block_updates")})
     extra = {}
     if args.workload == "c5":
         r = runs[0]
