@@ -358,6 +358,34 @@ __device__ __forceinline__ void term_of(const Inst &I, const int4 sc, int tau, i
     }
 }
 
+// Neighbour masks of the V consecutive points j0 .. j0+V-1: bit e set when neighbour e (+x, -x,
+// +y, -y, +z, -z) lies inside the grid.  One division of j0, then a running (x, y, z).
+template <int V> __device__ __forceinline__ void grid_masks(const Inst &I, int j0, unsigned *inb)
+{
+    int x = j0 % I.nx;
+    const int r = j0 / I.nx;
+    int y = (I.ndim >= 2) ? r % I.ny : 0, z = (I.ndim == 3) ? r / I.ny : 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const bool in = j0 + v < I.N;
+        unsigned m = 0;
+        if (in && x + 1 < I.nx) m |= 1u;
+        if (in && x > 0) m |= 2u;
+        if (in && I.ndim >= 2 && y + 1 < I.ny) m |= 4u;
+        if (in && I.ndim >= 2 && y > 0) m |= 8u;
+        if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
+        if (in && I.ndim == 3 && z > 0) m |= 32u;
+        inb[v] = m;
+        if (++x == I.nx) {
+            x = 0;
+            if (++y == I.ny) {
+                y = 0;
+                ++z;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int find_group(const long long *off, int g, int g_end, long long u)
 {
     if (u < off[g + 1]) return g;
@@ -744,21 +772,9 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         TS x1[V];
         const bool lag1 = (hh >= 1) && (j0 < I.N);
         if (lag1) load_vec<TS, V>(head_row(1), x1);
+        grid_masks<V>(I, j0, inb);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const int j = j0 + v;
-            const bool in = j < I.N;
-            const int x = j % I.nx, y = (I.ndim >= 2) ? (j / I.nx) % I.ny : 0, z = (I.ndim == 3) ? j / pl : 0;
-            unsigned m = 0;
-            if (in && x + 1 < I.nx) m |= 1u;
-            if (in && x > 0) m |= 2u;
-            if (in && I.ndim >= 2 && y + 1 < I.ny) m |= 4u;
-            if (in && I.ndim >= 2 && y > 0) m |= 8u;
-            if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
-            if (in && I.ndim == 3 && z > 0) m |= 32u;
-            inb[v] = m;
-            d[v] = uc[v] = up[v] = dn[v] = fw[v] = bk[v] = TS(0);
-        }
+        for (int v = 0; v < V; ++v) d[v] = uc[v] = up[v] = dn[v] = fw[v] = bk[v] = TS(0);
         if (j0 < I.N) {
             const bool full = (j0 + V <= I.N);
             if (full) {

@@ -459,19 +459,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     o[2] = w.z;
                     o[3] = w.w;
                 };
+                grid_masks<V>(I, j0, inb);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const int j = j0 + v;
                     const bool in = j < I.N;
-                    const int x = j % I.nx, y = (I.ndim >= 2) ? (j / I.nx) % I.ny : 0, z = (I.ndim == 3) ? j / pl : 0;
-                    unsigned m = 0;
-                    if (in && x + 1 < I.nx) m |= 1u;
-                    if (in && x > 0) m |= 2u;
-                    if (in && I.ndim >= 2 && y + 1 < I.ny) m |= 4u;
-                    if (in && I.ndim >= 2 && y > 0) m |= 8u;
-                    if (in && I.ndim == 3 && z + 1 < I.nz) m |= 16u;
-                    if (in && I.ndim == 3 && z > 0) m |= 32u;
-                    inb[v] = m;
 #pragma unroll
                     for (int e = 0; e < 6; ++e) nb[v][e] = 0.f;
                     lw[v] = (!in || !lo_k) ? 0.f : own ? own[V + v] : __ldcg(lo_k + j);
