@@ -171,7 +171,8 @@ int fd_get_status(fd_handle *h);
  * rows, 2 blocked far unit's bulk copy, 3 blocked update waiting for the far count, 4 blocked
  * update waiting for its own rows, 5 blocked update waiting for a halo tile, 6 per-step chunk
  * waiting for its rows, 7 per-step chunk's bulk copy, 8 per-step fixup waiting for a halo
- * tile, 9 the stall injected by FD_FLAG_INJECT_STALL.  info[1..6] are the site's operands
+ * tile, 9 the stall injected by FD_FLAG_INJECT_STALL, 10 blocked far unit waiting for the
+ * previous chunk's running sum.  info[1..6] are the site's operands
  * (step or block, tile, the counter target and the value last read, the launch's first step;
  * site 2 packs pairs into the high and low 32 bits), info[7] the CTA.  Only the first failure
  * since fd_set_state is kept.  Synchronises the stream. */

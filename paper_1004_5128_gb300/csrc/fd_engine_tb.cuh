@@ -131,20 +131,25 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 long long f = -1;  // far unit index within block gb, or -1 for an update unit
                 U.inst = gi.x;
                 if (I.ub) {
-                    // block-long update units first, so block gb-1's steps start as soon as its
-                    // far units have all arrived; then block gb's far units
-                    if (local < Tu) {
+                    // About one wave of block gb's far units (as many as the CTAs that the update
+                    // units leave), then block gb-1's block-long update units, then the rest of
+                    // block gb's far units.  An update unit is claimed when block gb-1's far
+                    // units are about to finish instead of holding its SM through their tail;
+                    // block gb's far units read rows up to block gb-2 only, so none of them
+                    // waits for these updates.
+                    const long long F1 = min(F, (long long)max(0, (int)gridDim.x - Tu));
+                    if (local >= F1 && local < F1 + Tu) {
                         const int kb1 = (gb - 1) * TB;
                         if (max(kb1, L.k0) >= min(kb1 + TB, k_end)) continue;  // no step in this launch
                         U.fix = 2;
                         U.b = gb - 1;
-                        U.tile = (int)local;
+                        U.tile = (int)(local - F1);
                         U.k = 0;
                         U.C = far_chunks<TB>(I, gb - 1);
                         U.chunk = 0;
                         U.r0 = U.r1 = 0;
                     } else {
-                        f = local - Tu;
+                        f = (local < F1) ? local : local - Tu;
                     }
                 } else {
                     int sseg = 0;  // segment s: far slice s, then the T update units of step s
@@ -358,16 +363,40 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 }
                 break;
             }
+            // With block-long update units, a running sum over the tile's chunks in chunk order:
+            // chunk c stores S_c = S_{c-1} + p_c (S_{-1} = 0), the same adds, in the same order,
+            // as a sequential sum of the C partials, and the update unit reads S_{C-1} alone
+            // (its setup is on the step-to-step chain).  Chunk c-1 was claimed earlier, so the
+            // wait ends; the tile's count says how many chunks are summed.  Per-step update
+            // units sum the C partials themselves: their many short chunks run side by side,
+            // where a chain of adds would serialise them.
+            const int c0 = U.chunk;
+            const bool chain = I.ub && c0 > 0;
+            if (chain) {
+                if (tid == 0) {
+                    const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, c0), L, 512);
+                    if (w < 0) note_failure(L, 10, b, tile, arrive_target(b, c0), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
+                    s_ok = w > 0;
+                }
+                __syncthreads();
+                if (!s_ok) break;
+            }
             if (j0 < I.N) {
+                auto add_store = [&](int t, int pl, float a0, float a1, float a2, float a3) {
+                    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (chain) sum = __ldcg(reinterpret_cast<const float4 *>(prow(c0 - 1, t, pl) + j0));
+                    sum.x += a0;
+                    sum.y += a1;
+                    sum.z += a2;
+                    sum.w += a3;
+                    *reinterpret_cast<float4 *>(prow(c0, t, pl) + j0) = sum;
+                };
 #pragma unroll
-                for (int t = 0; t < TB; ++t)
-                    *reinterpret_cast<float4 *>(prow(U.chunk, t, 0) + j0) =
-                        make_float4(acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
-                if (ADJ) {
-#pragma unroll
-                    for (int t = 0; t < (ADJ ? TB : 1); ++t)
-                        *reinterpret_cast<float4 *>(prow(U.chunk, t, 1) + j0) =
-                            make_float4(acc2[t][0], acc2[t][1], acc2[t][2], acc2[t][3]);
+                for (int t = 0; t < TB; ++t) {
+                    add_store(t, 0, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+                    if (ADJ)
+                        add_store(t, 1, acc2[ADJ ? t : 0][0], acc2[ADJ ? t : 0][1], acc2[ADJ ? t : 0][2],
+                                  acc2[ADJ ? t : 0][3]);
                 }
             }
             // CTA barrier, then one release add: cumulative over every thread's partial stores
@@ -685,73 +714,53 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             const int t0 = kf - kb, t1 = kl - kb;
             auto window = [&](int k) { return (I.mem_mode == 1) ? min(I.mem_L, k) : k; };
             if (j0 < I.N) {
-                // far part of every step: the block's partial rows in fixed chunk order
-                for (int t = t0; t < t1; ++t) {
-                    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), h2 = h;
-                    int c = 0;
-                    for (; c + 4 <= C; c += 4) {
-                        float4 w[4], w2[ADJ ? 4 : 1];
+                // Far part of every step from the running sum, then the rows before kf (the
+                // previous block's and, when this launch starts inside the block, the block's
+                // earlier ones), oldest first.  The sums stay in registers and each group of
+                // loads is in flight together: this setup is on the step-to-step chain.
+                float4 h[TB], h2[ADJ ? TB : 1];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 0) + j0));
-                            if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 1) + j0));
-                        }
+                for (int t = 0; t < TB; ++t) {
+                    h[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ADJ) h2[ADJ ? t : 0] = h[t];
+                    if (C > 0 && t >= t0 && t < t1) {
+                        h[t] = __ldcg(reinterpret_cast<const float4 *>(prow(C - 1, t, 0) + j0));
+                        if (ADJ) h2[ADJ ? t : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(C - 1, t, 1) + j0));
+                    }
+                }
+                for (int r = max(0, kb - TB); r < kf; r += 4) {
+                    float4 x[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            h.x += w[i].x;
-                            h.y += w[i].y;
-                            h.z += w[i].z;
-                            h.w += w[i].w;
+                    for (int i = 0; i < 4; ++i)
+                        x[i] = (r + i < kf) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int t = 0; t < TB; ++t) {
+                            const int lag = kb + t - (r + i);
+                            if (r + i >= kf || t < t0 || t >= t1 || lag > window(kb + t)) continue;
+                            const float cc = psi[lag];
+                            h[t].x = fmaf(cc, x[i].x, h[t].x);
+                            h[t].y = fmaf(cc, x[i].y, h[t].y);
+                            h[t].z = fmaf(cc, x[i].z, h[t].z);
+                            h[t].w = fmaf(cc, x[i].w, h[t].w);
                             if (ADJ) {
-                                h2.x += w2[ADJ ? i : 0].x;
-                                h2.y += w2[ADJ ? i : 0].y;
-                                h2.z += w2[ADJ ? i : 0].z;
-                                h2.w += w2[ADJ ? i : 0].w;
+                                const float c2 = dpsi[lag];
+                                float4 &g = h2[ADJ ? t : 0];
+                                g.x = fmaf(c2, x[i].x, g.x);
+                                g.y = fmaf(c2, x[i].y, g.y);
+                                g.z = fmaf(c2, x[i].z, g.z);
+                                g.w = fmaf(c2, x[i].w, g.w);
                             }
                         }
-                    }
-                    for (; c < C; ++c) {
-                        const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 0) + j0));
-                        h.x += w.x;
-                        h.y += w.y;
-                        h.z += w.z;
-                        h.w += w.w;
-                        if (ADJ) {
-                            const float4 w2 = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 1) + j0));
-                            h2.x += w2.x;
-                            h2.y += w2.y;
-                            h2.z += w2.z;
-                            h2.w += w2.w;
-                        }
-                    }
-                    Hs[t * nthr + tid] = h;
-                    if (ADJ) Hs2[t * nthr + tid] = h2;
                 }
-                // rows before kf: the previous block's and, when this launch starts inside the
-                // block, the block's earlier ones; oldest first
-                for (int r = max(0, kb - TB); r < kf; ++r) {
-                    const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow_at(r)));
-                    for (int t = t0; t < t1; ++t) {
-                        const int lag = kb + t - r;
-                        if (lag > window(kb + t)) continue;
-                        const float cc = psi[lag];
-                        float4 h = Hs[t * nthr + tid];
-                        h.x = fmaf(cc, x.x, h.x);
-                        h.y = fmaf(cc, x.y, h.y);
-                        h.z = fmaf(cc, x.z, h.z);
-                        h.w = fmaf(cc, x.w, h.w);
-                        Hs[t * nthr + tid] = h;
-                        if (ADJ) {
-                            const float c2 = dpsi[lag];
-                            float4 h2 = Hs2[t * nthr + tid];
-                            h2.x = fmaf(c2, x.x, h2.x);
-                            h2.y = fmaf(c2, x.y, h2.y);
-                            h2.z = fmaf(c2, x.z, h2.z);
-                            h2.w = fmaf(c2, x.w, h2.w);
-                            Hs2[t * nthr + tid] = h2;
-                        }
+#pragma unroll
+                for (int t = 0; t < TB; ++t)
+                    if (t >= t0 && t < t1) {
+                        Hs[t * nthr + tid] = h[t];
+                        if (ADJ) Hs2[t * nthr + tid] = h2[ADJ ? t : 0];
                     }
-                }
             }
             // the tile's own u^kf and low parts: registers, and u in shared memory for the stencil
             float own[2 * V];

@@ -172,7 +172,7 @@ def test_blocked_stall_injection_reports_its_site():
     assert e.value.code == L.FD_ERR_TIMEOUT
     # the first wait to give up is the injected one or one that depends on it
     info = s.error_info()
-    assert info["words"][0] in (1, 3, 4, 5, 9) and info["site"] != "none"
+    assert info["words"][0] in (1, 3, 4, 5, 9, 10) and info["site"] != "none"
     s.close()
     t = FRD(p, time_block=8)
     t.set_state(p["u0"])
