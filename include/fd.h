@@ -98,12 +98,15 @@ typedef struct fd_problem {
                             state precision (0 = 8 for F32/F64 history, 32 for BF16/F16) */
     int nz;              /* points along the third axis when ndim == 3, else 1 */
     int time_block;      /* 0, or 4 / 8 / 16: temporally blocked sum (F32 state, history and
-                            accumulation, full or short memory, no Kahan; with FD_FLAG_KEEP_TAPE
-                            4 or 8).  Rows older than the current block of time_block steps are
-                            read once per block into time_block accumulators (the Toeplitz
+                            accumulation, no Kahan; with FD_FLAG_KEEP_TAPE full or short memory
+                            and 4 or 8).  Rows older than the current block of time_block steps
+                            are read once per block into time_block accumulators (the Toeplitz
                             structure of eq. frac_norxn); the newest rows are summed per step.
-                            Same terms, grouped differently; history traffic drops by about
-                            time_block.  When the tiles are few against the grid (at most a
+                            Adaptive memory: the older rows carry the weights that the medians
+                            settle on (psi on the base interval, d psi at a median, 0 between,
+                            Definition 3.2) and each step's tail rows (Proposition 3.1) are summed
+                            per step.  Same terms, grouped differently; history traffic drops by
+                            about time_block (adaptive: all rows are read once per block).  When the tiles are few against the grid (at most a
                             quarter of its CTAs), one unit per tile carries a whole block's
                             updates and keeps the block's newest rows in on-chip memory, unless
                             FD_FLAG_STEP_UPDATES is set. */

@@ -14,7 +14,7 @@ Cache path: $FD_TUNE_CACHE, else ~/.cache/fd_tune.json.  When the cache has no e
 problem, `lookup` falls back to the table shipped with the package (tuned.json, measured on a
 GB300 with this tuner), first by exact key, then by the nearest step-count bucket.
 
-    python -m paper_1004_5128_gb300.autotune c2 c4 [--budget 60] [--out tuned.json]
+    python -m paper_1004_5128_gb300.autotune c2 c4 [--modes adaptive] [--budget 60] [--out tuned.json]
 """
 from __future__ import annotations
 
@@ -199,12 +199,13 @@ def _main():
     ap.add_argument("workloads", nargs="+")
     ap.add_argument("--budget", type=float, default=60.0, help="seconds per run")
     ap.add_argument("--K", type=int, default=0)
+    ap.add_argument("--modes", default="", help="comma-separated runs of each workload to tune")
     ap.add_argument("--out", default="", help="cache file (default: $FD_TUNE_CACHE or ~/.cache)")
     args = ap.parse_args()
     if args.out:
         os.environ["FD_TUNE_CACHE"] = os.path.abspath(args.out)
     for w in args.workloads:
-        for name, p, kw in synth.workload_runs(w, args.K):
+        for name, p, kw in synth.workload_runs(w, args.K, args.modes):
             t0 = time.time()
             if isinstance(p, list):
                 g = tune(None, batch=p, budget_s=args.budget, **kw)

@@ -181,8 +181,7 @@ int validate(const fd_problem *p)
         return FD_ERR_UNSUPPORTED;
     if (p->time_block) {
         if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16) return FD_ERR_INVALID_ARG;
-        if (p->state_dtype != FD_F32 || p->hist_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan ||
-            (p->mem_mode != FD_MEM_FULL && p->mem_mode != FD_MEM_SHORT))
+        if (p->state_dtype != FD_F32 || p->hist_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan)
             return FD_ERR_UNSUPPORTED;
         if (adj && !fdk::kernel_tb(p->time_block, true)) return FD_ERR_UNSUPPORTED;  // adjoint blocks: 4, 8
         // arrival words hold a block generation (blocks / 4) and a chunk count in 16 bits each
@@ -216,6 +215,9 @@ struct Geo {
     size_t smem;
     int planes;
     int npar;        // partial-row parities
+    // blocked, adaptive memory: first far row of each block (rows below it are tail rows of some
+    // step of the block, whose weights change from step to step; the update units add them)
+    std::vector<int> br0;
 };
 
 // Dynamic shared memory: stage ring, per-unit term tables (R coefficients x2, R slots), barriers.
@@ -242,13 +244,20 @@ int device_sms()
     return sms;
 }
 
+// Last lag of step k whose weight is settled: adaptive memory gives lag m <= e(k) the weight
+// g(m) of every later step (psi_m on the base interval, d psi_m at a median, 0 between medians,
+// Definition 3.2); lags e(k)+1 .. k are the step's tail, weight psi_m (k <= a: e(k) = k).
+inline int64_t settled_end(const int4 &e) { return std::max<int64_t>(e.x, (int64_t)e.z - 1); }
+
 // Far rows [rlo, rhi) of block b of the blocked kernel: rows older than the previous block,
-// limited to the short window.
-inline void block_rows(const fd_problem &p, int tb, int64_t b, int64_t &rlo, int64_t &rhi)
+// limited to the short window; with adaptive memory, from the block's first settled row.
+inline void block_rows(const fd_problem &p, const Geo &g, int64_t b, int64_t &rlo, int64_t &rhi)
 {
-    const int64_t kb = b * tb;
-    rhi = std::max<int64_t>(0, kb - tb);
-    rlo = (p.mem_mode == FD_MEM_SHORT) ? std::max<int64_t>(0, kb - p.mem_L) : 0;
+    const int64_t kb = b * g.tb;
+    rhi = std::max<int64_t>(0, kb - g.tb);
+    rlo = (p.mem_mode == FD_MEM_SHORT)                                    ? std::max<int64_t>(0, kb - p.mem_L)
+          : (p.mem_mode == FD_MEM_ADAPTIVE && b < (int64_t)g.br0.size()) ? g.br0[b]
+                                                                         : 0;
     rlo = std::min(rlo, rhi);
 }
 
@@ -257,7 +266,7 @@ inline void block_rows(const fd_problem &p, int tb, int64_t b, int64_t &rlo, int
 inline void block_chunks(const fd_problem &p, const Geo &g, int64_t b, int64_t &Rb, int64_t &Cb)
 {
     int64_t lo, hi;
-    block_rows(p, g.tb, b, lo, hi);
+    block_rows(p, g, b, lo, hi);
     const int64_t rows = hi - lo;
     Rb = g.R;
     if (g.cmax) Rb = std::max<int64_t>(Rb, (rows + g.cmax - 1) / g.cmax);
@@ -313,11 +322,19 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.ub = 0;
     g.cmax = 0;
     g.rwin = g.R;
+    g.br0.clear();
     if (g.tb) {
+        if (p.mem_mode == FD_MEM_ADAPTIVE) {
+            // rows 0 .. k-e(k)-1 are step k's tail: far rows start above every step's tail
+            g.br0.assign(g.nblocks, 0);
+            for (int64_t b = 0; b < g.nblocks; ++b)
+                for (int64_t k = b * g.tb; k < std::min<int64_t>((b + 1) * g.tb, p.max_steps); ++k)
+                    g.br0[b] = (int)std::max<int64_t>(g.br0[b], k - settled_end(s.step[k]));
+        }
         int64_t rmax = 0;
         for (int64_t b = 0; b < g.nblocks; ++b) {
             int64_t lo, hi;
-            block_rows(p, g.tb, b, lo, hi);
+            block_rows(p, g, b, lo, hi);
             rmax = std::max(rmax, hi - lo);
         }
         if (!p.chunk_terms) {
@@ -375,10 +392,14 @@ int64_t blocked_stream_rows(const fd_problem &p, const Geo &g)
     int64_t st = 0;
     for (int64_t b = 0; b < g.nblocks; ++b) {
         int64_t lo, hi;
-        block_rows(p, tb, b, lo, hi);
+        block_rows(p, g, b, lo, hi);
         st += hi - lo;
         // block-long update units read the previous block's rows once; later rows stay on chip
         if (g.ub) st += std::min<int64_t>(tb, b * tb);
+        // adaptive tail rows below the far rows: once per block-long unit, else once per step
+        if (p.mem_mode == FD_MEM_ADAPTIVE)
+            st += (int64_t)std::min<int64_t>(lo, (int64_t)g.br0[b]) *
+                  (g.ub ? 1 : std::min<int64_t>(tb, p.max_steps - b * tb));
     }
     if (g.ub) return st;
     for (int64_t k = 0; k < p.max_steps; ++k) {
@@ -398,7 +419,8 @@ struct Layout {
     char *part;
     unsigned *arrive, *done;
     char *psi, *dpsi, *gcoef;
-    int *glag;
+    char *gw;  // blocked, adaptive memory: settled weight g(m) of every lag
+    int *glag, *br0;
     int4 *sched;
     // adjoint
     char *ckpt, *seg, *rec[2], *ahist, *abuf[2];
@@ -433,6 +455,9 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     const size_t ng = std::max<size_t>(1, s.G.size());
     L.glag = (int *)c.take(sizeof(int) * ng);
     L.gcoef = c.take((size_t)g.sa * ng);
+    const bool gtab = g.tb && p.mem_mode == FD_MEM_ADAPTIVE;
+    L.gw = gtab ? c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa) : nullptr;
+    L.br0 = gtab ? (int *)c.take(sizeof(int) * (size_t)(g.nblocks + 1)) : nullptr;
     L.ckpt = L.seg = L.rec[0] = L.rec[1] = L.ahist = L.abuf[0] = L.abuf[1] = nullptr;
     L.dots = nullptr;
     L.ckpt_rows = L.seg_rows = 0;
@@ -473,8 +498,8 @@ Ctrl carve_ctrl(Carve &c)
 // Host-side tables of an instance, converted to the accumulator type.
 struct Tables {
     std::vector<double> psi, dpsi;
-    std::vector<unsigned char> psi_a, dpsi_a, gcoef_a;
-    std::vector<int> glag;
+    std::vector<unsigned char> psi_a, dpsi_a, gcoef_a, gw_a;
+    std::vector<int> glag, br0;
 };
 
 template <class TA> void to_acc(const std::vector<double> &x, std::vector<unsigned char> &out)
@@ -496,14 +521,27 @@ void build_tables(const fd_problem &p, const Sched &s, const Geo &g, Tables &t)
         gc[i] = (double)s.G[i].mult * t.psi[s.G[i].lag];
         t.glag[i] = s.G[i].lag;
     }
+    // blocked adaptive memory: g(m) = psi_m on the base interval [0, a], d psi_m at a median,
+    // 0 at the other lags (each median's weight, as the per-step schedule uses it)
+    std::vector<double> gw;
+    if (g.tb && p.mem_mode == FD_MEM_ADAPTIVE) {
+        gw.assign(n, 0.0);
+        for (int64_t m = 0; m <= std::min<int64_t>(p.mem_a, n - 1); ++m) gw[m] = t.psi[m];
+        for (size_t i = 0; i < s.G.size(); ++i)
+            if (s.G[i].lag < n) gw[s.G[i].lag] = gc[i];
+        t.br0 = g.br0;
+        t.br0.push_back(0);
+    }
     if (g.sa == 8) {
         to_acc<double>(t.psi, t.psi_a);
         to_acc<double>(t.dpsi, t.dpsi_a);
         to_acc<double>(gc, t.gcoef_a);
+        to_acc<double>(gw, t.gw_a);
     } else {
         to_acc<float>(t.psi, t.psi_a);
         to_acc<float>(t.dpsi, t.dpsi_a);
         to_acc<float>(gc, t.gcoef_a);
+        to_acc<float>(gw, t.gw_a);
     }
 }
 
@@ -522,6 +560,10 @@ int upload_tables(const fd_problem &p, const Sched &s, const Tables &t, const La
     CK(cudaMemcpyAsync(L.sched, s.step.data(), sizeof(int4) * s.step.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(L.glag, t.glag.data(), sizeof(int) * t.glag.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(L.gcoef, t.gcoef_a.data(), t.gcoef_a.size(), cudaMemcpyHostToDevice, st));
+    if (L.gw) {
+        CK(cudaMemcpyAsync(L.gw, t.gw_a.data(), t.gw_a.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(L.br0, t.br0.data(), sizeof(int) * t.br0.size(), cudaMemcpyHostToDevice, st));
+    }
     (void)p;
     return FD_OK;
 }
@@ -575,6 +617,8 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.sched = L.sched;
     I.g_lag = L.glag;
     I.g_coef = L.gcoef;
+    I.gw = L.gw;
+    I.br0 = L.br0;
     if (!adj && L.ckpt) {
         I.tape = L.ckpt;
         I.tape_k0 = 0;

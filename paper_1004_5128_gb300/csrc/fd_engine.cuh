@@ -81,6 +81,8 @@ struct Inst {
     const int4 *sched;       // per step: (nb, ng, tail_lo, tail_hi)
     const int *g_lag;        // adaptive medians (prefix-ordered)
     const char *g_coef;      // d * psi at the medians
+    const char *gw;          // blocked kernel, adaptive memory: settled weight g(m) of every lag
+    const int *br0;          // blocked kernel, adaptive memory: first far row of each block
     char *tape;              // optional u rows (checkpoints / recompute segment)
     const char *uadj;        // adjoint: forward states u^r
     double *dots;            // adjoint: [T][8] per-tile gradient partials

@@ -37,11 +37,22 @@ struct UnitTB {
 };
 
 // Far rows [rlo, rhi) of block b: rows older than the previous block, within the short window.
+// With adaptive memory the far rows start at the block's first settled row; the rows below
+// (tail rows of some step of the block) are added by the update units.
 template <int TB> __device__ __forceinline__ void far_rows(const Inst &I, int b, int &rlo, int &rhi)
 {
     const int kb = b * TB;
     rhi = max(0, kb - TB);
-    rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : 0);
+    rlo = min(rhi, (I.mem_mode == 1) ? max(0, kb - I.mem_L) : I.gw ? I.br0[b] : 0);
+}
+
+// Adaptive memory (Definitions 3.1-3.2): lags up to e(k) carry their settled weight g(m) at step
+// k (psi_m on the base interval, d psi_m at a median, 0 between medians), lags e(k)+1 .. k are
+// the step's tail, weight psi_m.  e(k) from the step's schedule (nb, ng, tail_lo, tail_hi).
+__device__ __forceinline__ int settled_end(const Inst &I, int k)
+{
+    const int4 e = I.sched[k];
+    return max(e.x, e.z - 1);
 }
 
 // Rows per far chunk of block b: R, or enough that the block has at most cmax chunks.
@@ -87,6 +98,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     __shared__ Inst I;
     __shared__ UnitTB U;
     __shared__ int s_cur_inst, s_ok, s_ok2, s_pipe;
+    __shared__ int s_ek[TB];  // block-long unit, adaptive memory: e(k) of the block's steps
     __shared__ double s_dred[ADJ ? 16 : 1][6];
 
     if (tid == 0) {
@@ -235,7 +247,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     const int q = e / WS, i = e - q * WS, w = i + q;
                     const int lag = lag0 + w;
                     const bool cut = (w >= nw) || (I.mem_mode == 1 && lag > I.mem_L);
-                    psw[q * WS + i] = cut ? 0.f : psi[lag];
+                    psw[q * WS + i] = cut ? 0.f : I.gw ? reinterpret_cast<const float *>(I.gw)[lag] : psi[lag];
                     if (ADJ) psw2[q * WS + i] = cut ? 0.f : reinterpret_cast<const float *>(I.dpsi)[lag];
                 }
             }
@@ -692,6 +704,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             // then rows by increasing row index), so results agree with them to the bit when
             // the chunks agree.  The sums live in the stage ring, idle during this unit.
             const int kf = max(kb, L.k0), kl = min(kb + TB, kend);
+            if (tid < TB) s_ek[tid] = (I.gw && kb + tid < I.ksteps) ? settled_end(I, kb + tid) : 0x7fffffff;
             if (tid < 32) {
                 int ok = 1;
                 if (tid == 0) {
@@ -728,33 +741,43 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         if (ADJ) h2[ADJ ? t : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(C - 1, t, 1) + j0));
                     }
                 }
-                for (int r = max(0, kb - TB); r < kf; r += 4) {
-                    float4 x[4];
+                // rows [ra, rb) with each step's weight of their lag, four loads in flight
+                const float *gwf = reinterpret_cast<const float *>(I.gw);
+                auto add_rows = [&](int ra, int rb) {
+                    for (int r = ra; r < rb; r += 4) {
+                        float4 x[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        x[i] = (r + i < kf) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int i = 0; i < 4; ++i)
+                            x[i] = (r + i < rb) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                        for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int t = 0; t < TB; ++t) {
-                            const int lag = kb + t - (r + i);
-                            if (r + i >= kf || t < t0 || t >= t1 || lag > window(kb + t)) continue;
-                            const float cc = psi[lag];
-                            h[t].x = fmaf(cc, x[i].x, h[t].x);
-                            h[t].y = fmaf(cc, x[i].y, h[t].y);
-                            h[t].z = fmaf(cc, x[i].z, h[t].z);
-                            h[t].w = fmaf(cc, x[i].w, h[t].w);
-                            if (ADJ) {
-                                const float c2 = dpsi[lag];
-                                float4 &g = h2[ADJ ? t : 0];
-                                g.x = fmaf(c2, x[i].x, g.x);
-                                g.y = fmaf(c2, x[i].y, g.y);
-                                g.z = fmaf(c2, x[i].z, g.z);
-                                g.w = fmaf(c2, x[i].w, g.w);
+                            for (int t = 0; t < TB; ++t) {
+                                const int lag = kb + t - (r + i);
+                                if (r + i >= rb || t < t0 || t >= t1 || lag > window(kb + t)) continue;
+                                const float cc = (I.gw && lag <= s_ek[t]) ? gwf[lag] : psi[lag];
+                                h[t].x = fmaf(cc, x[i].x, h[t].x);
+                                h[t].y = fmaf(cc, x[i].y, h[t].y);
+                                h[t].z = fmaf(cc, x[i].z, h[t].z);
+                                h[t].w = fmaf(cc, x[i].w, h[t].w);
+                                if (ADJ) {
+                                    const float c2 = dpsi[lag];
+                                    float4 &g = h2[ADJ ? t : 0];
+                                    g.x = fmaf(c2, x[i].x, g.x);
+                                    g.y = fmaf(c2, x[i].y, g.y);
+                                    g.z = fmaf(c2, x[i].z, g.z);
+                                    g.w = fmaf(c2, x[i].w, g.w);
+                                }
                             }
-                        }
+                    }
+                };
+                if (I.gw) {  // adaptive memory: the tail rows below the far rows
+                    int rlo, rhi;
+                    far_rows<TB>(I, b, rlo, rhi);
+                    add_rows(0, rlo);
                 }
+                add_rows(max(0, kb - TB), kf);
 #pragma unroll
                 for (int t = 0; t < TB; ++t)
                     if (t >= t0 && t < t1) {
@@ -799,7 +822,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     for (int t2 = t + 1; t2 < t1; ++t2) {
                         const int lag = t2 - t;
                         if (lag > window(kb + t2)) continue;
-                        const float cc = psi[lag];
+                        const float cc = (I.gw && lag <= s_ek[t2]) ? reinterpret_cast<const float *>(I.gw)[lag] : psi[lag];
                         float4 a = Hs[t2 * nthr + tid];
                         a.x = fmaf(cc, d[0], a.x);
                         a.y = fmaf(cc, d[1], a.y);
@@ -894,6 +917,32 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     H2[3] += w2.w;
                 }
             }
+            // weight of lag m at this step (adaptive memory: settled or tail weight)
+            const int ek = I.gw ? settled_end(I, k) : 0x7fffffff;
+            auto wgt = [&](int m) -> float {
+                return (I.gw && m <= ek) ? reinterpret_cast<const float *>(I.gw)[m] : psi[m];
+            };
+            if (!ADJ && I.gw) {
+                // adaptive memory: the tail rows below the far rows, oldest first
+                int rlo, rhi;
+                far_rows<TB>(I, b, rlo, rhi);
+                for (int r = 0; r < rlo; r += 4) {
+                    float4 x[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        x[i] = (r + i < rlo) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (r + i >= rlo) continue;
+                        const float cc = wgt(k - (r + i));
+                        H[0] = fmaf(cc, x[i].x, H[0]);
+                        H[1] = fmaf(cc, x[i].y, H[1]);
+                        H[2] = fmaf(cc, x[i].z, H[2]);
+                        H[3] = fmaf(cc, x[i].w, H[3]);
+                    }
+                }
+            }
             // head lags hk .. 2: rows this tile wrote at steps up to k-2, four loads in flight
             int m = hk;
             for (; m - 3 >= 2; m -= 4) {
@@ -902,7 +951,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 for (int i = 0; i < 4; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(m - i)));
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float cc = psi[m - i];
+                    const float cc = wgt(m - i);
                     H[0] = fmaf(cc, x[i].x, H[0]);
                     H[1] = fmaf(cc, x[i].y, H[1]);
                     H[2] = fmaf(cc, x[i].z, H[2]);
@@ -918,7 +967,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             }
             for (; m >= 2; --m) {
                 const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow(m)));
-                const float cc = psi[m];
+                const float cc = wgt(m);
                 H[0] = fmaf(cc, x.x, H[0]);
                 H[1] = fmaf(cc, x.y, H[1]);
                 H[2] = fmaf(cc, x.z, H[2]);

@@ -1,5 +1,5 @@
-"""Temporally blocked engine (time_block = 4 / 8 / 16; FP32, full and short memory) against the
-FP64 oracle and against properties that hold at full size, with block-long update units (the
+"""Temporally blocked engine (time_block = 4 / 8 / 16; FP32, full, short and adaptive memory)
+against the FP64 oracle and against properties that hold at full size, with block-long update units (the
 default where the tiles are few) and with one update unit per step (step_updates); the blocked
 reverse-time adjoint (time_block = 4 / 8) against the oracle's adjoint."""
 import numpy as np
@@ -52,6 +52,44 @@ def test_block_updates_equal_step_updates_bitwise(tb, chunk, mode, L):
         assert np.array_equal(outs[0], x)
 
 
+def ragged_adaptive(a, rule, K=300, bc=synth.BC_NOFLUX):
+    return synth.with_mode(ragged(bc, synth.MEM_FULL, K=K), synth.MEM_ADAPTIVE, a=a, rule=rule)
+
+
+@pytest.mark.parametrize("step_updates", [False, True])
+@pytest.mark.parametrize("tb", [4, 8, 16])
+@pytest.mark.parametrize("rule", [synth.ADAPT_PAPER, synth.ADAPT_PARTITION])
+@pytest.mark.parametrize("a", [2, 3, 10])
+def test_blocked_adaptive_matches_oracle(tb, rule, a, step_updates):
+    """Far rows carry the settled weights g(m) (psi on the base interval, d psi at the medians,
+    0 between); each step's tail rows (a = 2: tails longer than a block) and near rows take
+    that step's weights in the update units."""
+    p = ragged_adaptive(a, rule)
+    s = FRD(p, time_block=tb, chunk_terms=16, step_updates=step_updates)
+    assert s.geometry()["time_block"] == tb
+    s.set_state(p["u0"])
+    assert rel_inf(s.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5
+
+
+@pytest.mark.parametrize("tb,chunk", [(4, 16), (8, 24), (16, 40)])
+@pytest.mark.parametrize("a", [2, 10])
+def test_blocked_adaptive_block_updates_equal_step_updates_bitwise(tb, chunk, a):
+    """Block-long and per-step update units sum the same terms in the same order, in one
+    launch and in launches that start inside blocks."""
+    p = ragged_adaptive(a, synth.ADAPT_PAPER)
+    outs = []
+    for su in (False, True):
+        s = FRD(p, time_block=tb, chunk_terms=chunk, step_updates=su)
+        s.set_state(p["u0"])
+        outs.append(s.run(p["K"]).cpu().numpy())
+        s.set_state(p["u0"])
+        for n in (37, 5, 101, 1, 156):
+            s.step(n)
+        outs.append(s.run(0).cpu().numpy())
+    for x in outs[1:]:
+        assert np.array_equal(outs[0], x)
+
+
 def test_blocked_1d_many_tiles():
     p = synth.problem(1, 3001, 1, 0.55, 1.0, synth.dt_for_courant(0.2, 1.0, 1.0, 0.55), 1.0,
                       synth.BC_DIRICHLET0, react=(0, -0.05, 0, 0), K=400,
@@ -76,7 +114,7 @@ def test_blocked_launch_split_is_bitwise_invariant(step_updates):
 
 
 @pytest.mark.parametrize("step_updates", [False, True])
-@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_SHORT])
+@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_SHORT, synth.MEM_ADAPTIVE])
 def test_blocked_config2_full_size(mode, step_updates):
     """256^2, 5000 steps: eigenmode superposition against the oracle's scalar recursions, and
     the Gaussian input's mass balance."""

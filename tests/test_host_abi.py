@@ -133,8 +133,11 @@ def test_time_block_validation():
         with pytest.raises(L.FdError) as e:
             L.fd_workspace_bytes(make_problem(p, **bad))
         assert e.value.code == code
+    # adaptive memory blocks forward; its schedule has no adjoint
+    ad = synth.with_mode(p, synth.MEM_ADAPTIVE, a=10)
+    assert L.fd_workspace_bytes(make_problem(ad, time_block=8)) > L.fd_workspace_bytes(make_problem(ad)) > 0
     with pytest.raises(L.FdError) as e:
-        L.fd_workspace_bytes(make_problem(synth.with_mode(p, synth.MEM_ADAPTIVE, a=10), time_block=8))
+        L.fd_workspace_bytes(make_problem(ad, time_block=8, keep_tape=True))
     assert e.value.code == L.FD_ERR_UNSUPPORTED
 
 
