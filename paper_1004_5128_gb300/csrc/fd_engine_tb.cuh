@@ -263,24 +263,27 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc2[t][v] = 0.f;
 
-            auto issue = [&](int s) {
-                const int bb = (int)(n_issued % (uint32_t)NS);
+            // Stage s is filled by warp s mod (warps), one lane per row: the copies of a stage
+            // go out together and the issue work rotates over the warps instead of delaying
+            // one warp at every stage barrier.  Called by all lanes of the issuing warp.
+            const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+            auto issue = [&](int s, uint32_t slot) {
+                const int bb = (int)(slot % (uint32_t)NS);
                 const int a0 = s * RS, a1 = min(nrow, a0 + RS);
-                mbar_expect_tx(&bars[bb], (uint32_t)(tile_bytes * (a1 - a0)));
+                if (lane == 0) mbar_expect_tx(&bars[bb], (uint32_t)(tile_bytes * (a1 - a0)));
+                __syncwarp();
                 const char *col = I.hist + (size_t)tile * I.P * 4;
-                for (int a = a0; a < a1; ++a)
+                for (int a = a0 + lane; a < a1; a += 32)
                     bulk_g2s(stages + ((size_t)bb * RS + (a - a0)) * row_bytes,
                              col + (size_t)((r0 + a) % I.cap) * I.pitch, (uint32_t)tile_bytes, &bars[bb]);
             };
-            if (tid == 0) {
-                fence_proxy_async_global();
+            // every lane that issues copies orders the rows it acquired before the async proxy
+            if (lane < RS) fence_proxy_async_global();
+            {
                 const int pre = min(NS, nst);
-                for (int s = 0; s < pre; ++s) {
-                    issue(s);
-                    ++n_issued;
-                }
-            } else {
-                n_issued += (uint32_t)min(NS, nst);
+                for (int s = 0; s < pre; ++s)
+                    if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
+                n_issued += (uint32_t)pre;
             }
             for (int s = 0; s < nst; ++s) {
                 const int bb = (int)(n_used % (uint32_t)NS);
@@ -359,7 +362,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 ++n_used;
                 __syncthreads();
                 if (s + NS < nst) {
-                    if (tid == 0) issue(s + NS);
+                    if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
                     ++n_issued;
                 }
             }
