@@ -521,25 +521,28 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             toff[t] = slot;
         }
         __syncthreads();
-        auto issue = [&](int s) {  // thread 0: stage s of this unit into ring slot n_issued % NS
-            const int b = (int)(n_issued % (uint32_t)NS);
+        // Stage s of this unit into ring slot `slot` % NS, by warp s mod (warps), one lane per
+        // row: the copies of a stage go out together and the issue work rotates over the warps
+        // instead of delaying one warp at every stage barrier.  All lanes of the warp call it.
+        const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+        auto issue = [&](int s, uint32_t slot) {
+            const int b = (int)(slot % (uint32_t)NS);
             const int t0 = s * RS;
             const int t1 = min(nterm, t0 + RS);
-            mbar_expect_tx(&bars[b], (uint32_t)(tile_bytes * (t1 - t0)));
+            if (lane == 0) mbar_expect_tx(&bars[b], (uint32_t)(tile_bytes * (t1 - t0)));
+            __syncwarp();
             const char *col = I.hist + (size_t)tile * I.P * sizeof(TH);
-            for (int t = t0; t < t1; ++t)
+            for (int t = t0 + lane; t < t1; t += 32)
                 bulk_g2s(stages + ((size_t)b * RS + (t - t0)) * row_bytes, col + (size_t)toff[t] * I.pitch,
                          (uint32_t)tile_bytes, &bars[b]);
         };
-        if (tid == 0) {
-            fence_proxy_async_global();
+        // every lane that issues copies orders the rows it acquired before the async proxy
+        if (lane < RS) fence_proxy_async_global();
+        {
             const int pre = min(NS, nst);
-            for (int s = 0; s < pre; ++s) {
-                issue(s);
-                ++n_issued;
-            }
-        } else {
-            n_issued += (uint32_t)min(NS, nst);
+            for (int s = 0; s < pre; ++s)
+                if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
+            n_issued += (uint32_t)pre;
         }
         for (int s = 0; s < nst; ++s) {
             const int b = (int)(n_used % (uint32_t)NS);
@@ -581,7 +584,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             ++n_used;
             __syncthreads();  // slot b fully read by every thread
             if (s + NS < nst) {
-                if (tid == 0) issue(s + NS);
+                if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
                 ++n_issued;
             }
         }
