@@ -78,22 +78,26 @@ def test_config4_full_batch_sampled_vs_oracle(mode):
 
 
 @pytest.mark.parametrize("tb", [4, 8, 16])
-@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_SHORT])
+@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_SHORT, synth.MEM_ADAPTIVE])
 def test_small_uneven_blocked_batch_vs_oracle(tb, mode):
     """The temporally blocked kernel over a batch of uneven 1-D/2-D instances with their own
-    step counts (not multiples of the block), chunk sizes and short windows."""
+    step counts (not multiples of the block), chunk sizes, short windows and adaptive base
+    intervals (a = 2 .. 10, both median rules)."""
     probs = synth.config4(count=10, steps_range=(50, 300), side_range=(9, 60), n1_range=(5, 2000))
     if mode == synth.MEM_SHORT:
         probs = [synth.with_mode(p, synth.MEM_SHORT, L=7 + 13 * i) for i, p in enumerate(probs)]
+    if mode == synth.MEM_ADAPTIVE:
+        probs = [synth.with_mode(p, synth.MEM_ADAPTIVE, a=2 + i % 9, rule=i % 2) for i, p in enumerate(probs)]
     out, b = run_batch(probs, chunk_terms=24, time_block=tb)
     assert b.geometry(0)["time_block"] == tb
     for p, got in zip(probs, out):
         assert rel_inf(got, oracle.run(p)) < 1e-5
 
 
-def test_blocked_batch_equals_single_blocked_runs_bitwise():
+@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_ADAPTIVE])
+def test_blocked_batch_equals_single_blocked_runs_bitwise(mode):
     """Same blocks, chunks and summation order as one instance per launch."""
-    probs = synth.config4(count=6, steps_range=(100, 300), side_range=(20, 50), n1_range=(40, 900))
+    probs = synth.config4(mode=mode, count=6, steps_range=(100, 300), side_range=(20, 50), n1_range=(40, 900))
     b = FRDBatch(probs, chunk_terms=32, time_block=8)
     res = []
     for _ in range(2):

@@ -90,6 +90,22 @@ def test_blocked_adaptive_block_updates_equal_step_updates_bitwise(tb, chunk, a)
         assert np.array_equal(outs[0], x)
 
 
+@pytest.mark.parametrize("step_updates", [False, True])
+@pytest.mark.parametrize("tb", [8, 16])
+@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_ADAPTIVE])
+def test_blocked_3d_matches_oracle(tb, mode, step_updates):
+    """7-point stencil on a 13x11x9 grid (ragged last tile), mirror boundaries."""
+    n = 13 * 11 * 9
+    p = synth.problem(3, 13, 11, 0.65, 0.9, synth.dt_for_courant(0.05, 0.9, 1.0, 0.65), 1.0,
+                      synth.BC_NOFLUX, react=(0.02, -0.3, 0.1, -0.2), K=220, nz=9,
+                      u0=synth.SplitMix64(33).uniform(n, 0, 1))
+    if mode == synth.MEM_ADAPTIVE:
+        p = synth.with_mode(p, synth.MEM_ADAPTIVE, a=4)
+    s = FRD(p, time_block=tb, chunk_terms=16, tile_threads=128, step_updates=step_updates)
+    s.set_state(p["u0"])
+    assert rel_inf(s.run(p["K"]).cpu().double().numpy(), oracle.run(p)) < 1e-5
+
+
 def test_blocked_1d_many_tiles():
     p = synth.problem(1, 3001, 1, 0.55, 1.0, synth.dt_for_courant(0.2, 1.0, 1.0, 0.55), 1.0,
                       synth.BC_DIRICHLET0, react=(0, -0.05, 0, 0), K=400,
