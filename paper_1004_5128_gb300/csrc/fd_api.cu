@@ -227,8 +227,9 @@ inline size_t smem_bytes(const Geo &g, int rmax)
 }
 
 // Blocked kernel: stage ring (block-long update units keep their steps' memory sums and their
-// tile's state there, so it holds at least tb x planes + 2 rows, as the kernel assumes), four shifted copies of each coefficient window (psi, and
-// psi' for the adjoint), barriers.
+// tile's state there, so it holds at least tb x planes + 2 rows, as the kernel assumes), four
+// shifted copies of each coefficient window (psi, and psi' for the adjoint; with adaptive memory
+// the first shifted copy holds the nonzero masks of the window's four-row groups), barriers.
 inline size_t smem_bytes_tb(const Geo &g, int rwin)
 {
     const int ring = std::max(g.NS * g.RS, g.tb * g.planes + 2);

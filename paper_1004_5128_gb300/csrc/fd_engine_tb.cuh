@@ -94,6 +94,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     float *psw2 = psw + 4 * WS;                                                    // psi' window (ADJ)
     uint64_t *bars = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(psw + PLANES * 4 * WS) + 15) & ~uintptr_t(15));
+    // adaptive memory: bit j of gmask[lo] says w[lo + j] != 0 (the window of a four-row group);
+    // the sparse loop reads the unshifted copy only, so the masks take the first shifted copy
+    uint32_t *gmask = reinterpret_cast<uint32_t *>(psw + WS);
 
     __shared__ Inst I;
     __shared__ UnitTB U;
@@ -239,11 +242,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             tile_bytes = (tile_bytes + 15) & ~15ll;
 
             // coefficient window w[i] = psi_{lag0 + i}: row r, step kb+t uses w[(r1-1-r) + t]
+            const bool sparse = !ADJ && I.gw != nullptr;
             {
                 const float *psi = reinterpret_cast<const float *>(I.psi);
                 const int lag0 = kb - (r1 - 1);
                 const int nw = nrow + TB - 1;
-                for (int e = tid; e < 4 * WS; e += nthr) {
+                for (int e = tid; e < (sparse ? WS : 4 * WS); e += nthr) {
                     const int q = e / WS, i = e - q * WS, w = i + q;
                     const int lag = lag0 + w;
                     const bool cut = (w >= nw) || (I.mem_mode == 1 && lag > I.mem_L);
@@ -252,6 +256,16 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 }
             }
             __syncthreads();
+            // Adaptive memory: the settled weights are zero between medians (at least two of three
+            // lags in the far rows), so a four-row group multiplies only the lags its window holds.
+            if (sparse) {
+                for (int lo = tid; lo + 4 <= nrow; lo += nthr) {
+                    uint32_t m = 0;
+                    for (int j = 0; j < TB + 4; ++j) m |= (psw[lo + j] != 0.f ? 1u : 0u) << j;
+                    gmask[lo] = m;
+                }
+                __syncthreads();
+            }
 
             float acc[TB][V], acc2[ADJ ? TB : 1][V];
 #pragma unroll
@@ -304,6 +318,37 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const int rows = min(RS, nrow - s * RS);
                 const unsigned char *base = stages + (size_t)bb * RS * row_bytes + (size_t)tid * 16;
                 int r = 0;
+                if (sparse) {
+                    // Four rows at a time, lag by lag over the window's nonzero weights only.  Lag
+                    // J of the window meets row i at step t = J - 3 + i; J descending keeps each
+                    // accumulator's rows in increasing order, as in the dense loop below, and the
+                    // skipped products are exact zeros, so the sums are the dense loop's.
+                    for (; r + 4 <= rows; r += 4) {
+                        const int lo = nrow - 1 - (s * RS + r) - 3;
+                        const uint32_t m = gmask[lo];
+                        float x[4][V];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)(r + i) * row_bytes);
+                            x[i][0] = x4.x;
+                            x[i][1] = x4.y;
+                            x[i][2] = x4.z;
+                            x[i][3] = x4.w;
+                        }
+#pragma unroll
+                        for (int J = TB + 3; J >= 0; --J) {
+                            if (!(m & (1u << J))) continue;
+                            const float cj = psw[lo + J];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int t = J - 3 + i;
+                                if (t < 0 || t >= TB) continue;
+#pragma unroll
+                                for (int v = 0; v < V; ++v) acc[t][v] = fmaf(cj, x[i][v], acc[t][v]);
+                            }
+                        }
+                    }
+                }
                 // Four rows at a time.  Row a = s*RS + r + i uses w[wo - i + t], wo = nrow-1-(s*RS+r):
                 // the TB+3 coefficients w[wo-3 .. wo+TB-1] come in aligned 16-byte loads from the
                 // copy shifted by (wo-3) & 3 and serve all four rows from registers.
