@@ -267,11 +267,14 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 __syncthreads();
             }
 
-            float acc[TB][V], acc2[ADJ ? TB : 1][V];
+            // accumulators as point pairs: one packed two-lane FMA (each lane an IEEE fmaf)
+            // serves two points, halving the far loop's FMA instructions
+            float2 acc[TB][V / 2];
+            float acc2[ADJ ? TB : 1][V];
 #pragma unroll
             for (int t = 0; t < TB; ++t)
 #pragma unroll
-                for (int v = 0; v < V; ++v) acc[t][v] = 0.f;
+                for (int h = 0; h < V / 2; ++h) acc[t][h] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < (ADJ ? TB : 1); ++t)
 #pragma unroll
@@ -339,12 +342,14 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         for (int J = TB + 3; J >= 0; --J) {
                             if (!(m & (1u << J))) continue;
                             const float cj = psw[lo + J];
+                            const float2 cj2 = make_float2(cj, cj);
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 const int t = J - 3 + i;
                                 if (t < 0 || t >= TB) continue;
 #pragma unroll
-                                for (int v = 0; v < V; ++v) acc[t][v] = fmaf(cj, x[i][v], acc[t][v]);
+                                for (int h = 0; h < V / 2; ++h)
+                                    acc[t][h] = __ffma2_rn(cj2, make_float2(x[i][2 * h], x[i][2 * h + 1]), acc[t][h]);
                             }
                         }
                     }
@@ -378,7 +383,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
                         for (int t = 0; t < TB; ++t)
 #pragma unroll
-                            for (int v = 0; v < V; ++v) acc[t][v] = fmaf(c[3 - i + t], x[v], acc[t][v]);
+                            for (int h = 0; h < V / 2; ++h)
+                                acc[t][h] = __ffma2_rn(make_float2(c[3 - i + t], c[3 - i + t]), make_float2(x[2 * h], x[2 * h + 1]),
+                                                       acc[t][h]);
                         if (ADJ) {
 #pragma unroll
                             for (int t = 0; t < (ADJ ? TB : 1); ++t)
@@ -396,7 +403,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     for (int t = 0; t < TB; ++t) {
                         const float cc = psw[wo + t];
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[t][v] = fmaf(cc, x[v], acc[t][v]);
+                        for (int h = 0; h < V / 2; ++h)
+                            acc[t][h] = __ffma2_rn(make_float2(cc, cc), make_float2(x[2 * h], x[2 * h + 1]), acc[t][h]);
                         if (ADJ) {
                             const float cd = psw2[wo + t];
 #pragma unroll
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 };
 #pragma unroll
                 for (int t = 0; t < TB; ++t) {
-                    add_store(t, 0, acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+                    add_store(t, 0, acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
                     if (ADJ)
                         add_store(t, 1, acc2[ADJ ? t : 0][0], acc2[ADJ ? t : 0][1], acc2[ADJ ? t : 0][2],
                                   acc2[ADJ ? t : 0][3]);
