@@ -269,8 +269,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
             // accumulators as point pairs: one packed two-lane FMA (each lane an IEEE fmaf)
             // serves two points, halving the far loop's FMA instructions
-            float2 acc[TB][V / 2];
-            float acc2[ADJ ? TB : 1][V];
+            float2 acc[TB][V / 2], acc2[ADJ ? TB : 1][V / 2];
 #pragma unroll
             for (int t = 0; t < TB; ++t)
 #pragma unroll
@@ -278,7 +277,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
             for (int t = 0; t < (ADJ ? TB : 1); ++t)
 #pragma unroll
-                for (int v = 0; v < V; ++v) acc2[t][v] = 0.f;
+                for (int h = 0; h < V / 2; ++h) acc2[t][h] = make_float2(0.f, 0.f);
 
             // Stage s is filled by warp s mod (warps), one lane per row: the copies of a stage
             // go out together and the issue work rotates over the warps instead of delaying
@@ -390,8 +389,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
                             for (int t = 0; t < (ADJ ? TB : 1); ++t)
 #pragma unroll
-                                for (int v = 0; v < V; ++v)
-                                    acc2[t][v] = fmaf(c2[ADJ ? 3 - i + t : 0], x[v], acc2[t][v]);
+                                for (int h = 0; h < V / 2; ++h)
+                                    acc2[t][h] = __ffma2_rn(make_float2(c2[ADJ ? 3 - i + t : 0], c2[ADJ ? 3 - i + t : 0]),
+                                                            make_float2(x[2 * h], x[2 * h + 1]), acc2[t][h]);
                         }
                     }
                 }
@@ -408,7 +408,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         if (ADJ) {
                             const float cd = psw2[wo + t];
 #pragma unroll
-                            for (int v = 0; v < V; ++v) acc2[ADJ ? t : 0][v] = fmaf(cd, x[v], acc2[ADJ ? t : 0][v]);
+                            for (int h = 0; h < V / 2; ++h)
+                                acc2[ADJ ? t : 0][h] = __ffma2_rn(make_float2(cd, cd), make_float2(x[2 * h], x[2 * h + 1]),
+                                                                  acc2[ADJ ? t : 0][h]);
                         }
                     }
                 }
@@ -463,8 +465,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 for (int t = 0; t < TB; ++t) {
                     add_store(t, 0, acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
                     if (ADJ)
-                        add_store(t, 1, acc2[ADJ ? t : 0][0], acc2[ADJ ? t : 0][1], acc2[ADJ ? t : 0][2],
-                                  acc2[ADJ ? t : 0][3]);
+                        add_store(t, 1, acc2[ADJ ? t : 0][0].x, acc2[ADJ ? t : 0][0].y, acc2[ADJ ? t : 0][1].x,
+                                  acc2[ADJ ? t : 0][1].y);
                 }
             }
             // CTA barrier, then one release add: cumulative over every thread's partial stores
