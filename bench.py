@@ -135,11 +135,22 @@ def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
     return rows * N * sh + p["K"] * N * (2 * ss + sh)
 
 
+def code_hash(path: str) -> str:
+    """SHA-256 of a C/C++/CUDA source with its comments and blank space removed: the code that
+    the compiler sees, so that a comment edit does not count as a kernel change."""
+    import hashlib
+    import re
+    text = open(path, encoding="utf-8").read()
+    # string literals are kept whole (inline PTX holds no comment markers); comments go
+    pattern = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
+    code = pattern.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
+    return hashlib.sha256(" ".join(code.split()).encode()).hexdigest()
+
+
 def measured_traffic(key: str, geometry: dict):
     """DRAM bytes (read + write) of one launch from an ncu capture stored in profiles/traffic.json,
-    or None when there is none for this run, or when the kernel sources or the launch geometry
-    have changed since the counters were taken."""
-    import hashlib
+    or None when there is none for this run, or when the kernel code (comments aside) or the
+    launch geometry have changed since the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             entries = json.load(f)["entries"]
@@ -148,8 +159,7 @@ def measured_traffic(key: str, geometry: dict):
                 continue
             if any(geometry.get(k) != v for k, v in e["geometry"].items()):
                 continue
-            if all(hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest() == h
-                   for src, h in e["sources"].items()):
+            if all(code_hash(os.path.join(ROOT, src)) == h for src, h in e["sources"].items()):
                 return e["bytes"]
     except (OSError, KeyError, ValueError):
         return None

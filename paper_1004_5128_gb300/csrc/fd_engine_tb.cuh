@@ -1,4 +1,5 @@
-// fd_engine_tb.cuh -- temporally blocked variant of the engine (FP32, full and short memory).
+// fd_engine_tb.cuh -- temporally blocked variant of the engine (FP32; full, short and adaptive
+// memory).
 //
 // The full-memory sum is a Toeplitz product: row delta^r enters step k with weight
 // psi_{k-r} (eq. frac_norxn), so the steps k = kb .. kb+T-1 of one block all use the same old
@@ -11,6 +12,10 @@
 // block b+1 overlaps the T sequential updates of block b.  History traffic drops by about T
 // while the multiply-adds stay the same: the sum is the paper's, only grouped differently.
 // Short memory (eq. frac_shortmemory) is the same product with psi_m set to 0 for m > L.
+// Adaptive memory (Definitions 3.1-3.2) is the same product with the weights g(m) that the
+// medians settle on (psi_m on the base interval, d psi_m at a median, 0 between), for all rows
+// above the longest tail of the block's steps; the update units add those few oldest rows with
+// each step's own weights, and the far loop skips the zero weights.
 // The reverse-time adjoint (ADJ) has the same structure in adjoint steps over the rows
 // mu = L lambda, with a second accumulator for psi' = d psi / d gamma (see engine_kernel).
 //
@@ -22,8 +27,11 @@
 // tile's far count (group g-1) and its halo tiles' previous step (earlier in group g or in g-1);
 // a far unit of block g waits for block g-2's updates (group g-1).  Every wait therefore
 // targets units with smaller numbers, so the persistent grid cannot deadlock whatever the
-// residency.  Determinism, bounded waits, status words and the memory-ordering protocol are
-// those of engine_kernel.
+// residency.  Where the tiles are few, one block-long update unit per (block, tile) carries all
+// of the block's steps instead (placed after one wave of block g's far units, which never wait
+// for it); its sibling units must then be co-resident, which the host's tile limit ensures.
+// Determinism, bounded waits, status words and the memory-ordering protocol are those of
+// engine_kernel.
 #pragma once
 
 #include "fd_engine.cuh"
@@ -755,12 +763,13 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         if (U.fix == 2) {
             // ============================ block-long update unit: every step of block b, this tile
             // The block's steps run in order on this CTA.  The memory sum of step kb+t is the
-            // block's far partials, then the rows before the block (read once, oldest first),
-            // then the rows of the block's earlier steps, which this unit produced itself: each
-            // new delta^k is folded into the sums of the later steps right after its update.
-            // The summation order per step is that of the per-step units (partials by chunk,
-            // then rows by increasing row index), so results agree with them to the bit when
-            // the chunks agree.  The sums live in the stage ring, idle during this unit.
+            // running sum of the block's far chunks, then (adaptive memory) the tail rows below
+            // the far rows, then the rows before the block (read once, oldest first), then the
+            // rows of the block's earlier steps, which this unit produced itself: each new
+            // delta^k is folded into the sums of the later steps right after its update.  The
+            // summation order per step is that of the per-step units (partials by chunk, then
+            // rows by increasing row index), so results agree with them to the bit when the
+            // chunks agree.  The sums live in the stage ring, idle during this unit.
             const int kf = max(kb, L.k0), kl = min(kb + TB, kend);
             if (tid < TB) s_ek[tid] = (I.gw && kb + tid < I.ksteps) ? settled_end(I, kb + tid) : 0x7fffffff;
             if (tid < 32) {

@@ -153,3 +153,27 @@ def test_blocked_batch_validation():
     with pytest.raises(L.FdError) as e:
         L.fd_batch_workspace_bytes([make_problem(p, time_block=8, keep_tape=True) for p in probs])
     assert e.value.code == L.FD_ERR_UNSUPPORTED
+
+
+def test_bench_traffic_entries_follow_the_kernel_code(tmp_path):
+    """profiles/traffic.json entries are keyed to the kernel code with comments and blank space
+    removed: a comment edit keeps an entry, a code edit drops it."""
+    import importlib.util
+    import json
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    src = os.path.join(root, "paper_1004_5128_gb300", "csrc", "fd_engine_tb.cuh")
+    text = open(src).read()
+    h = bench.code_hash(src)
+    (tmp_path / "a.cuh").write_text(text.replace("const int lane = tid & 31", "/* x */ // y\n    const int lane = tid & 31", 1))
+    (tmp_path / "b.cuh").write_text(text.replace("const int lane = tid & 31", "const int lane = tid % 32", 1))
+    assert bench.code_hash(str(tmp_path / "a.cuh")) == h
+    assert bench.code_hash(str(tmp_path / "b.cuh")) != h
+    # an entry is reported for its own key and geometry only
+    e = json.load(open(os.path.join(root, "profiles", "traffic.json")))["entries"][0]
+    other = dict(e["geometry"], tile_threads=e["geometry"]["tile_threads"] // 2)
+    assert bench.measured_traffic(e["key"], other) is None
+    assert bench.measured_traffic("no such run", dict(e["geometry"])) is None
