@@ -373,9 +373,7 @@ int or_adjoint(const or_problem *p, const double *u0, long K, const double *targ
                double *J, double *dJ_du0, double *dJ_dgamma, double *dJ_dalpha,
                double dJ_dreact[4], int threads)
 {
-    if (check_problem(p, K) || (p->mem_mode != OR_MEM_FULL && p->mem_mode != OR_MEM_SHORT) || !u0 ||
-        !target || K < 1)
-        return -1;
+    if (check_problem(p, K) || !u0 || !target || K < 1) return -1;
     const long N = (long)p->nx * p->ny * p->nz;
     const double S = p->alpha * pow(p->dt, p->gamma) / (p->dx * p->dx);
     double *tape = malloc(sizeof(double) * (size_t)(K + 1) * (size_t)N);
@@ -387,11 +385,22 @@ int or_adjoint(const or_problem *p, const double *u0, long K, const double *targ
     double *du = malloc(sizeof(double) * (size_t)N);
     double *ltg = malloc(sizeof(double) * (size_t)N);
     double *uK = malloc(sizeof(double) * (size_t)N);
+    /* adaptive memory: wt[k * K + m] = multiplicity of lag m in step k's schedule */
+    int *wt = (p->mem_mode == OR_MEM_ADAPTIVE) ? calloc((size_t)K * (size_t)K, sizeof(int)) : NULL;
+    long *slag = (p->mem_mode == OR_MEM_ADAPTIVE) ? malloc(sizeof(long) * (size_t)(K + 1)) : NULL;
+    long *smul = (p->mem_mode == OR_MEM_ADAPTIVE) ? malloc(sizeof(long) * (size_t)(K + 1)) : NULL;
     int rc = 0;
-    if (!tape || !lam || !psi || !dpsi || !g || !gp || !du || !ltg || !uK) {
+    if (!tape || !lam || !psi || !dpsi || !g || !gp || !du || !ltg || !uK ||
+        (p->mem_mode == OR_MEM_ADAPTIVE && (!wt || !slag || !smul))) {
         rc = -2;
         goto done;
     }
+    if (wt)
+        for (long k = 0; k < K; ++k) {
+            const long n = or_schedule(p->mem_mode, p->mem_L, p->mem_a, p->adaptive_rule, k, slag, smul);
+            if (n < 0) { rc = -1; goto done; }
+            for (long t = 0; t < n; ++t) wt[(size_t)k * (size_t)K + (size_t)slag[t]] += (int)smul[t];
+        }
     rc = or_run(p, u0, K, uK, tape, threads);
     if (rc) goto done;
     or_weights(p->gamma, K + 1, psi, dpsi);
@@ -417,8 +426,15 @@ int or_adjoint(const or_problem *p, const double *u0, long K, const double *targ
             double s = 0, c = 0, sp = 0, cp = 0;
             for (long m = 0; m <= nm; ++m) {
                 const double l = lam[(size_t)(r + 1 + m) * (size_t)N + j];
-                nadd(&s, &c, psi[m] * l);
-                nadd(&sp, &cp, dpsi[m] * l);
+                if (wt) { /* delta^r enters step r+m with weight w_{r+m}(m) psi_m */
+                    const int w = wt[(size_t)(r + m) * (size_t)K + (size_t)m];
+                    if (!w) continue;
+                    nadd(&s, &c, ((double)w * psi[m]) * l);
+                    nadd(&sp, &cp, ((double)w * dpsi[m]) * l);
+                } else {
+                    nadd(&s, &c, psi[m] * l);
+                    nadd(&sp, &cp, dpsi[m] * l);
+                }
             }
             g[j] = s + c;
             gp[j] = sp + cp;
@@ -449,7 +465,7 @@ int or_adjoint(const or_problem *p, const double *u0, long K, const double *targ
         for (int i = 0; i < 4; ++i) dJ_dreact[i] = p->dt * (ds[2 + i] + dc[2 + i]);
 done:
     free(tape); free(lam); free(psi); free(dpsi); free(g); free(gp);
-    free(du); free(ltg); free(uK);
+    free(du); free(ltg); free(uK); free(wt); free(slag); free(smul);
     return rc;
 }
 

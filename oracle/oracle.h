@@ -72,18 +72,19 @@ int or_run(const or_problem *p, const double *u0, long K, double *uK, double *ta
 int or_run_cs(const or_problem *p, double gamma_im, double alpha_im, const double react_im[4],
               const double *u0_re, const double *u0_im, long K, double *uK_re, double *uK_im);
 
-/* FP64 reverse-time adjoint of the full- or short-memory scheme for
- * J = 1/2 sum_j (u^K_j - target_j)^2, following the discrete Lagrangian of
- * eq. frac_final:  lambda^K = u^K - target,
- *   g^r  = sum_{m=0}^{M(r)} psi_m  lambda^{r+1+m},
- *   g'^r = sum_{m=0}^{M(r)} psi'_m lambda^{r+1+m},
+/* FP64 reverse-time adjoint of the scheme for J = 1/2 sum_j (u^K_j - target_j)^2, following
+ * the discrete Lagrangian of eq. frac_final:  lambda^K = u^K - target,
+ *   g^r  = sum_{m=0}^{K-1-r} w_{r+m}(m) psi_m  lambda^{r+1+m},
+ *   g'^r = sum_{m=0}^{K-1-r} w_{r+m}(m) psi'_m lambda^{r+1+m},
  *   lambda^r = lambda^{r+1} + dt f'(u^r) lambda^{r+1} + S L^T g^r,
- * with M(r) = K-1-r (full memory) or min(L, K-1-r) (short memory: step k reads lags
- * m <= min(L, k) by eq. frac_shortmemory, so delta^r reaches the steps k = r+m with m <= L),
+ * where w_k(m) is the multiplicity of lag m in step k's schedule: delta^r enters step k = r+m
+ * with weight w_k(m) psi_m.  Full memory: w = 1.  Short memory: w = 1 for m <= L, else 0
+ * (eq. frac_shortmemory).  Adaptive memory: w_k(m) read from or_schedule(k) for every k
+ * (Definitions 3.1/3.2, Proposition 3.1; d at a median, 1 on the base interval and the tail).
  * S = alpha dt^g / dx^2, dJ/dalpha = (S/alpha) sum_r <L u^r, g^r>,
  * dJ/dgamma = S sum_r (ln dt <L u^r, g^r> + <L u^r, g'^r>),
  * dJ/dreact_i = dt sum_r <lambda^{r+1}, (u^r)^i>, dJ/du0 = lambda^0.
- * Requires mem_mode OR_MEM_FULL or OR_MEM_SHORT.  Any output pointer may be NULL. */
+ * Adaptive memory keeps a K x K table of multiplicities.  Any output pointer may be NULL. */
 int or_adjoint(const or_problem *p, const double *u0, long K, const double *target,
                double *J, double *dJ_du0, double *dJ_dgamma, double *dJ_dalpha,
                double dJ_dreact[4], int threads);

@@ -108,3 +108,41 @@ def test_short_memory_adjoint_matches_complex_step(bc, L):
     # the short-memory gradient differs from the full-memory one (the window matters)
     full = oracle.adjoint(synth.with_mode(p, synth.MEM_FULL), target)
     assert abs(full["dgamma"] - a["dgamma"]) > 1e-6 * abs(a["dgamma"])
+
+
+@pytest.mark.parametrize("bc,a,rule", [(synth.BC_DIRICHLET0, 3, 0), (synth.BC_NOFLUX, 2, 0),
+                                       (synth.BC_NOFLUX, 3, 1), (synth.BC_DIRICHLET0, 5, 0)])
+def test_adaptive_memory_adjoint_matches_complex_step(bc, a, rule):
+    """Adaptive memory (Definitions 3.1/3.2, Proposition 3.1): delta^r enters step r+m with the
+    multiplicity that lag m has in step r+m's schedule (d at a median, 1 on the base interval
+    and the tail, 0 elsewhere).  Using one step's schedule for all rows, or the settled weights
+    without the tails, fails these."""
+    p, target = adj_problem(bc)
+    p = synth.with_mode(p, synth.MEM_ADAPTIVE, a=a, rule=rule)
+    ad = oracle.adjoint(p, target)
+    assert abs(ad["J"] - J_of(p, target)) < 1e-14 * ad["J"]
+    dg = cs_grad(p, target, gamma_im=H_CS)
+    da = cs_grad(p, target, alpha_im=H_CS)
+    assert abs(ad["dgamma"] - dg) < 1e-11 * abs(dg)
+    assert abs(ad["dalpha"] - da) < 1e-11 * abs(da)
+    for i in range(4):
+        e = np.zeros(4)
+        e[i] = H_CS
+        dr = cs_grad(p, target, react_im=e)
+        assert abs(ad["dreact"][i] - dr) < 1e-11 * abs(dr), i
+    v = synth.SplitMix64(7).uniform(p["u0"].size, -1.0, 1.0)
+    dv = cs_grad(p, target, u0_im=H_CS * v)
+    assert abs(float(ad["du0"] @ v) - dv) < 1e-11 * abs(dv)
+    # the adaptive gradient differs from the full-memory one (40 steps reach interval 3 at a <= 3)
+    full = oracle.adjoint(synth.with_mode(p, synth.MEM_FULL), target)
+    assert abs(full["dgamma"] - ad["dgamma"]) > 1e-6 * abs(ad["dgamma"])
+
+
+def test_adaptive_memory_adjoint_equals_full_when_a_covers_the_run():
+    """With a >= K the adaptive schedule is the full one (Definition 3.1): identical gradients."""
+    p, target = adj_problem(synth.BC_NOFLUX)
+    full = oracle.adjoint(p, target)
+    ad = oracle.adjoint(synth.with_mode(p, synth.MEM_ADAPTIVE, a=p["K"]), target)
+    for key in ("J", "dgamma", "dalpha"):
+        assert ad[key] == full[key], key
+    assert np.array_equal(ad["du0"], full["du0"]) and np.array_equal(ad["dreact"], full["dreact"])
