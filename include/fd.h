@@ -236,8 +236,8 @@ const char *fd_strerror(int code);
  *  - Problems needing more scratch than FD_STATIC_SCRATCH_BYTES are rejected with
  *    FD_ERR_WORKSPACE before any device work.  p->max_steps is ignored (nsteps is the length);
  *    FD_FLAG_KEEP_TAPE is rejected with FD_ERR_UNSUPPORTED (forward only).
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *    with that device current); make that first call before any stream capture.
+ *  - Each call looks up the array's address on the current device (cudaGetSymbolAddress), so
+ *    the call works on whichever device is current and after a context reset.
  *  - Every call shares the one array and overwrites what the previous call left in it; calls
  *    whose work overlaps on the GPU (other streams, other host threads) race and must be
  *    serialised by the caller.

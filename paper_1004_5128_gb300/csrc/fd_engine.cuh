@@ -544,19 +544,22 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
             n_issued += (uint32_t)pre;
         }
+        int aborted = 0;
         for (int s = 0; s < nst; ++s) {
             const int b = (int)(n_used % (uint32_t)NS);
             const uint32_t par = (n_used / (uint32_t)NS) & 1u;
+            int tmo = 0;
             if (!mbar_try_wait(&bars[b], par)) {
                 const long long t0 = globaltimer();
                 while (!mbar_try_wait(&bars[b], par)) {
                     if (globaltimer() - t0 > L.timeout_ns) {
                         if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE) note_failure(L, 7, U.k, U.tile, 0, 0, 0, 0);
-                        break;  // the copy is still owed to this slot; see below
+                        tmo = 1;  // the copy is still owed to this slot; see below
+                        break;
                     }
                 }
             }
-            const int rows = min(RS, nterm - s * RS);
+            const int rows = tmo ? 0 : min(RS, nterm - s * RS);
             const unsigned char *base = stages + (size_t)b * RS * row_bytes + (size_t)tid * 16;
             for (int r = 0; r < rows; ++r) {
                 const uint4 w = *reinterpret_cast<const uint4 *>(base + (size_t)r * row_bytes);
@@ -581,14 +584,20 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     for (int v = 0; v < V; ++v) acc2[v] = fma(c2, x[v], acc2[v]);
                 }
             }
+            // slot b fully read by every thread.  A stage that any thread gave up on stops the
+            // unit: nothing more is issued, and the stage stays owed (n_used not advanced) for
+            // the drain below.
+            if (__syncthreads_or(tmo)) {
+                aborted = 1;
+                break;
+            }
             ++n_used;
-            __syncthreads();  // slot b fully read by every thread
             if (s + NS < nst) {
                 if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
                 ++n_issued;
             }
         }
-        if (tid == 0) s_pipe = (ld_volatile(L.err) == ERR_PIPE);
+        if (tid == 0) s_pipe = aborted || (ld_volatile(L.err) == ERR_PIPE);
         __syncthreads();
         if (s_pipe) {
             // A stage never completed: drain what is owed (bounded) and stop.

@@ -309,9 +309,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
                 n_issued += (uint32_t)pre;
             }
+            int aborted = 0;
             for (int s = 0; s < nst; ++s) {
                 const int bb = (int)(n_used % (uint32_t)NS);
                 const uint32_t ph = (n_used / (uint32_t)NS) & 1u;
+                int tmo = 0;
                 if (!mbar_try_wait(&bars[bb], ph)) {
                     const long long t0 = globaltimer();
                     while (!mbar_try_wait(&bars[bb], ph)) {
@@ -321,11 +323,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                                              ((long long)n_issued << 32) | n_used,
                                              (long long)*reinterpret_cast<volatile unsigned long long *>(&bars[bb]),
                                              ((long long)L.k0 << 32) | L.k_end, ((long long)r0 << 32) | r1);
+                            tmo = 1;  // the copy is still owed to this slot; see below
                             break;
                         }
                     }
                 }
-                const int rows = min(RS, nrow - s * RS);
+                const int rows = tmo ? 0 : min(RS, nrow - s * RS);
                 const unsigned char *base = stages + (size_t)bb * RS * row_bytes + (size_t)tid * 16;
                 int r = 0;
                 if (sparse) {
@@ -422,14 +425,19 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         }
                     }
                 }
+                // a stage that any thread gave up on stops the unit: nothing more is issued and
+                // the stage stays owed (n_used not advanced) for the bounded drain below
+                if (__syncthreads_or(tmo)) {
+                    aborted = 1;
+                    break;
+                }
                 ++n_used;
-                __syncthreads();
                 if (s + NS < nst) {
                     if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
                     ++n_issued;
                 }
             }
-            if (tid == 0) s_pipe = (ld_volatile(L.err) == ERR_PIPE);
+            if (tid == 0) s_pipe = aborted || (ld_volatile(L.err) == ERR_PIPE);
             __syncthreads();
             if (s_pipe) {
                 if (tid == 0) {

@@ -19,7 +19,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/fd.h"
 #include "fd_kernels.h"
@@ -32,30 +31,18 @@ static __device__ __align__(256) unsigned char fd_static_scratch[FD_STATIC_SCRAT
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-void *g_scratch[kMaxDevices];  // device address of fd_static_scratch, per device
-std::mutex g_setup;
-
-// Once per device, with that device current: the host-side name fd_static_scratch is only a
-// stand-in, so ask the runtime for the array's device address.
+// The host-side name fd_static_scratch is only a stand-in: ask the runtime for the array's
+// address on the current device.  This is done on every call, with the caller's device current,
+// and never cached: after cudaDeviceReset or a release of the primary context the module is
+// loaded again, possibly at another address.  Once the module is loaded the lookup is cheap.
 int scratch_address(char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, fd_static_scratch) != cudaSuccess || !p) {
         (void)cudaGetLastError();
         return FD_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) return FD_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_setup);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, fd_static_scratch) != cudaSuccess || !p) {
-            (void)cudaGetLastError();
-            return FD_ERR_CUDA;
-        }
-        g_scratch[dev] = p;
-    }
-    *out = static_cast<char *>(g_scratch[dev]);
+    *out = static_cast<char *>(p);
     return FD_OK;
 }
 
@@ -82,6 +69,7 @@ int check_problem(const fd_problem *p, int nsteps)
     if (p->ndim < 1 || p->ndim > 3) return FD_ERR_INVALID_ARG;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->ndim == 1 && p->ny != 1) || (p->ndim < 3 && p->nz != 1))
         return FD_ERR_INVALID_ARG;
+    if ((int64_t)p->nx * p->ny * p->nz > (int64_t)1 << 30) return FD_ERR_INVALID_ARG;
     if (!(p->gamma > 0.0 && p->gamma < 2.0) || !(p->alpha > 0.0) || !(p->dt > 0.0) || !(p->dx > 0.0))
         return FD_ERR_INVALID_ARG;
     for (double r : p->react)
@@ -227,6 +215,9 @@ extern "C" int fd_run_static(const fd_problem *p_in, const void *u0, int nsteps,
     char *base = nullptr;
     rc = scratch_address(&base);
     if (rc) return rc;
+    // every step takes at least 48 bytes of tables (weights, schedule, group offsets): longer runs
+    // cannot fit, and rejecting them here keeps the size arithmetic below far from overflow
+    if ((int64_t)nsteps * 48 > (int64_t)FD_STATIC_SCRATCH_BYTES) return FD_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int64_t N = (int64_t)p->nx * p->ny * p->nz;
     const int sh = esize(p->hist_dtype), ss = esize(p->state_dtype), sa = esize(p->accum_dtype);

@@ -64,3 +64,36 @@ def test_static_entry_refuses_problems_beyond_its_array():
                                ctypes.c_void_p(out.data_ptr()),
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == L.FD_ERR_WORKSPACE
+
+
+def _three_dims(n: int = 14, K: int = 160):
+    """3-D 14^3 (2744 points: a ragged last tile), no-flux, adaptive a=3."""
+    p = synth.problem(3, n, n, 0.7, 0.6, synth.dt_for_courant(0.1, 0.6, 1.0, 0.7), 1.0,
+                      synth.BC_NOFLUX, react=(0.0, -0.1, 0.0, 0.0), mem_mode=synth.MEM_ADAPTIVE,
+                      mem_a=3, K=K, u0=synth.SplitMix64(33).uniform(n ** 3, 0, 1), nz=n)
+    return p
+
+
+def test_static_entry_alternating_problems_against_oracle():
+    """Differently shaped problems in a row through the one shared array, each against the FP64
+    oracle: a ragged 2-D grid with BF16 history, a 3-D grid with FP16 (scaled) history, then the
+    first problem again, whose result must not depend on what the second call left behind.
+    The first call uses the library's default launch geometry."""
+    import oracle
+
+    a = synth.problem(2, 45, 37, 0.75, 0.7, synth.dt_for_courant(0.15, 0.7, 1.0, 0.75), 1.0,
+                      synth.BC_DIRICHLET0, react=(0.01, -0.2, 0.3, -0.4), K=220,
+                      u0=synth.SplitMix64(21).uniform(45 * 37, 0, 1))
+    b = _three_dims()
+    fa = make_problem(a, hist="bf16", kahan=True)            # default geometry
+    fb = make_problem(b, hist="f16", kahan=True, **GEOM)
+    ua = torch.from_numpy(a["u0"]).to("cuda", torch.float32)
+    ub = torch.from_numpy(b["u0"]).to("cuda", torch.float32)
+    ref_a, ref_b = oracle.run(a), oracle.run(b)
+    first = static_run(fa, ua, a["K"])
+    other = static_run(fb, ub, b["K"])
+    again = static_run(fa, ua, a["K"])
+    assert rel_inf(first, ref_a) < 2e-3
+    assert rel_inf(other, ref_b) < 2e-3
+    assert rel_inf(again, ref_a) < 2e-3
+    assert np.array_equal(first, again)
