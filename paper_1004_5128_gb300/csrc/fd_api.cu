@@ -181,9 +181,8 @@ int validate(const fd_problem *p)
         return FD_ERR_UNSUPPORTED;
     if (p->time_block) {
         if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16) return FD_ERR_INVALID_ARG;
-        if (p->state_dtype != FD_F32 || p->hist_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan)
-            return FD_ERR_UNSUPPORTED;
-        if (adj && !fdk::kernel_tb(p->time_block, true)) return FD_ERR_UNSUPPORTED;  // adjoint blocks: 4, 8
+        if (p->state_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan) return FD_ERR_UNSUPPORTED;
+        if (!fdk::kernel_tb(p->time_block, adj, p->hist_dtype)) return FD_ERR_UNSUPPORTED;
         // arrival words hold a block generation (blocks / 4) and a chunk count in 16 bits each
         if ((int64_t)p->max_steps / p->time_block / 4 >= 65535) return FD_ERR_INVALID_ARG;
     }
@@ -230,10 +229,10 @@ inline size_t smem_bytes(const Geo &g, int rmax)
 // tile's state there, so it holds at least tb x planes + 2 rows, as the kernel assumes), four
 // shifted copies of each coefficient window (psi, and psi' for the adjoint; with adaptive memory
 // the first shifted copy holds the nonzero masks of the window's four-row groups), barriers.
-inline size_t smem_bytes_tb(const Geo &g, int rwin)
+inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
 {
-    const int ring = std::max(g.NS * g.RS, g.tb * g.planes + 2);
-    return (size_t)ring * g.threads * 16 + (size_t)g.planes * 4 * ((rwin + g.tb + 7) & ~3) * 4 + 32 +
+    const size_t ring = std::max((size_t)g.NS * g.RS * g.threads * 4 * g.sh, (size_t)(g.tb * g.planes + 2) * g.threads * 16);
+    return ring + (size_t)g.planes * 4 * ((rwin + g.tb + 7) & ~3) * 4 + (f16 ? (size_t)rwin * 4 : 0) + 32 +
            8 * (size_t)g.NS;
 }
 
@@ -280,7 +279,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.sh = dtype_size(p.hist_dtype);
     g.ss = dtype_size(p.state_dtype);
     g.sa = dtype_size(p.accum_dtype);
-    g.V = 16 / g.sh;
+    g.V = p.time_block ? 4 : 16 / g.sh;  // the blocked kernel keeps four points per thread
     g.planes = (p.flags & FD_FLAG_KEEP_TAPE) ? 2 : 1;
     int th = threads_override ? threads_override : p.tile_threads;
     if (!th) {
@@ -358,10 +357,12 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         g.rwin = (int)rwin;
     }
     g.pitch = (int64_t)align_up((size_t)N * g.sh, kAlign);
-    g.hring_cap = g.hring_sep ? g.head + 1 : g.cap;
+    // low-precision history keeps its newest rows in FP32 too: the per-step kernel its head lags,
+    // the blocked kernel the rows of the current and the previous block
+    g.hring_cap = !g.hring_sep ? g.cap : g.tb ? 2 * g.tb : g.head + 1;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = g.tb ? smem_bytes_tb(g, g.rwin) : smem_bytes(g, g.R);
+    g.smem = g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -847,10 +848,10 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     h->ctrl_zero_base = (char *)h->L.arrive;
     h->ctrl_zero_bytes = sizeof(unsigned) * (h->g.npar + 1) * (size_t)h->g.T;
     const bool kahan = p->flags & FD_FLAG_KAHAN;
-    h->kfwd = p->time_block ? fdk::kernel_tb(p->time_block)
+    h->kfwd = p->time_block ? fdk::kernel_tb(p->time_block, false, p->hist_dtype)
                             : fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
     h->kadj = !(p->flags & FD_FLAG_KEEP_TAPE) ? nullptr
-              : p->time_block ? fdk::kernel_tb(p->time_block, true)
+              : p->time_block ? fdk::kernel_tb(p->time_block, true, p->hist_dtype)
                               : fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true);
     rc = set_smem_attr(h->kfwd, h->g.smem);
     if (!rc && h->kadj) rc = set_smem_attr(h->kadj, h->g.smem);
@@ -1149,7 +1150,7 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     b.rmax = 0;
     for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].tb ? b.g[i].rwin : b.g[i].R);
     b.tb = probs[0].time_block;
-    b.smem = b.tb ? smem_bytes_tb(b.g[0], b.rmax) : smem_bytes(b.g[0], b.rmax);
+    b.smem = b.tb ? smem_bytes_tb(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16) : smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
     b.ctrl = carve_ctrl(c);
     int64_t counters = 0;
@@ -1230,7 +1231,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
     b->ws = (char *)workspace;
     b->st = (cudaStream_t)cuda_stream;
     const bool kahan = b->p[0].flags & FD_FLAG_KAHAN;
-    b->kfn = b->tb ? fdk::kernel_tb(b->tb)
+    b->kfn = b->tb ? fdk::kernel_tb(b->tb, false, b->p[0].hist_dtype)
                    : fdk::kernel_for(b->p[0].state_dtype, b->p[0].hist_dtype, b->p[0].accum_dtype, kahan, false);
     Geo g0 = b->g[0];
     g0.smem = b->smem;  // the launch's shared memory: the largest chunk over the instances

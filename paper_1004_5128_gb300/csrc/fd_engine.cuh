@@ -61,6 +61,9 @@ struct Inst {
     int ksteps;              // steps the instance runs (its max_steps); bounds a batch launch
     int ub;                  // blocked kernel: 1 = one update unit per (block, tile)
     int cmax;                // blocked kernel: most far chunks per block (0 = no limit)
+    int ralign;              // blocked kernel: far chunks start on multiples of ralign rows (0, 1: any)
+    int tc_cols;             // blocked tensor-core kernel: tensor-memory columns per CTA
+    const void *tmap;        // blocked tensor-core kernel: tensor map of the history rows
     int tape_k0, tape_every, tape_rows;
     int adj_K, uadj_r0;      // adjoint: u^r is row (adj_K-1-k) - uadj_r0 of uadj
     double S, dt;

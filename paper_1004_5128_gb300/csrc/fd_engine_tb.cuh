@@ -34,7 +34,10 @@
 // engine_kernel.
 #pragma once
 
+#include <type_traits>
+
 #include "fd_engine.cuh"
+#include "fd_tc.cuh"
 
 namespace fdk {
 
@@ -42,6 +45,61 @@ struct UnitTB {
     int valid, inst, b, tile, chunk, C, r0, r1;
     int fix;  // 0: far unit; 1: update unit of step k
     int k;
+};
+
+// Four consecutive history values of one thread's column.  The blocked kernel keeps four points
+// per thread for every history type: 16 bytes of FP32, or 8 bytes of BF16 / FP16 (the FP16 rows
+// carry a power-of-two scale per (row, tile), applied by the reader).
+template <class TH> struct H4;
+template <> struct H4<float> {
+    static constexpr int BYTES = 16;
+    __device__ static void unpack(float4 w, float *x)
+    {
+        x[0] = w.x;
+        x[1] = w.y;
+        x[2] = w.z;
+        x[3] = w.w;
+    }
+    __device__ static void lds(const void *p, float *x) { unpack(*reinterpret_cast<const float4 *>(p), x); }
+    __device__ static void ldg(const void *p, float *x) { unpack(__ldcg(reinterpret_cast<const float4 *>(p)), x); }
+    __device__ static void stg(void *p, const float *d, float) { *reinterpret_cast<float4 *>(p) = make_float4(d[0], d[1], d[2], d[3]); }
+};
+template <> struct H4<__nv_bfloat16> {
+    static constexpr int BYTES = 8;
+    __device__ static void unpack(uint2 w, float *x)
+    {
+        x[0] = __uint_as_float(w.x << 16);
+        x[1] = __uint_as_float(w.x & 0xffff0000u);
+        x[2] = __uint_as_float(w.y << 16);
+        x[3] = __uint_as_float(w.y & 0xffff0000u);
+    }
+    __device__ static void lds(const void *p, float *x) { unpack(*reinterpret_cast<const uint2 *>(p), x); }
+    __device__ static void ldg(const void *p, float *x) { unpack(__ldcg(reinterpret_cast<const uint2 *>(p)), x); }
+    __device__ static void stg(void *p, const float *d, float)
+    {
+        __nv_bfloat162 a = __floats2bfloat162_rn(d[0], d[1]), b = __floats2bfloat162_rn(d[2], d[3]);
+        *reinterpret_cast<uint2 *>(p) = make_uint2(*reinterpret_cast<unsigned *>(&a), *reinterpret_cast<unsigned *>(&b));
+    }
+};
+template <> struct H4<__half> {
+    static constexpr int BYTES = 8;
+    __device__ static void unpack(uint2 w, float *x)
+    {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&w.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&w.y));
+        x[0] = a.x;
+        x[1] = a.y;
+        x[2] = b.x;
+        x[3] = b.y;
+    }
+    __device__ static void lds(const void *p, float *x) { unpack(*reinterpret_cast<const uint2 *>(p), x); }
+    __device__ static void ldg(const void *p, float *x) { unpack(__ldcg(reinterpret_cast<const uint2 *>(p)), x); }
+    // scale = 2^e per (row, tile), so the tile's largest |delta| lands in [2^14, 2^15)
+    __device__ static void stg(void *p, const float *d, float scale)
+    {
+        __half2 a = __floats2half2_rn(d[0] * scale, d[1] * scale), b = __floats2half2_rn(d[2] * scale, d[3] * scale);
+        *reinterpret_cast<uint2 *>(p) = make_uint2(*reinterpret_cast<unsigned *>(&a), *reinterpret_cast<unsigned *>(&b));
+    }
 };
 
 // Far rows [rlo, rhi) of block b: rows older than the previous block, within the short window.
@@ -63,12 +121,26 @@ __device__ __forceinline__ int settled_end(const Inst &I, int k)
     return max(e.x, e.z - 1);
 }
 
-// Rows per far chunk of block b: R, or enough that the block has at most cmax chunks.
+// First row of block b's far chunks: rlo, or rlo rounded down to a multiple of I.ralign (the
+// tensor-core path streams whole stages of ralign rows; rows below rlo then carry weight 0).
+// rhi is a multiple of the block length, which ralign divides, so every chunk is whole stages.
+template <int TB> __device__ __forceinline__ int far_origin(const Inst &I, int b)
+{
+    int rlo, rhi;
+    far_rows<TB>(I, b, rlo, rhi);
+    return I.ralign > 1 ? rlo - rlo % I.ralign : rlo;
+}
+
+// Rows per far chunk of block b: R, or enough that the block has at most cmax chunks (a multiple
+// of ralign).
 template <int TB> __device__ __forceinline__ int block_R(const Inst &I, int b)
 {
     int rlo, rhi;
     far_rows<TB>(I, b, rlo, rhi);
-    return I.cmax ? max(I.R, (rhi - rlo + I.cmax - 1) / I.cmax) : I.R;
+    const int rows = rhi - far_origin<TB>(I, b);
+    int Rb = I.cmax ? max(I.R, (rows + I.cmax - 1) / I.cmax) : I.R;
+    if (I.ralign > 1) Rb = (Rb + I.ralign - 1) / I.ralign * I.ralign;
+    return Rb;
 }
 
 // Far chunks of block b (at least one).
@@ -77,31 +149,52 @@ template <int TB> __device__ __forceinline__ int far_chunks(const Inst &I, int b
     int rlo, rhi;
     far_rows<TB>(I, b, rlo, rhi);
     const int Rb = block_R<TB>(I, b);
-    return max(1, (rhi - rlo + Rb - 1) / Rb);
+    return max(1, (rhi - far_origin<TB>(I, b) + Rb - 1) / Rb);
 }
 
-template <int TB, bool ADJ>
-__global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
+// TC: the far units run on the tensor cores (BF16 history only; CTAs of at most 256 threads).
+template <int TB, bool ADJ, class TH = float, bool TC = false>
+__global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Launch L)
 {
     constexpr int PLANES = ADJ ? 2 : 1;
-    constexpr int V = 4;  // FP32: one float4 column per thread
+    constexpr int V = 4;  // four points per thread: a float4 of state, H4<TH> of history
+    constexpr bool LOWP = sizeof(TH) == 2;
+    constexpr bool F16 = std::is_same<TH, __half>::value;
+    static_assert(!TC || (std::is_same<TH, __nv_bfloat16>::value && !ADJ && TB % 16 == 0),
+                  "tensor-core far units: BF16 history, forward, blocks of a multiple of 16 steps");
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     const int RS = L.stage_rows, NS = L.stages;
-    const int row_bytes = nthr * 16;
+    const int row_bytes = nthr * H4<TH>::BYTES;  // one history row of a tile in a stage
 
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the tensor-core path's swizzled operands need 1 KB-aligned atoms
+    unsigned char *smem = smem_raw;
+    if (TC) smem += (1024u - (tc::saddr(smem_raw) & 1023u)) & 1023u;
     unsigned char *stages = smem;
     // Coefficient window in four copies shifted by 0..3 elements, so that the TB coefficients
     // of any row are TB/4 aligned 16-byte loads: copy q holds w[i + q] at index i.
     const int WS = (L.rmax + TB + 7) & ~3;                                          // copy stride
     // the stage ring also holds a block-long update unit's sums and its tile's u^k, u^{k+1}:
-    // at least TB x PLANES + 2 rows
-    const int ring_rows = max(NS * RS, TB * PLANES + 2);
-    float *psw = reinterpret_cast<float *>(smem + (size_t)ring_rows * row_bytes);  // psi window
-    float *psw2 = psw + 4 * WS;                                                    // psi' window (ADJ)
+    // at least TB x PLANES + 2 rows of FP32 float4 columns
+    const size_t ring_bytes = max((size_t)NS * RS * row_bytes, (size_t)(TB * PLANES + 2) * nthr * 16);
+    float *psw = reinterpret_cast<float *>(smem + ring_bytes);  // psi window
+    float *psw2 = psw + 4 * WS;                                 // psi' window (ADJ)
+    float *rsc = psw + PLANES * 4 * WS;                         // FP16: the far rows' scales
     uint64_t *bars = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(psw + PLANES * 4 * WS) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(rsc + (F16 ? L.rmax : 0)) + 15) & ~uintptr_t(15));
+    // Tensor-core path: after the stage ring (A operands, RS rows x P points each), a ring of NS
+    // coefficient blocks (B operands, hi and lo halves of TB/8 atoms each), the coefficient
+    // window, and the barriers: full (bulk copies landed), empty (the MMAs that read a slot are
+    // done), bfull (coefficients written), done (all MMAs of a unit).
+    constexpr int BHALF = (TB / 8) * 1024;  // one half (hi or lo) of a coefficient block
+    unsigned char *bring = smem + ((ring_bytes + 1023) & ~(size_t)1023);
+    float *win = reinterpret_cast<float *>(bring + (size_t)NS * 2 * BHALF);
+    if (TC)
+        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(win + L.rmax + TB) + 15) & ~uintptr_t(15));
+    uint64_t *full = bars, *empty = bars + NS, *bfull = bars + 2 * NS, *done_bar = bars + 3 * NS;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_iss, s_mma;
     // adaptive memory: bit j of gmask[lo] says w[lo + j] != 0 (the window of a four-row group);
     // the sparse loop reads the unshifted copy only, so the masks take the first shifted copy
     uint32_t *gmask = reinterpret_cast<uint32_t *>(psw + WS);
@@ -111,14 +204,32 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     __shared__ int s_cur_inst, s_ok, s_ok2, s_pipe;
     __shared__ int s_ek[TB];  // block-long unit, adaptive memory: e(k) of the block's steps
     __shared__ double s_dred[ADJ ? 16 : 1][6];
+    __shared__ float s_wmax[F16 ? 16 : 1];  // FP16 history: per-warp largest |delta| of a row
 
     if (tid == 0) {
-        for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
+        if (TC) {
+            for (int b = 0; b < NS; ++b) {
+                mbar_init(&full[b], 1);
+                mbar_init(&empty[b], 1);
+                mbar_init(&bfull[b], (uint32_t)(nthr - 64));
+            }
+            mbar_init(done_bar, 1);
+        } else {
+            for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         s_cur_inst = -1;
     }
+    // tensor memory for the far accumulators: P/128 blocks of TB FP32 columns (tc_cols, a power
+    // of two), allocated once per CTA; the host keeps one CTA per SM
+    const uint32_t tc_cols = TC ? (uint32_t)L.inst[0].tc_cols : 0u;
+    if (TC && tid < 32) tc::tmem_alloc(&s_tmem, tc_cols);
+    if (TC) tc::fence_before();
     __syncthreads();
+    if (TC) tc::fence_after();
+    const uint32_t tmem = TC ? s_tmem : 0u;
+    uint32_t tc_use = 0, tc_done = 0;  // stages streamed and units finished by this CTA (TC)
 
     uint32_t n_issued = 0, n_used = 0;
     int ghint = L.g_begin;
@@ -206,7 +317,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     U.C = far_chunks<TB>(I, gb);
                     U.tile = (int)(f % I.T);
                     U.chunk = (int)(f / I.T);
-                    U.r0 = min(rhi, rlo + U.chunk * Rb);
+                    U.r0 = min(rhi, far_origin<TB>(I, gb) + U.chunk * Rb);
                     U.r1 = min(rhi, U.r0 + Rb);
                     U.k = 0;
                     // far rows up to r1-1 written (block-long units: their whole block, whose
@@ -243,252 +354,447 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         };
 
         if (!U.fix) {
-            // ================================================================ far unit
-            const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;
-            const int nst = (nrow + RS - 1) / RS;
-            long long tile_bytes = (long long)min(I.P, I.N - tile * I.P) * 4ll;
-            tile_bytes = (tile_bytes + 15) & ~15ll;
-
-            // coefficient window w[i] = psi_{lag0 + i}: row r, step kb+t uses w[(r1-1-r) + t]
-            const bool sparse = !ADJ && I.gw != nullptr;
-            {
-                const float *psi = reinterpret_cast<const float *>(I.psi);
-                const int lag0 = kb - (r1 - 1);
-                const int nw = nrow + TB - 1;
-                for (int e = tid; e < (sparse ? WS : 4 * WS); e += nthr) {
-                    const int q = e / WS, i = e - q * WS, w = i + q;
-                    const int lag = lag0 + w;
-                    const bool cut = (w >= nw) || (I.mem_mode == 1 && lag > I.mem_L);
-                    psw[q * WS + i] = cut ? 0.f : I.gw ? reinterpret_cast<const float *>(I.gw)[lag] : psi[lag];
-                    if (ADJ) psw2[q * WS + i] = cut ? 0.f : reinterpret_cast<const float *>(I.dpsi)[lag];
-                }
-            }
-            __syncthreads();
-            // Adaptive memory: the settled weights are zero between medians (at least two of three
-            // lags in the far rows), so a four-row group multiplies only the lags its window holds.
-            if (sparse) {
-                for (int lo = tid; lo + 4 <= nrow; lo += nthr) {
-                    uint32_t m = 0;
-                    for (int j = 0; j < TB + 4; ++j) m |= (psw[lo + j] != 0.f ? 1u : 0u) << j;
-                    gmask[lo] = m;
-                }
-                __syncthreads();
-            }
-
-            // accumulators as point pairs: one packed two-lane FMA (each lane an IEEE fmaf)
-            // serves two points, halving the far loop's FMA instructions
-            float2 acc[TB][V / 2], acc2[ADJ ? TB : 1][V / 2];
-#pragma unroll
-            for (int t = 0; t < TB; ++t)
-#pragma unroll
-                for (int h = 0; h < V / 2; ++h) acc[t][h] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int t = 0; t < (ADJ ? TB : 1); ++t)
-#pragma unroll
-                for (int h = 0; h < V / 2; ++h) acc2[t][h] = make_float2(0.f, 0.f);
-
-            // Stage s is filled by warp s mod (warps), one lane per row: the copies of a stage
-            // go out together and the issue work rotates over the warps instead of delaying
-            // one warp at every stage barrier.  Called by all lanes of the issuing warp.
-            const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-            auto issue = [&](int s, uint32_t slot) {
-                const int bb = (int)(slot % (uint32_t)NS);
-                const int a0 = s * RS, a1 = min(nrow, a0 + RS);
-                if (lane == 0) mbar_expect_tx(&bars[bb], (uint32_t)(tile_bytes * (a1 - a0)));
-                __syncwarp();
-                const char *col = I.hist + (size_t)tile * I.P * 4;
-                for (int a = a0 + lane; a < a1; a += 32)
-                    bulk_g2s(stages + ((size_t)bb * RS + (a - a0)) * row_bytes,
-                             col + (size_t)((r0 + a) % I.cap) * I.pitch, (uint32_t)tile_bytes, &bars[bb]);
-            };
-            // every lane that issues copies orders the rows it acquired before the async proxy
-            if (lane < RS) fence_proxy_async_global();
-            {
-                const int pre = min(NS, nst);
-                for (int s = 0; s < pre; ++s)
-                    if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
-                n_issued += (uint32_t)pre;
-            }
-            int aborted = 0;
-            for (int s = 0; s < nst; ++s) {
-                const int bb = (int)(n_used % (uint32_t)NS);
-                const uint32_t ph = (n_used / (uint32_t)NS) & 1u;
-                int tmo = 0;
-                if (!mbar_try_wait(&bars[bb], ph)) {
-                    const long long t0 = globaltimer();
-                    while (!mbar_try_wait(&bars[bb], ph)) {
-                        if (globaltimer() - t0 > L.timeout_ns) {
-                            if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE)
-                                note_failure(L, 2, ((long long)b << 32) | tile, ((long long)s << 32) | nst,
-                                             ((long long)n_issued << 32) | n_used,
-                                             (long long)*reinterpret_cast<volatile unsigned long long *>(&bars[bb]),
-                                             ((long long)L.k0 << 32) | L.k_end, ((long long)r0 << 32) | r1);
-                            tmo = 1;  // the copy is still owed to this slot; see below
-                            break;
-                        }
+            if constexpr (TC) {
+                // ============================================== far unit on the tensor cores
+                // D[p][t] = sum over rows r in [r0, r1) of H[r][p] * c(t, r), c(t, r) = w(kb + t - r):
+                // M = 128 points, N = TB steps, K = 16 rows per MMA, FP32 accumulators in tensor
+                // memory (block m of the tile's P/128 point blocks at columns m*TB ...).  The
+                // weights are split into BF16 hi + lo halves (two MMAs per K slice), so they keep
+                // about 16 significant bits.  Roles: warp 0 lane 0 issues the tensor-map copies of
+                // the history stages, warp 1 lane 0 issues the MMAs, the other warps write each
+                // stage's coefficient block; mbarriers order them, with no CTA barrier per stage.
+                const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;  // whole stages (multiples of RS)
+                const int nst = nrow / RS;
+                const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
+                const int MB = I.P / 128;
+                int rlo_t, rhi_t;
+                far_rows<TB>(I, b, rlo_t, rhi_t);  // rows below rlo_t are not far rows of this block
+                {
+                    // coefficient window win[j] = w(lag0 + j), lag0 = kb - (r1 - 1): row r, step kb+t
+                    // uses win[(r1 - 1 - r) + t]; short memory cuts lags beyond its window
+                    const float *wsrc = reinterpret_cast<const float *>(I.gw ? I.gw : I.psi);
+                    const int lag0 = kb - (r1 - 1);
+                    for (int j = tid; j < nrow + TB - 1; j += nthr) {
+                        const int lag = lag0 + j;
+                        win[j] = (I.mem_mode == 1 && lag > I.mem_L) ? 0.f : wsrc[lag];
+                    }
+                    if (tid == 0) {
+                        s_abort = 0;
+                        s_iss = 0;
+                        s_mma = 0;
                     }
                 }
-                const int rows = tmo ? 0 : min(RS, nrow - s * RS);
-                const unsigned char *base = stages + (size_t)bb * RS * row_bytes + (size_t)tid * 16;
-                int r = 0;
-                if (sparse) {
-                    // Four rows at a time, lag by lag over the window's nonzero weights only.  Lag
-                    // J of the window meets row i at step t = J - 3 + i; J descending keeps each
-                    // accumulator's rows in increasing order, as in the dense loop below, and the
-                    // skipped products are exact zeros, so the sums are the dense loop's.
-                    for (; r + 4 <= rows; r += 4) {
-                        const int lo = nrow - 1 - (s * RS + r) - 3;
-                        const uint32_t m = gmask[lo];
-                        float x[4][V];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)(r + i) * row_bytes);
-                            x[i][0] = x4.x;
-                            x[i][1] = x4.y;
-                            x[i][2] = x4.z;
-                            x[i][3] = x4.w;
+                __syncthreads();
+                auto give_up = [&](int site_s, uint64_t *bar) {
+                    if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE)
+                        note_failure(L, 11, ((long long)b << 32) | tile, ((long long)site_s << 32) | nst,
+                                     (long long)tc_use, (long long)*reinterpret_cast<volatile unsigned long long *>(bar),
+                                     ((long long)L.k0 << 32) | L.k_end, ((long long)r0 << 32) | r1);
+                    atomicExch(&s_abort, 1);
+                };
+                // bounded wait for an mbarrier phase; false when it gave up (or another role did)
+                auto wait_bar = [&](uint64_t *bar, uint32_t parity, int site_s) -> bool {
+                    if (mbar_try_wait(bar, parity)) return true;
+                    const long long t0 = globaltimer();
+                    while (!mbar_try_wait(bar, parity)) {
+                        if (*reinterpret_cast<volatile int *>(&s_abort)) return false;
+                        if (globaltimer() - t0 > L.timeout_ns) {
+                            give_up(site_s, bar);
+                            return false;
                         }
-#pragma unroll
-                        for (int J = TB + 3; J >= 0; --J) {
-                            if (!(m & (1u << J))) continue;
-                            const float cj = psw[lo + J];
-                            const float2 cj2 = make_float2(cj, cj);
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const int t = J - 3 + i;
-                                if (t < 0 || t >= TB) continue;
-#pragma unroll
-                                for (int h = 0; h < V / 2; ++h)
-                                    acc[t][h] = __ffma2_rn(cj2, make_float2(x[i][2 * h], x[i][2 * h + 1]), acc[t][h]);
+                    }
+                    return true;
+                };
+                constexpr uint32_t IDESC = tc::idesc_bf16_amn(128, TB);
+                if (warp == 0) {
+                    if (lane == 0) {  // history stages: P/64 boxes of 64 points x RS rows each
+                        for (int s = 0; s < nst; ++s) {
+                            const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
+                            if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
+                            unsigned char *a = stages + (size_t)slot * RS * row_bytes;
+                            mbar_expect_tx(&full[slot], (uint32_t)(RS * row_bytes));
+                            for (int j = 0; j < I.P / 64; ++j)
+                                tc::tma_load_2d(a + (size_t)j * RS * 128, I.tmap, tile * I.P + 64 * j, r0 + s * RS, &full[slot]);
+                            s_iss = s + 1;
+                        }
+                    }
+                } else if (warp == 1) {
+                    if (lane == 0) {
+                        for (int s = 0; s < nst; ++s) {
+                            const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
+                            const uint32_t ph = (use / (uint32_t)NS) & 1u;
+                            if (!wait_bar(&full[slot], ph, s) || !wait_bar(&bfull[slot], ph, s)) break;
+                            tc::fence_after();
+                            const uint32_t a0 = tc::saddr(stages + (size_t)slot * RS * row_bytes);
+                            const uint32_t bh = tc::saddr(bring + (size_t)slot * 2 * BHALF), bl = bh + BHALF;
+                            for (int m = 0; m < MB; ++m)
+                                for (int kk = 0; kk < RS / 16; ++kk) {
+                                    // A: points 128m.., rows 16kk..; atoms of 64 points are RS*128
+                                    // bytes apart (LBO), atoms of 8 rows 1 KB apart (SBO)
+                                    const uint64_t ad = tc::desc_sw128(a0 + (uint32_t)(2 * m * RS * 128 + kk * 2048),
+                                                                       (uint32_t)(RS * 128), 1024u);
+                                    const uint32_t d = tmem + (uint32_t)(m * TB);
+                                    const uint32_t acc = (s | kk) ? 1u : 0u;
+                                    tc::mma_f16(d, ad, tc::desc_sw128(bh + (uint32_t)(kk * 32), 16u, 1024u), IDESC, acc);
+                                    tc::mma_f16(d, ad, tc::desc_sw128(bl + (uint32_t)(kk * 32), 16u, 1024u), IDESC, 1u);
+                                }
+                            tc::commit(&empty[slot]);  // the slot is free once these MMAs are done
+                            s_mma = s + 1;
+                        }
+                        if (nst > 0) tc::commit(done_bar);  // every MMA this unit issued
+                    }
+                } else {
+                    // coefficient blocks, K-major with the 128-byte swizzle: step t is row t of the
+                    // block (atom t/8, row t%8), stage row i its K index
+                    const int nb = nthr - 64, me = tid - 64;
+                    for (int s = 0; s < nst; ++s) {
+                        const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
+                        if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
+                        unsigned char *bh = bring + (size_t)slot * 2 * BHALF;
+                        for (int e = me; e < TB * RS; e += nb) {
+                            const int t = e / RS, i = e - t * RS;
+                            const int r = r0 + s * RS + i;
+                            const float c = (r < rlo_t) ? 0.f : win[(r1 - 1 - r) + t];
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(c);
+                            const __nv_bfloat16 lo = __float2bfloat16_rn(c - __bfloat162float(hi));
+                            const int row = t & 7;
+                            const int off = (t >> 3) * 1024 + row * 128 + (((i >> 3) ^ row) << 4) + (i & 7) * 2;
+                            *reinterpret_cast<__nv_bfloat16 *>(bh + off) = hi;
+                            *reinterpret_cast<__nv_bfloat16 *>(bh + BHALF + off) = lo;
+                        }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(&bfull[slot])) : "memory");
+                    }
+                }
+                __syncthreads();
+                if (s_abort) {
+                    // stop: wait (bounded) for the copies and MMAs already issued, then leave
+                    if (tid == 32 && s_mma > 0) {
+                        const long long t0 = globaltimer();
+                        while (!mbar_try_wait(done_bar, tc_done & 1u) && globaltimer() - t0 < L.timeout_ns) {
+                        }
+                    }
+                    if (tid == 0) {
+                        const long long t0 = globaltimer();
+                        for (int s = s_mma; s < s_iss; ++s) {
+                            const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
+                            while (!mbar_try_wait(&full[slot], (use / (uint32_t)NS) & 1u) &&
+                                   globaltimer() - t0 < L.timeout_ns) {
                             }
                         }
                     }
-                }
-                // Four rows at a time.  Row a = s*RS + r + i uses w[wo - i + t], wo = nrow-1-(s*RS+r):
-                // the TB+3 coefficients w[wo-3 .. wo+TB-1] come in aligned 16-byte loads from the
-                // copy shifted by (wo-3) & 3 and serve all four rows from registers.
-                for (; r + 4 <= rows; r += 4) {
-                    const int lo = nrow - 1 - (s * RS + r) - 3;
-                    const int cq = (lo & 3) * WS + (lo & ~3);
-                    float c[TB + 4], c2[ADJ ? TB + 4 : 1];
-#pragma unroll
-                    for (int j = 0; j < TB + 4; j += 4) {
-                        const float4 c4 = *reinterpret_cast<const float4 *>(psw + cq + j);
-                        c[j] = c4.x;
-                        c[j + 1] = c4.y;
-                        c[j + 2] = c4.z;
-                        c[j + 3] = c4.w;
-                        if (ADJ) {
-                            const float4 d4 = *reinterpret_cast<const float4 *>(psw2 + cq + j);
-                            c2[ADJ ? j : 0] = d4.x;
-                            c2[ADJ ? j + 1 : 0] = d4.y;
-                            c2[ADJ ? j + 2 : 0] = d4.z;
-                            c2[ADJ ? j + 3 : 0] = d4.w;
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)(r + i) * row_bytes);
-                        const float x[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-                        for (int t = 0; t < TB; ++t)
-#pragma unroll
-                            for (int h = 0; h < V / 2; ++h)
-                                acc[t][h] = __ffma2_rn(make_float2(c[3 - i + t], c[3 - i + t]), make_float2(x[2 * h], x[2 * h + 1]),
-                                                       acc[t][h]);
-                        if (ADJ) {
-#pragma unroll
-                            for (int t = 0; t < (ADJ ? TB : 1); ++t)
-#pragma unroll
-                                for (int h = 0; h < V / 2; ++h)
-                                    acc2[t][h] = __ffma2_rn(make_float2(c2[ADJ ? 3 - i + t : 0], c2[ADJ ? 3 - i + t : 0]),
-                                                            make_float2(x[2 * h], x[2 * h + 1]), acc2[t][h]);
-                        }
-                    }
-                }
-                for (; r < rows; ++r) {  // remaining rows one at a time (unshifted copy)
-                    const float4 x4 = *reinterpret_cast<const float4 *>(base + (size_t)r * row_bytes);
-                    const float x[4] = {x4.x, x4.y, x4.z, x4.w};
-                    const int wo = nrow - 1 - (s * RS + r);
-#pragma unroll
-                    for (int t = 0; t < TB; ++t) {
-                        const float cc = psw[wo + t];
-#pragma unroll
-                        for (int h = 0; h < V / 2; ++h)
-                            acc[t][h] = __ffma2_rn(make_float2(cc, cc), make_float2(x[2 * h], x[2 * h + 1]), acc[t][h]);
-                        if (ADJ) {
-                            const float cd = psw2[wo + t];
-#pragma unroll
-                            for (int h = 0; h < V / 2; ++h)
-                                acc2[ADJ ? t : 0][h] = __ffma2_rn(make_float2(cd, cd), make_float2(x[2 * h], x[2 * h + 1]),
-                                                                  acc2[ADJ ? t : 0][h]);
-                        }
-                    }
-                }
-                // a stage that any thread gave up on stops the unit: nothing more is issued and
-                // the stage stays owed (n_used not advanced) for the bounded drain below
-                if (__syncthreads_or(tmo)) {
-                    aborted = 1;
+                    __syncthreads();
                     break;
                 }
-                ++n_used;
-                if (s + NS < nst) {
-                    if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
-                    ++n_issued;
-                }
-            }
-            if (tid == 0) s_pipe = aborted || (ld_volatile(L.err) == ERR_PIPE);
-            __syncthreads();
-            if (s_pipe) {
-                if (tid == 0) {
-                    const long long t0 = globaltimer();
-                    while (n_used < n_issued && globaltimer() - t0 < L.timeout_ns) {
-                        const int bb = (int)(n_used % (uint32_t)NS);
-                        if (mbar_try_wait(&bars[bb], (n_used / (uint32_t)NS) & 1u)) ++n_used;
+                tc_use += (uint32_t)nst;
+                if (nst > 0) {
+                    if (!mbar_try_wait(done_bar, tc_done & 1u)) {
+                        const long long t0 = globaltimer();
+                        while (!mbar_try_wait(done_bar, tc_done & 1u))
+                            if (globaltimer() - t0 > L.timeout_ns) {
+                                give_up(nst, done_bar);
+                                break;
+                            }
                     }
+                    ++tc_done;
                 }
-                break;
-            }
-            // With block-long update units, a running sum over the tile's chunks in chunk order:
-            // chunk c stores S_c = S_{c-1} + p_c (S_{-1} = 0), the same adds, in the same order,
-            // as a sequential sum of the C partials, and the update unit reads S_{C-1} alone
-            // (its setup is on the step-to-step chain).  Chunk c-1 was claimed earlier, so the
-            // wait ends; the tile's count says how many chunks are summed.  Per-step update
-            // units sum the C partials themselves: their many short chunks run side by side,
-            // where a chain of adds would serialise them.
-            const int c0 = U.chunk;
-            const bool chain = I.ub && c0 > 0;
-            if (chain) {
-                if (tid == 0) {
+                tc::fence_after();
+                // chunk c stores the running sum S_c = S_{c-1} + p_c with block-long update units
+                const int c0 = U.chunk;
+                const bool chain = I.ub && c0 > 0;
+                if (chain && tid == 0) {
                     const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, c0), L, 512);
                     if (w < 0) note_failure(L, 10, b, tile, arrive_target(b, c0), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
-                    s_ok = w > 0;
+                    if (w <= 0) atomicExch(&s_abort, 1);
                 }
                 __syncthreads();
-                if (!s_ok) break;
-            }
-            if (j0 < I.N) {
-                auto add_store = [&](int t, int pl, float a0, float a1, float a2, float a3) {
-                    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (chain) sum = __ldcg(reinterpret_cast<const float4 *>(prow(c0 - 1, t, pl) + j0));
-                    sum.x += a0;
-                    sum.y += a1;
-                    sum.z += a2;
-                    sum.w += a3;
-                    *reinterpret_cast<float4 *>(prow(c0, t, pl) + j0) = sum;
-                };
+                if (s_abort) break;
+                // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. of point blocks
+                // m = w / 4, w / 4 + nwarp / 4, ...; each thread holds one point's TB sums
+                const int q = warp & 3;
+                for (int m = warp >> 2; m < MB; m += nwarp >> 2) {
+                    const int j = tile * I.P + m * 128 + q * 32 + lane;
+                    float v[TB];
+                    if (nst > 0) {
 #pragma unroll
-                for (int t = 0; t < TB; ++t) {
-                    add_store(t, 0, acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
-                    if (ADJ)
-                        add_store(t, 1, acc2[ADJ ? t : 0][0].x, acc2[ADJ ? t : 0][0].y, acc2[ADJ ? t : 0][1].x,
-                                  acc2[ADJ ? t : 0][1].y);
+                        for (int c = 0; c < TB; c += 16)
+                            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(m * TB + c), v + c);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < TB; ++t) v[t] = 0.f;
+                    }
+                    if (j < I.N) {
+#pragma unroll
+                        for (int t = 0; t < TB; ++t) {
+                            float sum = v[t];
+                            if (chain) sum = __ldcg(prow(c0 - 1, t, 0) + j) + v[t];
+                            prow(c0, t, 0)[j] = sum;
+                        }
+                    }
                 }
+                // CTA barrier, then one release add: cumulative over every thread's partial stores
+                tc::fence_before();
+                __syncthreads();
+                if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
+                continue;
+            } else {
+                // ================================================================ far unit
+                const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;
+                const int nst = (nrow + RS - 1) / RS;
+                long long tile_bytes = (long long)min(I.P, I.N - tile * I.P) * (long long)sizeof(TH);
+                tile_bytes = (tile_bytes + 15) & ~15ll;
+
+                // coefficient window w[i] = psi_{lag0 + i}: row r, step kb+t uses w[(r1-1-r) + t]
+                const bool sparse = !ADJ && I.gw != nullptr;
+                {
+                    const float *psi = reinterpret_cast<const float *>(I.psi);
+                    const int lag0 = kb - (r1 - 1);
+                    const int nw = nrow + TB - 1;
+                    for (int e = tid; e < (sparse ? WS : 4 * WS); e += nthr) {
+                        const int q = e / WS, i = e - q * WS, w = i + q;
+                        const int lag = lag0 + w;
+                        const bool cut = (w >= nw) || (I.mem_mode == 1 && lag > I.mem_L);
+                        psw[q * WS + i] = cut ? 0.f : I.gw ? reinterpret_cast<const float *>(I.gw)[lag] : psi[lag];
+                        if (ADJ) psw2[q * WS + i] = cut ? 0.f : reinterpret_cast<const float *>(I.dpsi)[lag];
+                    }
+                }
+                __syncthreads();
+                // Adaptive memory: the settled weights are zero between medians (at least two of three
+                // lags in the far rows), so a four-row group multiplies only the lags its window holds.
+                if (sparse) {
+                    for (int lo = tid; lo + 4 <= nrow; lo += nthr) {
+                        uint32_t m = 0;
+                        for (int j = 0; j < TB + 4; ++j) m |= (psw[lo + j] != 0.f ? 1u : 0u) << j;
+                        gmask[lo] = m;
+                    }
+                    __syncthreads();
+                }
+
+                // FP16 history: the power-of-two scale of each far row on this tile
+                if (F16) {
+                    for (int a = tid; a < nrow; a += nthr)
+                        rsc[a] = __ldcg(I.hscale + (size_t)((r0 + a) % I.cap) * I.T + tile);
+                    __syncthreads();
+                }
+
+                // accumulators as point pairs: one packed two-lane FMA (each lane an IEEE fmaf)
+                // serves two points, halving the far loop's FMA instructions
+                float2 acc[TB][V / 2], acc2[ADJ ? TB : 1][V / 2];
+    #pragma unroll
+                for (int t = 0; t < TB; ++t)
+    #pragma unroll
+                    for (int h = 0; h < V / 2; ++h) acc[t][h] = make_float2(0.f, 0.f);
+    #pragma unroll
+                for (int t = 0; t < (ADJ ? TB : 1); ++t)
+    #pragma unroll
+                    for (int h = 0; h < V / 2; ++h) acc2[t][h] = make_float2(0.f, 0.f);
+
+                // Stage s is filled by warp s mod (warps), one lane per row: the copies of a stage
+                // go out together and the issue work rotates over the warps instead of delaying
+                // one warp at every stage barrier.  Called by all lanes of the issuing warp.
+                const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+                auto issue = [&](int s, uint32_t slot) {
+                    const int bb = (int)(slot % (uint32_t)NS);
+                    const int a0 = s * RS, a1 = min(nrow, a0 + RS);
+                    if (lane == 0) mbar_expect_tx(&bars[bb], (uint32_t)(tile_bytes * (a1 - a0)));
+                    __syncwarp();
+                    const char *col = I.hist + (size_t)tile * I.P * sizeof(TH);
+                    for (int a = a0 + lane; a < a1; a += 32)
+                        bulk_g2s(stages + ((size_t)bb * RS + (a - a0)) * row_bytes,
+                                 col + (size_t)((r0 + a) % I.cap) * I.pitch, (uint32_t)tile_bytes, &bars[bb]);
+                };
+                // every lane that issues copies orders the rows it acquired before the async proxy
+                if (lane < RS) fence_proxy_async_global();
+                {
+                    const int pre = min(NS, nst);
+                    for (int s = 0; s < pre; ++s)
+                        if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
+                    n_issued += (uint32_t)pre;
+                }
+                int aborted = 0;
+                for (int s = 0; s < nst; ++s) {
+                    const int bb = (int)(n_used % (uint32_t)NS);
+                    const uint32_t ph = (n_used / (uint32_t)NS) & 1u;
+                    int tmo = 0;
+                    if (!mbar_try_wait(&bars[bb], ph)) {
+                        const long long t0 = globaltimer();
+                        while (!mbar_try_wait(&bars[bb], ph)) {
+                            if (globaltimer() - t0 > L.timeout_ns) {
+                                if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE)
+                                    note_failure(L, 2, ((long long)b << 32) | tile, ((long long)s << 32) | nst,
+                                                 ((long long)n_issued << 32) | n_used,
+                                                 (long long)*reinterpret_cast<volatile unsigned long long *>(&bars[bb]),
+                                                 ((long long)L.k0 << 32) | L.k_end, ((long long)r0 << 32) | r1);
+                                tmo = 1;  // the copy is still owed to this slot; see below
+                                break;
+                            }
+                        }
+                    }
+                    const int rows = tmo ? 0 : min(RS, nrow - s * RS);
+                    const unsigned char *base = stages + (size_t)bb * RS * row_bytes + (size_t)tid * H4<TH>::BYTES;
+                    // row a of the unit (a = s*RS + row within the stage), converted to FP32
+                    auto ldrow = [&](int rr, float *x) {
+                        H4<TH>::lds(base + (size_t)rr * row_bytes, x);
+                        if (F16) {
+                            const float sc = rsc[s * RS + rr];
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) x[v] *= sc;
+                        }
+                    };
+                    int r = 0;
+                    if (sparse) {
+                        // Four rows at a time, lag by lag over the window's nonzero weights only.  Lag
+                        // J of the window meets row i at step t = J - 3 + i; J descending keeps each
+                        // accumulator's rows in increasing order, as in the dense loop below, and the
+                        // skipped products are exact zeros, so the sums are the dense loop's.
+                        for (; r + 4 <= rows; r += 4) {
+                            const int lo = nrow - 1 - (s * RS + r) - 3;
+                            const uint32_t m = gmask[lo];
+                            float x[4][V];
+    #pragma unroll
+                            for (int i = 0; i < 4; ++i) ldrow(r + i, x[i]);
+    #pragma unroll
+                            for (int J = TB + 3; J >= 0; --J) {
+                                if (!(m & (1u << J))) continue;
+                                const float cj = psw[lo + J];
+                                const float2 cj2 = make_float2(cj, cj);
+    #pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    const int t = J - 3 + i;
+                                    if (t < 0 || t >= TB) continue;
+    #pragma unroll
+                                    for (int h = 0; h < V / 2; ++h)
+                                        acc[t][h] = __ffma2_rn(cj2, make_float2(x[i][2 * h], x[i][2 * h + 1]), acc[t][h]);
+                                }
+                            }
+                        }
+                    }
+                    // Four rows at a time.  Row a = s*RS + r + i uses w[wo - i + t], wo = nrow-1-(s*RS+r):
+                    // the TB+3 coefficients w[wo-3 .. wo+TB-1] come in aligned 16-byte loads from the
+                    // copy shifted by (wo-3) & 3 and serve all four rows from registers.
+                    for (; r + 4 <= rows; r += 4) {
+                        const int lo = nrow - 1 - (s * RS + r) - 3;
+                        const int cq = (lo & 3) * WS + (lo & ~3);
+                        float c[TB + 4], c2[ADJ ? TB + 4 : 1];
+    #pragma unroll
+                        for (int j = 0; j < TB + 4; j += 4) {
+                            const float4 c4 = *reinterpret_cast<const float4 *>(psw + cq + j);
+                            c[j] = c4.x;
+                            c[j + 1] = c4.y;
+                            c[j + 2] = c4.z;
+                            c[j + 3] = c4.w;
+                            if (ADJ) {
+                                const float4 d4 = *reinterpret_cast<const float4 *>(psw2 + cq + j);
+                                c2[ADJ ? j : 0] = d4.x;
+                                c2[ADJ ? j + 1 : 0] = d4.y;
+                                c2[ADJ ? j + 2 : 0] = d4.z;
+                                c2[ADJ ? j + 3 : 0] = d4.w;
+                            }
+                        }
+    #pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float x[4];
+                            ldrow(r + i, x);
+    #pragma unroll
+                            for (int t = 0; t < TB; ++t)
+    #pragma unroll
+                                for (int h = 0; h < V / 2; ++h)
+                                    acc[t][h] = __ffma2_rn(make_float2(c[3 - i + t], c[3 - i + t]), make_float2(x[2 * h], x[2 * h + 1]),
+                                                           acc[t][h]);
+                            if (ADJ) {
+    #pragma unroll
+                                for (int t = 0; t < (ADJ ? TB : 1); ++t)
+    #pragma unroll
+                                    for (int h = 0; h < V / 2; ++h)
+                                        acc2[t][h] = __ffma2_rn(make_float2(c2[ADJ ? 3 - i + t : 0], c2[ADJ ? 3 - i + t : 0]),
+                                                                make_float2(x[2 * h], x[2 * h + 1]), acc2[t][h]);
+                            }
+                        }
+                    }
+                    for (; r < rows; ++r) {  // remaining rows one at a time (unshifted copy)
+                        float x[4];
+                        ldrow(r, x);
+                        const int wo = nrow - 1 - (s * RS + r);
+    #pragma unroll
+                        for (int t = 0; t < TB; ++t) {
+                            const float cc = psw[wo + t];
+    #pragma unroll
+                            for (int h = 0; h < V / 2; ++h)
+                                acc[t][h] = __ffma2_rn(make_float2(cc, cc), make_float2(x[2 * h], x[2 * h + 1]), acc[t][h]);
+                            if (ADJ) {
+                                const float cd = psw2[wo + t];
+    #pragma unroll
+                                for (int h = 0; h < V / 2; ++h)
+                                    acc2[ADJ ? t : 0][h] = __ffma2_rn(make_float2(cd, cd), make_float2(x[2 * h], x[2 * h + 1]),
+                                                                      acc2[ADJ ? t : 0][h]);
+                            }
+                        }
+                    }
+                    // a stage that any thread gave up on stops the unit: nothing more is issued and
+                    // the stage stays owed (n_used not advanced) for the bounded drain below
+                    if (__syncthreads_or(tmo)) {
+                        aborted = 1;
+                        break;
+                    }
+                    ++n_used;
+                    if (s + NS < nst) {
+                        if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
+                        ++n_issued;
+                    }
+                }
+                if (tid == 0) s_pipe = aborted || (ld_volatile(L.err) == ERR_PIPE);
+                __syncthreads();
+                if (s_pipe) {
+                    if (tid == 0) {
+                        const long long t0 = globaltimer();
+                        while (n_used < n_issued && globaltimer() - t0 < L.timeout_ns) {
+                            const int bb = (int)(n_used % (uint32_t)NS);
+                            if (mbar_try_wait(&bars[bb], (n_used / (uint32_t)NS) & 1u)) ++n_used;
+                        }
+                    }
+                    break;
+                }
+                // With block-long update units, a running sum over the tile's chunks in chunk order:
+                // chunk c stores S_c = S_{c-1} + p_c (S_{-1} = 0), the same adds, in the same order,
+                // as a sequential sum of the C partials, and the update unit reads S_{C-1} alone
+                // (its setup is on the step-to-step chain).  Chunk c-1 was claimed earlier, so the
+                // wait ends; the tile's count says how many chunks are summed.  Per-step update
+                // units sum the C partials themselves: their many short chunks run side by side,
+                // where a chain of adds would serialise them.
+                const int c0 = U.chunk;
+                const bool chain = I.ub && c0 > 0;
+                if (chain) {
+                    if (tid == 0) {
+                        const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, c0), L, 512);
+                        if (w < 0) note_failure(L, 10, b, tile, arrive_target(b, c0), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
+                        s_ok = w > 0;
+                    }
+                    __syncthreads();
+                    if (!s_ok) break;
+                }
+                if (j0 < I.N) {
+                    auto add_store = [&](int t, int pl, float a0, float a1, float a2, float a3) {
+                        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (chain) sum = __ldcg(reinterpret_cast<const float4 *>(prow(c0 - 1, t, pl) + j0));
+                        sum.x += a0;
+                        sum.y += a1;
+                        sum.z += a2;
+                        sum.w += a3;
+                        *reinterpret_cast<float4 *>(prow(c0, t, pl) + j0) = sum;
+                    };
+    #pragma unroll
+                    for (int t = 0; t < TB; ++t) {
+                        add_store(t, 0, acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
+                        if (ADJ)
+                            add_store(t, 1, acc2[ADJ ? t : 0][0].x, acc2[ADJ ? t : 0][0].y, acc2[ADJ ? t : 0][1].x,
+                                      acc2[ADJ ? t : 0][1].y);
+                    }
+                }
+                // CTA barrier, then one release add: cumulative over every thread's partial stores
+                __syncthreads();
+                if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
+                continue;
             }
-            // CTA barrier, then one release add: cumulative over every thread's partial stores
-            __syncthreads();
-            if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
-            continue;
         }
 
         const float S = (float)I.S, dt = (float)I.dt;
@@ -498,8 +804,21 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         const float *dpsi = reinterpret_cast<const float *>(I.dpsi);
         const bool mirror = (I.bc == 1);
         const int kend = min(L.k_end, I.ksteps);
+        // Rows of the newest 2T steps in FP32: the history itself for FP32 history, else the ring
+        // of FP32 rows kept beside the low-precision history (row r in slot r mod hring_cap).
         auto hrow_at = [&](int r) -> const float * {
-            return reinterpret_cast<const float *>(I.hist + (size_t)(r % I.cap) * I.pitch) + j0;
+            return reinterpret_cast<const float *>(I.hring + (size_t)(r % I.hring_cap) * I.hring_pitch) + j0;
+        };
+        // Four values of history row r (any age) converted to FP32, FP16 scale applied.
+        auto hist4 = [&](int r) -> float4 {
+            float x[4];
+            H4<TH>::ldg(I.hist + (size_t)(r % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), x);
+            if (F16) {
+                const float sc = __ldcg(I.hscale + (size_t)(r % I.cap) * I.T + tile);
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] *= sc;
+            }
+            return make_float4(x[0], x[1], x[2], x[3]);
         };
 
         // Phase B of step k on this tile: wait for u^k on the halo tiles, optionally add lag 1
@@ -730,9 +1049,33 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         own[V + v] = nlv[v];
                     }
                 }
-                if (I.hist_write)
-                    *reinterpret_cast<float4 *>(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * 4) =
+                if (I.hist_write) {
+                    // delta^k in FP32 for the near lags (for FP32 history, the history row itself)
+                    *reinterpret_cast<float4 *>(I.hring + (size_t)(k % I.hring_cap) * I.hring_pitch + (size_t)j0 * 4) =
                         make_float4(d[0], d[1], d[2], d[3]);
+                    if (LOWP && !F16)
+                        H4<TH>::stg(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), d, 1.f);
+                }
+            }
+            if (F16 && I.hist_write) {
+                // FP16 row: a power-of-two scale per (row, tile) from the tile's largest |delta|
+                float amax = 0.f;
+#pragma unroll
+                for (int v = 0; v < V; ++v) amax = fmaxf(amax, fabsf(d[v]));  // zero past the grid's end
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                if ((tid & 31) == 0) s_wmax[tid >> 5] = amax;
+                __syncthreads();
+                float m = 0.f;
+                for (int w = 0; w < (nthr + 31) / 32; ++w) m = fmaxf(m, s_wmax[w]);
+                int e = 0;
+                if (m > 0.f && isfinite(m)) {
+                    int ex;
+                    frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
+                    e = max(-100, min(100, 15 - ex));
+                }
+                if (tid == 0) I.hscale[(size_t)(k % I.cap) * I.T + tile] = ldexpf(1.f, -e);
+                if (j0 < I.N) H4<TH>::stg(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), d, ldexpf(1.f, e));
             }
             if (bad) atomicOr(L.nonfinite, 1u);
             if (ADJ) {
@@ -818,13 +1161,15 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 }
                 // rows [ra, rb) with each step's weight of their lag, four loads in flight
                 const float *gwf = reinterpret_cast<const float *>(I.gw);
-                auto add_rows = [&](int ra, int rb) {
+                // (old: tail rows from the history of any age; else the near rows in FP32)
+                auto add_rows = [&](int ra, int rb, bool old) {
                     for (int r = ra; r < rb; r += 4) {
                         float4 x[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            x[i] = (r + i < rb) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                            x[i] = (r + i >= rb) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : old         ? hist4(r + i)
+                                                 : __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)));
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -850,9 +1195,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 if (I.gw) {  // adaptive memory: the tail rows below the far rows
                     int rlo, rhi;
                     far_rows<TB>(I, b, rlo, rhi);
-                    add_rows(0, rlo);
+                    add_rows(0, rlo, true);
                 }
-                add_rows(max(0, kb - TB), kf);
+                add_rows(max(0, kb - TB), kf, false);
 #pragma unroll
                 for (int t = 0; t < TB; ++t)
                     if (t >= t0 && t < t1) {
@@ -1004,9 +1349,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 for (int r = 0; r < rlo; r += 4) {
                     float4 x[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        x[i] = (r + i < rlo) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int i = 0; i < 4; ++i) x[i] = (r + i < rlo) ? hist4(r + i) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         if (r + i >= rlo) continue;
@@ -1057,6 +1400,16 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             }
         }
         if (!phase_b(k, hk >= 1, H, H2, d, k == min(kb + TB, kend) - 1, nullptr, nullptr, nullptr)) break;
+    }
+    // every exit from the unit loop is CTA-uniform; the tensor memory goes back once all of the
+    // CTA's tensor-core work has completed (a failed unit waits for its MMAs before it exits)
+    if (TC) {
+        tc::fence_before();
+        __syncthreads();
+        if (tid < 32) {
+            tc::fence_after();
+            tc::tmem_dealloc(tmem, tc_cols);
+        }
     }
 }
 

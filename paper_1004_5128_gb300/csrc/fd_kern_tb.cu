@@ -2,8 +2,9 @@
 #include "fd_kernels.h"
 
 namespace fdk {
-const void *kernel_tb(int tb, bool adj)
+const void *kernel_tb(int tb, bool adj, int hist)
 {
+    if (hist != 1) return adj ? nullptr : kernel_tb_lowp(tb, hist);
     if (adj) {  // two accumulator sets: blocks of at most 8 steps fit the register budget
         switch (tb) {
         case 4: return (const void *)engine_tb_kernel<4, true>;

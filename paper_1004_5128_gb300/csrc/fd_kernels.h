@@ -9,6 +9,8 @@ const void *kernel_for(int state, int hist, int acc, bool kahan, bool adj);
 const void *kernel_f64(bool kahan, bool adj);
 const void *kernel_f32(bool kahan, bool adj);
 const void *kernel_lowp(int hist, bool kahan, bool adj);
-// Temporally blocked FP32 kernel for a block of tb steps (forward 4/8/16, adjoint 4/8), else nullptr.
-const void *kernel_tb(int tb, bool adj = false);
+// Temporally blocked kernel (FP32 state and accumulation) for a block of tb steps and a history
+// dtype (FD_F32: forward 4/8/16, adjoint 4/8; FD_BF16 / FD_F16: forward 4/8/16), else nullptr.
+const void *kernel_tb(int tb, bool adj = false, int hist = 1);
+const void *kernel_tb_lowp(int tb, int hist);
 }  // namespace fdk

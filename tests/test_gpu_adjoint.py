@@ -1,5 +1,8 @@
 """GPU parity of the checkpointed reverse-time adjoint against the FP64 oracle adjoint, and the
-autograd binding.  J = 1/2 |u^K - target|^2; gradients w.r.t. gamma, alpha, react, u0."""
+autograd binding.  J = 1/2 |u^K - target|^2; gradients w.r.t. gamma, alpha, react, u0.
+
+Tolerances are the stated ones: 1e-12 (FP64) and 1e-5 (FP32), each relative to the largest
+magnitude of the reference gradient (infinity norm for dJ/du0 and dJ/dreact)."""
 import numpy as np
 import pytest
 import torch
@@ -7,6 +10,8 @@ import torch
 import oracle
 from paper_1004_5128_gb300 import FRD, FRDFunction, synth
 from tests.helpers import rel_inf
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +46,7 @@ def compare(r, ref, tol):
 def test_adjoint_fp64_vs_oracle(bc):
     p, tgt = small(bc)
     r = gpu_adjoint(p, tgt, "f64", ckpt=40)  # 3 full segments + a ragged one
-    compare(r, oracle.adjoint(p, tgt), 1e-10)
+    compare(r, oracle.adjoint(p, tgt), TOL["f64"])
 
 
 def test_adjoint_fp64_1d_many_tiles():
@@ -51,13 +56,13 @@ def test_adjoint_fp64_1d_many_tiles():
                       u0=g.uniform(n, 0, 1))
     tgt = g.uniform(n, 0, 1)
     r = gpu_adjoint(p, tgt, "f64", ckpt=50, tile_threads=64, chunk_terms=16)
-    compare(r, oracle.adjoint(p, tgt), 1e-10)
+    compare(r, oracle.adjoint(p, tgt), TOL["f64"])
 
 
 def test_adjoint_fp32_vs_oracle():
     p, tgt = small(synth.BC_DIRICHLET0, nx=48, ny=40, K=300)
     r = gpu_adjoint(p, tgt, "f32", ckpt=64)
-    compare(r, oracle.adjoint(p, tgt), 2e-4)
+    compare(r, oracle.adjoint(p, tgt), TOL["f32"])
 
 
 def test_adjoint_config5_reduced_vs_oracle():
@@ -65,7 +70,7 @@ def test_adjoint_config5_reduced_vs_oracle():
     p = synth.config5(K=300)
     tgt = oracle.run(synth.config5(K=300, target=True))
     r = gpu_adjoint(p, tgt, "f32", ckpt=200)
-    compare(r, oracle.adjoint(p, tgt), 2e-4)
+    compare(r, oracle.adjoint(p, tgt), TOL["f32"])
 
 
 def test_adjoint_config5_full_size_fp64_vs_central_differences():
@@ -118,8 +123,9 @@ def test_adjoint_config5_full_size_fp64_vs_central_differences():
     assert abs(float(r64["du0"] @ v) - ref) < 1e-6 * abs(ref)
     r32 = gpu_adjoint(p, tgt.cpu().numpy(), "f32", ckpt=200)
     for key in ("dgamma", "dalpha"):
-        assert abs(r32[key] - r64[key]) < 1e-3 * abs(r64[key])
-    assert rel_inf(r32["du0"], r64["du0"]) < 1e-3
+        assert abs(r32[key] - r64[key]) < TOL["f32"] * abs(r64[key])
+    assert rel_inf(r32["du0"], r64["du0"]) < TOL["f32"]
+    assert np.max(np.abs(np.array(r32["dreact"]) - r64["dreact"])) < TOL["f32"] * np.max(np.abs(r64["dreact"]))
 
 
 def test_autograd_function():
@@ -134,18 +140,18 @@ def test_autograd_function():
     loss.backward()
     ref = oracle.adjoint(p, tgt)
     assert abs(loss.item() - ref["J"]) < 1e-12 * ref["J"]
-    assert rel_inf(u0.grad.cpu().numpy(), ref["du0"]) < 1e-10
-    assert abs(gam.grad.item() - ref["dgamma"]) < 1e-10 * abs(ref["dgamma"])
-    assert abs(alp.grad.item() - ref["dalpha"]) < 1e-10 * abs(ref["dalpha"])
-    assert np.max(np.abs(react.grad.numpy() - ref["dreact"])) < 1e-10 * np.max(np.abs(ref["dreact"]))
+    assert rel_inf(u0.grad.cpu().numpy(), ref["du0"]) < TOL["f64"]
+    assert abs(gam.grad.item() - ref["dgamma"]) < TOL["f64"] * abs(ref["dgamma"])
+    assert abs(alp.grad.item() - ref["dalpha"]) < TOL["f64"] * abs(ref["dalpha"])
+    assert np.max(np.abs(react.grad.numpy() - ref["dreact"])) < TOL["f64"] * np.max(np.abs(ref["dreact"]))
 
 
-@pytest.mark.parametrize("state,tol", [("f64", 1e-10), ("f32", 2e-4)])
+@pytest.mark.parametrize("state", ["f64", "f32"])
 @pytest.mark.parametrize("L", [9, 40])
-def test_short_memory_adjoint_vs_oracle(state, tol, L):
+def test_short_memory_adjoint_vs_oracle(state, L):
     """Short memory: the adjoint sums each row over the transposed window (lags m <= L), with
     checkpoint segments of 40 steps over 150."""
     p, tgt = small(synth.BC_NOFLUX)
     p = synth.with_mode(p, synth.MEM_SHORT, L=L)
     r = gpu_adjoint(p, tgt, state, ckpt=40)
-    compare(r, oracle.adjoint(p, tgt), tol)
+    compare(r, oracle.adjoint(p, tgt), TOL[state])

@@ -176,7 +176,7 @@ def test_blocked_adjoint_matches_oracle(tb, bc, step_updates):
     p = ragged(bc, synth.MEM_FULL, K=230)
     tgt = synth.SplitMix64(3).uniform(p["nx"] * p["ny"], 0, 0.8)
     compare_grads(blocked_adjoint(p, tgt, tb, ckpt=50, chunk_terms=16, step_updates=step_updates),
-                  oracle.adjoint(p, tgt), 2e-4)
+                  oracle.adjoint(p, tgt), 1e-5)
 
 
 def test_blocked_adjoint_config5_reduced():
@@ -184,7 +184,7 @@ def test_blocked_adjoint_config5_reduced():
     config's checkpoint spacing of 200 steps."""
     p = synth.config5(K=600)
     tgt = oracle.run(synth.config5(K=600, target=True))
-    compare_grads(blocked_adjoint(p, tgt, 8, ckpt=200), oracle.adjoint(p, tgt), 2e-4)
+    compare_grads(blocked_adjoint(p, tgt, 8, ckpt=200), oracle.adjoint(p, tgt), 1e-5)
 
 
 def test_blocked_adjoint_rejects_blocks_of_16():
@@ -240,4 +240,4 @@ def test_blocked_short_memory_adjoint_matches_oracle(tb, L, step_updates):
     p = ragged(synth.BC_DIRICHLET0, synth.MEM_SHORT, L=L, K=230)
     tgt = synth.SplitMix64(4).uniform(p["nx"] * p["ny"], 0, 0.8)
     compare_grads(blocked_adjoint(p, tgt, tb, ckpt=50, chunk_terms=16, step_updates=step_updates),
-                  oracle.adjoint(p, tgt), 2e-4)
+                  oracle.adjoint(p, tgt), 1e-5)
