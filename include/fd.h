@@ -65,6 +65,8 @@ enum { FD_F64 = 0, FD_F32 = 1, FD_BF16 = 2, FD_F16 = 3 };
                                       launch ends with FD_ERR_TIMEOUT (GPU stays usable) */
 #define FD_FLAG_STEP_UPDATES 32u   /* time_block: one update unit per step and tile even where
                                       block-long update units would fit (see time_block) */
+#define FD_FLAG_FMA_FAR 64u        /* time_block with BF16 history: multiply the far rows on the
+                                      CUDA cores instead of the tensor cores (see time_block) */
 
 typedef struct fd_problem {
     int ndim;            /* 1, 2 or 3 (3-D: the 7-point analogue of eq. deltasimp) */
@@ -97,9 +99,15 @@ typedef struct fd_problem {
     int head_lags;       /* lags 1..head_lags are summed by the per-tile update from rows kept in
                             state precision (0 = 8 for F32/F64 history, 32 for BF16/F16) */
     int nz;              /* points along the third axis when ndim == 3, else 1 */
-    int time_block;      /* 0, or 4 / 8 / 16: temporally blocked sum (F32 state, history and
-                            accumulation, no Kahan; with FD_FLAG_KEEP_TAPE full or short memory
-                            and 4 or 8).  Rows older than the current block of time_block steps
+    int time_block;      /* 0, or 4 / 8 / 16 (BF16 history also 32): temporally blocked sum (F32
+                            state and accumulation, F32 / BF16 / F16 history, no Kahan; with
+                            FD_FLAG_KEEP_TAPE F32 history, full or short memory and 4 or 8).
+                            With BF16 history and blocks of 16 or 32 the far rows are multiplied
+                            on the tensor cores (tcgen05, FP32 accumulation in tensor memory, the
+                            weights split into BF16 hi + lo halves; tile_threads 128 or 256,
+                            stage_rows 16 or 32 dividing time_block) unless FD_FLAG_FMA_FAR.
+                            Low-precision history keeps the newest 2 time_block rows in FP32 as
+                            well.  Rows older than the current block of time_block steps
                             are read once per block into time_block accumulators (the Toeplitz
                             structure of eq. frac_norxn); the newest rows are summed per step.
                             Adaptive memory: the older rows carry the weights that the medians
@@ -196,6 +204,7 @@ typedef struct fd_geometry {
                                   block plus every step's newest (head) rows */
     int time_block;
     int block_updates;       /* time_block: 1 when one unit per tile carries a whole block's updates */
+    int far_tensor_cores;    /* time_block: 1 when the far rows are multiplied on the tensor cores */
 } fd_geometry;
 int fd_get_geometry(fd_handle *h, fd_geometry *g);
 

@@ -62,10 +62,13 @@ def lib():
         L.or_run_cs.argtypes = [pp, ctypes.c_double, ctypes.c_double, dp, dp, dp, ctypes.c_long,
                                 dp, dp]
         L.or_adjoint.argtypes = [pp, dp, ctypes.c_long, dp, dp, dp, dp, dp, dp, ctypes.c_int]
+        L.or_run_bf16.argtypes = [pp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, dp, ctypes.c_int]
+        L.or_round_bf16.argtypes = [ctypes.c_double]
+        L.or_round_bf16.restype = ctypes.c_double
         L.or_scalar_mode.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int, ctypes.c_long,
                                                              ctypes.c_long, ctypes.c_int,
                                                              ctypes.c_double, ctypes.c_long, dp]
-        for f in (L.or_weights, L.or_run, L.or_run_cs, L.or_adjoint, L.or_scalar_mode):
+        for f in (L.or_weights, L.or_run, L.or_run_cs, L.or_adjoint, L.or_scalar_mode, L.or_run_bf16):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -118,6 +121,25 @@ def run(p: dict, K: int | None = None, u0=None, tape: bool = False, threads: int
     if rc != 0:
         raise ValueError(f"or_run failed ({rc})")
     return (uK, tp) if tape else uK
+
+
+def run_bf16(p: dict, blk: int, head: int, K: int | None = None, threads: int = 0):
+    """u^K with history rows stored in BF16 beyond the FP32 window: at step k, lags up to
+    head + (k mod blk) (blk = 0: up to head) use delta as computed, older lags its BF16 rounding
+    (the storage rule of the mixed-precision GPU runs)."""
+    K = p["K"] if K is None else K
+    u0 = np.ascontiguousarray(p["u0"], dtype=np.float64)
+    uK = np.empty(p["nx"] * p["ny"] * p.get("nz", 1))
+    s = _problem(p)
+    rc = lib().or_run_bf16(ctypes.byref(s), _dp(u0), K, blk, head, _dp(uK), threads)
+    if rc != 0:
+        raise ValueError(f"or_run_bf16 failed ({rc})")
+    return uK
+
+
+def round_bf16(x: float) -> float:
+    """x rounded to BF16 (8 significant bits, to nearest, ties to even)."""
+    return lib().or_round_bf16(float(x))
 
 
 def run_cs(p: dict, K: int | None = None, gamma_im=0.0, alpha_im=0.0, react_im=None,

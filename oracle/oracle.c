@@ -291,6 +291,66 @@ int or_run(const or_problem *p, const double *u0, long K, double *uK, double *ta
     return 0;
 }
 
+/* ------------------------------------------------ BF16-stored history forward */
+
+double or_round_bf16(double x)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    const double f = frexp(x, &e); /* x = f 2^e, 0.5 <= |f| < 1: 8 significant bits = f 2^8 */
+    return ldexp(nearbyint(ldexp(f, 8)), e - 8);
+}
+
+int or_run_bf16(const or_problem *p, const double *u0, long K, long blk, long head, double *uK, int threads)
+{
+    if (check_problem(p, K) || !u0 || !uK || blk < 0 || head < 0) return -1;
+    const long N = (long)p->nx * p->ny * p->nz;
+    const long cap = history_rows(p, K);
+    const double S = p->alpha * pow(p->dt, p->gamma) / (p->dx * p->dx);
+
+    double *psi = malloc(sizeof(double) * (size_t)(K + 1));
+    double *hist = malloc(sizeof(double) * (size_t)cap * (size_t)N);  /* delta as computed */
+    double *hist16 = malloc(sizeof(double) * (size_t)cap * (size_t)N); /* its BF16 rounding */
+    double *u = malloc(sizeof(double) * (size_t)N);
+    double *un = malloc(sizeof(double) * (size_t)N);
+    long *lag = malloc(sizeof(long) * (size_t)(K + 1));
+    long *mult = malloc(sizeof(long) * (size_t)(K + 1));
+    if (!psi || !hist || !hist16 || !u || !un || !lag || !mult) {
+        free(psi); free(hist); free(hist16); free(u); free(un); free(lag); free(mult);
+        return -2;
+    }
+    or_weights(p->gamma, K + 1, psi, NULL);
+    memcpy(u, u0, sizeof(double) * (size_t)N);
+#ifdef _OPENMP
+    const int nthr = threads > 0 ? threads : omp_get_max_threads();
+#else
+    (void)threads;
+#endif
+    for (long k = 0; k < K; ++k) {
+        double *row = hist + (size_t)(k % cap) * (size_t)N;
+        apply_L(p, u, row); /* delta^k */
+        for (long j = 0; j < N; ++j) hist16[(size_t)(k % cap) * (size_t)N + j] = or_round_bf16(row[j]);
+        const long n = or_schedule(p->mem_mode, p->mem_L, p->mem_a, p->adaptive_rule, k, lag, mult);
+        const long w = head + (blk > 0 ? k % blk : 0); /* lags <= w as computed */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthr)
+#endif
+        for (long j = 0; j < N; ++j) {
+            double sum = 0.0, cmp = 0.0;
+            for (long t = 0; t < n; ++t) { /* ascending lag */
+                const double *h = (lag[t] <= w ? hist : hist16) + (size_t)((k - lag[t]) % cap) * (size_t)N;
+                nadd(&sum, &cmp, (double)mult[t] * psi[lag[t]] * h[j]);
+            }
+            /* eq. frac_final with f outside the memory sum */
+            un[j] = u[j] + p->dt * react_f(p->react, u[j]) + S * (sum + cmp);
+        }
+        double *tmp = u; u = un; un = tmp;
+    }
+    memcpy(uK, u, sizeof(double) * (size_t)N);
+    free(psi); free(hist); free(hist16); free(u); free(un); free(lag); free(mult);
+    return 0;
+}
+
 /* ------------------------------------------------------ complex-step forward */
 
 static void apply_L_cs(const or_problem *p, const double complex *u, double complex *out)

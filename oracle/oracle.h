@@ -66,6 +66,17 @@ long or_schedule(int mem_mode, long L, long a, int rule, long k, long *lag, long
  * -2 on allocation failure. */
 int or_run(const or_problem *p, const double *u0, long K, double *uK, double *tape, int threads);
 
+/* BF16 storage of a value: round to 8 significant bits, to nearest, ties to even (the 16-bit
+ * brain floating-point format has FP32's exponent range and 8 significant bits). */
+double or_round_bf16(double x);
+
+/* or_run with history rows stored in BF16 beyond an FP32 window: at step k the lags
+ * m <= head + (blk > 0 ? k mod blk : 0) use delta^{k-m} as computed, older lags its BF16
+ * rounding.  This is the storage rule of the mixed-precision GPU runs (not part of the paper):
+ * per-step kernel blk = 0, head = its FP32 head lags; blocked kernel blk = head = the block
+ * length.  With head >= K it equals or_run bit for bit. */
+int or_run_bf16(const or_problem *p, const double *u0, long K, long blk, long head, double *uK, int threads);
+
 /* Forward run in double complex (complex-step differentiation): the
  * imaginary parts of u0, gamma, alpha and react carry the perturbation.
  * Plain (uncompensated) summation.  Returns u^K as separate re/im arrays. */

@@ -33,6 +33,7 @@ FD_FLAG_KEEP_TAPE = 4
 FD_FLAG_INJECT_STALL = 8
 FD_FLAG_PLAIN_STATE = 16
 FD_FLAG_STEP_UPDATES = 32
+FD_FLAG_FMA_FAR = 64
 
 # every function include/fd.h declares
 EXPORTS = (
@@ -75,7 +76,8 @@ class FdGeometry(ctypes.Structure):
                                             "head_lags")] + [
         ("units_total", ctypes.c_int64), ("hist_rows_total", ctypes.c_int64),
         ("terms_total", ctypes.c_int64), ("stream_rows_total", ctypes.c_int64),
-        ("time_block", ctypes.c_int), ("block_updates", ctypes.c_int)]
+        ("time_block", ctypes.c_int), ("block_updates", ctypes.c_int),
+        ("far_tensor_cores", ctypes.c_int)]
 
 
 _lib = None

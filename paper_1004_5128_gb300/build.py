@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfd.so")
 
-SOURCES = ["fd_api.cu", "fd_kern_f64.cu", "fd_kern_f32.cu", "fd_kern_lowp.cu", "fd_kern_tb.cu", "fd_kern_tb_lowp.cu",
+SOURCES = ["fd_api.cu", "fd_kern_f64.cu", "fd_kern_f32.cu", "fd_kern_lowp.cu", "fd_kern_tb.cu", "fd_kern_tb_lowp.cu", "fd_kern_tb_tc.cu",
            "fd_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

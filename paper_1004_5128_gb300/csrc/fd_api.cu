@@ -5,6 +5,7 @@
 // FP64/integers, lays out the caller's workspace, uploads the tables and drives
 // the persistent engine (fd_engine.cuh): forward launches, the checkpointed
 // reverse-time adjoint, and multi-instance batches recorded as a CUDA graph.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -146,6 +147,14 @@ inline int64_t n_terms(const int4 &e) { return (int64_t)e.x + e.y + (e.w >= e.z 
 
 // ------------------------------------------------------------------ validation
 
+// Blocked runs with BF16 history and blocks of 16 or 32 multiply their far rows on the tensor
+// cores unless FD_FLAG_FMA_FAR asks for the CUDA-core loop.
+inline bool tc_far(const fd_problem &p)
+{
+    return (p.time_block == 16 || p.time_block == 32) && p.hist_dtype == FD_BF16 && !(p.flags & FD_FLAG_FMA_FAR) &&
+           !(p.flags & FD_FLAG_KEEP_TAPE);
+}
+
 int validate(const fd_problem *p)
 {
     if (!p) return FD_ERR_INVALID_ARG;
@@ -180,9 +189,16 @@ int validate(const fd_problem *p)
                 !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)))
         return FD_ERR_UNSUPPORTED;
     if (p->time_block) {
-        if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16) return FD_ERR_INVALID_ARG;
+        const bool tc = tc_far(*p);
+        if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16 && !(tc && p->time_block == 32))
+            return p->time_block == 32 ? FD_ERR_UNSUPPORTED : FD_ERR_INVALID_ARG;
         if (p->state_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan) return FD_ERR_UNSUPPORTED;
-        if (!fdk::kernel_tb(p->time_block, adj, p->hist_dtype)) return FD_ERR_UNSUPPORTED;
+        if (!fdk::kernel_tb(p->time_block, adj, p->hist_dtype, tc)) return FD_ERR_UNSUPPORTED;
+        if (tc) {  // point blocks of 128 (tile_threads 128 or 256), whole K slices of 16 rows per stage
+            if (p->tile_threads && p->tile_threads != 128 && p->tile_threads != 256) return FD_ERR_INVALID_ARG;
+            if (p->stage_rows && ((p->stage_rows != 16 && p->stage_rows != 32) || p->time_block % p->stage_rows))
+                return FD_ERR_INVALID_ARG;
+        }
         // arrival words hold a block generation (blocks / 4) and a chunk count in 16 bits each
         if ((int64_t)p->max_steps / p->time_block / 4 >= 65535) return FD_ERR_INVALID_ARG;
     }
@@ -205,6 +221,8 @@ struct Geo {
     int cmax;        // blocked: most far chunks per block (0: chunks of R rows)
     int rwin;        // blocked: largest far chunk (rows), the coefficient window's length
     int nblocks;     // blocks of tb steps covering max_steps
+    int tc;          // blocked, BF16 history: far units on the tensor cores
+    int ralign;      // blocked: far chunks start on multiples of ralign rows (tensor cores: RS)
     int hring_sep;   // separate state-precision head ring
     int hring_cap;
     int64_t hring_pitch;
@@ -236,6 +254,16 @@ inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
            8 * (size_t)g.NS;
 }
 
+// Tensor-core blocked kernel: stage ring (RS rows x P points of BF16, at least the block-long
+// units' sums), 1 KB-aligned; NS coefficient blocks (hi and lo halves of tb/8 1 KB atoms); the
+// coefficient window; 3 NS + 1 barriers; 1 KB of slack to align the base.
+inline size_t smem_bytes_tc(const Geo &g, int rwin)
+{
+    const size_t ring = std::max((size_t)g.NS * g.RS * g.threads * 8, (size_t)(g.tb * g.planes + 2) * g.threads * 16);
+    return align_up(ring, 1024) + (size_t)g.NS * 2 * (g.tb / 8) * 1024 + (size_t)(rwin + g.tb) * 4 + 16 +
+           8 * (size_t)(3 * g.NS + 1) + 1024;
+}
+
 int device_sms()
 {
     int dev = 0, sms = 0;
@@ -261,15 +289,20 @@ inline void block_rows(const fd_problem &p, const Geo &g, int64_t b, int64_t &rl
     rlo = std::min(rlo, rhi);
 }
 
+// First row of a block's far chunks: its first far row, rounded down to a multiple of ralign on
+// the tensor-core path (which streams whole stages; the rows below the far rows get weight 0).
+inline int64_t block_origin(const Geo &g, int64_t lo) { return g.ralign > 1 ? lo - lo % g.ralign : lo; }
+
 // Far chunking of block b: chunks of R rows, or, with cmax, of max(R, ceil(rows / cmax)) rows,
 // so that a block-long update unit sums at most cmax partial rows per step.
 inline void block_chunks(const fd_problem &p, const Geo &g, int64_t b, int64_t &Rb, int64_t &Cb)
 {
     int64_t lo, hi;
     block_rows(p, g, b, lo, hi);
-    const int64_t rows = hi - lo;
+    const int64_t rows = hi - block_origin(g, lo);
     Rb = g.R;
     if (g.cmax) Rb = std::max<int64_t>(Rb, (rows + g.cmax - 1) / g.cmax);
+    if (g.ralign > 1) Rb = (Rb + g.ralign - 1) / g.ralign * g.ralign;
     Cb = std::max<int64_t>(1, (rows + Rb - 1) / Rb);
 }
 
@@ -281,24 +314,31 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.sa = dtype_size(p.accum_dtype);
     g.V = p.time_block ? 4 : 16 / g.sh;  // the blocked kernel keeps four points per thread
     g.planes = (p.flags & FD_FLAG_KEEP_TAPE) ? 2 : 1;
+    g.tc = tc_far(p);
     int th = threads_override ? threads_override : p.tile_threads;
     if (!th) {
         th = 256;
         const int64_t need = (N + g.V - 1) / g.V;
         while (th > 64 && need <= th / 2) th /= 2;
     }
+    if (g.tc) th = (th >= 256) ? 256 : 128;  // point blocks of 128 lanes; four warps per lane quarter
     g.threads = th;
     g.P = th * g.V;
     g.T = (int)((N + g.P - 1) / g.P);
-    g.RS = p.stage_rows ? p.stage_rows : 8;
-    g.NS = p.stages ? p.stages : 3;
-    g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 2;
+    // tensor cores: stages of 32 rows where the block allows (one tensor-map box per stage, 64 KB
+    // at 256 threads, two of them in shared memory), else 16 rows in five stages
+    const int tc_rs = (g.tc && p.time_block % 32 == 0) ? 32 : 16;
+    g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
+    g.NS = p.stages ? p.stages : g.tc ? (g.RS >= 32 ? 2 : 5) : 3;
+    g.ctas = g.tc ? 1 : p.ctas_per_sm ? p.ctas_per_sm : 2;  // tensor memory: one CTA per SM
+    g.ralign = g.tc ? g.RS : 1;
     int sms = device_sms();
     if (sms <= 0) sms = 152;
     g.grid = sms * g.ctas;
     g.cap = p.max_steps;
     // short memory keeps a ring of L+1 rows, unless the adjoint's recompute will read old rows
-    if (p.mem_mode == FD_MEM_SHORT && !(p.flags & FD_FLAG_KEEP_TAPE))
+    // (the tensor-map copies of the tensor-core path take whole stages, so they keep every row)
+    if (p.mem_mode == FD_MEM_SHORT && !(p.flags & FD_FLAG_KEEP_TAPE) && !g.tc)
         g.cap = (int)std::min<int64_t>((int64_t)p.mem_L + 1, p.max_steps);
     g.cap = std::max(g.cap, 1);
     g.hring_sep = (p.hist_dtype != p.state_dtype);
@@ -338,10 +378,13 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
             rmax = std::max(rmax, hi - lo);
         }
         if (!p.chunk_terms) {
+            // tensor cores: longer chunks, as each chunk writes tb FP32 partial rows against its
+            // 16-bit history rows (partial traffic 4 tb / R of the history's)
             int64_t r = (rmax * g.T + 4LL * g.grid - 1) / (4LL * g.grid);
-            r = std::min<int64_t>(std::max<int64_t>(r, 2 * g.RS), 512);
+            r = std::min<int64_t>(std::max<int64_t>(r, 2 * g.RS), g.tc ? 2048 : 512);
             g.R = (int)((r + g.RS - 1) / g.RS * g.RS);
         }
+        if (g.ralign > 1) g.R = (g.R + g.ralign - 1) / g.ralign * g.ralign;
         // Block-long update units need every tile's unit resident at once: allow them when the
         // tiles are at most a quarter of the SMs, so at least three quarters keep streaming.
         g.ub = !(p.flags & FD_FLAG_STEP_UPDATES) && (int64_t)g.T * 4 <= sms;
@@ -362,7 +405,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = !g.hring_sep ? g.cap : g.tb ? 2 * g.tb : g.head + 1;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
+    g.smem = g.tc ? smem_bytes_tc(g, g.rwin) : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -395,7 +438,7 @@ int64_t blocked_stream_rows(const fd_problem &p, const Geo &g)
     for (int64_t b = 0; b < g.nblocks; ++b) {
         int64_t lo, hi;
         block_rows(p, g, b, lo, hi);
-        st += hi - lo;
+        st += hi - block_origin(g, lo);
         // block-long update units read the previous block's rows once; later rows stay on chip
         if (g.ub) st += std::min<int64_t>(tb, b * tb);
         // adaptive tail rows below the far rows: once per block-long unit, else once per step
@@ -424,6 +467,7 @@ struct Layout {
     char *gw;  // blocked, adaptive memory: settled weight g(m) of every lag
     int *glag, *br0;
     int4 *sched;
+    char *tmap;  // tensor-core path: tensor map of the history rows (128 bytes, 64-byte aligned)
     // adjoint
     char *ckpt, *seg, *rec[2], *ahist, *abuf[2];
     double *dots;
@@ -460,6 +504,7 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     const bool gtab = g.tb && p.mem_mode == FD_MEM_ADAPTIVE;
     L.gw = gtab ? c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa) : nullptr;
     L.br0 = gtab ? (int *)c.take(sizeof(int) * (size_t)(g.nblocks + 1)) : nullptr;
+    L.tmap = g.tc ? c.take(128) : nullptr;
     L.ckpt = L.seg = L.rec[0] = L.rec[1] = L.ahist = L.abuf[0] = L.abuf[1] = nullptr;
     L.dots = nullptr;
     L.ckpt_rows = L.seg_rows = 0;
@@ -570,6 +615,66 @@ int upload_tables(const fd_problem &p, const Sched &s, const Tables &t, const La
     return FD_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor-core path: the history rows as a BF16 tensor read with the 128-byte swizzle the MMA's A
+// operand expects, in boxes of 64 points (128 bytes) x RS rows.  Preferred: a 3-D view (64 points,
+// rows, groups of 64 points; the group stride of 128 bytes is below the row pitch) whose one box
+// per stage covers all P/64 groups of a tile.  If the driver refuses that view, a 2-D view
+// (points, rows) with one box per group.  Points past the padded row read as zeros.  Encoded on
+// the host, copied into the workspace; returns the rank used (0 on failure).
+int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return 0;
+    {
+        const cuuint64_t dims[3] = {64u, (cuuint64_t)g.cap, (cuuint64_t)(g.pitch / 128)};
+        const cuuint64_t strides[2] = {(cuuint64_t)g.pitch, 128u};
+        const cuuint32_t box[3] = {64u, (cuuint32_t)g.RS, (cuuint32_t)(g.P / 64)};
+        const cuuint32_t es[3] = {1u, 1u, 1u};
+        if (enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+            CUDA_SUCCESS)
+            return 3;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)(g.pitch / 2), (cuuint64_t)g.cap};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.pitch};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)g.RS};
+    const cuuint32_t es[2] = {1u, 1u};
+    if (enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+        CUDA_SUCCESS)
+        return 2;
+    return 0;
+}
+
+int upload_tmap(const Geo &g, const Layout &L, Inst &I, cudaStream_t st)
+{
+    if (!g.tc) return FD_OK;
+    alignas(64) CUtensorMap m;
+    I.tmap_rank = encode_tmap(g, L, &m);
+    if (!I.tmap_rank) return FD_ERR_CUDA;
+    CK(cudaMemcpyAsync(L.tmap, &m, sizeof(m), cudaMemcpyHostToDevice, st));
+    return FD_OK;
+}
+
 Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
 {
     Inst I;
@@ -592,6 +697,13 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.ksteps = p.max_steps;
     I.ub = g.ub;
     I.cmax = g.cmax;
+    I.ralign = g.ralign;
+    I.tmap = L.tmap;
+    if (g.tc) {  // tensor-memory columns: P/128 point blocks of tb FP32 accumulators, a power of two
+        int cols = 32;
+        while (cols < (g.P / 128) * g.tb) cols *= 2;
+        I.tc_cols = cols;
+    }
     I.npar = g.npar;
     I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
     I.tape_every = 1;
@@ -848,7 +960,7 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     h->ctrl_zero_base = (char *)h->L.arrive;
     h->ctrl_zero_bytes = sizeof(unsigned) * (h->g.npar + 1) * (size_t)h->g.T;
     const bool kahan = p->flags & FD_FLAG_KAHAN;
-    h->kfwd = p->time_block ? fdk::kernel_tb(p->time_block, false, p->hist_dtype)
+    h->kfwd = p->time_block ? fdk::kernel_tb(p->time_block, false, p->hist_dtype, h->g.tc)
                             : fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false);
     h->kadj = !(p->flags & FD_FLAG_KEEP_TAPE) ? nullptr
               : p->time_block ? fdk::kernel_tb(p->time_block, true, p->hist_dtype)
@@ -881,6 +993,7 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     const size_t used = (size_t)((char *)h->d_inst - h->ws);
     if (cudaMemsetAsync(h->ws, 0, used, st) != cudaSuccess) rc = FD_ERR_CUDA;
     if (!rc) rc = upload_tables(*p, h->s, h->t, h->L, st);
+    if (!rc) rc = upload_tmap(h->g, h->L, h->inst_fwd, st);
     if (!rc && cudaMemcpyAsync(h->d_goff, h->goff.data(), sizeof(long long) * h->goff.size(),
                                cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = FD_ERR_CUDA;
@@ -1061,6 +1174,7 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     g->terms_total = (rows + (int64_t)h->s.step.size()) * N;
     g->time_block = h->g.tb;
     g->block_updates = h->g.ub;
+    g->far_tensor_cores = h->g.tc;
     g->stream_rows_total = h->g.tb ? blocked_stream_rows(h->p, h->g) : rows;
     return FD_OK;
 }
@@ -1150,7 +1264,9 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     b.rmax = 0;
     for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].tb ? b.g[i].rwin : b.g[i].R);
     b.tb = probs[0].time_block;
-    b.smem = b.tb ? smem_bytes_tb(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16) : smem_bytes(b.g[0], b.rmax);
+    b.smem = b.g[0].tc ? smem_bytes_tc(b.g[0], b.rmax)
+             : b.tb    ? smem_bytes_tb(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16)
+                       : smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
     b.ctrl = carve_ctrl(c);
     int64_t counters = 0;
@@ -1231,7 +1347,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
     b->ws = (char *)workspace;
     b->st = (cudaStream_t)cuda_stream;
     const bool kahan = b->p[0].flags & FD_FLAG_KAHAN;
-    b->kfn = b->tb ? fdk::kernel_tb(b->tb, false, b->p[0].hist_dtype)
+    b->kfn = b->tb ? fdk::kernel_tb(b->tb, false, b->p[0].hist_dtype, b->g[0].tc)
                    : fdk::kernel_for(b->p[0].state_dtype, b->p[0].hist_dtype, b->p[0].accum_dtype, kahan, false);
     Geo g0 = b->g[0];
     g0.smem = b->smem;  // the launch's shared memory: the largest chunk over the instances
@@ -1247,6 +1363,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         build_tables(b->p[i], b->s[i], b->g[i], b->t[i]);
         rc = upload_tables(b->p[i], b->s[i], b->t[i], b->L[i], st);
         insts[i] = make_inst(b->p[i], b->g[i], b->L[i], false);
+        if (!rc) rc = upload_tmap(b->g[i], b->L[i], insts[i], st);
     }
     if (!rc && cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst) * insts.size(), cudaMemcpyHostToDevice,
                                st) != cudaSuccess)

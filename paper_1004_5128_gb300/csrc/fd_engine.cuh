@@ -63,6 +63,7 @@ struct Inst {
     int cmax;                // blocked kernel: most far chunks per block (0 = no limit)
     int ralign;              // blocked kernel: far chunks start on multiples of ralign rows (0, 1: any)
     int tc_cols;             // blocked tensor-core kernel: tensor-memory columns per CTA
+    int tmap_rank;           // blocked tensor-core kernel: 3 = one box per stage, 2 = one per 64 points
     const void *tmap;        // blocked tensor-core kernel: tensor map of the history rows
     int tape_k0, tape_every, tape_rows;
     int adj_K, uadj_r0;      // adjoint: u^r is row (adj_K-1-k) - uadj_r0 of uadj

@@ -407,14 +407,18 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                 };
                 constexpr uint32_t IDESC = tc::idesc_bf16_amn(128, TB);
                 if (warp == 0) {
-                    if (lane == 0) {  // history stages: P/64 boxes of 64 points x RS rows each
+                    if (lane == 0) {  // history stages: 64 points x RS rows per point group
                         for (int s = 0; s < nst; ++s) {
                             const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
                             if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
                             unsigned char *a = stages + (size_t)slot * RS * row_bytes;
                             mbar_expect_tx(&full[slot], (uint32_t)(RS * row_bytes));
-                            for (int j = 0; j < I.P / 64; ++j)
-                                tc::tma_load_2d(a + (size_t)j * RS * 128, I.tmap, tile * I.P + 64 * j, r0 + s * RS, &full[slot]);
+                            if (I.tmap_rank == 3)  // one box: 64 points x RS rows x P/64 point groups
+                                tc::tma_load_3d(a, I.tmap, 0, r0 + s * RS, tile * (I.P / 64), &full[slot]);
+                            else
+                                for (int j = 0; j < I.P / 64; ++j)
+                                    tc::tma_load_2d(a + (size_t)j * RS * 128, I.tmap, tile * I.P + 64 * j, r0 + s * RS,
+                                                    &full[slot]);
                             s_iss = s + 1;
                         }
                     }
@@ -1300,17 +1304,19 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
 #pragma unroll
         for (int v = 0; v < V; ++v) H[v] = H2[v] = 0.f;
         if (j0 < I.N) {
-            // far part: chunk partials in fixed order, four loads in flight
+            // far part: chunk partials in fixed order, G loads in flight (the unit is latency-bound:
+            // its loads are all it does before the halo wait)
+            constexpr int G = ADJ ? 4 : TC ? 16 : 8;
             int c = 0;
-            for (; c + 4 <= C; c += 4) {
-                float4 w[4], w2[ADJ ? 4 : 1];
+            for (; c + G <= C; c += G) {
+                float4 w[G], w2[ADJ ? G : 1];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < G; ++i) {
                     w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 0) + j0));
                     if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 1) + j0));
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < G; ++i) {
                     H[0] += w[i].x;
                     H[1] += w[i].y;
                     H[2] += w[i].z;
@@ -1361,14 +1367,14 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     }
                 }
             }
-            // head lags hk .. 2: rows this tile wrote at steps up to k-2, four loads in flight
+            // head lags hk .. 2: rows this tile wrote at steps up to k-2, G loads in flight
             int m = hk;
-            for (; m - 3 >= 2; m -= 4) {
-                float4 x[4];
+            for (; m - (G - 1) >= 2; m -= G) {
+                float4 x[G];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(m - i)));
+                for (int i = 0; i < G; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(m - i)));
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < G; ++i) {
                     const float cc = wgt(m - i);
                     H[0] = fmaf(cc, x[i].x, H[0]);
                     H[1] = fmaf(cc, x[i].y, H[1]);

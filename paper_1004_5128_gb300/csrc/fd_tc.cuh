@@ -103,5 +103,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, 
         : "memory");
 }
 
+// The same for a 3-D box at (x, y, z).
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(saddr(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
+        : "memory");
+}
+
 }  // namespace tc
 }  // namespace fdk

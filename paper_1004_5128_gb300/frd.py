@@ -21,7 +21,7 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
                  inject_stall: bool = False, tile_threads: int = 0, chunk_terms: int = 0,
                  stage_rows: int = 0, stages: int = 0, ctas_per_sm: int = 0,
                  head_lags: int = 0, plain_state: bool = False, time_block: int = 0,
-                 step_updates: bool = False) -> L.FdProblem:
+                 step_updates: bool = False, fma_far: bool = False) -> L.FdProblem:
     """fd_problem for a synth-style problem dict."""
     s = L.FdProblem()
     s.ndim, s.nx, s.ny = p["ndim"], p["nx"], p["ny"]
@@ -38,7 +38,8 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
                (L.FD_FLAG_ALLOW_UNSTABLE if allow_unstable else 0) |
                (L.FD_FLAG_INJECT_STALL if inject_stall else 0) |
                (L.FD_FLAG_PLAIN_STATE if plain_state else 0) |
-               (L.FD_FLAG_STEP_UPDATES if step_updates else 0))
+               (L.FD_FLAG_STEP_UPDATES if step_updates else 0) |
+               (L.FD_FLAG_FMA_FAR if fma_far else 0))
     s.max_steps = int(max_steps if max_steps is not None else p["K"])
     s.ckpt_every, s.timeout_ms = ckpt_every, timeout_ms
     s.tile_threads, s.chunk_terms, s.stage_rows = tile_threads, chunk_terms, stage_rows
@@ -55,7 +56,7 @@ def _require_cuda():
 
 
 GEOMETRY_KEYS = ("tile_threads", "chunk_terms", "stage_rows", "stages", "ctas_per_sm", "head_lags",
-                 "time_block", "step_updates")
+                 "time_block", "step_updates", "fma_far")
 
 
 class FRD:

@@ -68,6 +68,9 @@ def test_config3_mixed_precision_128(hist):
     assert s.status() == 0
     ref = oracle.run(p, threads=0)
     assert rel_inf(got, ref) < TOL[hist]
+    if hist == "bf16":  # the oracle with the same storage rule: head lags 1..32 in FP32
+        assert s.geometry()["head_lags"] == 32
+        assert rel_inf(got, oracle.run_bf16(p, 0, 32, threads=0)) < 5e-5  # rounding flips, as blocked
 
 
 def test_deterministic_and_launch_split_invariant():
