@@ -1,11 +1,13 @@
 """Benchmark: GL history terms/s of the GB300 engine (one JSON line on rank 0).
 
-Default workload (c2): 2-D 256x256 no-flux fractional reaction-diffusion (gamma=0.8,
-alpha=0.5, f=-0.1u, S=0.1, eight seeded Gaussians), 5000 steps in each of the three
-memory modes (full, short window 500, adaptive a=10), FP32.  One benchmark step = the
-three 5000-step runs from u0.  Other workloads:
+Default workload (c3, the largest configuration): 2-D 512x512 Dirichlet fractional
+reaction-diffusion (gamma=0.6, f=u(1-u)-0.05u, S=0.1, seeded U[0,0.1] noise), 20000 steps of
+full memory with BF16, FP16 and FP32 history.  One benchmark step = the three 20000-step runs
+from u0.  Also reported, measured outside the timed region: each run's error against the FP64
+oracle at 128x128 x 2000 steps and against the FP32-history run at full size, and the c5
+forward + adjoint rate against a plain FP32 forward.  Other workloads:
   c1  1-D N=256, 1000 steps, full memory, FP64
-  c3  2-D 512x512, 20000 steps, BF16 / FP16 / FP32 history
+  c2  2-D 256x256 no-flux, 5000 steps, full / short L=500 / adaptive a=10 memory, FP32
   c4  64 uneven instances in one persistent launch (full and adaptive memory)
   c5  128x128, 4000 steps: forward + checkpointed adjoint, against a plain FP32 forward
 
@@ -39,8 +41,10 @@ CONFIG_NAMES = {
     "c2": "2-D 256x256 no-flux, gamma=0.8, alpha=0.5, f=-0.1u, S=0.1, 8 Gaussians, 5000 steps x "
           "{full, short L=500, adaptive a=10}, FP32",
     "c1": "1-D N=256 Dirichlet, gamma=0.5, S=0.2, 1000 steps, full memory, FP64",
-    "c3": "2-D 512x512 Dirichlet, gamma=0.6, f=u(1-u)-0.05u, 20000 steps, full memory, "
-          "{BF16, FP16, FP32} history, FP32 (Kahan) accumulation",
+    "c3": "2-D 512x512 Dirichlet, gamma=0.6, alpha=1, f=u(1-u)-0.05u, S=0.1, U[0,0.1] noise, 20000 "
+          "steps, full memory; history BF16 and FP16 (row-tile scaled), far rows on tcgen05 tensor "
+          "cores in blocks of 32 steps, and FP32, far rows on CUDA cores in blocks of 16; FP32 state and "
+          "accumulation, FP64-generated weights",
     "c4": "64 instances (32 1-D N 64-4096, 32 2-D side 64-384), gamma~U[0.3,0.95], steps "
           "U{1000..8000}, one persistent launch (CUDA graph), {full, adaptive a=10}, FP32",
     "c5": "2-D 128x128 Dirichlet, gamma=0.7, alpha=0.8, f=-0.1u, 4000 steps, FP32: forward with "
@@ -127,12 +131,16 @@ def problems(name: str, K: int = 0, modes: str = ""):
 def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
     """History rows the launch's kernel must read plus, per step, the u read/write and the delta
     write.  Per-step kernel: every lag >= 1 of every step.  Temporally blocked kernel: the far rows
-    once per block plus each step's newest rows."""
+    once per block in the history's precision, plus each step's newest rows; with 16-bit history
+    those come from the FP32 ring, which every step also writes."""
     N = p["nx"] * p["ny"] * p.get("nz", 1)
     sh = HBYTES[kw.get("hist", kw.get("state", "f32"))]
     ss = 8 if kw.get("state") == "f64" else 4
     rows = geo.get("stream_rows_total", geo["hist_rows_total"])
-    return rows * N * sh + p["K"] * N * (2 * ss + sh)
+    if not geo.get("time_block") or sh == ss:
+        return rows * N * sh + p["K"] * N * (2 * ss + sh)
+    head = geo["head_rows_total"]
+    return (rows - head) * N * sh + head * N * 4 + p["K"] * N * (2 * ss + sh + 4)
 
 
 def code_hash(path: str) -> str:
@@ -304,6 +312,63 @@ class AdjointRun:
         L.fd_adjoint(self.s.h, self.hdj.data_ptr(), self.hout.data_ptr())
 
 
+def _rel_inf(a, ref) -> float:
+    a, ref = np.asarray(a, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(a - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def side_measurements(runs, dev) -> dict:
+    """Measured outside the timed region: each config-3 run's error against the FP64 oracle at
+    the size it finishes in seconds (128x128, 2000 steps, same kernel options) and, at full size,
+    against the FP32-history run; and the config-5 forward + checkpointed adjoint rate against a
+    plain FP32 forward, with the gradients' error against the oracle's adjoint at 600 steps."""
+    import torch
+
+    import oracle
+    from paper_1004_5128_gb300 import FRD, synth
+    out = {"tolerance": {"bf16": 2e-3, "f16": 2e-3, "f32": 1e-5}}
+    finals = {r.name: r.s.state().cpu().double().numpy() for r in runs if hasattr(r, "s")}
+    q = synth.config3(n=128, K=2000)
+    ref = oracle.run(q, threads=0)
+    errs = {}
+    for r in runs:
+        s = FRD(q, device=dev, **r.kw)
+        s.set_state(q["u0"])
+        e = {"vs_oracle_128x128_K2000": _rel_inf(s.run(q["K"]).cpu().double().numpy(), ref)}
+        s.close()
+        if r.name != "f32" and "f32" in finals:
+            e["vs_fp32_history_512x512_K20000"] = _rel_inf(finals[r.name], finals["f32"])
+        errs[r.name] = e
+    out["errors"] = errs
+
+    a = AdjointRun("adjoint", synth.config5(), {}, {}, dev)
+    a.launch()
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(a.s.stream)
+        a.launch()
+        e1.record(a.s.stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    plain = a.time_plain()
+    K = a.p["K"]
+    q5 = synth.config5(K=600)
+    tgt = oracle.run(synth.config5(K=600, target=True), threads=0)
+    s = FRD(q5, device=dev, keep_tape=True, ckpt_every=200)
+    s.set_state(q5["u0"])
+    uK = s.run(q5["K"])
+    g = s.adjoint(uK - torch.as_tensor(tgt, device=uK.device, dtype=uK.dtype))
+    s.close()
+    go = oracle.adjoint(q5, tgt, threads=0)
+    gerr = max(abs(g["dgamma"] - go["dgamma"]) / abs(go["dgamma"]), abs(g["dalpha"] - go["dalpha"]) / abs(go["dalpha"]),
+               _rel_inf(g["du0"].cpu().numpy(), go["du0"]), _rel_inf(g["dreact"], go["dreact"]))
+    out["adjoint"] = {"workload": CONFIG_NAMES["c5"], "fwd_adjoint_steps_per_s": K / (best / 1e3),
+                      "plain_fp32_fwd_steps_per_s": K / (plain / 1e3), "fwd_adjoint_over_plain_fwd_time": best / plain,
+                      "grad_error_vs_oracle_adjoint_K600": gerr, "tolerance": 1e-5}
+    return out
+
+
 def make_runs(args, dev):
     geo = {}
     for item in filter(None, args.geom.split(",")):
@@ -374,7 +439,9 @@ def run_ours(args):
                              alg_bytes=r.alg, gbs=r.alg / (per / 1e3) / 1e9,
                              geometry={k: g.get(k) for k in ("tile_threads", "tiles", "chunk_terms",
                                                              "stage_rows", "stages", "ctas_per_sm",
-                                                             "grid", "head_lags", "time_block", "block_updates")})
+                                                             "grid", "head_lags", "time_block", "block_updates",
+                                                             "far_tensor_cores")})
+        modes[r.name]["frac_of_measured_hbm"] = round(modes[r.name]["gbs"] / peaks()[0], 4)
     extra = {}
     if args.workload == "c5":
         r = runs[0]
@@ -388,11 +455,16 @@ def run_ours(args):
         # the roofline line is for the plain forward launch (one engine launch, timed alone)
         modes[r.name]["gbs"] = r.alg / (plain_ms / 1e3) / 1e9
         modes[r.name]["roofline_launch"] = "plain FP32 forward"
+    if args.workload == "c3" and not args.no_extra and rank == 0:
+        extra = side_measurements(runs, dev)
     dom = max(modes, key=lambda k: modes[k]["ms"])
     peak, which = peaks()
     ach = modes[dom]["gbs"]
-    kname = f"engine_tb_kernel<{modes[dom]['geometry']['time_block']}>" \
-        if modes[dom]["geometry"].get("time_block") else "engine_kernel"
+    gd = modes[dom]["geometry"]
+    hist = next(r.kw.get("hist", r.kw.get("state", "f32")) for r in runs if r.name == dom)
+    kname = (f"engine_tb_kernel<{gd['time_block']}, {hist} history"
+             f"{', tensor-core far units' if gd.get('far_tensor_cores') else ''}>") \
+        if gd.get("time_block") else "engine_kernel"
     traffic = None if (args.geom or args.K) else measured_traffic(f"{args.workload}:{dom}",
                                                                   modes[dom]["geometry"])
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
@@ -408,7 +480,8 @@ def run_ours(args):
             h2d += a
             d2h += b
         torch.cuda.synchronize()
-        k = max(1, args.steps)
+        # the config-3 step is seconds long: its end-to-end leg times at most two steps
+        k = max(1, min(args.steps, 2) if args.workload == "c3" else args.steps)
         w0 = time.perf_counter()
         for _ in range(k):
             for r in runs:
@@ -425,7 +498,7 @@ def run_ours(args):
         kw0 = runs[0].kw
         dtype = "f64" if kw0.get("state") == "f64" else "f32"
         if args.workload == "c3":
-            dtype = "f32 state, bf16/f16/f32 history"
+            dtype = "f32 state and accumulation; bf16, f16 and f32 history"
         line = {
             "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -433,8 +506,8 @@ def run_ours(args):
             "data": "synthetic (seeded SplitMix64 inputs)",
             "config": {"workload": CONFIG_NAMES[args.workload] +
                        (f" [K={args.K}]" if args.K else "") + (f" [{args.modes}]" if args.modes else ""),
-                       "l2": "a 258 MB L2 flush before every run; histories of the full/adaptive "
-                             "runs exceed L2",
+                       "l2": "a 258 MB L2 flush before every run; every run's history exceeds L2 "
+                             "(config 3: 10.5 GB BF16/FP16, 21 GB FP32)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "modes": modes, "roofline": roof, "e2e": e2e,
             "gpu_launches": sum(r.launches for r in runs) * args.steps,
@@ -525,7 +598,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "c2", "c4", "c5"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the error and adjoint side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

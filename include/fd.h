@@ -205,6 +205,8 @@ typedef struct fd_geometry {
     int time_block;
     int block_updates;       /* time_block: 1 when one unit per tile carries a whole block's updates */
     int far_tensor_cores;    /* time_block: 1 when the far rows are multiplied on the tensor cores */
+    int64_t head_rows_total; /* time_block: of stream_rows_total, the rows of the newest 2 time_block
+                                steps that the update units read (FP32, also for 16-bit history) */
 } fd_geometry;
 int fd_get_geometry(fd_handle *h, fd_geometry *g);
 

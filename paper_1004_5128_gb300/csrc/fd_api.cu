@@ -147,12 +147,12 @@ inline int64_t n_terms(const int4 &e) { return (int64_t)e.x + e.y + (e.w >= e.z 
 
 // ------------------------------------------------------------------ validation
 
-// Blocked runs with BF16 history and blocks of 16 or 32 multiply their far rows on the tensor
-// cores unless FD_FLAG_FMA_FAR asks for the CUDA-core loop.
+// Blocked runs with BF16 or FP16 history and blocks of 16 or 32 multiply their far rows on the
+// tensor cores unless FD_FLAG_FMA_FAR asks for the CUDA-core loop.
 inline bool tc_far(const fd_problem &p)
 {
-    return (p.time_block == 16 || p.time_block == 32) && p.hist_dtype == FD_BF16 && !(p.flags & FD_FLAG_FMA_FAR) &&
-           !(p.flags & FD_FLAG_KEEP_TAPE);
+    return (p.time_block == 16 || p.time_block == 32) && (p.hist_dtype == FD_BF16 || p.hist_dtype == FD_F16) &&
+           !(p.flags & FD_FLAG_FMA_FAR) && !(p.flags & FD_FLAG_KEEP_TAPE);
 }
 
 int validate(const fd_problem *p)
@@ -257,11 +257,11 @@ inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
 // Tensor-core blocked kernel: stage ring (RS rows x P points of BF16, at least the block-long
 // units' sums), 1 KB-aligned; NS coefficient blocks (hi and lo halves of tb/8 1 KB atoms); the
 // coefficient window; 3 NS + 1 barriers; 1 KB of slack to align the base.
-inline size_t smem_bytes_tc(const Geo &g, int rwin)
+inline size_t smem_bytes_tc(const Geo &g, int rwin, bool f16)
 {
     const size_t ring = std::max((size_t)g.NS * g.RS * g.threads * 8, (size_t)(g.tb * g.planes + 2) * g.threads * 16);
-    return align_up(ring, 1024) + (size_t)g.NS * 2 * (g.tb / 8) * 1024 + (size_t)(rwin + g.tb) * 4 + 16 +
-           8 * (size_t)(3 * g.NS + 1) + 1024;
+    return align_up(ring, 1024) + (size_t)g.NS * 2 * (g.tb / 8) * 1024 + (size_t)(rwin + g.tb + (f16 ? rwin : 0)) * 4 +
+           16 + 8 * (size_t)(3 * g.NS + 1) + 1024;
 }
 
 int device_sms()
@@ -405,7 +405,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = !g.hring_sep ? g.cap : g.tb ? 2 * g.tb : g.head + 1;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    g.smem = g.tc ? smem_bytes_tc(g, g.rwin) : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
+    g.smem = g.tc ? smem_bytes_tc(g, g.rwin, p.hist_dtype == FD_F16) : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -431,27 +431,28 @@ inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
 // History rows the blocked kernel reads over max_steps steps: the far rows once per block, then
 // every step's head rows (lags 1 .. min(k - kb + tb, n(k))), or, with block-long update units,
 // the previous block's rows once per block.
-int64_t blocked_stream_rows(const fd_problem &p, const Geo &g)
+int64_t blocked_stream_rows(const fd_problem &p, const Geo &g, int64_t *head_rows = nullptr)
 {
     const int tb = g.tb;
-    int64_t st = 0;
+    int64_t st = 0, hd = 0;
     for (int64_t b = 0; b < g.nblocks; ++b) {
         int64_t lo, hi;
         block_rows(p, g, b, lo, hi);
         st += hi - block_origin(g, lo);
         // block-long update units read the previous block's rows once; later rows stay on chip
-        if (g.ub) st += std::min<int64_t>(tb, b * tb);
+        if (g.ub) hd += std::min<int64_t>(tb, b * tb);
         // adaptive tail rows below the far rows: once per block-long unit, else once per step
         if (p.mem_mode == FD_MEM_ADAPTIVE)
             st += (int64_t)std::min<int64_t>(lo, (int64_t)g.br0[b]) *
                   (g.ub ? 1 : std::min<int64_t>(tb, p.max_steps - b * tb));
     }
-    if (g.ub) return st;
-    for (int64_t k = 0; k < p.max_steps; ++k) {
-        const int64_t nb = (p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(p.mem_L, k) : k;
-        st += std::min<int64_t>(k - (k / tb) * tb + tb, nb);
-    }
-    return st;
+    if (!g.ub)
+        for (int64_t k = 0; k < p.max_steps; ++k) {
+            const int64_t nb = (p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(p.mem_L, k) : k;
+            hd += std::min<int64_t>(k - (k / tb) * tb + tb, nb);
+        }
+    if (head_rows) *head_rows = hd;
+    return st + hd;
 }
 
 // Device-side layout of one instance inside the workspace.
@@ -640,16 +641,17 @@ EncodeTiledFn encode_tiled()
 // per stage covers all P/64 groups of a tile.  If the driver refuses that view, a 2-D view
 // (points, rows) with one box per group.  Points past the padded row read as zeros.  Encoded on
 // the host, copied into the workspace; returns the rank used (0 on failure).
-int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m)
+int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, bool f16)
 {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return 0;
+    const CUtensorMapDataType dt = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     {
         const cuuint64_t dims[3] = {64u, (cuuint64_t)g.cap, (cuuint64_t)(g.pitch / 128)};
         const cuuint64_t strides[2] = {(cuuint64_t)g.pitch, 128u};
         const cuuint32_t box[3] = {64u, (cuuint32_t)g.RS, (cuuint32_t)(g.P / 64)};
         const cuuint32_t es[3] = {1u, 1u, 1u};
-        if (enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        if (enc(m, dt, 3, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
             CUDA_SUCCESS)
             return 3;
@@ -658,18 +660,18 @@ int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m)
     const cuuint64_t strides[1] = {(cuuint64_t)g.pitch};
     const cuuint32_t box[2] = {64u, (cuuint32_t)g.RS};
     const cuuint32_t es[2] = {1u, 1u};
-    if (enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (enc(m, dt, 2, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
         CUDA_SUCCESS)
         return 2;
     return 0;
 }
 
-int upload_tmap(const Geo &g, const Layout &L, Inst &I, cudaStream_t st)
+int upload_tmap(const fd_problem &p, const Geo &g, const Layout &L, Inst &I, cudaStream_t st)
 {
     if (!g.tc) return FD_OK;
     alignas(64) CUtensorMap m;
-    I.tmap_rank = encode_tmap(g, L, &m);
+    I.tmap_rank = encode_tmap(g, L, &m, p.hist_dtype == FD_F16);
     if (!I.tmap_rank) return FD_ERR_CUDA;
     CK(cudaMemcpyAsync(L.tmap, &m, sizeof(m), cudaMemcpyHostToDevice, st));
     return FD_OK;
@@ -993,7 +995,7 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     const size_t used = (size_t)((char *)h->d_inst - h->ws);
     if (cudaMemsetAsync(h->ws, 0, used, st) != cudaSuccess) rc = FD_ERR_CUDA;
     if (!rc) rc = upload_tables(*p, h->s, h->t, h->L, st);
-    if (!rc) rc = upload_tmap(h->g, h->L, h->inst_fwd, st);
+    if (!rc) rc = upload_tmap(*p, h->g, h->L, h->inst_fwd, st);
     if (!rc && cudaMemcpyAsync(h->d_goff, h->goff.data(), sizeof(long long) * h->goff.size(),
                                cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = FD_ERR_CUDA;
@@ -1175,7 +1177,8 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     g->time_block = h->g.tb;
     g->block_updates = h->g.ub;
     g->far_tensor_cores = h->g.tc;
-    g->stream_rows_total = h->g.tb ? blocked_stream_rows(h->p, h->g) : rows;
+    g->head_rows_total = 0;
+    g->stream_rows_total = h->g.tb ? blocked_stream_rows(h->p, h->g, &g->head_rows_total) : rows;
     return FD_OK;
 }
 
@@ -1264,7 +1267,7 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     b.rmax = 0;
     for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].tb ? b.g[i].rwin : b.g[i].R);
     b.tb = probs[0].time_block;
-    b.smem = b.g[0].tc ? smem_bytes_tc(b.g[0], b.rmax)
+    b.smem = b.g[0].tc ? smem_bytes_tc(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16)
              : b.tb    ? smem_bytes_tb(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16)
                        : smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
@@ -1363,7 +1366,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         build_tables(b->p[i], b->s[i], b->g[i], b->t[i]);
         rc = upload_tables(b->p[i], b->s[i], b->t[i], b->L[i], st);
         insts[i] = make_inst(b->p[i], b->g[i], b->L[i], false);
-        if (!rc) rc = upload_tmap(b->g[i], b->L[i], insts[i], st);
+        if (!rc) rc = upload_tmap(b->p[i], b->g[i], b->L[i], insts[i], st);
     }
     if (!rc && cudaMemcpyAsync(b->d_inst, insts.data(), sizeof(Inst) * insts.size(), cudaMemcpyHostToDevice,
                                st) != cudaSuccess)
@@ -1492,9 +1495,11 @@ int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g)
     g->units_total = units;
     g->hist_rows_total = rows;
     g->terms_total = (rows + (int64_t)b->s[i].step.size()) * N;
-    g->stream_rows_total = q.tb ? blocked_stream_rows(b->p[i], q) : rows;
+    g->head_rows_total = 0;
+    g->stream_rows_total = q.tb ? blocked_stream_rows(b->p[i], q, &g->head_rows_total) : rows;
     g->time_block = q.tb;
     g->block_updates = q.ub;
+    g->far_tensor_cores = q.tc;
     return FD_OK;
 }
 

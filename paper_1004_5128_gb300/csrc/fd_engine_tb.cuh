@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
     constexpr int V = 4;  // four points per thread: a float4 of state, H4<TH> of history
     constexpr bool LOWP = sizeof(TH) == 2;
     constexpr bool F16 = std::is_same<TH, __half>::value;
-    static_assert(!TC || (std::is_same<TH, __nv_bfloat16>::value && !ADJ && TB % 16 == 0),
-                  "tensor-core far units: BF16 history, forward, blocks of a multiple of 16 steps");
+    static_assert(!TC || (LOWP && !ADJ && TB % 16 == 0),
+                  "tensor-core far units: BF16 or FP16 history, forward, blocks of a multiple of 16 steps");
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     const int RS = L.stage_rows, NS = L.stages;
@@ -190,11 +190,13 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
     constexpr int BHALF = (TB / 8) * 1024;  // one half (hi or lo) of a coefficient block
     unsigned char *bring = smem + ((ring_bytes + 1023) & ~(size_t)1023);
     float *win = reinterpret_cast<float *>(bring + (size_t)NS * 2 * BHALF);
+    float *wsc = win + L.rmax + TB;  // FP16: the unit's row scales
     if (TC)
-        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(win + L.rmax + TB) + 15) & ~uintptr_t(15));
+        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(wsc + (F16 ? L.rmax : 0)) + 15) & ~uintptr_t(15));
     uint64_t *full = bars, *empty = bars + NS, *bfull = bars + 2 * NS, *done_bar = bars + 3 * NS;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort, s_iss, s_mma;
+    __shared__ float s_bnorm;  // FP16 tensor-core unit: power of two that scales its coefficients
     // adaptive memory: bit j of gmask[lo] says w[lo + j] != 0 (the window of a four-row group);
     // the sparse loop reads the unshifted copy only, so the masks take the first shifted copy
     uint32_t *gmask = reinterpret_cast<uint32_t *>(psw + WS);
@@ -374,9 +376,24 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     // uses win[(r1 - 1 - r) + t]; short memory cuts lags beyond its window
                     const float *wsrc = reinterpret_cast<const float *>(I.gw ? I.gw : I.psi);
                     const int lag0 = kb - (r1 - 1);
+                    float amax = 0.f, smax = 0.f;
                     for (int j = tid; j < nrow + TB - 1; j += nthr) {
                         const int lag = lag0 + j;
                         win[j] = (I.mem_mode == 1 && lag > I.mem_L) ? 0.f : wsrc[lag];
+                        amax = fmaxf(amax, fabsf(win[j]));
+                    }
+                    if (F16) {
+                        // FP16 rows hold delta * 2^e per (row, tile): the row's scale 2^-e joins its
+                        // weights, and one power of two per unit keeps the largest coefficient in
+                        // [2^13, 2^14), so both FP16 halves stay normal; the epilogue divides it out
+                        for (int a = tid; a < nrow; a += nthr) {
+                            wsc[a] = __ldcg(I.hscale + (size_t)((r0 + a) % I.cap) * I.T + tile);
+                            smax = fmaxf(smax, wsc[a]);
+                        }
+                        float m = amax * smax;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                        if ((tid & 31) == 0) s_wmax[tid >> 5] = m;
                     }
                     if (tid == 0) {
                         s_abort = 0;
@@ -385,6 +402,17 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     }
                 }
                 __syncthreads();
+                if (F16) {
+                    if (tid == 0) {
+                        float m = 0.f;
+                        for (int w = 0; w < nthr / 32; ++w) m = fmaxf(m, s_wmax[w]);
+                        int ex = 0;
+                        if (m > 0.f && isfinite(m)) frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
+                        s_bnorm = ldexpf(1.f, max(-120, min(120, 14 - ex)));
+                    }
+                    __syncthreads();
+                }
+                const float bnorm = F16 ? s_bnorm : 1.f, binv = 1.f / bnorm;  // powers of two
                 auto give_up = [&](int site_s, uint64_t *bar) {
                     if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE)
                         note_failure(L, 11, ((long long)b << 32) | tile, ((long long)site_s << 32) | nst,
@@ -405,7 +433,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     }
                     return true;
                 };
-                constexpr uint32_t IDESC = tc::idesc_bf16_amn(128, TB);
+                constexpr uint32_t IDESC = tc::idesc_f16_amn(128, TB, !F16);
                 if (warp == 0) {
                     if (lane == 0) {  // history stages: 64 points x RS rows per point group
                         for (int s = 0; s < nst; ++s) {
@@ -458,13 +486,20 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         for (int e = me; e < TB * RS; e += nb) {
                             const int t = e / RS, i = e - t * RS;
                             const int r = r0 + s * RS + i;
-                            const float c = (r < rlo_t) ? 0.f : win[(r1 - 1 - r) + t];
-                            const __nv_bfloat16 hi = __float2bfloat16_rn(c);
-                            const __nv_bfloat16 lo = __float2bfloat16_rn(c - __bfloat162float(hi));
+                            float c = (r < rlo_t) ? 0.f : win[(r1 - 1 - r) + t];
+                            if (F16) c *= wsc[r - r0] * bnorm;
+                            TH hi, lo;
+                            if constexpr (F16) {
+                                hi = __float2half_rn(c);
+                                lo = __float2half_rn(c - __half2float(hi));
+                            } else {
+                                hi = __float2bfloat16_rn(c);
+                                lo = __float2bfloat16_rn(c - __bfloat162float(hi));
+                            }
                             const int row = t & 7;
                             const int off = (t >> 3) * 1024 + row * 128 + (((i >> 3) ^ row) << 4) + (i & 7) * 2;
-                            *reinterpret_cast<__nv_bfloat16 *>(bh + off) = hi;
-                            *reinterpret_cast<__nv_bfloat16 *>(bh + BHALF + off) = lo;
+                            *reinterpret_cast<TH *>(bh + off) = hi;
+                            *reinterpret_cast<TH *>(bh + BHALF + off) = lo;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(&bfull[slot])) : "memory");
@@ -526,6 +561,10 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     } else {
 #pragma unroll
                         for (int t = 0; t < TB; ++t) v[t] = 0.f;
+                    }
+                    if (F16) {  // exact: a power of two
+#pragma unroll
+                        for (int t = 0; t < TB; ++t) v[t] *= binv;
                     }
                     if (j < I.N) {
 #pragma unroll

@@ -1,14 +1,24 @@
-// Temporally blocked kernels whose far units run on the tensor cores (tcgen05): BF16 history,
-// FP32 state and accumulation, forward only, blocks of 16 and 32 steps.
+// Temporally blocked kernels whose far units run on the tensor cores (tcgen05): BF16 or FP16
+// (row-tile scaled) history, FP32 state and accumulation, forward only, blocks of 16 and 32 steps.
 #include "fd_kernels.h"
 
 namespace fdk {
-const void *kernel_tb_tc(int tb)
+const void *kernel_tb_tc(int tb, int hist)
 {
-    switch (tb) {
-    case 16: return (const void *)engine_tb_kernel<16, false, __nv_bfloat16, true>;
-    case 32: return (const void *)engine_tb_kernel<32, false, __nv_bfloat16, true>;
-    default: return nullptr;
+    if (hist == 2) {
+        switch (tb) {
+        case 16: return (const void *)engine_tb_kernel<16, false, __nv_bfloat16, true>;
+        case 32: return (const void *)engine_tb_kernel<32, false, __nv_bfloat16, true>;
+        default: return nullptr;
+        }
     }
+    if (hist == 3) {
+        switch (tb) {
+        case 16: return (const void *)engine_tb_kernel<16, false, __half, true>;
+        case 32: return (const void *)engine_tb_kernel<32, false, __half, true>;
+        default: return nullptr;
+        }
+    }
+    return nullptr;
 }
 }  // namespace fdk

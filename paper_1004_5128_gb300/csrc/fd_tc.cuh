@@ -2,7 +2,7 @@
 // written as inline PTX for sm_103a.
 //
 // The temporally blocked far product is a contraction: T steps x P points x R rows per unit
-// (the Toeplitz form of the memory sum, eq. frac_norxn).  With BF16 history it runs as
+// (the Toeplitz form of the memory sum, eq. frac_norxn).  With BF16 or FP16 history it runs as
 //     D[p][t] += sum_r H[r][p] * C[r][t]        (M = 128 points, N = T steps, K = 16 rows)
 // with the history tile H^T as the MN-major A operand, loaded by the tensor-map unit with a
 // 128-byte swizzle, the coefficient block C as the K-major B operand written by the CTA with the
@@ -33,12 +33,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor of kind::f16 with FP32 accumulation: BF16 A and B, A MN-major, B K-major,
-// N at bits 17-22 (N / 8), M at bits 24-28 (M / 16).
-__host__ __device__ constexpr uint32_t idesc_bf16_amn(int M, int N)
+// Instruction descriptor of kind::f16 with FP32 accumulation: A and B both BF16 (bf16 = true) or
+// both FP16, A MN-major, B K-major, N at bits 17-22 (N / 8), M at bits 24-28 (M / 16).
+__host__ __device__ constexpr uint32_t idesc_f16_amn(int M, int N, bool bf16)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | (1u << 15) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // D (tensor memory) = A B + (acc ? D : 0), issued by one thread.

@@ -105,19 +105,31 @@ TC_MODES = [("full", synth.MEM_FULL, 0, 0), ("short40", synth.MEM_SHORT, 40, 0),
 @pytest.mark.parametrize("step_updates", [False, True])
 @pytest.mark.parametrize("tb,rs,threads", [(16, 16, 256), (32, 16, 256), (32, 32, 256), (16, 16, 128)])
 @pytest.mark.parametrize("name,mode,L,a", TC_MODES, ids=[m[0] for m in TC_MODES])
-def test_tensor_core_far_units_match_oracle_and_cuda_cores(name, mode, L, a, tb, rs, threads, step_updates):
+@pytest.mark.parametrize("hist", ["bf16", "f16"])
+def test_tensor_core_far_units_match_oracle_and_cuda_cores(hist, name, mode, L, a, tb, rs, threads, step_updates):
+    """FP16 rows carry their (row, tile) scales in the coefficients, normalised per unit."""
     p = ragged(synth.BC_NOFLUX, mode, L, a, K=300)
-    geo = dict(hist="bf16", time_block=tb, chunk_terms=2 * rs, stage_rows=rs, tile_threads=threads,
+    geo = dict(hist=hist, time_block=tb, chunk_terms=2 * rs, stage_rows=rs, tile_threads=threads,
                step_updates=step_updates)
     got, s = run(p, **geo)
     g = s.geometry()
     assert g["far_tensor_cores"] == 1 and g["time_block"] == tb and g["tile_threads"] == threads
     assert rel_inf(got, oracle.run(p)) < TOL
-    assert rel_inf(got, oracle.run_bf16(p, tb, tb)) < ROUNDED_TOL
+    if hist == "bf16":
+        assert rel_inf(got, oracle.run_bf16(p, tb, tb)) < ROUNDED_TOL
     if tb == 16:
         fma, s2 = run(p, fma_far=True, **dict(geo, stage_rows=8))
         assert s2.geometry()["far_tensor_cores"] == 0
         assert rel_inf(got, fma) < ROUNDED_TOL
+
+
+def test_tensor_core_fp16_tiny_field():
+    """A field of size 1e-6 on the FP16 tensor-core path: row scales near 2^20 and weights below
+    one meet in the coefficients, which the per-unit power of two brings back into FP16 range."""
+    p = ragged(synth.BC_DIRICHLET0, synth.MEM_FULL, K=200, scale=1e-6)
+    got, s = run(p, hist="f16", time_block=32, chunk_terms=64)
+    assert s.geometry()["far_tensor_cores"] == 1
+    assert rel_inf(got, oracle.run(p)) < TOL
 
 
 def test_tensor_core_config3_128_vs_oracle_and_split_invariance():
