@@ -145,6 +145,20 @@ int build_schedule(const fd_problem &p, int64_t K, Sched &s)
 
 inline int64_t n_terms(const int4 &e) { return (int64_t)e.x + e.y + (e.w >= e.z ? e.w - e.z + 1 : 0); }
 
+// The adjoint of adaptive memory runs the full-memory adjoint with the settled weights (plus the
+// tail terms' corrections): its work units are those of full memory.
+inline bool adaptive_adjoint(const fd_problem &p)
+{
+    return p.mem_mode == FD_MEM_ADAPTIVE && (p.flags & FD_FLAG_KEEP_TAPE);
+}
+inline fd_problem full_memory(const fd_problem &p)
+{
+    fd_problem q = p;
+    q.mem_mode = FD_MEM_FULL;
+    return q;
+}
+inline int4 full_step(int64_t k) { return make_int4((int)k, 0, 1, 0); }
+
 // ------------------------------------------------------------------ validation
 
 // Blocked runs with BF16 or FP16 history and blocks of 16 or 32 multiply their far rows on the
@@ -185,9 +199,7 @@ int validate(const fd_problem *p)
     const bool adj = p->flags & FD_FLAG_KEEP_TAPE;
     if (!fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false))
         return FD_ERR_UNSUPPORTED;
-    if (adj && ((p->mem_mode != FD_MEM_FULL && p->mem_mode != FD_MEM_SHORT) ||
-                !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)))
-        return FD_ERR_UNSUPPORTED;
+    if (adj && !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)) return FD_ERR_UNSUPPORTED;
     if (p->time_block) {
         const bool tc = tc_far(*p);
         if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16 && !(tc && p->time_block == 32))
@@ -346,6 +358,8 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     if (!g.hring_sep && g.cap < g.head + 1) g.head = std::max(1, g.cap - 1);
     int64_t nmax = 0;
     for (const int4 &e : s.step) nmax = std::max(nmax, n_terms(e) - std::min<int64_t>(g.head, e.x));
+    if (adaptive_adjoint(p) && p.max_steps > 1)  // the adjoint's steps have full memory's terms
+        nmax = std::max(nmax, (int64_t)(p.max_steps - 1) - std::min<int64_t>(g.head, p.max_steps - 1));
     if (p.chunk_terms) {
         g.R = p.chunk_terms;
     } else {
@@ -371,12 +385,16 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
                 for (int64_t k = b * g.tb; k < std::min<int64_t>((b + 1) * g.tb, p.max_steps); ++k)
                     g.br0[b] = (int)std::max<int64_t>(g.br0[b], k - settled_end(s.step[k]));
         }
+        // (with the adjoint of adaptive memory, also the full-memory blocks the adjoint runs)
+        const fd_problem pf = full_memory(p);
+        const int nprob = adaptive_adjoint(p) ? 2 : 1;
         int64_t rmax = 0;
-        for (int64_t b = 0; b < g.nblocks; ++b) {
-            int64_t lo, hi;
-            block_rows(p, g, b, lo, hi);
-            rmax = std::max(rmax, hi - lo);
-        }
+        for (int ip = 0; ip < nprob; ++ip)
+            for (int64_t b = 0; b < g.nblocks; ++b) {
+                int64_t lo, hi;
+                block_rows(ip ? pf : p, g, b, lo, hi);
+                rmax = std::max(rmax, hi - lo);
+            }
         if (!p.chunk_terms) {
             // tensor cores: longer chunks, as each chunk writes tb FP32 partial rows against its
             // 16-bit history rows (partial traffic 4 tb / R of the history's)
@@ -390,12 +408,13 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         g.ub = !(p.flags & FD_FLAG_STEP_UPDATES) && (int64_t)g.T * 4 <= sms;
         g.cmax = g.ub ? std::max(1, 128 / g.tb) : 0;
         int64_t cmaxb = 1, rwin = g.R;
-        for (int64_t b = 0; b < g.nblocks; ++b) {
-            int64_t Rb, Cb;
-            block_chunks(p, g, b, Rb, Cb);
-            cmaxb = std::max(cmaxb, Cb);
-            rwin = std::max(rwin, Rb);
-        }
+        for (int ip = 0; ip < nprob; ++ip)
+            for (int64_t b = 0; b < g.nblocks; ++b) {
+                int64_t Rb, Cb;
+                block_chunks(ip ? pf : p, g, b, Rb, Cb);
+                cmaxb = std::max(cmaxb, Cb);
+                rwin = std::max(rwin, Rb);
+            }
         g.maxC = (int)cmaxb;
         g.rwin = (int)rwin;
     }
@@ -455,6 +474,38 @@ int64_t blocked_stream_rows(const fd_problem &p, const Geo &g, int64_t *head_row
     return st + hd;
 }
 
+// Adjoint of adaptive memory: every step's tail terms (lags m beyond its settled end e(k), weight
+// psi_m where the adjoint uses g(m)), grouped by the adjoint row r = k - m they reach, ascending in k
+// within a row (Definitions 3.1/3.2, Proposition 3.1).  With weights, each entry carries
+// psi_m - g(m) and the same for the gamma derivatives; without, only the layout is computed.
+struct TailList {
+    std::vector<int> off;  // rows + 1 offsets
+    std::vector<fdk::AdjTail> e;
+};
+void tail_terms(const Sched &s, const std::vector<double> *psi, const std::vector<double> *dpsi,
+                const std::vector<double> *gw, const std::vector<double> *dgw, TailList &t)
+{
+    const int64_t K = (int64_t)s.step.size();
+    int64_t rows = 0;
+    for (int64_t k = 0; k < K; ++k) rows = std::max(rows, k - settled_end(s.step[k]));
+    t.off.assign((size_t)rows + 1, 0);
+    for (int64_t k = 0; k < K; ++k)
+        for (int64_t r = 0; r < k - settled_end(s.step[k]); ++r) ++t.off[(size_t)r + 1];
+    for (int64_t r = 0; r < rows; ++r) t.off[(size_t)r + 1] += t.off[(size_t)r];
+    t.e.assign((size_t)t.off[(size_t)rows], fdk::AdjTail{0, 0, 0.0, 0.0});
+    std::vector<int> cur(t.off.begin(), t.off.end() - 1);
+    for (int64_t k = 0; k < K; ++k)
+        for (int64_t r = 0; r < k - settled_end(s.step[k]); ++r) {
+            fdk::AdjTail &x = t.e[(size_t)cur[(size_t)r]++];
+            const int64_t m = k - r;
+            x.k = (int)k;
+            if (psi) {
+                x.w = (*psi)[m] - (*gw)[m];
+                x.w2 = (*dpsi)[m] - (*dgw)[m];
+            }
+        }
+}
+
 // Device-side layout of one instance inside the workspace.
 struct Layout {
     char *ubuf[2];
@@ -469,6 +520,13 @@ struct Layout {
     int *glag, *br0;
     int4 *sched;
     char *tmap;  // tensor-core path: tensor map of the history rows (128 bytes, 64-byte aligned)
+    // adjoint of adaptive memory: d/dgamma of the settled weights, the full-memory schedule the
+    // per-step adjoint runs, and the tail terms by adjoint row
+    char *dgw;
+    int4 *asched;
+    int *acorr_off;
+    fdk::AdjTail *acorr;
+    int acorr_rows;
     // adjoint
     char *ckpt, *seg, *rec[2], *ahist, *abuf[2];
     double *dots;
@@ -502,9 +560,22 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     const size_t ng = std::max<size_t>(1, s.G.size());
     L.glag = (int *)c.take(sizeof(int) * ng);
     L.gcoef = c.take((size_t)g.sa * ng);
-    const bool gtab = g.tb && p.mem_mode == FD_MEM_ADAPTIVE;
-    L.gw = gtab ? c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa) : nullptr;
-    L.br0 = gtab ? (int *)c.take(sizeof(int) * (size_t)(g.nblocks + 1)) : nullptr;
+    const bool btab = g.tb && p.mem_mode == FD_MEM_ADAPTIVE, aad = adaptive_adjoint(p);
+    const size_t wlen = (size_t)(p.max_steps + 1 + g.tb) * g.sa;
+    L.gw = (btab || aad) ? c.take(wlen) : nullptr;
+    L.br0 = btab ? (int *)c.take(sizeof(int) * (size_t)(g.nblocks + 1)) : nullptr;
+    L.dgw = aad ? c.take(wlen) : nullptr;
+    L.asched = (aad && !g.tb) ? (int4 *)c.take(sizeof(int4) * (size_t)p.max_steps) : nullptr;
+    L.acorr_off = nullptr;
+    L.acorr = nullptr;
+    L.acorr_rows = 0;
+    if (aad) {
+        TailList tl;
+        tail_terms(s, nullptr, nullptr, nullptr, nullptr, tl);
+        L.acorr_rows = (int)tl.off.size() - 1;
+        L.acorr_off = (int *)c.take(sizeof(int) * tl.off.size());
+        L.acorr = (fdk::AdjTail *)c.take(sizeof(fdk::AdjTail) * std::max<size_t>(1, tl.e.size()));
+    }
     L.tmap = g.tc ? c.take(128) : nullptr;
     L.ckpt = L.seg = L.rec[0] = L.rec[1] = L.ahist = L.abuf[0] = L.abuf[1] = nullptr;
     L.dots = nullptr;
@@ -546,8 +617,10 @@ Ctrl carve_ctrl(Carve &c)
 // Host-side tables of an instance, converted to the accumulator type.
 struct Tables {
     std::vector<double> psi, dpsi;
-    std::vector<unsigned char> psi_a, dpsi_a, gcoef_a, gw_a;
+    std::vector<unsigned char> psi_a, dpsi_a, gcoef_a, gw_a, dgw_a;
     std::vector<int> glag, br0;
+    std::vector<int4> asched;
+    TailList tail;
 };
 
 template <class TA> void to_acc(const std::vector<double> &x, std::vector<unsigned char> &out)
@@ -571,25 +644,43 @@ void build_tables(const fd_problem &p, const Sched &s, const Geo &g, Tables &t)
     }
     // blocked adaptive memory: g(m) = psi_m on the base interval [0, a], d psi_m at a median,
     // 0 at the other lags (each median's weight, as the per-step schedule uses it)
-    std::vector<double> gw;
-    if (g.tb && p.mem_mode == FD_MEM_ADAPTIVE) {
+    // adjoint of adaptive memory: dg/dgamma likewise (d psi'_m at a median), the full-memory
+    // schedule of the per-step adjoint, and the tail terms
+    std::vector<double> gw, dgw;
+    if ((g.tb && p.mem_mode == FD_MEM_ADAPTIVE) || adaptive_adjoint(p)) {
         gw.assign(n, 0.0);
-        for (int64_t m = 0; m <= std::min<int64_t>(p.mem_a, n - 1); ++m) gw[m] = t.psi[m];
+        dgw.assign(n, 0.0);
+        for (int64_t m = 0; m <= std::min<int64_t>(p.mem_a, n - 1); ++m) {
+            gw[m] = t.psi[m];
+            dgw[m] = t.dpsi[m];
+        }
         for (size_t i = 0; i < s.G.size(); ++i)
-            if (s.G[i].lag < n) gw[s.G[i].lag] = gc[i];
-        t.br0 = g.br0;
-        t.br0.push_back(0);
+            if (s.G[i].lag < n) {
+                gw[s.G[i].lag] = gc[i];
+                dgw[s.G[i].lag] = (double)s.G[i].mult * t.dpsi[s.G[i].lag];
+            }
+        if (g.tb) {
+            t.br0 = g.br0;
+            t.br0.push_back(0);
+        }
+    }
+    if (adaptive_adjoint(p)) {
+        if (!g.tb)
+            for (int64_t k = 0; k < p.max_steps; ++k) t.asched.push_back(full_step(k));
+        tail_terms(s, &t.psi, &t.dpsi, &gw, &dgw, t.tail);
     }
     if (g.sa == 8) {
         to_acc<double>(t.psi, t.psi_a);
         to_acc<double>(t.dpsi, t.dpsi_a);
         to_acc<double>(gc, t.gcoef_a);
         to_acc<double>(gw, t.gw_a);
+        to_acc<double>(dgw, t.dgw_a);
     } else {
         to_acc<float>(t.psi, t.psi_a);
         to_acc<float>(t.dpsi, t.dpsi_a);
         to_acc<float>(gc, t.gcoef_a);
         to_acc<float>(gw, t.gw_a);
+        to_acc<float>(dgw, t.dgw_a);
     }
 }
 
@@ -608,9 +699,16 @@ int upload_tables(const fd_problem &p, const Sched &s, const Tables &t, const La
     CK(cudaMemcpyAsync(L.sched, s.step.data(), sizeof(int4) * s.step.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(L.glag, t.glag.data(), sizeof(int) * t.glag.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(L.gcoef, t.gcoef_a.data(), t.gcoef_a.size(), cudaMemcpyHostToDevice, st));
-    if (L.gw) {
-        CK(cudaMemcpyAsync(L.gw, t.gw_a.data(), t.gw_a.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(L.br0, t.br0.data(), sizeof(int) * t.br0.size(), cudaMemcpyHostToDevice, st));
+    if (L.gw) CK(cudaMemcpyAsync(L.gw, t.gw_a.data(), t.gw_a.size(), cudaMemcpyHostToDevice, st));
+    if (L.br0) CK(cudaMemcpyAsync(L.br0, t.br0.data(), sizeof(int) * t.br0.size(), cudaMemcpyHostToDevice, st));
+    if (L.dgw) CK(cudaMemcpyAsync(L.dgw, t.dgw_a.data(), t.dgw_a.size(), cudaMemcpyHostToDevice, st));
+    if (L.asched)
+        CK(cudaMemcpyAsync(L.asched, t.asched.data(), sizeof(int4) * t.asched.size(), cudaMemcpyHostToDevice, st));
+    if (L.acorr_off) {
+        CK(cudaMemcpyAsync(L.acorr_off, t.tail.off.data(), sizeof(int) * t.tail.off.size(), cudaMemcpyHostToDevice, st));
+        if (!t.tail.e.empty())
+            CK(cudaMemcpyAsync(L.acorr, t.tail.e.data(), sizeof(fdk::AdjTail) * t.tail.e.size(), cudaMemcpyHostToDevice,
+                               st));
     }
     (void)p;
     return FD_OK;
@@ -746,6 +844,18 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
         I.uadj = L.seg;
         I.dots = L.dots;
     }
+    if (adj && p.mem_mode == FD_MEM_ADAPTIVE) {
+        // full memory with the settled weights g(m), dg/dgamma, plus the tail terms
+        I.psi = L.gw;
+        I.dpsi = L.dgw;
+        I.mem_mode = FD_MEM_FULL;
+        I.gw = nullptr;
+        I.br0 = nullptr;
+        if (L.asched) I.sched = L.asched;
+        I.acorr_off = L.acorr_off;
+        I.acorr = L.acorr;
+        I.acorr_rows = L.acorr_rows;
+    }
     return I;
 }
 
@@ -810,19 +920,25 @@ struct fd_handle {
     long long *d_goff;
     int2 *d_ginfo;
     std::vector<long long> goff;
+    // adjoint of adaptive memory: the adjoint's groups (full memory's units)
+    long long *d_agoff;
+    int2 *d_aginfo;
+    std::vector<long long> agoff;
     const void *kfwd, *kadj;
     int64_t k;
     int bad;                 // state invalid after a failed launch
 };
 
 static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin, int g_end, int k0,
-                  int k_end = 0)
+                  int k_end = 0, bool adj_groups = false)
 {
+    const bool ag = adj_groups && h->d_agoff;
+    const std::vector<long long> &goff = ag ? h->agoff : h->goff;
     Launch L;
     std::memset(&L, 0, sizeof(L));
     L.inst = d_inst;
-    L.g_off = h->d_goff;
-    L.g_info = h->d_ginfo;
+    L.g_off = ag ? h->d_agoff : h->d_goff;
+    L.g_info = ag ? h->d_aginfo : h->d_ginfo;
     L.g_begin = g_begin;
     L.g_end = g_end;
     L.k0 = k0;
@@ -837,7 +953,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.timeout_ns = (long long)(h->p.timeout_ms ? h->p.timeout_ms : 10000) * 1000000LL;
     CK(cudaMemsetAsync(h->ctrl.queue, 0, sizeof(unsigned long long), h->st));
     CK(cudaMemsetAsync(h->ctrl_zero_base, 0, h->ctrl_zero_bytes, h->st));
-    const int64_t units = h->goff[g_end] - h->goff[g_begin];
+    const int64_t units = goff[g_end] - goff[g_begin];
     const int grid = (int)std::min<int64_t>(h->g.grid, units);
     void *args[] = {&L};
     CK(cudaLaunchKernel(fn, dim3(grid), dim3(h->g.threads), args, h->g.smem, h->st));
@@ -846,11 +962,11 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
 
 // Steps [k0, k1) with fn: the per-step kernel's groups are steps; the blocked kernel's are the
 // blocks that intersect the span, plus the group holding the last block's updates.
-static int launch_steps(fd_handle *h, const void *fn, const Inst *d_inst, int k0, int k1)
+static int launch_steps(fd_handle *h, const void *fn, const Inst *d_inst, int k0, int k1, bool adj_groups = false)
 {
     const int tb = h->g.tb;
-    if (tb) return launch(h, fn, d_inst, k0 / tb, (k1 + tb - 1) / tb + 1, k0, k1);
-    return launch(h, fn, d_inst, k0, k1, k0, k1);
+    if (tb) return launch(h, fn, d_inst, k0 / tb, (k1 + tb - 1) / tb + 1, k0, k1, adj_groups);
+    return launch(h, fn, d_inst, k0, k1, k0, k1, adj_groups);
 }
 
 // A zero nz (structs initialised before the field existed) means a single plane.
@@ -876,6 +992,10 @@ static int prepare(const fd_problem *p, Sched &s, Geo &g, size_t *bytes, Layout 
     c.take(sizeof(Inst) * 2);                                     // device instance descriptors
     c.take(sizeof(long long) * (size_t)(p->max_steps + 2));       // group offsets
     c.take(sizeof(int2) * (size_t)(p->max_steps + 2));            // group info
+    if (adaptive_adjoint(*p)) {                                   // the adjoint's groups
+        c.take(sizeof(long long) * (size_t)(p->max_steps + 2));
+        c.take(sizeof(int2) * (size_t)(p->max_steps + 2));
+    }
     if (bytes) *bytes = c.off;
     if (Lout) *Lout = L;
     if (ctrl) *ctrl = cc;
@@ -958,6 +1078,12 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
         h->d_inst = (Inst *)c.take(sizeof(Inst) * 2);
         h->d_goff = (long long *)c.take(sizeof(long long) * (size_t)(p->max_steps + 2));
         h->d_ginfo = (int2 *)c.take(sizeof(int2) * (size_t)(p->max_steps + 2));
+        h->d_agoff = nullptr;
+        h->d_aginfo = nullptr;
+        if (adaptive_adjoint(*p)) {
+            h->d_agoff = (long long *)c.take(sizeof(long long) * (size_t)(p->max_steps + 2));
+            h->d_aginfo = (int2 *)c.take(sizeof(int2) * (size_t)(p->max_steps + 2));
+        }
     }
     h->ctrl_zero_base = (char *)h->L.arrive;
     h->ctrl_zero_bytes = sizeof(unsigned) * (h->g.npar + 1) * (size_t)h->g.T;
@@ -987,6 +1113,16 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
     }
     h->goff[ngroups] = acc;
     info[ngroups] = make_int2(0, ngroups);
+    if (h->d_agoff) {  // adjoint of adaptive memory: full memory's units, same group numbering
+        const fd_problem pf = full_memory(*p);
+        h->agoff.resize((size_t)ngroups + 1);
+        long long a2 = 0;
+        for (int k = 0; k < ngroups; ++k) {
+            h->agoff[k] = a2;
+            a2 += h->g.tb ? block_units(pf, h->g, k) : step_units(h->g, full_step(k));
+        }
+        h->agoff[ngroups] = a2;
+    }
     build_tables(*p, h->s, h->g, h->t);
     h->inst_fwd = make_inst(*p, h->g, h->L, false);
     h->inst_adj = (p->flags & FD_FLAG_KEEP_TAPE) ? make_inst(*p, h->g, h->L, true) : h->inst_fwd;
@@ -1001,6 +1137,12 @@ int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_st
         rc = FD_ERR_CUDA;
     if (!rc && cudaMemcpyAsync(h->d_ginfo, info.data(), sizeof(int2) * info.size(), cudaMemcpyHostToDevice,
                                st) != cudaSuccess)
+        rc = FD_ERR_CUDA;
+    if (!rc && h->d_agoff &&
+        (cudaMemcpyAsync(h->d_agoff, h->agoff.data(), sizeof(long long) * h->agoff.size(), cudaMemcpyHostToDevice,
+                         st) != cudaSuccess ||
+         cudaMemcpyAsync(h->d_aginfo, info.data(), sizeof(int2) * info.size(), cudaMemcpyHostToDevice, st) !=
+             cudaSuccess))
         rc = FD_ERR_CUDA;
     Inst both[2] = {h->inst_fwd, h->inst_adj};
     if (!rc && cudaMemcpyAsync(h->d_inst, both, sizeof(both), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -1132,7 +1274,7 @@ int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma
             if (rc) break;
         }
         // adjoint steps q = K-ce .. K-1-c  (r = K-1-q from ce-1 down to c)
-        rc = launch_steps(h, h->kadj, &h->d_inst[1], K - ce, K - c);
+        rc = launch_steps(h, h->kadj, &h->d_inst[1], K - ce, K - c, true);
         if (rc) break;
     }
     // restore the forward descriptor

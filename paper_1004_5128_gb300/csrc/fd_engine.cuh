@@ -90,7 +90,54 @@ struct Inst {
     char *tape;              // optional u rows (checkpoints / recompute segment)
     const char *uadj;        // adjoint: forward states u^r
     double *dots;            // adjoint: [T][8] per-tile gradient partials
+    const int *acorr_off;    // adjoint of adaptive memory: tail terms of row r at [off[r], off[r+1])
+    const struct AdjTail *acorr;
+    int acorr_rows;          // rows r = 0 .. acorr_rows-1 have tail terms
 };
+
+// Adjoint of adaptive memory.  The adjoint sums every (step k, lag m) pair with the weight g(m)
+// that the medians settle on (Definitions 3.1/3.2: psi_m on the base interval, d psi_m at a
+// median, 0 between), which is the forward weight of every lag up to the step's settled end e(k).
+// A tail lag m > e(k) has forward weight psi_m instead; such a term reaches adjoint row r = k - m,
+// and only rows below the longest tail have any.  Row r's list holds (k, psi_m - g(m),
+// d/dgamma of the same), ascending in k.
+struct AdjTail {
+    int k, pad;
+    double w, w2;
+};
+
+// Adds row r's tail terms to the adjoint memory sums H, H2 of adjoint step q (r = adj_K-1-q): the
+// term of step k reads mu^{k+1}, the row of adjoint step adj_K-1-k, from the adjoint history.
+// Eight rows in flight per thread.
+template <class TS, class TA, int V>
+__device__ __forceinline__ void adjoint_tail(const Inst &I, int q, int j0, TA *H, TA *H2)
+{
+    const int r = I.adj_K - 1 - q;
+    if (!I.acorr || r < 0 || r >= I.acorr_rows || j0 >= I.N) return;
+    const int e0 = I.acorr_off[r], e1 = I.acorr_off[r + 1];
+    constexpr int G = 8;
+    for (int e = e0; e < e1; e += G) {
+        TS x[G][V];
+        TA w[G], w2[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const bool on = e + i < e1 && I.acorr[e + i].k < I.adj_K;
+            w[i] = on ? (TA)I.acorr[e + i].w : TA(0);
+            w2[i] = on ? (TA)I.acorr[e + i].w2 : TA(0);
+            const int row = on ? I.adj_K - 1 - I.acorr[e + i].k : 0;
+            const TS *src = reinterpret_cast<const TS *>(I.hist + (size_t)(row % I.cap) * I.pitch) + j0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[i][v] = (on && j0 + v < I.N) ? __ldcg(src + v) : TS(0);
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                H[v] = fma(w[i], (TA)x[i][v], H[v]);
+                H2[v] = fma(w2[i], (TA)x[i][v], H2[v]);
+            }
+    }
+}
 
 struct Launch {
     const Inst *inst;
@@ -829,6 +876,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             H[v] += KAHAN ? (hs[v] - hc[v]) : hs[v];
             if (ADJ) H2[v] += hs2[v];
         }
+        if (ADJ) adjoint_tail<TS, TA, V>(I, k, j0, H, H2);
         float amax = 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {

@@ -997,6 +997,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         if (m & 32u) nb[v][5] = get1(j - pl);
                     }
                 }
+                if (ADJ) adjoint_tail<float, float, V>(I, k, j0, H, H2);
                 if (add_lag1) {  // lag 1 completes the memory sum
                     const float cc = psi[1];
                     H[0] = fmaf(cc, x1.x, H[0]);

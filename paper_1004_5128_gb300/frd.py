@@ -204,8 +204,9 @@ class FRDFunction(torch.autograd.Function):
     """u^K = FRD(u0; gamma, alpha, react) with the reverse-time adjoint as its backward.
 
     forward(u0, gamma, alpha, react, cfg): cfg = dict(problem=<synth dict>, K=steps,
-    state="f32"|"f64", ckpt_every=C).  Gradients flow to u0, gamma, alpha and react
-    (a length-4 tensor); full memory only.
+    state="f32"|"f64", ckpt_every=C, options=dict(...) of further FRD options such as
+    time_block).  Gradients flow to u0, gamma, alpha and react (a length-4 tensor), for the
+    full, short and adaptive memory of the problem.
     """
 
     @staticmethod
@@ -216,7 +217,7 @@ class FRDFunction(torch.autograd.Function):
         p["react"] = [float(x) for x in torch.as_tensor(react).reshape(-1).tolist()]
         K = int(cfg["K"])
         solver = FRD(p, device=u0.device, max_steps=K, state=cfg.get("state", "f32"), keep_tape=True,
-                     ckpt_every=int(cfg.get("ckpt_every", 200)))
+                     ckpt_every=int(cfg.get("ckpt_every", 200)), **cfg.get("options", {}))
         solver.set_state(u0.detach())
         uK = solver.run(K)
         ctx.solver = solver

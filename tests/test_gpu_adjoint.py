@@ -155,3 +155,51 @@ def test_short_memory_adjoint_vs_oracle(state, L):
     p = synth.with_mode(p, synth.MEM_SHORT, L=L)
     r = gpu_adjoint(p, tgt, state, ckpt=40)
     compare(r, oracle.adjoint(p, tgt), TOL[state])
+
+
+ADAPT = [(2, synth.ADAPT_PAPER), (3, synth.ADAPT_PAPER), (10, synth.ADAPT_PAPER), (2, synth.ADAPT_PARTITION),
+         (3, synth.ADAPT_PARTITION)]
+
+
+@pytest.mark.parametrize("state", ["f64", "f32"])
+@pytest.mark.parametrize("a,rule", ADAPT)
+def test_adaptive_memory_adjoint_vs_oracle(state, a, rule):
+    """Adaptive memory (Definitions 3.1/3.2, Proposition 3.1): the adjoint sums every lag with the
+    weight the medians settle on and corrects the tail terms of each step; checkpoint segments of
+    40 steps over 150."""
+    p, tgt = small(synth.BC_NOFLUX)
+    p = synth.with_mode(p, synth.MEM_ADAPTIVE, a=a, rule=rule)
+    r = gpu_adjoint(p, tgt, state, ckpt=40)
+    compare(r, oracle.adjoint(p, tgt), TOL[state])
+
+
+@pytest.mark.parametrize("step_updates", [False, True])
+@pytest.mark.parametrize("tb", [4, 8])
+@pytest.mark.parametrize("a,rule", ADAPT)
+def test_adaptive_memory_blocked_adjoint_vs_oracle(tb, a, rule, step_updates):
+    """The blocked adjoint of adaptive memory: far rows with the settled weights, launches that
+    start inside blocks (checkpoints every 50 of 230 steps), several far chunks per block."""
+    g = synth.SplitMix64(5)
+    p = synth.problem(2, 45, 37, 0.75, 0.7, synth.dt_for_courant(0.15, 0.7, 1.0, 0.75), 1.0, synth.BC_DIRICHLET0,
+                      react=(0.01, -0.2, 0.3, -0.4), mem_mode=synth.MEM_ADAPTIVE, mem_a=a, adaptive_rule=rule,
+                      K=230, u0=g.uniform(45 * 37, 0, 1))
+    tgt = g.uniform(45 * 37, 0, 0.8)
+    r = gpu_adjoint(p, tgt, "f32", ckpt=50, time_block=tb, chunk_terms=16, step_updates=step_updates)
+    compare(r, oracle.adjoint(p, tgt), TOL["f32"])
+
+
+def test_autograd_function_adaptive_memory():
+    p, tgt = small(synth.BC_DIRICHLET0, nx=16, ny=16, K=90)
+    p = synth.with_mode(p, synth.MEM_ADAPTIVE, a=3)
+    dev = torch.device("cuda")
+    u0 = torch.tensor(p["u0"], device=dev, requires_grad=True)
+    gam = torch.tensor(p["gamma"], dtype=torch.float64, requires_grad=True)
+    alp = torch.tensor(p["alpha"], dtype=torch.float64, requires_grad=True)
+    react = torch.tensor(p["react"], dtype=torch.float64, requires_grad=True)
+    uK = FRDFunction.apply(u0, gam, alp, react, dict(problem=p, K=p["K"], state="f64", ckpt_every=25))
+    loss = 0.5 * ((uK - torch.tensor(tgt, device=dev)) ** 2).sum()
+    loss.backward()
+    ref = oracle.adjoint(p, tgt)
+    assert rel_inf(u0.grad.cpu().numpy(), ref["du0"]) < TOL["f64"]
+    assert abs(gam.grad.item() - ref["dgamma"]) < TOL["f64"] * abs(ref["dgamma"])
+    assert abs(alp.grad.item() - ref["dalpha"]) < TOL["f64"] * abs(ref["dalpha"])

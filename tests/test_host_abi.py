@@ -67,14 +67,13 @@ def test_validation_codes():
     assert e.value.code == L.FD_ERR_UNSTABLE
     fp.flags |= L.FD_FLAG_ALLOW_UNSTABLE
     assert L.fd_workspace_bytes(fp) > 0
-    # adjoint: full and short memory (the short run then keeps every row for the recompute);
-    # the adaptive schedule has no adjoint
+    # adjoint: full, short (the short run then keeps every row for the recompute) and adaptive
+    # memory (settled weights plus the tail terms' table)
     q = make_problem(synth.with_mode(p, synth.MEM_SHORT, L=5), max_steps=10, keep_tape=True)
     assert L.fd_workspace_bytes(q) > 0
     q = make_problem(synth.with_mode(p, synth.MEM_ADAPTIVE, a=3), max_steps=10, keep_tape=True)
-    with pytest.raises(L.FdError) as e:
-        L.fd_workspace_bytes(q)
-    assert e.value.code == L.FD_ERR_UNSUPPORTED
+    assert L.fd_workspace_bytes(q) > L.fd_workspace_bytes(make_problem(synth.with_mode(p, synth.MEM_ADAPTIVE, a=3),
+                                                                       max_steps=10))
     # bf16 history with an f64 state is not a built combination
     q = make_problem(p, max_steps=10, state="f64", hist="bf16")
     with pytest.raises(L.FdError) as e:
@@ -141,12 +140,11 @@ def test_time_block_validation():
         with pytest.raises(L.FdError) as e:
             L.fd_workspace_bytes(make_problem(p, **bad))
         assert e.value.code == code
-    # adaptive memory blocks forward; its schedule has no adjoint
+    # adaptive memory blocks forward and adjoint (blocks of 4 or 8)
     ad = synth.with_mode(p, synth.MEM_ADAPTIVE, a=10)
     assert L.fd_workspace_bytes(make_problem(ad, time_block=8)) > L.fd_workspace_bytes(make_problem(ad)) > 0
-    with pytest.raises(L.FdError) as e:
-        L.fd_workspace_bytes(make_problem(ad, time_block=8, keep_tape=True))
-    assert e.value.code == L.FD_ERR_UNSUPPORTED
+    assert L.fd_workspace_bytes(make_problem(ad, time_block=8, keep_tape=True)) > \
+        L.fd_workspace_bytes(make_problem(ad, time_block=8))
 
 
 def test_blocked_batch_validation():
