@@ -63,12 +63,14 @@ def lib():
                                 dp, dp]
         L.or_adjoint.argtypes = [pp, dp, ctypes.c_long, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         L.or_run_bf16.argtypes = [pp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, dp, ctypes.c_int]
+        L.or_run_closed.argtypes = [pp, dp, ctypes.c_long, ctypes.c_double, dp, lp, ctypes.c_int]
         L.or_round_bf16.argtypes = [ctypes.c_double]
         L.or_round_bf16.restype = ctypes.c_double
         L.or_scalar_mode.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int, ctypes.c_long,
                                                              ctypes.c_long, ctypes.c_int,
                                                              ctypes.c_double, ctypes.c_long, dp]
-        for f in (L.or_weights, L.or_run, L.or_run_cs, L.or_adjoint, L.or_scalar_mode, L.or_run_bf16):
+        for f in (L.or_weights, L.or_run, L.or_run_cs, L.or_adjoint, L.or_scalar_mode, L.or_run_bf16,
+                  L.or_run_closed):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -135,6 +137,21 @@ def run_bf16(p: dict, blk: int, head: int, K: int | None = None, threads: int = 
     if rc != 0:
         raise ValueError(f"or_run_bf16 failed ({rc})")
     return uK
+
+
+def run_closed(p: dict, tau: float, K: int | None = None, threads: int = 0):
+    """Closed-loop adaptive memory (reading of the Discussion): (u^K, terms used over the run).
+    A median stands for its increment only while the history's relative variation across the
+    increment, from per-row maxima of |delta^r - delta^(r-1)| and |delta^r|, stays below tau."""
+    K = p["K"] if K is None else K
+    u0 = np.ascontiguousarray(p["u0"], dtype=np.float64)
+    uK = np.empty(p["nx"] * p["ny"] * p.get("nz", 1))
+    n = ctypes.c_long(0)
+    s = _problem(p)
+    rc = lib().or_run_closed(ctypes.byref(s), _dp(u0), K, float(tau), _dp(uK), ctypes.byref(n), threads)
+    if rc != 0:
+        raise ValueError(f"or_run_closed failed ({rc})")
+    return uK, int(n.value)
 
 
 def round_bf16(x: float) -> float:

@@ -351,6 +351,81 @@ int or_run_bf16(const or_problem *p, const double *u0, long K, long blk, long he
     return 0;
 }
 
+/* ------------------------------------------------ closed-loop adaptive memory */
+
+int or_run_closed(const or_problem *p, const double *u0, long K, double tau, double *uK, long *nterms,
+                  int threads)
+{
+    if (check_problem(p, K) || !u0 || !uK || p->mem_mode != OR_MEM_ADAPTIVE || !(tau >= 0.0)) return -1;
+    const long N = (long)p->nx * p->ny * p->nz;
+    const double S = p->alpha * pow(p->dt, p->gamma) / (p->dx * p->dx);
+    double *psi = malloc(sizeof(double) * (size_t)(K + 1));
+    double *hist = malloc(sizeof(double) * (size_t)K * (size_t)N);
+    double *D = calloc((size_t)K, sizeof(double)); /* D_r: largest change from row r-1 to row r */
+    double *M = calloc((size_t)K, sizeof(double)); /* M_r: largest |delta^r| */
+    double *u = malloc(sizeof(double) * (size_t)N);
+    double *un = malloc(sizeof(double) * (size_t)N);
+    long *lag = malloc(sizeof(long) * (size_t)(K + 1));
+    long *mult = malloc(sizeof(long) * (size_t)(K + 1));
+    /* the step's terms after the feedback: a median, or its increment's lags one by one */
+    long *tl = malloc(sizeof(long) * (size_t)(K + 1) * 2);
+    double *tc = malloc(sizeof(double) * (size_t)(K + 1) * 2);
+    if (!psi || !hist || !D || !M || !u || !un || !lag || !mult || !tl || !tc) {
+        free(psi); free(hist); free(D); free(M); free(u); free(un); free(lag); free(mult); free(tl); free(tc);
+        return -2;
+    }
+    or_weights(p->gamma, K + 1, psi, NULL);
+    memcpy(u, u0, sizeof(double) * (size_t)N);
+#ifdef _OPENMP
+    const int nthr = threads > 0 ? threads : omp_get_max_threads();
+#else
+    (void)threads;
+#endif
+    long total = 0;
+    for (long k = 0; k < K; ++k) {
+        double *row = hist + (size_t)k * (size_t)N;
+        apply_L(p, u, row); /* delta^k */
+        for (long j = 0; j < N; ++j) {
+            M[k] = fmax(M[k], fabs(row[j]));
+            if (k) D[k] = fmax(D[k], fabs(row[j] - row[(long)j - N]));
+        }
+        const long n = or_schedule(p->mem_mode, p->mem_L, p->mem_a, p->adaptive_rule, k, lag, mult);
+        long nt = 0;
+        for (long t = 0; t < n; ++t) {
+            const long m = lag[t], d = mult[t];
+            if (d == 1) {
+                tl[nt] = m; tc[nt] = psi[m]; ++nt;
+                continue;
+            }
+            const long h = (d - 1) / 2, lo = m - h, hi = m + h; /* the increment's lags */
+            double var = 0.0;
+            for (long r = k - hi + 1; r <= k - lo; ++r) var += D[r];
+            const double ref = M[k - m];
+            const int smooth = isinf(tau) || ((ref > 0.0) ? (var / ref < tau) : (var == 0.0 && tau > 0.0));
+            if (smooth) {
+                tl[nt] = m; tc[nt] = (double)d * psi[m]; ++nt;
+            } else {
+                for (long l = lo; l <= hi; ++l) { tl[nt] = l; tc[nt] = psi[l]; ++nt; }
+            }
+        }
+        total += nt;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthr)
+#endif
+        for (long j = 0; j < N; ++j) {
+            double sum = 0.0, cmp = 0.0;
+            for (long t = 0; t < nt; ++t) nadd(&sum, &cmp, tc[t] * hist[(size_t)(k - tl[t]) * (size_t)N + j]);
+            /* eq. frac_final with f outside the memory sum */
+            un[j] = u[j] + p->dt * react_f(p->react, u[j]) + S * (sum + cmp);
+        }
+        double *tmp = u; u = un; un = tmp;
+    }
+    memcpy(uK, u, sizeof(double) * (size_t)N);
+    if (nterms) *nterms = total;
+    free(psi); free(hist); free(D); free(M); free(u); free(un); free(lag); free(mult); free(tl); free(tc);
+    return 0;
+}
+
 /* ------------------------------------------------------ complex-step forward */
 
 static void apply_L_cs(const or_problem *p, const double complex *u, double complex *out)

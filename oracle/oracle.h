@@ -77,6 +77,21 @@ double or_round_bf16(double x);
  * length.  With head >= K it equals or_run bit for bit. */
 int or_run_bf16(const or_problem *p, const double *u0, long K, long blk, long head, double *uK, int threads);
 
+/* Closed-loop adaptive memory (a reading of the Discussion, Section 4: the spacing of the
+ * backward sum follows the derivative of the past history, a form of feedback).  Each step starts
+ * from the adaptive schedule of p (Definitions 3.1/3.2, Proposition 3.1).  A median m that stands
+ * for an increment of d = 2i-1 lags m-i+1 .. m+i-1 is kept, with weight d psi_m, only while the
+ * history is smooth across the increment:
+ *     V = (sum over the increment's rows r but its oldest of D_r) / M_{k-m}  <  tau,
+ * where D_r = max_j |delta^r_j - delta^{r-1}_j| and M_r = max_j |delta^r_j| are computed once per
+ * row (V bounds the relative change of the history across the increment, field-wide so that
+ * every point shares one schedule; tau = +inf keeps every median).  Otherwise the increment's lags are summed one by one with
+ * weight psi.  tau = +inf gives or_run's adaptive result bit for bit; tau = 0 with the partition
+ * rule gives full memory.  *nterms (if not NULL) receives the number of (lag, weight) terms used
+ * over the run, lag 0 included.  Returns as or_run. */
+int or_run_closed(const or_problem *p, const double *u0, long K, double tau, double *uK, long *nterms,
+                  int threads);
+
 /* Forward run in double complex (complex-step differentiation): the
  * imaginary parts of u0, gamma, alpha and react carry the perturbation.
  * Plain (uncompensated) summation.  Returns u^K as separate re/im arrays. */
