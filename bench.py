@@ -369,13 +369,28 @@ def side_measurements(runs, dev) -> dict:
     return out
 
 
-def make_runs(args, dev):
+def shard_runs(runs: list, ws: int, rank: int) -> tuple:
+    """This rank's share of the workload: a batch's instances split over the ranks by
+    parallel.shard (strong scaling: the ranks together run the one batch), single-instance runs
+    as replicas (weak scaling: every rank runs the whole step)."""
+    from paper_1004_5128_gb300 import parallel
+    out, sharded = [], False
+    for name, p, kw in runs:
+        if isinstance(p, list) and ws > 1:
+            p = [p[i] for i in parallel.shard(p, ws)[rank]]
+            sharded = True
+        out.append((name, p, kw))
+    return out, sharded
+
+
+def make_runs(args, dev, ws: int = 1, rank: int = 0):
     geo = {}
     for item in filter(None, args.geom.split(",")):
         k_, v_ = item.split("=")
         geo[k_] = int(v_)
     cls = {"c4": BatchRun, "c5": AdjointRun}.get(args.workload, SingleRun)
-    return [cls(name, p, kw, geo, dev) for name, p, kw in problems(args.workload, args.K, args.modes)]
+    runs, sharded = shard_runs(problems(args.workload, args.K, args.modes), ws, rank)
+    return [cls(name, p, kw, geo, dev) for name, p, kw in runs], sharded
 
 
 # ------------------------------------------------------------------------------- our arm
@@ -392,7 +407,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    runs = make_runs(args, dev)
+    runs, sharded = make_runs(args, dev, ws, rank)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
     def one_step(events=None):
@@ -428,8 +443,9 @@ def run_ours(args):
     for r in runs:
         if r.status() != 0:
             raise SystemExit(f"engine status error in timed region ({r.name})")
-    terms_step = sum(r.terms for r in runs)
-    value = ws * terms_step * args.steps / (ms / 1e3)
+    # every rank's terms (replicas: the same step on each; a sharded batch: its own instances)
+    terms_step = parallel.sum_over_ranks(sum(r.terms for r in runs))
+    value = terms_step * args.steps / (ms / 1e3)
 
     modes = {}
     for r in runs:
@@ -488,8 +504,9 @@ def run_ours(args):
                 r.e2e_run()
         torch.cuda.synchronize()
         we = parallel.max_over_ranks(time.perf_counter() - w0)
-        e2e = {"value": ws * terms_step * k / we, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        e2e = {"value": terms_step * k / we, "unit": "terms/s",
+               "h2d_bytes_per_step": int(parallel.sum_over_ranks(h2d)),
+               "d2h_bytes_per_step": int(parallel.sum_over_ranks(d2h))}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -502,13 +519,14 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (seeded SplitMix64 inputs)",
             "config": {"workload": CONFIG_NAMES[args.workload] +
                        (f" [K={args.K}]" if args.K else "") + (f" [{args.modes}]" if args.modes else ""),
                        "l2": "a 258 MB L2 flush before every run; every run's history exceeds L2 "
                              "(config 3: 10.5 GB BF16/FP16, 21 GB FP32)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                       "parallelism": (f"instances sharded over {ws} GPUs (parallel.shard)" if sharded
+                                       else f"replicas x{ws}" if ws > 1 else "single GPU")},
             "modes": modes, "roofline": roof, "e2e": e2e,
             "gpu_launches": sum(r.launches for r in runs) * args.steps,
             "clocks": ck, "cpu_baseline": cpu,

@@ -139,34 +139,43 @@ int fd_schedule(const fd_problem *p, int64_t k, int64_t *lags, int64_t *mult, in
  * buffers when FD_FLAG_KEEP_TAPE is set). */
 int fd_workspace_bytes(const fd_problem *p, size_t *bytes);
 
-/* Bind a handle to a caller-owned device workspace and stream.  Validates p,
+/* Bind a handle for the scheme of eq. frac_final (Section 2.2) with the memory of p (eq.
+ * frac_norxn, eq. frac_shortmemory or Proposition 3.1) to a caller-owned device workspace and
+ * stream.  Validates p,
  * checks stability (unless FD_FLAG_ALLOW_UNSTABLE), builds the weight and
  * schedule tables on the host and uploads them.  The handle is at step 0 with
  * an all-zero state until fd_set_state.  Synchronises the stream once. */
 int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_stream,
             fd_handle **out);
 
-/* Copy u^0 (N values of state_dtype; device or host pointer) and reset to step 0. */
+/* Copy u^0 (N values of state_dtype; device or host pointer), the initial field of eq. fracdiff,
+ * and reset to step 0 (empty history). */
 int fd_set_state(fd_handle *h, const void *u0);
 
-/* Enqueue nsteps steps (one persistent launch); returns without synchronising.
+/* Enqueue nsteps steps of eq. frac_final, u^{k+1} = u^k + dt f(u^k) + S sum c delta^{k-m}, each
+ * appending delta^k = L u^k (eq. deltasimp) to the history (one persistent launch); returns
+ * without synchronising.
  * Fails with FD_ERR_STATE if the total would exceed max_steps. */
 int fd_step(fd_handle *h, int nsteps);
 
-/* fd_step(nsteps), then copy u^k to u_out (device or host; NULL = no copy),
+/* fd_step(nsteps) (eq. frac_final), then copy u^k to u_out (device or host; NULL = no copy),
  * synchronise the stream and return the device status (FD_ERR_NONFINITE,
  * FD_ERR_TIMEOUT, ...). */
 int fd_run(fd_handle *h, int nsteps, void *u_out);
 
-/* Enqueue a copy of the current state u^k to u_out (device or host). */
+/* Enqueue a copy of the current state u^k of eq. frac_final to u_out (device or host). */
 int fd_get_state(fd_handle *h, void *u_out);
 
 /* Current step k of the handle. */
 int64_t fd_current_step(fd_handle *h);
 
-/* Reverse-time adjoint of J(u^K) for the K steps taken since fd_set_state
- * (full or short memory, F32 or F64 state/history, FD_FLAG_KEEP_TAPE required; short memory
- * transposes its window: delta^r reaches the steps r+m with m <= L, eq. frac_shortmemory).
+/* Reverse-time adjoint of J(u^K) for the K steps taken since fd_set_state: the transpose of
+ * the linearised eq. frac_final, lambda^r = lambda^{r+1} + dt f'(u^r) lambda^{r+1} + S L^T g^r,
+ * g^r = sum_m w_{r+m}(m) psi_m lambda^{r+1+m} (w: lag m's multiplicity in step r+m's schedule).
+ * F32 or F64 state/history, FD_FLAG_KEEP_TAPE required.  Short memory transposes its window
+ * (delta^r reaches the steps r+m with m <= L, eq. frac_shortmemory); adaptive memory sums every
+ * lag with the weight the medians settle on (Definitions 3.1/3.2) and corrects each step's tail
+ * terms (Proposition 3.1), which reach only the rows below the longest tail.
  * dJ_duK: N values (state dtype, device or host) = dJ/du^K.  Outputs dJ/du^0
  * (N values, device or host; may be NULL) and the scalar gradients with respect
  * to gamma (through psi and dt^g), alpha and react[0..3] (each may be NULL).
@@ -183,7 +192,8 @@ int fd_get_status(fd_handle *h);
  * update waiting for its own rows, 5 blocked update waiting for a halo tile, 6 per-step chunk
  * waiting for its rows, 7 per-step chunk's bulk copy, 8 per-step fixup waiting for a halo
  * tile, 9 the stall injected by FD_FLAG_INJECT_STALL, 10 blocked far unit waiting for the
- * previous chunk's running sum.  info[1..6] are the site's operands
+ * previous chunk's running sum, 11 tensor-core far unit waiting for a copy, its coefficient
+ * block or its MMAs (operands as for site 2).  info[1..6] are the site's operands
  * (step or block, tile, the counter target and the value last read, the launch's first step;
  * site 2 packs pairs into the high and low 32 bits), info[7] the CTA.  Only the first failure
  * since fd_set_state is kept.  Synchronises the stream. */
@@ -211,7 +221,9 @@ typedef struct fd_geometry {
 int fd_get_geometry(fd_handle *h, fd_geometry *g);
 
 /* ---- batches: many independent instances in one persistent launch ----
- * Instance i runs probs[i].max_steps steps; all instances share one device
+ * Each instance is its own problem of eq. frac_final (own grid, gamma, alpha, f, memory and step
+ * count).  Instance i runs probs[i].max_steps steps (a batch takes each instance's step count
+ * from its max_steps, not from a separate array); all instances share one device
  * work queue ordered by step, so uneven sizes and step counts balance across
  * the GPU.  The launch is recorded once as a CUDA graph (workspace reset +
  * persistent kernel) and replayed by fd_batch_run.  Histories and geometry
@@ -227,8 +239,8 @@ int fd_batch_get_status(fd_batch *b);                          /* synchronises *
 int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g);  /* instance i's resolved geometry */
 int fd_batch_destroy(fd_batch *b);
 
-/* One-shot batch: init, set u_io[i] as u^0, run, write u^{K_i} back to u_io[i]
- * (device or host pointers), synchronise, destroy. */
+/* One-shot batch of eq. frac_final instances: init, set u_io[i] as u^0, run probs[i].max_steps
+ * steps, write u^{K_i} back to u_io[i] (device or host pointers), synchronise, destroy. */
 int fd_run_batch(const fd_problem *probs, int count, void *const *u_io, void *workspace,
                  size_t ws_bytes, void *cuda_stream);
 

@@ -205,7 +205,8 @@ def fd_get_status(h: int) -> int:
 ERROR_SITES = {0: "none", 1: "blocked far unit: history rows", 2: "blocked far unit: bulk copy",
                3: "blocked update: far count", 4: "blocked update: own rows",
                5: "blocked update: halo tile", 6: "chunk: history rows", 7: "chunk: bulk copy",
-               8: "fixup: halo tile", 9: "injected stall", 10: "blocked far unit: running sum"}
+               8: "fixup: halo tile", 9: "injected stall", 10: "blocked far unit: running sum",
+               11: "tensor-core far unit: copy, coefficients or MMAs"}
 
 
 def fd_get_error_info(h: int) -> dict:

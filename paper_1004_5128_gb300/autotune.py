@@ -29,7 +29,7 @@ from . import _lib as L
 from .frd import FRD, FRDBatch
 
 PARAMS = {
-    "time_block": [0, 8, 16],
+    "time_block": [0, 8, 16, 32],
     "step_updates": [0, 1],
     "tile_threads": [128, 256, 512],
     "chunk_terms": [32, 64, 128, 256, 512],
@@ -157,13 +157,15 @@ def _time_batch(probs, geo, reps, **kw) -> float:
 
 
 def tune(p, state: str = "f32", hist: str | None = None, kahan: bool = False, reps: int = 2,
-         budget_s: float = 60.0, batch: list | None = None, verbose: bool = False) -> dict:
+         budget_s: float = 60.0, batch: list | None = None, verbose: bool = False, **fixed) -> dict:
     """Coordinate descent over PARAMS from the defaults; returns and caches the best geometry.
 
     With `batch` (a list of problems) the whole batch launch is timed instead of `p` alone.
+    Geometry options passed in `fixed` (e.g. time_block) are held at their value and kept in
+    the result.
     """
     kw = dict(state=state, hist=hist, kahan=kahan)
-    cur: dict = {}
+    cur: dict = dict(fixed)
     timer = (lambda g: _time_batch(batch, g, reps, **kw)) if batch else \
         (lambda g: _time_single(p, g, reps, **kw))
     best = timer(cur)
@@ -172,6 +174,8 @@ def tune(p, state: str = "f32", hist: str | None = None, kahan: bool = False, re
     while improved and time.time() < t_end:
         improved = False
         for name, values in PARAMS.items():
+            if name in fixed:
+                continue
             for v in values:
                 if time.time() > t_end:
                     break

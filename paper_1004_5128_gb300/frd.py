@@ -59,6 +59,18 @@ GEOMETRY_KEYS = ("tile_threads", "chunk_terms", "stage_rows", "stages", "ctas_pe
                  "time_block", "step_updates", "fma_far")
 
 
+def tuned_geometry(p: dict, kw: dict) -> dict:
+    """The autotuner's geometry for a handle with options kw, unless kw sets one itself.  A
+    taped handle (adjoint) takes blocks of at most 8 steps, the blocked adjoint's limit."""
+    if any(k in kw for k in GEOMETRY_KEYS):
+        return {}
+    from .autotune import lookup
+    geo = lookup(p, kw.get("state", "f32"), kw.get("hist"), kw.get("kahan", False))
+    if kw.get("keep_tape") and geo.get("time_block", 0) > 8:
+        geo["time_block"] = 8
+    return geo
+
+
 class FRD:
     """One problem instance bound to a device workspace and a stream.
 
@@ -68,12 +80,8 @@ class FRD:
     def __init__(self, p: dict, device: str | torch.device = "cuda", stream=None, tuned: bool = True,
                  **kw):
         _require_cuda()
-        if tuned and not any(k in kw for k in GEOMETRY_KEYS):
-            from .autotune import lookup
-            geo = lookup(p, kw.get("state", "f32"), kw.get("hist"), kw.get("kahan", False))
-            if kw.get("keep_tape") and geo.get("time_block", 0) > 8:
-                geo["time_block"] = 8  # blocked adjoint: blocks of at most 8 steps
-            kw.update(geo)
+        if tuned:
+            kw.update(tuned_geometry(p, kw))
         self.problem = p
         self.prob = make_problem(p, **kw)
         self.device = torch.device(device)

@@ -112,3 +112,32 @@ def test_blocked_batch_equals_single_blocked_runs_bitwise(mode):
         s = FRD(p, chunk_terms=32, tile_threads=256, time_block=8)
         s.set_state(p["u0"])
         assert np.array_equal(s.run(p["K"]).cpu().numpy(), x)
+
+
+@pytest.mark.parametrize("mode", [synth.MEM_FULL, synth.MEM_ADAPTIVE])
+def test_config4_full_batch_large_instances_vs_scalar_recursions(mode):
+    """The 64-instance workload with the shipped (tuned) geometry, large instances included: the
+    three most expensive 1-D and three most expensive 2-D instances start from a superposition
+    of Laplacian eigenmodes, so the oracle's scalar recursion of each mode (same weights,
+    schedule and linear reaction) gives their exact result at full size; the three cheapest
+    instances are compared with the oracle element by element."""
+    from tests.helpers import laplacian_eigenvalue
+    probs = [dict(p) for p in synth.config4(mode=mode)]
+    cost = [p["nx"] * p["ny"] * p["K"] ** 2 for p in probs]
+    order = list(np.argsort(cost))
+    big1 = [i for i in order[::-1] if probs[i]["ndim"] == 1][:3]
+    big2 = [i for i in order[::-1] if probs[i]["ndim"] == 2][:3]
+    modes = {1: [(1, 1, 1.0), (3, 1, 0.5), (40, 1, 0.05)], 2: [(1, 1, 1.0), (3, 2, 0.5), (30, 17, 0.05)]}
+    refs = {}
+    for i in big1 + big2:
+        p = probs[i]
+        ms = modes[p["ndim"]]
+        p["u0"] = sum(c * synth.eigenmode(p, qx, qy) for qx, qy, c in ms)
+        refs[i] = sum(c * oracle.scalar_mode(p, laplacian_eigenvalue(p, qx, qy))[-1] * synth.eigenmode(p, qx, qy)
+                      for qx, qy, c in ms)
+    out, b = run_batch(probs)
+    assert b.geometry(0)["time_block"] == 16   # the tuned batch geometry
+    for i in big1 + big2:
+        assert rel_inf(out[i], refs[i]) < 1e-5, (i, probs[i]["nx"], probs[i]["K"])
+    for i in order[:3]:
+        assert rel_inf(out[i], oracle.run(probs[i])) < 1e-5

@@ -163,3 +163,20 @@ def test_tensor_core_batch_matches_single_runs():
     for i, p in enumerate(probs):
         one, _ = run(p, **geo)
         assert np.array_equal(bt.state(i).cpu().double().numpy(), one)
+
+
+def test_tensor_core_stall_injection_times_out_and_gpu_stays_usable():
+    """A wait nothing will satisfy ends the tensor-core launch with FD_ERR_TIMEOUT; every CTA
+    gives its tensor memory back on the way out, and the next handle runs normally."""
+    from paper_1004_5128_gb300 import _lib as L
+    p = ragged(synth.BC_NOFLUX, synth.MEM_FULL, K=120)
+    s = FRD(p, hist="bf16", time_block=32, inject_stall=True, timeout_ms=200)
+    s.set_state(p["u0"])
+    with pytest.raises(L.FdError) as e:
+        s.run(p["K"])
+    assert e.value.code == L.FD_ERR_TIMEOUT
+    assert s.error_info()["site"] != "none"
+    s.close()
+    got, t = run(p, hist="bf16", time_block=32)
+    assert t.geometry()["far_tensor_cores"] == 1
+    assert rel_inf(got, oracle.run(p)) < TOL
