@@ -217,6 +217,7 @@ typedef struct fd_geometry {
     int far_tensor_cores;    /* time_block: 1 when the far rows are multiplied on the tensor cores */
     int64_t head_rows_total; /* time_block: of stream_rows_total, the rows of the newest 2 time_block
                                 steps that the update units read (FP32, also for 16-bit history) */
+    int64_t smem_bytes;      /* dynamic shared memory per CTA */
 } fd_geometry;
 int fd_get_geometry(fd_handle *h, fd_geometry *g);
 

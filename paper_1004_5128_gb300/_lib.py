@@ -77,7 +77,8 @@ class FdGeometry(ctypes.Structure):
         ("units_total", ctypes.c_int64), ("hist_rows_total", ctypes.c_int64),
         ("terms_total", ctypes.c_int64), ("stream_rows_total", ctypes.c_int64),
         ("time_block", ctypes.c_int), ("block_updates", ctypes.c_int),
-        ("far_tensor_cores", ctypes.c_int), ("head_rows_total", ctypes.c_int64)]
+        ("far_tensor_cores", ctypes.c_int), ("head_rows_total", ctypes.c_int64),
+        ("smem_bytes", ctypes.c_int64)]
 
 
 _lib = None

@@ -234,6 +234,7 @@ struct Geo {
     int rwin;        // blocked: largest far chunk (rows), the coefficient window's length
     int nblocks;     // blocks of tb steps covering max_steps
     int tc;          // blocked, BF16 history: far units on the tensor cores
+    int near;        // blocked, per-step update units, blocks of 16+: one near unit per (block, tile)
     int ralign;      // blocked: far chunks start on multiples of ralign rows (tensor cores: RS)
     int hring_sep;   // separate state-precision head ring
     int hring_cap;
@@ -267,12 +268,13 @@ inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
 }
 
 // Tensor-core blocked kernel: stage ring (RS rows x P points of BF16, at least the block-long
-// units' sums), 1 KB-aligned; NS coefficient blocks (hi and lo halves of tb/8 1 KB atoms); the
+// units' sums), 1 KB-aligned; NS coefficient blocks (tb/8 1 KB atoms, hi and lo halves side by
+// side); the
 // coefficient window; 3 NS + 1 barriers; 1 KB of slack to align the base.
 inline size_t smem_bytes_tc(const Geo &g, int rwin, bool f16)
 {
-    const size_t ring = std::max((size_t)g.NS * g.RS * g.threads * 8, (size_t)(g.tb * g.planes + 2) * g.threads * 16);
-    return align_up(ring, 1024) + (size_t)g.NS * 2 * (g.tb / 8) * 1024 + (size_t)(rwin + g.tb + (f16 ? rwin : 0)) * 4 +
+    const size_t ring = (size_t)g.NS * g.RS * g.threads * 8;  // no block-long update units
+    return align_up(ring, 1024) + (size_t)g.NS * (g.tb / 8) * 1024 + (size_t)(rwin + g.tb + (f16 ? rwin : 0)) * 4 +
            16 + 8 * (size_t)(3 * g.NS + 1) + 1024;
 }
 
@@ -338,11 +340,11 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.P = th * g.V;
     g.T = (int)((N + g.P - 1) / g.P);
     // tensor cores: stages of 32 rows where the block allows (one tensor-map box per stage, 64 KB
-    // at 256 threads, two of them in shared memory), else 16 rows in five stages
+    // at 256 threads, three of them in shared memory), else 16 rows in five stages
     const int tc_rs = (g.tc && p.time_block % 32 == 0) ? 32 : 16;
     g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
     g.NS = p.stages ? p.stages : g.tc ? (g.RS >= 32 ? 2 : 5) : 3;
-    g.ctas = g.tc ? 1 : p.ctas_per_sm ? p.ctas_per_sm : 2;  // tensor memory: one CTA per SM
+    g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 2;
     g.ralign = g.tc ? g.RS : 1;
     int sms = device_sms();
     if (sms <= 0) sms = 152;
@@ -374,6 +376,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.npar = npar_for(g.tb);
     g.nblocks = g.tb ? (p.max_steps + g.tb - 1) / g.tb : 0;
     g.ub = 0;
+    g.near = 0;
     g.cmax = 0;
     g.rwin = g.R;
     g.br0.clear();
@@ -405,7 +408,8 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         if (g.ralign > 1) g.R = (g.R + g.ralign - 1) / g.ralign * g.ralign;
         // Block-long update units need every tile's unit resident at once: allow them when the
         // tiles are at most a quarter of the SMs, so at least three quarters keep streaming.
-        g.ub = !(p.flags & FD_FLAG_STEP_UPDATES) && (int64_t)g.T * 4 <= sms;
+        // (the tensor-core kernels have none)
+        g.ub = !(p.flags & FD_FLAG_STEP_UPDATES) && !g.tc && (int64_t)g.T * 4 <= sms;
         g.cmax = g.ub ? std::max(1, 128 / g.tb) : 0;
         int64_t cmaxb = 1, rwin = g.R;
         for (int ip = 0; ip < nprob; ++ip)
@@ -415,7 +419,11 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
                 cmaxb = std::max(cmaxb, Cb);
                 rwin = std::max(rwin, Rb);
             }
-        g.maxC = (int)cmaxb;
+        // Near units: with per-step update units and blocks of 16 or more, the previous block's
+        // rows enter each step through one partial row (after the far chunks') instead of as
+        // TB head lags read by every step's update
+        g.near = !g.ub && g.tb >= 16;
+        g.maxC = (int)cmaxb + g.near;
         g.rwin = (int)rwin;
     }
     g.pitch = (int64_t)align_up((size_t)N * g.sh, kAlign);
@@ -424,6 +432,11 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = !g.hring_sep ? g.cap : g.tb ? 2 * g.tb : g.head + 1;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
+    if (g.tc) {  // each CTA allocates P/128 x tb tensor-memory columns (a power of two) of 512
+        int cols = 32;
+        while (cols < (g.P / 128) * g.tb) cols *= 2;
+        g.ctas = std::max(1, std::min(g.ctas, 512 / cols));
+    }
     g.smem = g.tc ? smem_bytes_tc(g, g.rwin, p.hist_dtype == FD_F16) : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
 }
 
@@ -442,7 +455,7 @@ inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
     if (b < g.nblocks) {
         int64_t Rb, Cb;
         block_chunks(p, g, b, Rb, Cb);
-        far = (int64_t)g.T * Cb;
+        far = (int64_t)g.T * (Cb + g.near);  // far chunks, then the near units
     }
     return far + (b >= 1 ? (int64_t)g.T * (g.ub ? 1 : g.tb) : 0);
 }
@@ -468,7 +481,9 @@ int64_t blocked_stream_rows(const fd_problem &p, const Geo &g, int64_t *head_row
     if (!g.ub)
         for (int64_t k = 0; k < p.max_steps; ++k) {
             const int64_t nb = (p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(p.mem_L, k) : k;
-            hd += std::min<int64_t>(k - (k / tb) * tb + tb, nb);
+            const int64_t t = k - (k / tb) * tb;
+            hd += std::min<int64_t>(g.near ? t : t + tb, nb);
+            if (g.near && t == 0) hd += std::min<int64_t>(tb, k);  // the near unit's rows, once per block
         }
     if (head_rows) *head_rows = hd;
     return st + hd;
@@ -798,6 +813,7 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.ub = g.ub;
     I.cmax = g.cmax;
     I.ralign = g.ralign;
+    I.near = g.near;
     I.tmap = L.tmap;
     if (g.tc) {  // tensor-memory columns: P/128 point blocks of tb FP32 accumulators, a power of two
         int cols = 32;
@@ -1319,6 +1335,7 @@ int fd_get_geometry(fd_handle *h, fd_geometry *g)
     g->time_block = h->g.tb;
     g->block_updates = h->g.ub;
     g->far_tensor_cores = h->g.tc;
+    g->smem_bytes = (int64_t)h->g.smem;
     g->head_rows_total = 0;
     g->stream_rows_total = h->g.tb ? blocked_stream_rows(h->p, h->g, &g->head_rows_total) : rows;
     return FD_OK;
@@ -1642,6 +1659,7 @@ int fd_batch_get_geometry(fd_batch *b, int i, fd_geometry *g)
     g->time_block = q.tb;
     g->block_updates = q.ub;
     g->far_tensor_cores = q.tc;
+    g->smem_bytes = (int64_t)b->smem;
     return FD_OK;
 }
 

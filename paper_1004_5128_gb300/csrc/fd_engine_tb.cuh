@@ -43,7 +43,7 @@ namespace fdk {
 
 struct UnitTB {
     int valid, inst, b, tile, chunk, C, r0, r1;
-    int fix;  // 0: far unit; 1: update unit of step k
+    int fix;  // 0: far unit; 1: update unit of step k; 2: block-long update unit; 3: near unit
     int k;
 };
 
@@ -152,7 +152,8 @@ template <int TB> __device__ __forceinline__ int far_chunks(const Inst &I, int b
     return max(1, (rhi - far_origin<TB>(I, b) + Rb - 1) / Rb);
 }
 
-// TC: the far units run on the tensor cores (BF16 history only; CTAs of at most 256 threads).
+// TC: the far units run on the tensor cores (BF16 or FP16 history; CTAs of at most 256 threads;
+// one update unit per step and tile).
 template <int TB, bool ADJ, class TH = float, bool TC = false>
 __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Launch L)
 {
@@ -177,19 +178,23 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
     const int WS = (L.rmax + TB + 7) & ~3;                                          // copy stride
     // the stage ring also holds a block-long update unit's sums and its tile's u^k, u^{k+1}:
     // at least TB x PLANES + 2 rows of FP32 float4 columns
-    const size_t ring_bytes = max((size_t)NS * RS * row_bytes, (size_t)(TB * PLANES + 2) * nthr * 16);
+    // (the tensor-core kernels have no block-long update units: their ring holds the stages only)
+    const size_t ring_bytes =
+        TC ? (size_t)NS * RS * row_bytes : max((size_t)NS * RS * row_bytes, (size_t)(TB * PLANES + 2) * nthr * 16);
     float *psw = reinterpret_cast<float *>(smem + ring_bytes);  // psi window
     float *psw2 = psw + 4 * WS;                                 // psi' window (ADJ)
     float *rsc = psw + PLANES * 4 * WS;                         // FP16: the far rows' scales
     uint64_t *bars = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(rsc + (F16 ? L.rmax : 0)) + 15) & ~uintptr_t(15));
     // Tensor-core path: after the stage ring (A operands, RS rows x P points each), a ring of NS
-    // coefficient blocks (B operands, hi and lo halves of TB/8 atoms each), the coefficient
+    // coefficient blocks (B operands, hi and lo halves side by side in TB/8 atoms), the coefficient
     // window, and the barriers: full (bulk copies landed), empty (the MMAs that read a slot are
     // done), bfull (coefficients written), done (all MMAs of a unit).
-    constexpr int BHALF = (TB / 8) * 1024;  // one half (hi or lo) of a coefficient block
+    // one coefficient block: TB/8 atoms of 8 steps x 64 K elements, hi halves at K 0..RS-1 and
+    // lo halves at K RS..2RS-1 of the same rows (RS <= 32)
+    constexpr int BBLK = (TB / 8) * 1024;
     unsigned char *bring = smem + ((ring_bytes + 1023) & ~(size_t)1023);
-    float *win = reinterpret_cast<float *>(bring + (size_t)NS * 2 * BHALF);
+    float *win = reinterpret_cast<float *>(bring + (size_t)NS * BBLK);
     float *wsc = win + L.rmax + TB;  // FP16: the unit's row scales
     if (TC)
         bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(wsc + (F16 ? L.rmax : 0)) + 15) & ~uintptr_t(15));
@@ -287,12 +292,32 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     } else {
                         f = (local < F1) ? local : local - Tu;
                     }
+                } else if (I.near && gb * TB < I.ksteps && local >= (L.g_off[g + 1] - L.g_off[g]) - I.T) {
+                    // near unit of block gb (the group's last T units): the previous block's rows
+                    // for every step of block gb, once block gb-1's updates of the tile are done
+                    const int kb = gb * TB;
+                    if (kb >= k_end) continue;  // block starts at or after the launch's end
+                    U.fix = 3;
+                    U.b = gb;
+                    U.tile = (int)(local - ((L.g_off[g + 1] - L.g_off[g]) - I.T));
+                    U.C = far_chunks<TB>(I, gb);
+                    U.chunk = U.C;  // its partial rows follow the far chunks'
+                    U.r0 = max(0, kb - TB);
+                    U.r1 = kb;
+                    U.k = 0;
+                    if (kb - L.k0 > 0) {
+                        const int w = wait_until(&I.done[U.tile], (unsigned)(kb - L.k0), L, 512);
+                        if (w < 0) note_failure(L, 12, gb, U.tile, kb - L.k0, ld_acquire(&I.done[U.tile]), L.k0, 0);
+                        if (w <= 0) ok = 0;
+                    }
+                    break;
                 } else {
                     int sseg = 0;  // segment s: far slice s, then the T update units of step s
                     const int Ts = Tu / TB;
-                    while (sseg + 1 < TB && (long long)(sseg + 1) * Ts + (long long)(sseg + 1) * F / TB <= local) ++sseg;
-                    const long long fs0 = (long long)sseg * F / TB;
-                    const long long fsn = (long long)(sseg + 1) * F / TB - fs0;  // far units in slice s
+                    const long long F0 = F - (I.near && gb * TB < I.ksteps ? I.T : 0);  // far units proper
+                    while (sseg + 1 < TB && (long long)(sseg + 1) * Ts + (long long)(sseg + 1) * F0 / TB <= local) ++sseg;
+                    const long long fs0 = (long long)sseg * F0 / TB;
+                    const long long fsn = (long long)(sseg + 1) * F0 / TB - fs0;  // far units in slice s
                     const long long off = local - ((long long)sseg * Ts + fs0);
                     if (off >= fsn) {  // update unit: block gb-1, step s
                         const int k = (gb - 1) * TB + sseg;
@@ -458,7 +483,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                             if (!wait_bar(&full[slot], ph, s) || !wait_bar(&bfull[slot], ph, s)) break;
                             tc::fence_after();
                             const uint32_t a0 = tc::saddr(stages + (size_t)slot * RS * row_bytes);
-                            const uint32_t bh = tc::saddr(bring + (size_t)slot * 2 * BHALF), bl = bh + BHALF;
+                            const uint32_t bh = tc::saddr(bring + (size_t)slot * BBLK), bl = bh + (uint32_t)(RS * 2);
                             for (int m = 0; m < MB; ++m)
                                 for (int kk = 0; kk < RS / 16; ++kk) {
                                     // A: points 128m.., rows 16kk..; atoms of 64 points are RS*128
@@ -482,7 +507,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     for (int s = 0; s < nst; ++s) {
                         const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
                         if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
-                        unsigned char *bh = bring + (size_t)slot * 2 * BHALF;
+                        unsigned char *bh = bring + (size_t)slot * BBLK;
                         for (int e = me; e < TB * RS; e += nb) {
                             const int t = e / RS, i = e - t * RS;
                             const int r = r0 + s * RS + i;
@@ -496,10 +521,10 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                                 hi = __float2bfloat16_rn(c);
                                 lo = __float2bfloat16_rn(c - __bfloat162float(hi));
                             }
-                            const int row = t & 7;
-                            const int off = (t >> 3) * 1024 + row * 128 + (((i >> 3) ^ row) << 4) + (i & 7) * 2;
-                            *reinterpret_cast<TH *>(bh + off) = hi;
-                            *reinterpret_cast<TH *>(bh + BHALF + off) = lo;
+                            const int row = t & 7, base = (t >> 3) * 1024 + row * 128;
+                            auto off = [&](int kq) { return base + (((kq >> 3) ^ row) << 4) + (kq & 7) * 2; };
+                            *reinterpret_cast<TH *>(bh + off(i)) = hi;
+                            *reinterpret_cast<TH *>(bh + off(RS + i)) = lo;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(&bfull[slot])) : "memory");
@@ -1155,7 +1180,62 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
             return true;
         };
 
-        if (U.fix == 2) {
+        if (U.fix == 3) {
+            // ======================= near unit: the previous block's rows for every step of block b
+            // N_t = sum over rows r = kb-TB .. kb-1 (oldest first) of w_{kb+t}(kb+t-r) delta^r, from
+            // the FP32 rows: psi (short memory: 0 beyond the window; adaptive memory: the settled
+            // weight g(m) up to the step's e(k), psi beyond).  Written as partial row C of block b
+            // and counted like a far chunk, so each step's update reads one row for these lags
+            // instead of TB.  The weights are staged in the idle stage ring.
+            const int r0 = U.r0, r1 = U.r1, mlo = kb - r1 + 1;
+            float *spsi = reinterpret_cast<float *>(stages), *sgw = spsi + 2 * TB;
+            const float *gwf = reinterpret_cast<const float *>(I.gw);
+            for (int e = tid; e < 2 * TB; e += nthr) {
+                const int m = mlo + e;
+                const float c = (I.mem_mode == 1 && m > I.mem_L) ? 0.f : psi[m];
+                spsi[e] = c;
+                sgw[e] = gwf ? gwf[m] : c;
+            }
+            if (tid < TB) s_ek[tid] = (gwf && kb + tid < I.ksteps) ? settled_end(I, kb + tid) : 0x7fffffff;
+            __syncthreads();
+            float2 acc[TB][2];
+#pragma unroll
+            for (int t = 0; t < TB; ++t) acc[t][0] = acc[t][1] = make_float2(0.f, 0.f);
+            for (int r = r0; r < r1; r += 8) {
+                float4 x[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    x[i] = (r + i < r1 && j0 < I.N) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (r + i >= r1) continue;
+#pragma unroll
+                    for (int t = 0; t < TB; ++t) {
+                        const int m = kb + t - (r + i);
+                        const float c = (gwf && m <= s_ek[t]) ? sgw[m - mlo] : spsi[m - mlo];
+                        const float2 c2 = make_float2(c, c);
+                        acc[t][0] = __ffma2_rn(c2, make_float2(x[i].x, x[i].y), acc[t][0]);
+                        acc[t][1] = __ffma2_rn(c2, make_float2(x[i].z, x[i].w), acc[t][1]);
+                    }
+                }
+            }
+            if (j0 < I.N) {
+#pragma unroll
+                for (int t = 0; t < TB; ++t)
+                    if (kb + t < I.ksteps)
+                        *reinterpret_cast<float4 *>(prow(C, t, 0) + j0) =
+                            make_float4(acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
+            }
+            // the ring is filled by bulk copies again: order this thread's accesses before them;
+            // then a CTA barrier and one release add, as for a far chunk
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
+            continue;
+        }
+
+        if constexpr (!TC) if (U.fix == 2) {
             // ============================ block-long update unit: every step of block b, this tile
             // The block's steps run in order on this CTA.  The memory sum of step kb+t is the
             // running sum of the block's far chunks, then (adaptive memory) the tail rows below
@@ -1321,9 +1401,11 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
         // partials by chunk, then lags hk .. 1.
         if (tid < 32) {  // the two waits run in parallel lanes
             int ok = 1;
-            if (tid == 0) {
-                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C), L, 512);
-                if (w < 0) note_failure(L, 3, k, tile, arrive_target(b, C), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
+            if (tid == 0) {  // the far chunks and, with near units, the near partial
+                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C + I.near), L, 512);
+                if (w < 0)
+                    note_failure(L, 3, k, tile, arrive_target(b, C + I.near), ld_acquire(&I.arrive[par * I.T + tile]),
+                                 L.k0, 0);
                 ok = w > 0;
             }
             if (tid == 1 && rel > 1) {
@@ -1338,7 +1420,10 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
         if (!s_ok) break;
 
         const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
-        const int hk = min(t + TB, nb);  // head: lags 1 .. min(k-kb+T, n_base(k)), descending
+        // head: lags 1 .. min(k-kb+T, n_base(k)), descending; with a near unit only the block's
+        // own rows, lags 1 .. min(k-kb, n_base(k)) (the near partial holds the previous block's)
+        const int hk = I.near ? min(t, nb) : min(t + TB, nb);
+        const int CP = C + I.near;  // partial rows to sum
         auto hrow = [&](int m) -> const float * { return hrow_at(k - m); };
         float H[V], H2[V], d[V];
 #pragma unroll
@@ -1348,7 +1433,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
             // its loads are all it does before the halo wait)
             constexpr int G = ADJ ? 4 : TC ? 16 : 8;
             int c = 0;
-            for (; c + G <= C; c += G) {
+            for (; c + G <= CP; c += G) {
                 float4 w[G], w2[ADJ ? G : 1];
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
@@ -1369,7 +1454,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     }
                 }
             }
-            for (; c < C; ++c) {
+            for (; c < CP; ++c) {
                 const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 0) + j0));
                 H[0] += w.x;
                 H[1] += w.y;

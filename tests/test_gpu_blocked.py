@@ -37,7 +37,9 @@ def test_blocked_matches_oracle(tb, bc, mode, L, step_updates):
 def test_block_updates_equal_step_updates_bitwise(tb, chunk, mode, L):
     """With the same far chunks (chunk rows at least the block's rows over its chunk limit), the
     block-long units sum each step's terms in the per-step units' order: identical bits, in
-    one launch and in launches that start inside blocks."""
+    one launch and in launches that start inside blocks.  With blocks of 16 the per-step units
+    take the previous block's rows from a near unit's partial sum, a different grouping: the
+    two then agree to rounding, and each kind is split-invariant to the bit."""
     p = ragged(synth.BC_NOFLUX, mode, L)
     outs = []
     for su in (False, True):
@@ -48,8 +50,11 @@ def test_block_updates_equal_step_updates_bitwise(tb, chunk, mode, L):
         for n in (37, 5, 101, 1, 156):
             s.step(n)
         outs.append(s.run(0).cpu().numpy())
-    for x in outs[1:]:
-        assert np.array_equal(outs[0], x)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[2], outs[3])
+    if tb < 16:
+        assert np.array_equal(outs[0], outs[2])
+    else:
+        assert rel_inf(outs[0], outs[2]) < 1e-6
 
 
 def ragged_adaptive(a, rule, K=300, bc=synth.BC_NOFLUX):
@@ -75,7 +80,7 @@ def test_blocked_adaptive_matches_oracle(tb, rule, a, step_updates):
 @pytest.mark.parametrize("a", [2, 10])
 def test_blocked_adaptive_block_updates_equal_step_updates_bitwise(tb, chunk, a):
     """Block-long and per-step update units sum the same terms in the same order, in one
-    launch and in launches that start inside blocks."""
+    launch and in launches that start inside blocks (blocks of 16: to rounding, as above)."""
     p = ragged_adaptive(a, synth.ADAPT_PAPER)
     outs = []
     for su in (False, True):
@@ -86,8 +91,11 @@ def test_blocked_adaptive_block_updates_equal_step_updates_bitwise(tb, chunk, a)
         for n in (37, 5, 101, 1, 156):
             s.step(n)
         outs.append(s.run(0).cpu().numpy())
-    for x in outs[1:]:
-        assert np.array_equal(outs[0], x)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[2], outs[3])
+    if tb < 16:
+        assert np.array_equal(outs[0], outs[2])
+    else:
+        assert rel_inf(outs[0], outs[2]) < 1e-6
 
 
 @pytest.mark.parametrize("step_updates", [False, True])
