@@ -207,7 +207,8 @@ int validate(const fd_problem *p)
         if (p->state_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan) return FD_ERR_UNSUPPORTED;
         if (!fdk::kernel_tb(p->time_block, adj, p->hist_dtype, tc)) return FD_ERR_UNSUPPORTED;
         if (tc) {  // point blocks of 128 (tile_threads 128 or 256), whole K slices of 16 rows per stage
-            if (p->tile_threads && p->tile_threads != 128 && p->tile_threads != 256) return FD_ERR_INVALID_ARG;
+            if (p->tile_threads && p->tile_threads != 128 && p->tile_threads != 256 && p->tile_threads != 512)
+                return FD_ERR_INVALID_ARG;
             if (p->stage_rows && ((p->stage_rows != 16 && p->stage_rows != 32) || p->time_block % p->stage_rows))
                 return FD_ERR_INVALID_ARG;
         }
@@ -234,6 +235,8 @@ struct Geo {
     int rwin;        // blocked: largest far chunk (rows), the coefficient window's length
     int nblocks;     // blocks of tb steps covering max_steps
     int tc;          // blocked, BF16 history: far units on the tensor cores
+    int halves;      // tensor cores: each CTA runs as two halves of `threads` threads
+    size_t smem_half;  // tensor cores: dynamic shared memory of one half
     int near;        // blocked, per-step update units, blocks of 16+: one near unit per (block, tile)
     int ralign;      // blocked: far chunks start on multiples of ralign rows (tensor cores: RS)
     int hring_sep;   // separate state-precision head ring
@@ -267,15 +270,16 @@ inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
            8 * (size_t)g.NS;
 }
 
-// Tensor-core blocked kernel: stage ring (RS rows x P points of BF16, at least the block-long
-// units' sums), 1 KB-aligned; NS coefficient blocks (tb/8 1 KB atoms, hi and lo halves side by
-// side); the
-// coefficient window; 3 NS + 1 barriers; 1 KB of slack to align the base.
-inline size_t smem_bytes_tc(const Geo &g, int rwin, bool f16)
+// Tensor-core blocked kernel, one half of a CTA: stage ring (RS rows x P points of 16-bit
+// history), 1 KB-aligned; NS coefficient blocks (tb/8 1 KB atoms, hi and lo halves side by side);
+// the coefficient window (and FP16 row scales); 3 NS + 1 barriers; rounded up to 1 KB.  The CTA
+// takes two halves plus 1 KB of slack to align the base.
+inline size_t smem_half_tc(const Geo &g, int rwin, bool f16)
 {
     const size_t ring = (size_t)g.NS * g.RS * g.threads * 8;  // no block-long update units
-    return align_up(ring, 1024) + (size_t)g.NS * (g.tb / 8) * 1024 + (size_t)(rwin + g.tb + (f16 ? rwin : 0)) * 4 +
-           16 + 8 * (size_t)(3 * g.NS + 1) + 1024;
+    return align_up(align_up(ring, 1024) + (size_t)g.NS * (g.tb / 8) * 1024 +
+                        (size_t)(rwin + g.tb + (f16 ? rwin : 0)) * 4 + 16 + 8 * (size_t)(3 * g.NS + 1),
+                    1024);
 }
 
 int device_sms()
@@ -335,20 +339,22 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         const int64_t need = (N + g.V - 1) / g.V;
         while (th > 64 && need <= th / 2) th /= 2;
     }
-    if (g.tc) th = (th >= 256) ? 256 : 128;  // point blocks of 128 lanes; four warps per lane quarter
+    // tensor cores: point blocks of 128, four warps per lane quarter, per half of a CTA
+    if (g.tc) th = (th >= 256) ? 256 : 128;
+    g.halves = g.tc ? 2 : 1;
     g.threads = th;
     g.P = th * g.V;
     g.T = (int)((N + g.P - 1) / g.P);
-    // tensor cores: stages of 32 rows where the block allows (one tensor-map box per stage, 64 KB
-    // at 256 threads, three of them in shared memory), else 16 rows in five stages
-    const int tc_rs = (g.tc && p.time_block % 32 == 0) ? 32 : 16;
+    // tensor cores: stages of 16 rows (32 where the block allows at 128 threads), as many as fit in
+    // 80 KB per half of a CTA (2 .. 5)
+    const int tc_rs = (g.tc && p.time_block % 32 == 0 && th <= 128) ? 32 : 16;
     g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
-    g.NS = p.stages ? p.stages : g.tc ? (g.RS >= 32 ? 2 : 5) : 3;
+    g.NS = p.stages ? p.stages : g.tc ? std::max(2, std::min(5, (80 << 10) / (g.RS * th * 8))) : 3;
     g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 2;
     g.ralign = g.tc ? g.RS : 1;
     int sms = device_sms();
     if (sms <= 0) sms = 152;
-    g.grid = sms * g.ctas;
+    g.grid = sms * g.ctas * g.halves;  // units are processed by grid (half-)CTAs
     g.cap = p.max_steps;
     // short memory keeps a ring of L+1 rows, unless the adjoint's recompute will read old rows
     // (the tensor-map copies of the tensor-core path take whole stages, so they keep every row)
@@ -377,6 +383,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.nblocks = g.tb ? (p.max_steps + g.tb - 1) / g.tb : 0;
     g.ub = 0;
     g.near = 0;
+    g.smem_half = 0;
     g.cmax = 0;
     g.rwin = g.R;
     g.br0.clear();
@@ -432,12 +439,13 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = !g.hring_sep ? g.cap : g.tb ? 2 * g.tb : g.head + 1;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
-    if (g.tc) {  // each CTA allocates P/128 x tb tensor-memory columns (a power of two) of 512
+    if (g.tc) {  // each half allocates P/128 x tb tensor-memory columns (a power of two) of 512
         int cols = 32;
         while (cols < (g.P / 128) * g.tb) cols *= 2;
-        g.ctas = std::max(1, std::min(g.ctas, 512 / cols));
+        g.ctas = std::max(1, std::min(g.ctas, 512 / (cols * g.halves)));
+        g.smem_half = smem_half_tc(g, g.rwin, p.hist_dtype == FD_F16);
     }
-    g.smem = g.tc ? smem_bytes_tc(g, g.rwin, p.hist_dtype == FD_F16) : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
+    g.smem = g.tc ? g.halves * g.smem_half + 1024 : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -896,7 +904,7 @@ int set_smem_attr(const void *fn, size_t smem)
 int resolve_grid(const void *fn, Geo &g)
 {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, g.threads, g.smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, g.threads * g.halves, g.smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return FD_ERR_CUDA;
     }
@@ -904,7 +912,7 @@ int resolve_grid(const void *fn, Geo &g)
     g.ctas = std::min(g.ctas, occ);
     int sms = device_sms();
     if (sms <= 0) return FD_ERR_CUDA;
-    g.grid = sms * g.ctas;
+    g.grid = sms * g.ctas * g.halves;
     return FD_OK;
 }
 
@@ -962,6 +970,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.stage_rows = h->g.RS;
     L.stages = h->g.NS;
     L.rmax = h->g.tb ? h->g.rwin : h->g.R;
+    L.smem_half = (int)h->g.smem_half;
     L.queue = h->ctrl.queue;
     L.err = h->ctrl.err;
     L.nonfinite = h->ctrl.nonfinite;
@@ -970,9 +979,10 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     CK(cudaMemsetAsync(h->ctrl.queue, 0, sizeof(unsigned long long), h->st));
     CK(cudaMemsetAsync(h->ctrl_zero_base, 0, h->ctrl_zero_bytes, h->st));
     const int64_t units = goff[g_end] - goff[g_begin];
-    const int grid = (int)std::min<int64_t>(h->g.grid, units);
+    const int hv = h->g.halves;
+    const int grid = (int)((std::min<int64_t>(h->g.grid, units) + hv - 1) / hv);
     void *args[] = {&L};
-    CK(cudaLaunchKernel(fn, dim3(grid), dim3(h->g.threads), args, h->g.smem, h->st));
+    CK(cudaLaunchKernel(fn, dim3(grid), dim3(h->g.threads * hv), args, h->g.smem, h->st));
     return FD_OK;
 }
 
@@ -1385,7 +1395,7 @@ struct fd_batch {
     std::vector<int2> ginfo;
     const void *kfn;
     int threads, RS, NS, grid, rmax, tb;
-    size_t smem;
+    size_t smem, smem_half;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
@@ -1426,7 +1436,8 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     b.rmax = 0;
     for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].tb ? b.g[i].rwin : b.g[i].R);
     b.tb = probs[0].time_block;
-    b.smem = b.g[0].tc ? smem_bytes_tc(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16)
+    b.smem_half = b.g[0].tc ? smem_half_tc(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16) : 0;
+    b.smem = b.g[0].tc ? b.g[0].halves * b.smem_half + 1024
              : b.tb    ? smem_bytes_tb(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16)
                        : smem_bytes(b.g[0], b.rmax);
     Carve c(ws);
@@ -1551,6 +1562,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         L.stage_rows = b->RS;
         L.stages = b->NS;
         L.rmax = b->rmax;
+        L.smem_half = (int)b->smem_half;
         L.queue = b->ctrl.queue;
         L.err = b->ctrl.err;
         L.nonfinite = b->ctrl.nonfinite;
@@ -1571,8 +1583,9 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         std::memset(&kp, 0, sizeof(kp));
         void *args[] = {&L};
         kp.func = (void *)b->kfn;
-        kp.gridDim = dim3((unsigned)std::min<long long>(b->grid, b->goff.back()));
-        kp.blockDim = dim3(b->threads);
+        const int hv = b->g[0].halves;
+        kp.gridDim = dim3((unsigned)((std::min<long long>(b->grid, b->goff.back()) + hv - 1) / hv));
+        kp.blockDim = dim3(b->threads * hv);
         kp.sharedMemBytes = (unsigned)b->smem;
         kp.kernelParams = args;
         if (cudaGraphCreate(&b->graph, 0) != cudaSuccess ||

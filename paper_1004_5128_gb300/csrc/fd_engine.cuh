@@ -149,6 +149,7 @@ struct Launch {
     int k_end;               // one past the last step of the launch (blocked kernel)
     int stage_rows, stages;
     int rmax;                // largest chunk (terms) over the launch's instances
+    int smem_half;           // tensor-core kernels: dynamic shared memory of each half of a CTA
     unsigned long long *queue;
     int *err;
     unsigned *nonfinite;

@@ -152,10 +152,22 @@ template <int TB> __device__ __forceinline__ int far_chunks(const Inst &I, int b
     return max(1, (rhi - far_origin<TB>(I, b) + Rb - 1) / Rb);
 }
 
-// TC: the far units run on the tensor cores (BF16 or FP16 history; CTAs of at most 256 threads;
-// one update unit per step and tile).
+// TC: the far units run on the tensor cores (BF16 or FP16 history; one update unit per step and
+// tile).
+// Shared state of one unit-processing CTA (the tensor-core kernels run two per CTA, see below).
+struct VShared {
+    Inst I;
+    UnitTB U;
+    int s_cur_inst, s_ok, s_ok2, s_pipe;
+    int s_abort, s_iss, s_mma;
+    float s_bnorm;       // FP16 tensor-core unit: power of two that scales its coefficients
+    int s_ek[32];        // adaptive memory: e(k) of the block's steps
+    float s_wmax[16];    // FP16 history: per-warp largest |delta| of a row
+    double s_dred[16][6];  // adjoint: per-warp gradient partials
+};
+
 template <int TB, bool ADJ, class TH = float, bool TC = false>
-__global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Launch L)
+__global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 {
     constexpr int PLANES = ADJ ? 2 : 1;
     constexpr int V = 4;  // four points per thread: a float4 of state, H4<TH> of history
@@ -163,15 +175,39 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
     constexpr bool F16 = std::is_same<TH, __half>::value;
     static_assert(!TC || (LOWP && !ADJ && TB % 16 == 0),
                   "tensor-core far units: BF16 or FP16 history, forward, blocks of a multiple of 16 steps");
-    const int tid = threadIdx.x;
-    const int nthr = blockDim.x;
+    // A kernel holding tensor memory runs one CTA per SM, so the tensor-core kernels split each
+    // CTA into two halves that work as independent CTAs: own claim loop, shared state and shared
+    // memory, own named barrier, half of the CTA's tensor memory.  While one half runs an update
+    // unit (latency-bound) the other keeps streaming far rows.
+    constexpr int HALVES = TC ? 2 : 1;
+    const int nthr = blockDim.x / HALVES;
+    const int half = threadIdx.x / nthr;
+    const int tid = threadIdx.x - half * nthr;
     const int RS = L.stage_rows, NS = L.stages;
     const int row_bytes = nthr * H4<TH>::BYTES;  // one history row of a tile in a stage
+    // CTA (half) barriers
+    auto csync = [&]() {
+        if (TC)
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(nthr) : "memory");
+        else
+            __syncthreads();
+    };
+    auto csync_or = [&](int pred) -> int {
+        if (!TC) return __syncthreads_or(pred);
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred pp, qq;\n\tsetp.ne.b32 pp, %1, 0;\n\t"
+            "bar.red.or.pred qq, %2, %3, pp;\n\tselp.u32 %0, 1, 0, qq;\n\t}"
+            : "=r"(r)
+            : "r"(pred), "r"(1 + half), "r"(nthr)
+            : "memory");
+        return (int)r;
+    };
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    // the tensor-core path's swizzled operands need 1 KB-aligned atoms
+    // the tensor-core path's swizzled operands need 1 KB-aligned atoms; each half has its region
     unsigned char *smem = smem_raw;
-    if (TC) smem += (1024u - (tc::saddr(smem_raw) & 1023u)) & 1023u;
+    if (TC) smem += ((1024u - (tc::saddr(smem_raw) & 1023u)) & 1023u) + (size_t)half * L.smem_half;
     unsigned char *stages = smem;
     // Coefficient window in four copies shifted by 0..3 elements, so that the TB coefficients
     // of any row are TB/4 aligned 16-byte loads: copy q holds w[i + q] at index i.
@@ -200,18 +236,21 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
         bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(wsc + (F16 ? L.rmax : 0)) + 15) & ~uintptr_t(15));
     uint64_t *full = bars, *empty = bars + NS, *bfull = bars + 2 * NS, *done_bar = bars + 3 * NS;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort, s_iss, s_mma;
-    __shared__ float s_bnorm;  // FP16 tensor-core unit: power of two that scales its coefficients
     // adaptive memory: bit j of gmask[lo] says w[lo + j] != 0 (the window of a four-row group);
     // the sparse loop reads the unshifted copy only, so the masks take the first shifted copy
     uint32_t *gmask = reinterpret_cast<uint32_t *>(psw + WS);
 
-    __shared__ Inst I;
-    __shared__ UnitTB U;
-    __shared__ int s_cur_inst, s_ok, s_ok2, s_pipe;
-    __shared__ int s_ek[TB];  // block-long unit, adaptive memory: e(k) of the block's steps
-    __shared__ double s_dred[ADJ ? 16 : 1][6];
-    __shared__ float s_wmax[F16 ? 16 : 1];  // FP16 history: per-warp largest |delta| of a row
+    static_assert(TB <= 32, "s_ek holds 32 steps");
+    __shared__ VShared vsh[HALVES];
+    VShared &VS = vsh[half];
+    Inst &I = VS.I;
+    UnitTB &U = VS.U;
+    int &s_cur_inst = VS.s_cur_inst, &s_ok = VS.s_ok, &s_ok2 = VS.s_ok2, &s_pipe = VS.s_pipe;
+    int &s_abort = VS.s_abort, &s_iss = VS.s_iss, &s_mma = VS.s_mma;
+    float &s_bnorm = VS.s_bnorm;
+    int *s_ek = VS.s_ek;
+    float *s_wmax = VS.s_wmax;
+    double(*s_dred)[6] = VS.s_dred;
 
     if (tid == 0) {
         if (TC) {
@@ -228,14 +267,14 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         s_cur_inst = -1;
     }
-    // tensor memory for the far accumulators: P/128 blocks of TB FP32 columns (tc_cols, a power
-    // of two), allocated once per CTA; the host keeps one CTA per SM
+    // tensor memory for the far accumulators: P/128 blocks of TB FP32 columns per half (tc_cols,
+    // a power of two), allocated once per CTA (one CTA per SM)
     const uint32_t tc_cols = TC ? (uint32_t)L.inst[0].tc_cols : 0u;
-    if (TC && tid < 32) tc::tmem_alloc(&s_tmem, tc_cols);
+    if (TC && threadIdx.x < 32) tc::tmem_alloc(&s_tmem, tc_cols * HALVES);
     if (TC) tc::fence_before();
     __syncthreads();
     if (TC) tc::fence_after();
-    const uint32_t tmem = TC ? s_tmem : 0u;
+    const uint32_t tmem = TC ? s_tmem + (uint32_t)half * tc_cols : 0u;
     uint32_t tc_use = 0, tc_done = 0;  // stages streamed and units finished by this CTA (TC)
 
     uint32_t n_issued = 0, n_used = 0;
@@ -278,7 +317,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     // units are about to finish instead of holding its SM through their tail;
                     // block gb's far units read rows up to block gb-2 only, so none of them
                     // waits for these updates.
-                    const long long F1 = min(F, (long long)max(0, (int)gridDim.x - Tu));
+                    const long long F1 = min(F, (long long)max(0, (int)gridDim.x * HALVES - Tu));
                     if (local >= F1 && local < F1 + Tu) {
                         const int kb1 = (gb - 1) * TB;
                         if (max(kb1, L.k0) >= min(kb1 + TB, k_end)) continue;  // no step in this launch
@@ -363,7 +402,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
             }
             U.valid = ok;
         }
-        __syncthreads();
+        csync();
         if (!U.valid) break;
 
         const int tile = U.tile, C = U.C, b = U.b, kb = b * TB;
@@ -426,7 +465,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         s_mma = 0;
                     }
                 }
-                __syncthreads();
+                csync();
                 if (F16) {
                     if (tid == 0) {
                         float m = 0.f;
@@ -435,7 +474,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         if (m > 0.f && isfinite(m)) frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
                         s_bnorm = ldexpf(1.f, max(-120, min(120, 14 - ex)));
                     }
-                    __syncthreads();
+                    csync();
                 }
                 const float bnorm = F16 ? s_bnorm : 1.f, binv = 1.f / bnorm;  // powers of two
                 auto give_up = [&](int site_s, uint64_t *bar) {
@@ -530,7 +569,8 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(&bfull[slot])) : "memory");
                     }
                 }
-                __syncthreads();
+                __syncwarp();  // warps 0 and 1: the other lanes wait for lane 0's loop
+                csync();
                 if (s_abort) {
                     // stop: wait (bounded) for the copies and MMAs already issued, then leave
                     if (tid == 32 && s_mma > 0) {
@@ -547,7 +587,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                             }
                         }
                     }
-                    __syncthreads();
+                    csync();
                     break;
                 }
                 tc_use += (uint32_t)nst;
@@ -571,7 +611,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     if (w < 0) note_failure(L, 10, b, tile, arrive_target(b, c0), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
                     if (w <= 0) atomicExch(&s_abort, 1);
                 }
-                __syncthreads();
+                csync();
                 if (s_abort) break;
                 // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. of point blocks
                 // m = w / 4, w / 4 + nwarp / 4, ...; each thread holds one point's TB sums
@@ -602,7 +642,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                 }
                 // CTA barrier, then one release add: cumulative over every thread's partial stores
                 tc::fence_before();
-                __syncthreads();
+                csync();
                 if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
                 continue;
             } else {
@@ -626,7 +666,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         if (ADJ) psw2[q * WS + i] = cut ? 0.f : reinterpret_cast<const float *>(I.dpsi)[lag];
                     }
                 }
-                __syncthreads();
+                csync();
                 // Adaptive memory: the settled weights are zero between medians (at least two of three
                 // lags in the far rows), so a four-row group multiplies only the lags its window holds.
                 if (sparse) {
@@ -635,14 +675,14 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         for (int j = 0; j < TB + 4; ++j) m |= (psw[lo + j] != 0.f ? 1u : 0u) << j;
                         gmask[lo] = m;
                     }
-                    __syncthreads();
+                    csync();
                 }
 
                 // FP16 history: the power-of-two scale of each far row on this tile
                 if (F16) {
                     for (int a = tid; a < nrow; a += nthr)
                         rsc[a] = __ldcg(I.hscale + (size_t)((r0 + a) % I.cap) * I.T + tile);
-                    __syncthreads();
+                    csync();
                 }
 
                 // accumulators as point pairs: one packed two-lane FMA (each lane an IEEE fmaf)
@@ -800,7 +840,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     }
                     // a stage that any thread gave up on stops the unit: nothing more is issued and
                     // the stage stays owed (n_used not advanced) for the bounded drain below
-                    if (__syncthreads_or(tmo)) {
+                    if (csync_or(tmo)) {
                         aborted = 1;
                         break;
                     }
@@ -811,7 +851,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     }
                 }
                 if (tid == 0) s_pipe = aborted || (ld_volatile(L.err) == ERR_PIPE);
-                __syncthreads();
+                csync();
                 if (s_pipe) {
                     if (tid == 0) {
                         const long long t0 = globaltimer();
@@ -837,7 +877,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                         if (w < 0) note_failure(L, 10, b, tile, arrive_target(b, c0), ld_acquire(&I.arrive[par * I.T + tile]), L.k0, 0);
                         s_ok = w > 0;
                     }
-                    __syncthreads();
+                    csync();
                     if (!s_ok) break;
                 }
                 if (j0 < I.N) {
@@ -859,7 +899,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     }
                 }
                 // CTA barrier, then one release add: cumulative over every thread's partial stores
-                __syncthreads();
+                csync();
                 if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
                 continue;
             }
@@ -920,7 +960,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                 ok = __all_sync(0xffffffffu, ok);
                 if (tid == 0) s_ok2 = ok;
             }
-            __syncthreads();
+            csync();
             if (!s_ok2) return false;
             const float *uk = reinterpret_cast<const float *>(I.ubuf[k & 1]);
             float *un = reinterpret_cast<float *>(I.ubuf[(k + 1) & 1]);
@@ -1134,7 +1174,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
                 if ((tid & 31) == 0) s_wmax[tid >> 5] = amax;
-                __syncthreads();
+                csync();
                 float m = 0.f;
                 for (int w = 0; w < (nthr + 31) / 32; ++w) m = fmaxf(m, s_wmax[w]);
                 int e = 0;
@@ -1162,7 +1202,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
             // only after that step's release, and the fence covers all of the thread's earlier
             // stores.
             if (!own || last) fence_proxy_async_global();
-            __syncthreads();
+            csync();
             if (tid == 0) {
                 if (ADJ) {  // per-tile gradient partials, one writer per tile, in step order
                     double *dd = I.dots + (size_t)tile * 8;
@@ -1197,40 +1237,43 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                 sgw[e] = gwf ? gwf[m] : c;
             }
             if (tid < TB) s_ek[tid] = (gwf && kb + tid < I.ksteps) ? settled_end(I, kb + tid) : 0x7fffffff;
-            __syncthreads();
-            float2 acc[TB][2];
+            csync();
+            constexpr int TG = TB < 16 ? TB : 16;  // steps per pass (register budget)
+            for (int tg = 0; tg < TB; tg += TG) {
+                float2 acc[TG][2];
 #pragma unroll
-            for (int t = 0; t < TB; ++t) acc[t][0] = acc[t][1] = make_float2(0.f, 0.f);
-            for (int r = r0; r < r1; r += 8) {
-                float4 x[8];
+                for (int t = 0; t < TG; ++t) acc[t][0] = acc[t][1] = make_float2(0.f, 0.f);
+                for (int r = r0; r < r1; r += 8) {
+                    float4 x[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    x[i] = (r + i < r1 && j0 < I.N) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
-                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int i = 0; i < 8; ++i)
+                        x[i] = (r + i < r1 && j0 < I.N) ? __ldcg(reinterpret_cast<const float4 *>(hrow_at(r + i)))
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (r + i >= r1) continue;
+                    for (int i = 0; i < 8; ++i) {
+                        if (r + i >= r1) continue;
 #pragma unroll
-                    for (int t = 0; t < TB; ++t) {
-                        const int m = kb + t - (r + i);
-                        const float c = (gwf && m <= s_ek[t]) ? sgw[m - mlo] : spsi[m - mlo];
-                        const float2 c2 = make_float2(c, c);
-                        acc[t][0] = __ffma2_rn(c2, make_float2(x[i].x, x[i].y), acc[t][0]);
-                        acc[t][1] = __ffma2_rn(c2, make_float2(x[i].z, x[i].w), acc[t][1]);
+                        for (int t = 0; t < TG; ++t) {
+                            const int m = kb + tg + t - (r + i);
+                            const float c = (gwf && m <= s_ek[tg + t]) ? sgw[m - mlo] : spsi[m - mlo];
+                            const float2 c2 = make_float2(c, c);
+                            acc[t][0] = __ffma2_rn(c2, make_float2(x[i].x, x[i].y), acc[t][0]);
+                            acc[t][1] = __ffma2_rn(c2, make_float2(x[i].z, x[i].w), acc[t][1]);
+                        }
                     }
                 }
-            }
-            if (j0 < I.N) {
+                if (j0 < I.N) {
 #pragma unroll
-                for (int t = 0; t < TB; ++t)
-                    if (kb + t < I.ksteps)
-                        *reinterpret_cast<float4 *>(prow(C, t, 0) + j0) =
-                            make_float4(acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
+                    for (int t = 0; t < TG; ++t)
+                        if (kb + tg + t < I.ksteps)
+                            *reinterpret_cast<float4 *>(prow(C, tg + t, 0) + j0) =
+                                make_float4(acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
+                }
             }
             // the ring is filled by bulk copies again: order this thread's accesses before them;
             // then a CTA barrier and one release add, as for a far chunk
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
+            csync();
             if (tid == 0) atom_add_acq_rel(&I.arrive[par * I.T + tile], 1u);
             continue;
         }
@@ -1262,7 +1305,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                 ok = __all_sync(0xffffffffu, ok);
                 if (tid == 0) s_ok = ok;
             }
-            __syncthreads();
+            csync();
             if (!s_ok) break;
             float4 *Hs = reinterpret_cast<float4 *>(stages);  // [TB][nthr] sums of the block's steps
             float4 *Hs2 = Hs + TB * nthr;                      // psi' sums (adjoint)
@@ -1343,7 +1386,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
                     if (j < I.N) us[(kf & 1) * I.P + (j - t0p)] = own[v];
                 }
             }
-            __syncthreads();
+            csync();
             bool stop = false;
             for (int t = t0; t < t1; ++t) {
                 const int k = kb + t;
@@ -1416,7 +1459,7 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
             ok = __all_sync(0xffffffffu, ok);
             if (tid == 0) s_ok = ok;
         }
-        __syncthreads();
+        csync();
         if (!s_ok) break;
 
         const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
@@ -1536,10 +1579,10 @@ __global__ void __launch_bounds__(TC ? 256 : 512, 1) engine_tb_kernel(const Laun
     // CTA's tensor-core work has completed (a failed unit waits for its MMAs before it exits)
     if (TC) {
         tc::fence_before();
-        __syncthreads();
-        if (tid < 32) {
+        __syncthreads();  // both halves
+        if (threadIdx.x < 32) {
             tc::fence_after();
-            tc::tmem_dealloc(tmem, tc_cols);
+            tc::tmem_dealloc(s_tmem, tc_cols * HALVES);
         }
     }
 }
