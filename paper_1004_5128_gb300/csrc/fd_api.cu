@@ -165,7 +165,8 @@ inline int4 full_step(int64_t k) { return make_int4((int)k, 0, 1, 0); }
 // tensor cores unless FD_FLAG_FMA_FAR asks for the CUDA-core loop.
 inline bool tc_far(const fd_problem &p)
 {
-    return (p.time_block == 16 || p.time_block == 32) && (p.hist_dtype == FD_BF16 || p.hist_dtype == FD_F16) &&
+    return (p.time_block == 16 || p.time_block == 32 || p.time_block == 64) &&
+           (p.hist_dtype == FD_BF16 || p.hist_dtype == FD_F16) &&
            !(p.flags & FD_FLAG_FMA_FAR) && !(p.flags & FD_FLAG_KEEP_TAPE);
 }
 
@@ -202,8 +203,9 @@ int validate(const fd_problem *p)
     if (adj && !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)) return FD_ERR_UNSUPPORTED;
     if (p->time_block) {
         const bool tc = tc_far(*p);
-        if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16 && !(tc && p->time_block == 32))
-            return p->time_block == 32 ? FD_ERR_UNSUPPORTED : FD_ERR_INVALID_ARG;
+        if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16 &&
+            !(tc && (p->time_block == 32 || p->time_block == 64)))
+            return (p->time_block == 32 || p->time_block == 64) ? FD_ERR_UNSUPPORTED : FD_ERR_INVALID_ARG;
         if (p->state_dtype != FD_F32 || p->accum_dtype != FD_F32 || kahan) return FD_ERR_UNSUPPORTED;
         if (!fdk::kernel_tb(p->time_block, adj, p->hist_dtype, tc)) return FD_ERR_UNSUPPORTED;
         if (tc) {  // point blocks of 128 (tile_threads 128 or 256), whole K slices of 16 rows per stage
@@ -237,6 +239,7 @@ struct Geo {
     int tc;          // blocked, BF16 history: far units on the tensor cores
     int halves;      // tensor cores: each CTA runs as two halves of `threads` threads
     size_t smem_half;  // tensor cores: dynamic shared memory of one half
+    int tmem_cols;     // tensor cores: tensor-memory columns a CTA allocates (at most 512)
     int near;        // blocked, per-step update units, blocks of 16+: one near unit per (block, tile)
     int ralign;      // blocked: far chunks start on multiples of ralign rows (tensor cores: RS)
     int hring_sep;   // separate state-precision head ring
@@ -339,17 +342,21 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         const int64_t need = (N + g.V - 1) / g.V;
         while (th > 64 && need <= th / 2) th /= 2;
     }
-    // tensor cores: point blocks of 128, four warps per lane quarter, per half of a CTA
-    if (g.tc) th = (th >= 256) ? 256 : 128;
+    // tensor cores: point blocks of 128, four warps per lane quarter, per half of a CTA; blocks of
+    // 64 steps take 128 threads, so that both halves' accumulators fit the 512 tensor-memory columns
+    if (g.tc) th = (th >= 256 && p.time_block <= 32) ? 256 : 128;
     g.halves = g.tc ? 2 : 1;
     g.threads = th;
     g.P = th * g.V;
     g.T = (int)((N + g.P - 1) / g.P);
     // tensor cores: stages of 16 rows (32 where the block allows at 128 threads), as many as fit in
-    // 80 KB per half of a CTA (2 .. 5)
+    // 88 KB per half of a CTA (2 .. 5)
     const int tc_rs = (g.tc && p.time_block % 32 == 0 && th <= 128) ? 32 : 16;
     g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
-    g.NS = p.stages ? p.stages : g.tc ? std::max(2, std::min(5, (80 << 10) / (g.RS * th * 8))) : 3;
+    // (a tensor-core stage: RS rows of 16-bit history plus its coefficient block)
+    g.NS = p.stages ? p.stages
+           : g.tc   ? std::max(2, std::min(5, (88 << 10) / (g.RS * th * 8 + (p.time_block / 8) * 1024)))
+                    : 3;
     g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 2;
     g.ralign = g.tc ? g.RS : 1;
     int sms = device_sms();
@@ -439,9 +446,11 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_cap = !g.hring_sep ? g.cap : g.tb ? 2 * g.tb : g.head + 1;
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
+    g.tmem_cols = 0;
     if (g.tc) {  // each half allocates P/128 x tb tensor-memory columns (a power of two) of 512
         int cols = 32;
         while (cols < (g.P / 128) * g.tb) cols *= 2;
+        g.tmem_cols = cols * g.halves;
         g.ctas = std::max(1, std::min(g.ctas, 512 / (cols * g.halves)));
         g.smem_half = smem_half_tc(g, g.rwin, p.hist_dtype == FD_F16);
     }
@@ -1011,6 +1020,7 @@ static int prepare(const fd_problem *p, Sched &s, Geo &g, size_t *bytes, Layout 
     if (rc) return rc;
     build_schedule(*p, p->max_steps, s);
     make_geo(*p, s, 0, g);
+    if (g.tmem_cols > 512) return FD_ERR_INVALID_ARG;  // a CTA's tensor memory holds 512 columns
     Carve c(ws);
     Ctrl cc = carve_ctrl(c);
     Layout L;
@@ -1428,6 +1438,7 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     for (int i = 0; i < count; ++i) {
         build_schedule(probs[i], probs[i].max_steps, b.s[i]);
         make_geo(probs[i], b.s[i], threads, b.g[i]);
+        if (b.g[i].tmem_cols > 512) return FD_ERR_INVALID_ARG;  // a CTA's tensor memory holds 512 columns
         tiles += b.g[i].T;
     }
     b.threads = threads;

@@ -161,7 +161,7 @@ struct VShared {
     int s_cur_inst, s_ok, s_ok2, s_pipe;
     int s_abort, s_iss, s_mma;
     float s_bnorm;       // FP16 tensor-core unit: power of two that scales its coefficients
-    int s_ek[32];        // adaptive memory: e(k) of the block's steps
+    int s_ek[64];        // adaptive memory: e(k) of the block's steps
     float s_wmax[16];    // FP16 history: per-warp largest |delta| of a row
     double s_dred[16][6];  // adjoint: per-warp gradient partials
 };
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // the sparse loop reads the unshifted copy only, so the masks take the first shifted copy
     uint32_t *gmask = reinterpret_cast<uint32_t *>(psw + WS);
 
-    static_assert(TB <= 32, "s_ek holds 32 steps");
+    static_assert(TB <= 64, "s_ek holds 64 steps");
     __shared__ VShared vsh[HALVES];
     VShared &VS = vsh[half];
     Inst &I = VS.I;

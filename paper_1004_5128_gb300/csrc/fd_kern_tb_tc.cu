@@ -1,5 +1,5 @@
 // Temporally blocked kernels whose far units run on the tensor cores (tcgen05): BF16 or FP16
-// (row-tile scaled) history, FP32 state and accumulation, forward only, blocks of 16 and 32 steps.
+// (row-tile scaled) history, FP32 state and accumulation, forward only, blocks of 16, 32 and 64 steps.
 #include "fd_kernels.h"
 
 namespace fdk {
@@ -9,6 +9,7 @@ const void *kernel_tb_tc(int tb, int hist)
         switch (tb) {
         case 16: return (const void *)engine_tb_kernel<16, false, __nv_bfloat16, true>;
         case 32: return (const void *)engine_tb_kernel<32, false, __nv_bfloat16, true>;
+        case 64: return (const void *)engine_tb_kernel<64, false, __nv_bfloat16, true>;
         default: return nullptr;
         }
     }
@@ -16,6 +17,7 @@ const void *kernel_tb_tc(int tb, int hist)
         switch (tb) {
         case 16: return (const void *)engine_tb_kernel<16, false, __half, true>;
         case 32: return (const void *)engine_tb_kernel<32, false, __half, true>;
+        case 64: return (const void *)engine_tb_kernel<64, false, __half, true>;
         default: return nullptr;
         }
     }

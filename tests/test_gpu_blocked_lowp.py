@@ -105,7 +105,7 @@ TC_MODES = [("full", synth.MEM_FULL, 0, 0), ("short40", synth.MEM_SHORT, 40, 0),
 
 
 @pytest.mark.parametrize("step_updates", [False, True])
-@pytest.mark.parametrize("tb,rs,threads", [(16, 16, 256), (32, 16, 256), (32, 32, 128), (16, 16, 128)])
+@pytest.mark.parametrize("tb,rs,threads", [(16, 16, 256), (32, 16, 256), (32, 32, 128), (16, 16, 128), (64, 16, 128)])
 @pytest.mark.parametrize("name,mode,L,a", TC_MODES, ids=[m[0] for m in TC_MODES])
 @pytest.mark.parametrize("hist", ["bf16", "f16"])
 def test_tensor_core_far_units_match_oracle_and_cuda_cores(hist, name, mode, L, a, tb, rs, threads, step_updates):

@@ -127,11 +127,13 @@ def test_time_block_validation():
     assert taped > L.fd_workspace_bytes(make_problem(p, keep_tape=True)) > 0
     # BF16 / FP16 history blocks forward; BF16 with blocks of 16 or 32 on the tensor cores
     for ok in (dict(time_block=8, hist="bf16"), dict(time_block=16, hist="f16"),
-               dict(time_block=32, hist="bf16"), dict(time_block=16, hist="bf16", fma_far=True)):
+               dict(time_block=32, hist="bf16"), dict(time_block=64, hist="f16"),
+               dict(time_block=16, hist="bf16", fma_far=True)):
         assert L.fd_workspace_bytes(make_problem(p, **ok)) > 0
     for bad, code in ((dict(time_block=5), L.FD_ERR_INVALID_ARG),
                       (dict(time_block=8, hist="bf16", keep_tape=True), L.FD_ERR_UNSUPPORTED),
                       (dict(time_block=32), L.FD_ERR_UNSUPPORTED),
+                      (dict(time_block=64), L.FD_ERR_UNSUPPORTED),
                       (dict(time_block=32, hist="bf16", fma_far=True), L.FD_ERR_UNSUPPORTED),
                       (dict(time_block=32, hist="bf16", tile_threads=192), L.FD_ERR_INVALID_ARG),
                       (dict(time_block=16, hist="bf16", stage_rows=32), L.FD_ERR_INVALID_ARG),
