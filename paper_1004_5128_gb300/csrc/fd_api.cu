@@ -165,9 +165,10 @@ inline int4 full_step(int64_t k) { return make_int4((int)k, 0, 1, 0); }
 // tensor cores unless FD_FLAG_FMA_FAR asks for the CUDA-core loop.
 inline bool tc_far(const fd_problem &p)
 {
-    return (p.time_block == 16 || p.time_block == 32 || p.time_block == 64) &&
-           (p.hist_dtype == FD_BF16 || p.hist_dtype == FD_F16) &&
-           !(p.flags & FD_FLAG_FMA_FAR) && !(p.flags & FD_FLAG_KEEP_TAPE);
+    const bool lowp = (p.time_block == 16 || p.time_block == 32 || p.time_block == 64) &&
+                      (p.hist_dtype == FD_BF16 || p.hist_dtype == FD_F16);
+    const bool split = (p.time_block == 32 || p.time_block == 64) && p.hist_dtype == FD_F32;
+    return (lowp || split) && !(p.flags & FD_FLAG_FMA_FAR) && !(p.flags & FD_FLAG_KEEP_TAPE);
 }
 
 int validate(const fd_problem *p)
@@ -236,7 +237,8 @@ struct Geo {
     int cmax;        // blocked: most far chunks per block (0: chunks of R rows)
     int rwin;        // blocked: largest far chunk (rows), the coefficient window's length
     int nblocks;     // blocks of tb steps covering max_steps
-    int tc;          // blocked, BF16 history: far units on the tensor cores
+    int tc;          // blocked: far units on the tensor cores
+    int hplanes;     // history planes: 2 for FP32 history on the tensor cores (FP16 hi and lo), else 1
     int halves;      // tensor cores: each CTA runs as two halves of `threads` threads
     size_t smem_half;  // tensor cores: dynamic shared memory of one half
     int tmem_cols;     // tensor cores: tensor-memory columns a CTA allocates (at most 512)
@@ -273,15 +275,15 @@ inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
            8 * (size_t)g.NS;
 }
 
-// Tensor-core blocked kernel, one half of a CTA: stage ring (RS rows x P points of 16-bit
-// history), 1 KB-aligned; NS coefficient blocks (tb/8 1 KB atoms, hi and lo halves side by side);
-// the coefficient window (and FP16 row scales); 3 NS + 1 barriers; rounded up to 1 KB.  The CTA
-// takes two halves plus 1 KB of slack to align the base.
-inline size_t smem_half_tc(const Geo &g, int rwin, bool f16)
+// Tensor-core blocked kernel, one half of a CTA: stage ring (RS rows x P points of 16-bit history,
+// in two planes for paired FP32 history), 1 KB-aligned; NS coefficient blocks (tb/8 1 KB atoms, hi and lo halves
+// side by side); the coefficient window (and the row scales of FP16 or paired history); 3 NS + 1
+// barriers; rounded up to 1 KB.  The CTA takes two halves plus 1 KB of slack to align the base.
+inline size_t smem_half_tc(const Geo &g, int rwin, bool scaled)
 {
-    const size_t ring = (size_t)g.NS * g.RS * g.threads * 8;  // no block-long update units
+    const size_t ring = (size_t)g.NS * g.RS * g.threads * 4 * g.sh * g.hplanes;  // no block-long update units
     return align_up(align_up(ring, 1024) + (size_t)g.NS * (g.tb / 8) * 1024 +
-                        (size_t)(rwin + g.tb + (f16 ? rwin : 0)) * 4 + 16 + 8 * (size_t)(3 * g.NS + 1),
+                        (size_t)(rwin + g.tb + (scaled ? rwin : 0)) * 4 + 16 + 8 * (size_t)(3 * g.NS + 1),
                     1024);
 }
 
@@ -330,12 +332,14 @@ inline void block_chunks(const fd_problem &p, const Geo &g, int64_t b, int64_t &
 void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
 {
     const int64_t N = (int64_t)p.nx * p.ny * p.nz;
-    g.sh = dtype_size(p.hist_dtype);
+    g.tc = tc_far(p);
+    // FP32 history on the tensor cores is stored as two FP16 planes (hi, lo) with row-tile scales
+    g.hplanes = (g.tc && p.hist_dtype == FD_F32) ? 2 : 1;
+    g.sh = g.hplanes == 2 ? 2 : dtype_size(p.hist_dtype);  // bytes of one stored element per plane
     g.ss = dtype_size(p.state_dtype);
     g.sa = dtype_size(p.accum_dtype);
     g.V = p.time_block ? 4 : 16 / g.sh;  // the blocked kernel keeps four points per thread
     g.planes = (p.flags & FD_FLAG_KEEP_TAPE) ? 2 : 1;
-    g.tc = tc_far(p);
     int th = threads_override ? threads_override : p.tile_threads;
     if (!th) {
         th = 256;
@@ -343,19 +347,20 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         while (th > 64 && need <= th / 2) th /= 2;
     }
     // tensor cores: point blocks of 128, four warps per lane quarter, per half of a CTA; blocks of
-    // 64 steps take 128 threads, so that both halves' accumulators fit the 512 tensor-memory columns
-    if (g.tc) th = (th >= 256 && p.time_block <= 32) ? 256 : 128;
+    // 64 steps take 128 threads, so that both halves' accumulators fit the 512 tensor-memory columns;
+    // FP32 history takes 128 threads, so that two halves' stages of 16 FP32 rows fit shared memory
+    if (g.tc) th = (th >= 256 && p.time_block <= 32 && g.hplanes == 1) ? 256 : 128;
     g.halves = g.tc ? 2 : 1;
     g.threads = th;
     g.P = th * g.V;
     g.T = (int)((N + g.P - 1) / g.P);
-    // tensor cores: stages of 16 rows (32 where the block allows at 128 threads), as many as fit in
-    // 88 KB per half of a CTA (2 .. 5)
-    const int tc_rs = (g.tc && p.time_block % 32 == 0 && th <= 128) ? 32 : 16;
+    // tensor cores: stages of 16 rows (32 where the block allows at 128 threads of 16-bit history),
+    // as many as fit in 88 KB per half of a CTA (2 .. 5)
+    const int tc_rs = (g.tc && p.time_block % 32 == 0 && th <= 128 && g.hplanes == 1) ? 32 : 16;
     g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
-    // (a tensor-core stage: RS rows of 16-bit history plus its coefficient block)
+    // (a tensor-core stage: RS rows of history plus its coefficient block)
     g.NS = p.stages ? p.stages
-           : g.tc   ? std::max(2, std::min(5, (88 << 10) / (g.RS * th * 8 + (p.time_block / 8) * 1024)))
+           : g.tc   ? std::max(2, std::min(5, (88 << 10) / (g.RS * th * 4 * g.sh * g.hplanes + (p.time_block / 8) * 1024)))
                     : 3;
     g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 2;
     g.ralign = g.tc ? g.RS : 1;
@@ -368,7 +373,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     if (p.mem_mode == FD_MEM_SHORT && !(p.flags & FD_FLAG_KEEP_TAPE) && !g.tc)
         g.cap = (int)std::min<int64_t>((int64_t)p.mem_L + 1, p.max_steps);
     g.cap = std::max(g.cap, 1);
-    g.hring_sep = (p.hist_dtype != p.state_dtype);
+    g.hring_sep = (p.hist_dtype != p.state_dtype) || g.hplanes == 2;
     g.head = p.head_lags ? p.head_lags : (g.hring_sep ? 32 : 8);
     if (!g.hring_sep && g.cap < g.head + 1) g.head = std::max(1, g.cap - 1);
     int64_t nmax = 0;
@@ -452,7 +457,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         while (cols < (g.P / 128) * g.tb) cols *= 2;
         g.tmem_cols = cols * g.halves;
         g.ctas = std::max(1, std::min(g.ctas, 512 / (cols * g.halves)));
-        g.smem_half = smem_half_tc(g, g.rwin, p.hist_dtype == FD_F16);
+        g.smem_half = smem_half_tc(g, g.rwin, p.hist_dtype != FD_BF16);
     }
     g.smem = g.tc ? g.halves * g.smem_half + 1024 : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
 }
@@ -579,9 +584,12 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
         L.alo[i] = (comp && adj) ? c.take(ubytes) : nullptr;
         L.rlo[i] = (comp && adj) ? c.take(ubytes) : nullptr;
     }
-    L.hist = c.take((size_t)g.cap * g.pitch);
+    L.hist = c.take((size_t)g.cap * g.pitch * g.hplanes);
     L.hring = g.hring_sep ? c.take((size_t)g.hring_cap * g.hring_pitch) : L.hist;
-    L.hscale = (p.hist_dtype == FD_F16) ? (float *)c.take((size_t)g.cap * g.T * sizeof(float)) : nullptr;
+    // power-of-two scales per (row, tile): FP16 history, and paired FP32 history
+    L.hscale = (p.hist_dtype == FD_F16 || g.hplanes == 2)
+                   ? (float *)c.take((size_t)g.cap * g.T * sizeof(float))
+                   : nullptr;
     L.part = c.take((size_t)g.npar * g.maxC * g.planes * std::max(1, g.tb) * g.part_pitch);
     L.arrive = external_counters ? counters
                                  : (unsigned *)c.take(sizeof(unsigned) * (g.npar + 1) * (size_t)g.T);
@@ -765,19 +773,23 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// Tensor-core path: the history rows as a BF16 tensor read with the 128-byte swizzle the MMA's A
+// Tensor-core path: the history rows as a 16-bit tensor (BF16, FP16, or the hi and lo FP16 planes
+// of paired FP32 history as one tensor of 2 cap rows) read with the 128-byte swizzle the MMA's A
 // operand expects, in boxes of 64 points (128 bytes) x RS rows.  Preferred: a 3-D view (64 points,
 // rows, groups of 64 points; the group stride of 128 bytes is below the row pitch) whose one box
 // per stage covers all P/64 groups of a tile.  If the driver refuses that view, a 2-D view
 // (points, rows) with one box per group.  Points past the padded row read as zeros.  Encoded on
 // the host, copied into the workspace; returns the rank used (0 on failure).
-int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, bool f16)
+int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, int hist)
 {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return 0;
-    const CUtensorMapDataType dt = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    // (paired FP32 history: FP16, both planes as one tensor of 2 cap rows)
+    const CUtensorMapDataType dt =
+        hist == FD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t rows = (cuuint64_t)g.cap * g.hplanes;
     {
-        const cuuint64_t dims[3] = {64u, (cuuint64_t)g.cap, (cuuint64_t)(g.pitch / 128)};
+        const cuuint64_t dims[3] = {64u, rows, (cuuint64_t)(g.pitch / 128)};
         const cuuint64_t strides[2] = {(cuuint64_t)g.pitch, 128u};
         const cuuint32_t box[3] = {64u, (cuuint32_t)g.RS, (cuuint32_t)(g.P / 64)};
         const cuuint32_t es[3] = {1u, 1u, 1u};
@@ -786,7 +798,7 @@ int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, bool f16)
             CUDA_SUCCESS)
             return 3;
     }
-    const cuuint64_t dims[2] = {(cuuint64_t)(g.pitch / 2), (cuuint64_t)g.cap};
+    const cuuint64_t dims[2] = {(cuuint64_t)(g.pitch / 2), rows};
     const cuuint64_t strides[1] = {(cuuint64_t)g.pitch};
     const cuuint32_t box[2] = {64u, (cuuint32_t)g.RS};
     const cuuint32_t es[2] = {1u, 1u};
@@ -801,7 +813,7 @@ int upload_tmap(const fd_problem &p, const Geo &g, const Layout &L, Inst &I, cud
 {
     if (!g.tc) return FD_OK;
     alignas(64) CUtensorMap m;
-    I.tmap_rank = encode_tmap(g, L, &m, p.hist_dtype == FD_F16);
+    I.tmap_rank = encode_tmap(g, L, &m, p.hist_dtype);
     if (!I.tmap_rank) return FD_ERR_CUDA;
     CK(cudaMemcpyAsync(L.tmap, &m, sizeof(m), cudaMemcpyHostToDevice, st));
     return FD_OK;
@@ -1441,13 +1453,17 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
         if (b.g[i].tmem_cols > 512) return FD_ERR_INVALID_ARG;  // a CTA's tensor memory holds 512 columns
         tiles += b.g[i].T;
     }
-    b.threads = threads;
+    // the launch's threads per (half-)CTA: the instances' resolved tile width (the tensor-core
+    // kernels fix it by history type and block length), the same for every instance
+    for (int i = 1; i < count; ++i)
+        if (b.g[i].threads != b.g[0].threads) return FD_ERR_INVALID_ARG;
+    b.threads = b.g[0].threads;
     b.RS = b.g[0].RS;
     b.NS = b.g[0].NS;
     b.rmax = 0;
     for (int i = 0; i < count; ++i) b.rmax = std::max(b.rmax, b.g[i].tb ? b.g[i].rwin : b.g[i].R);
     b.tb = probs[0].time_block;
-    b.smem_half = b.g[0].tc ? smem_half_tc(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16) : 0;
+    b.smem_half = b.g[0].tc ? smem_half_tc(b.g[0], b.rmax, probs[0].hist_dtype != FD_BF16) : 0;
     b.smem = b.g[0].tc ? b.g[0].halves * b.smem_half + 1024
              : b.tb    ? smem_bytes_tb(b.g[0], b.rmax, probs[0].hist_dtype == FD_F16)
                        : smem_bytes(b.g[0], b.rmax);

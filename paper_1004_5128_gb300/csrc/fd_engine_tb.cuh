@@ -173,8 +173,15 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     constexpr int V = 4;  // four points per thread: a float4 of state, H4<TH> of history
     constexpr bool LOWP = sizeof(TH) == 2;
     constexpr bool F16 = std::is_same<TH, __half>::value;
-    static_assert(!TC || (LOWP && !ADJ && TB % 16 == 0),
-                  "tensor-core far units: BF16 or FP16 history, forward, blocks of a multiple of 16 steps");
+    static_assert(!TC || (!ADJ && TB % 16 == 0), "tensor-core far units: forward, blocks of a multiple of 16 steps");
+    // FP32 history on the tensor cores is kept as a pair of FP16 planes: row r holds
+    // hi = fp16(delta 2^e) and lo = fp16(delta 2^e - hi) (about 22 significant bits together), the
+    // lo plane cap rows after the hi plane; the far units multiply both (three MMAs per K slice).
+    // FP16 and paired history carry a power-of-two scale 2^-e per (row, tile), which joins the
+    // coefficients.
+    constexpr bool PAIR = TC && !LOWP;
+    constexpr bool SCALED = F16 || PAIR;
+    using TB16 = typename std::conditional<SCALED, __half, __nv_bfloat16>::type;  // MMA operand type
     // A kernel holding tensor memory runs one CTA per SM, so the tensor-core kernels split each
     // CTA into two halves that work as independent CTAs: own claim loop, shared state and shared
     // memory, own named barrier, half of the CTA's tensor memory.  While one half runs an update
@@ -231,9 +238,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     constexpr int BBLK = (TB / 8) * 1024;
     unsigned char *bring = smem + ((ring_bytes + 1023) & ~(size_t)1023);
     float *win = reinterpret_cast<float *>(bring + (size_t)NS * BBLK);
-    float *wsc = win + L.rmax + TB;  // FP16: the unit's row scales
+    float *wsc = win + L.rmax + TB;  // FP16 or paired history: the unit's row scales
     if (TC)
-        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(wsc + (F16 ? L.rmax : 0)) + 15) & ~uintptr_t(15));
+        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(wsc + (SCALED ? L.rmax : 0)) + 15) & ~uintptr_t(15));
     uint64_t *full = bars, *empty = bars + NS, *bfull = bars + 2 * NS, *done_bar = bars + 3 * NS;
     __shared__ uint32_t s_tmem;
     // adaptive memory: bit j of gmask[lo] says w[lo + j] != 0 (the window of a four-row group);
@@ -425,9 +432,10 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 // D[p][t] = sum over rows r in [r0, r1) of H[r][p] * c(t, r), c(t, r) = w(kb + t - r):
                 // M = 128 points, N = TB steps, K = 16 rows per MMA, FP32 accumulators in tensor
                 // memory (block m of the tile's P/128 point blocks at columns m*TB ...).  The
-                // weights are split into BF16 hi + lo halves (two MMAs per K slice), so they keep
-                // about 16 significant bits.  Roles: warp 0 lane 0 issues the tensor-map copies of
-                // the history stages, warp 1 lane 0 issues the MMAs, the other warps write each
+                // weights are split into 16-bit hi + lo halves (two MMAs per K slice), so they keep
+                // about 16 (BF16) or 22 (FP16) significant bits; paired FP32 history adds its lo
+                // plane (a third MMA).  Roles: warp 0 lane 0 issues the tensor-map copies of the
+                // history stages, warp 1 lane 0 issues the MMAs, the other warps write each
                 // stage's coefficient block; mbarriers order them, with no CTA barrier per stage.
                 const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;  // whole stages (multiples of RS)
                 const int nst = nrow / RS;
@@ -446,10 +454,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         win[j] = (I.mem_mode == 1 && lag > I.mem_L) ? 0.f : wsrc[lag];
                         amax = fmaxf(amax, fabsf(win[j]));
                     }
-                    if (F16) {
-                        // FP16 rows hold delta * 2^e per (row, tile): the row's scale 2^-e joins its
-                        // weights, and one power of two per unit keeps the largest coefficient in
-                        // [2^13, 2^14), so both FP16 halves stay normal; the epilogue divides it out
+                    if (SCALED) {
+                        // FP16 rows hold delta * 2^e per (row, tile) (paired rows their hi and lo
+                        // parts): the row's scale 2^-e joins its weights, and one power of two per
+                        // unit keeps the largest coefficient in [2^13, 2^14), so both FP16 halves
+                        // stay normal; the epilogue divides it out
                         for (int a = tid; a < nrow; a += nthr) {
                             wsc[a] = __ldcg(I.hscale + (size_t)((r0 + a) % I.cap) * I.T + tile);
                             smax = fmaxf(smax, wsc[a]);
@@ -466,7 +475,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     }
                 }
                 csync();
-                if (F16) {
+                if (SCALED) {
                     if (tid == 0) {
                         float m = 0.f;
                         for (int w = 0; w < nthr / 32; ++w) m = fmaxf(m, s_wmax[w]);
@@ -476,7 +485,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     }
                     csync();
                 }
-                const float bnorm = F16 ? s_bnorm : 1.f, binv = 1.f / bnorm;  // powers of two
+                const float bnorm = SCALED ? s_bnorm : 1.f, binv = 1.f / bnorm;  // powers of two
                 auto give_up = [&](int site_s, uint64_t *bar) {
                     if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE)
                         note_failure(L, 11, ((long long)b << 32) | tile, ((long long)site_s << 32) | nst,
@@ -497,20 +506,26 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     }
                     return true;
                 };
-                constexpr uint32_t IDESC = tc::idesc_f16_amn(128, TB, !F16);
+                constexpr uint32_t IDESC = tc::idesc_f16_amn(128, TB, !SCALED);
                 if (warp == 0) {
                     if (lane == 0) {  // history stages: 64 points x RS rows per point group
+                        // (paired history: the hi plane's box, then the lo plane's, cap rows on)
+                        const size_t plane_bytes = (size_t)RS * I.P * 2;
                         for (int s = 0; s < nst; ++s) {
                             const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
                             if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
                             unsigned char *a = stages + (size_t)slot * RS * row_bytes;
                             mbar_expect_tx(&full[slot], (uint32_t)(RS * row_bytes));
-                            if (I.tmap_rank == 3)  // one box: 64 points x RS rows x P/64 point groups
-                                tc::tma_load_3d(a, I.tmap, 0, r0 + s * RS, tile * (I.P / 64), &full[slot]);
-                            else
-                                for (int j = 0; j < I.P / 64; ++j)
-                                    tc::tma_load_2d(a + (size_t)j * RS * 128, I.tmap, tile * I.P + 64 * j, r0 + s * RS,
-                                                    &full[slot]);
+                            for (int pl = 0; pl < (PAIR ? 2 : 1); ++pl) {
+                                unsigned char *ap = a + pl * plane_bytes;
+                                const int y = r0 + s * RS + pl * I.cap;
+                                if (I.tmap_rank == 3)  // one box: 64 points x RS rows x P/64 point groups
+                                    tc::tma_load_3d(ap, I.tmap, 0, y, tile * (I.P / 64), &full[slot]);
+                                else
+                                    for (int j = 0; j < I.P / 64; ++j)
+                                        tc::tma_load_2d(ap + (size_t)j * RS * 128, I.tmap, tile * I.P + 64 * j, y,
+                                                        &full[slot]);
+                            }
                             s_iss = s + 1;
                         }
                     }
@@ -523,6 +538,22 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             tc::fence_after();
                             const uint32_t a0 = tc::saddr(stages + (size_t)slot * RS * row_bytes);
                             const uint32_t bh = tc::saddr(bring + (size_t)slot * BBLK), bl = bh + (uint32_t)(RS * 2);
+                            if (PAIR) {
+                                // A: hi plane as below, the lo plane RS*P*2 bytes further
+                                const uint32_t lo_off = (uint32_t)(RS * I.P * 2);
+                                for (int m = 0; m < MB; ++m)
+                                    for (int kk = 0; kk < RS / 16; ++kk) {
+                                        const uint32_t ah = a0 + (uint32_t)(2 * m * RS * 128 + kk * 2048);
+                                        const uint64_t dh = tc::desc_sw128(ah, (uint32_t)(RS * 128), 1024u);
+                                        const uint64_t dl = tc::desc_sw128(ah + lo_off, (uint32_t)(RS * 128), 1024u);
+                                        const uint32_t d = tmem + (uint32_t)(m * TB);
+                                        const uint32_t acc = (s | kk) ? 1u : 0u;
+                                        const uint64_t bdh = tc::desc_sw128(bh + (uint32_t)(kk * 32), 16u, 1024u);
+                                        tc::mma_f16(d, dh, bdh, IDESC, acc);
+                                        tc::mma_f16(d, dh, tc::desc_sw128(bl + (uint32_t)(kk * 32), 16u, 1024u), IDESC, 1u);
+                                        tc::mma_f16(d, dl, bdh, IDESC, 1u);
+                                    }
+                            } else
                             for (int m = 0; m < MB; ++m)
                                 for (int kk = 0; kk < RS / 16; ++kk) {
                                     // A: points 128m.., rows 16kk..; atoms of 64 points are RS*128
@@ -551,9 +582,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             const int t = e / RS, i = e - t * RS;
                             const int r = r0 + s * RS + i;
                             float c = (r < rlo_t) ? 0.f : win[(r1 - 1 - r) + t];
-                            if (F16) c *= wsc[r - r0] * bnorm;
-                            TH hi, lo;
-                            if constexpr (F16) {
+                            if (SCALED) c *= wsc[r - r0] * bnorm;
+                            TB16 hi, lo;
+                            if constexpr (SCALED) {
                                 hi = __float2half_rn(c);
                                 lo = __float2half_rn(c - __half2float(hi));
                             } else {
@@ -562,8 +593,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             }
                             const int row = t & 7, base = (t >> 3) * 1024 + row * 128;
                             auto off = [&](int kq) { return base + (((kq >> 3) ^ row) << 4) + (kq & 7) * 2; };
-                            *reinterpret_cast<TH *>(bh + off(i)) = hi;
-                            *reinterpret_cast<TH *>(bh + off(RS + i)) = lo;
+                            *reinterpret_cast<TB16 *>(bh + off(i)) = hi;
+                            *reinterpret_cast<TB16 *>(bh + off(RS + i)) = lo;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(&bfull[slot])) : "memory");
@@ -627,7 +658,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
                         for (int t = 0; t < TB; ++t) v[t] = 0.f;
                     }
-                    if (F16) {  // exact: a power of two
+                    if (SCALED) {  // exact: a power of two
 #pragma unroll
                         for (int t = 0; t < TB; ++t) v[t] *= binv;
                     }
@@ -917,11 +948,21 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         auto hrow_at = [&](int r) -> const float * {
             return reinterpret_cast<const float *>(I.hring + (size_t)(r % I.hring_cap) * I.hring_pitch) + j0;
         };
-        // Four values of history row r (any age) converted to FP32, FP16 scale applied.
+        // Four values of history row r (any age) converted to FP32, FP16 scale applied (paired
+        // history: hi + lo).
         auto hist4 = [&](int r) -> float4 {
             float x[4];
-            H4<TH>::ldg(I.hist + (size_t)(r % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), x);
-            if (F16) {
+            if constexpr (PAIR) {
+                const char *row = I.hist + (size_t)(r % I.cap) * I.pitch + (size_t)j0 * 2;
+                float xl[4];
+                H4<__half>::ldg(row, x);
+                H4<__half>::ldg(row + (size_t)I.cap * I.pitch, xl);
+#pragma unroll
+                for (int v = 0; v < V; ++v) x[v] += xl[v];
+            } else {
+                H4<TH>::ldg(I.hist + (size_t)(r % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), x);
+            }
+            if (SCALED) {
                 const float sc = __ldcg(I.hscale + (size_t)(r % I.cap) * I.T + tile);
 #pragma unroll
                 for (int v = 0; v < V; ++v) x[v] *= sc;
@@ -1166,8 +1207,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         H4<TH>::stg(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), d, 1.f);
                 }
             }
-            if (F16 && I.hist_write) {
-                // FP16 row: a power-of-two scale per (row, tile) from the tile's largest |delta|
+            if (SCALED && I.hist_write) {
+                // FP16 row (or FP32 row as an FP16 hi/lo pair): a power-of-two scale per (row,
+                // tile) from the tile's largest |delta|
                 float amax = 0.f;
 #pragma unroll
                 for (int v = 0; v < V; ++v) amax = fmaxf(amax, fabsf(d[v]));  // zero past the grid's end
@@ -1184,7 +1226,22 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     e = max(-100, min(100, 15 - ex));
                 }
                 if (tid == 0) I.hscale[(size_t)(k % I.cap) * I.T + tile] = ldexpf(1.f, -e);
-                if (j0 < I.N) H4<TH>::stg(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), d, ldexpf(1.f, e));
+                if (j0 < I.N) {
+                    const float sc = ldexpf(1.f, e);
+                    char *row = I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * 2;
+                    if (F16) {
+                        H4<__half>::stg(row, d, sc);
+                    } else {  // paired: hi = fp16(d 2^e), lo = fp16(d 2^e - hi), both exact scalings
+                        float dh[V], dr[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            dh[v] = __half2float(__float2half_rn(d[v] * sc));
+                            dr[v] = d[v] * sc - dh[v];
+                        }
+                        H4<__half>::stg(row, dh, 1.f);
+                        H4<__half>::stg(row + (size_t)I.cap * I.pitch, dr, 1.f);
+                    }
+                }
             }
             if (bad) atomicOr(L.nonfinite, 1u);
             if (ADJ) {

@@ -4,7 +4,7 @@
 namespace fdk {
 const void *kernel_tb(int tb, bool adj, int hist, bool tc)
 {
-    if (tc) return (adj || (hist != 2 && hist != 3)) ? nullptr : kernel_tb_tc(tb, hist);
+    if (tc) return adj ? nullptr : kernel_tb_tc(tb, hist);
     if (hist != 1) return adj ? nullptr : kernel_tb_lowp(tb, hist);
     if (adj) {  // two accumulator sets: blocks of at most 8 steps fit the register budget
         switch (tb) {

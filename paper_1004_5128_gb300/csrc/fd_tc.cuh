@@ -16,6 +16,10 @@
 //    in the row (K) direction SBO bytes apart.
 //  * B, K-major: an atom holds 8 steps (N) x 64 rows (K, one 128-byte row per step).  Atoms
 //    adjacent in N are SBO bytes apart; a K slice of 16 starts 32 bytes further into the atom.
+//
+// FP32 history runs as the same FP16 product, three MMAs per K slice (hi.hi + hi.lo + lo.hi): each
+// row is stored as two FP16 planes, hi = fp16(delta 2^e) and lo = fp16(delta 2^e - hi), with a
+// power-of-two scale 2^-e per (row, tile) that joins the coefficients (about 22 significant bits).
 #pragma once
 
 #include <stdint.h>

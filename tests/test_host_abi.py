@@ -125,15 +125,18 @@ def test_time_block_validation():
     # the blocked adjoint keeps two accumulator sets: blocks of 4 and 8 steps only
     taped = L.fd_workspace_bytes(make_problem(p, time_block=8, keep_tape=True))
     assert taped > L.fd_workspace_bytes(make_problem(p, keep_tape=True)) > 0
-    # BF16 / FP16 history blocks forward; BF16 with blocks of 16 or 32 on the tensor cores
+    # BF16 / FP16 history blocks forward; blocks of 16, 32 or 64 on the tensor cores; FP32 history
+    # with blocks of 32 or 64 on the tensor cores (split into FP16 hi and lo parts)
     for ok in (dict(time_block=8, hist="bf16"), dict(time_block=16, hist="f16"),
                dict(time_block=32, hist="bf16"), dict(time_block=64, hist="f16"),
-               dict(time_block=16, hist="bf16", fma_far=True)):
+               dict(time_block=16, hist="bf16", fma_far=True),
+               dict(time_block=32), dict(time_block=64), dict(time_block=32, tile_threads=256)):
         assert L.fd_workspace_bytes(make_problem(p, **ok)) > 0
     for bad, code in ((dict(time_block=5), L.FD_ERR_INVALID_ARG),
                       (dict(time_block=8, hist="bf16", keep_tape=True), L.FD_ERR_UNSUPPORTED),
-                      (dict(time_block=32), L.FD_ERR_UNSUPPORTED),
-                      (dict(time_block=64), L.FD_ERR_UNSUPPORTED),
+                      (dict(time_block=32, fma_far=True), L.FD_ERR_UNSUPPORTED),
+                      (dict(time_block=32, keep_tape=True), L.FD_ERR_UNSUPPORTED),
+                      (dict(time_block=64, keep_tape=True), L.FD_ERR_UNSUPPORTED),
                       (dict(time_block=32, hist="bf16", fma_far=True), L.FD_ERR_UNSUPPORTED),
                       (dict(time_block=32, hist="bf16", tile_threads=192), L.FD_ERR_INVALID_ARG),
                       (dict(time_block=16, hist="bf16", stage_rows=32), L.FD_ERR_INVALID_ARG),
