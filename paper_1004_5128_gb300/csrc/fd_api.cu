@@ -239,6 +239,7 @@ struct Geo {
     int nblocks;     // blocks of tb steps covering max_steps
     int tc;          // blocked: far units on the tensor cores
     int hplanes;     // history planes: 2 for FP32 history on the tensor cores (FP16 hi and lo), else 1
+    int fsub;        // tensor cores: far units per (chunk, tile), each of P/fsub points (else 1)
     int halves;      // tensor cores: each CTA runs as two halves of `threads` threads
     size_t smem_half;  // tensor cores: dynamic shared memory of one half
     int tmem_cols;     // tensor cores: tensor-memory columns a CTA allocates (at most 512)
@@ -281,7 +282,7 @@ inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
 // barriers; rounded up to 1 KB.  The CTA takes two halves plus 1 KB of slack to align the base.
 inline size_t smem_half_tc(const Geo &g, int rwin, bool scaled)
 {
-    const size_t ring = (size_t)g.NS * g.RS * g.threads * 4 * g.sh * g.hplanes;  // no block-long update units
+    const size_t ring = (size_t)g.NS * g.RS * (g.threads * 4 / g.fsub) * g.sh * g.hplanes;  // no block-long update units
     return align_up(align_up(ring, 1024) + (size_t)g.NS * (g.tb / 8) * 1024 +
                         (size_t)(rwin + g.tb + (scaled ? rwin : 0)) * 4 + 16 + 8 * (size_t)(3 * g.NS + 1),
                     1024);
@@ -346,10 +347,8 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         const int64_t need = (N + g.V - 1) / g.V;
         while (th > 64 && need <= th / 2) th /= 2;
     }
-    // tensor cores: point blocks of 128, four warps per lane quarter, per half of a CTA; blocks of
-    // 64 steps take 128 threads, so that both halves' accumulators fit the 512 tensor-memory columns;
-    // FP32 history takes 128 threads, so that two halves' stages of 16 FP32 rows fit shared memory
-    if (g.tc) th = (th >= 256 && p.time_block <= 32 && g.hplanes == 1) ? 256 : 128;
+    // tensor cores: point blocks of 128, four warps per lane quarter, per half of a CTA
+    if (g.tc) th = (th >= 256) ? 256 : 128;
     g.halves = g.tc ? 2 : 1;
     g.threads = th;
     g.P = th * g.V;
@@ -358,9 +357,17 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     // as many as fit in 88 KB per half of a CTA (2 .. 5)
     const int tc_rs = (g.tc && p.time_block % 32 == 0 && th <= 128 && g.hplanes == 1) ? 32 : 16;
     g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
+    // Far sub-tiles: a tensor-core far unit covers P/fsub points, so that both halves' accumulators
+    // (P/fsub/128 x tb columns each) fit the 512 tensor-memory columns and a stage of RS rows
+    // (two planes for paired history) stays within 32 KB; the update units keep the whole tile.
+    g.fsub = 1;
+    if (g.tc)
+        while (g.fsub < g.P / 128 &&
+               ((g.P / g.fsub / 128) * p.time_block > 256 || (size_t)g.RS * (g.P / g.fsub) * 2 * g.hplanes > (32u << 10)))
+            g.fsub *= 2;
     // (a tensor-core stage: RS rows of history plus its coefficient block)
     g.NS = p.stages ? p.stages
-           : g.tc   ? std::max(2, std::min(5, (88 << 10) / (g.RS * th * 4 * g.sh * g.hplanes + (p.time_block / 8) * 1024)))
+           : g.tc   ? std::max(2, std::min(5, (88 << 10) / (g.RS * (g.P / g.fsub) * g.sh * g.hplanes + (p.time_block / 8) * 1024)))
                     : 3;
     g.ctas = p.ctas_per_sm ? p.ctas_per_sm : 2;
     g.ralign = g.tc ? g.RS : 1;
@@ -452,9 +459,9 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.hring_pitch = g.hring_sep ? (int64_t)align_up(align_up((size_t)N, 8) * g.ss, kAlign) : g.pitch;
     g.part_pitch = (int64_t)align_up((size_t)(align_up((size_t)N, 8)) * g.sa, kAlign);
     g.tmem_cols = 0;
-    if (g.tc) {  // each half allocates P/128 x tb tensor-memory columns (a power of two) of 512
+    if (g.tc) {  // each half allocates P/fsub/128 x tb tensor-memory columns (a power of two) of 512
         int cols = 32;
-        while (cols < (g.P / 128) * g.tb) cols *= 2;
+        while (cols < (g.P / g.fsub / 128) * g.tb) cols *= 2;
         g.tmem_cols = cols * g.halves;
         g.ctas = std::max(1, std::min(g.ctas, 512 / (cols * g.halves)));
         g.smem_half = smem_half_tc(g, g.rwin, p.hist_dtype != FD_BF16);
@@ -477,7 +484,7 @@ inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
     if (b < g.nblocks) {
         int64_t Rb, Cb;
         block_chunks(p, g, b, Rb, Cb);
-        far = (int64_t)g.T * (Cb + g.near);  // far chunks, then the near units
+        far = (int64_t)g.T * (Cb * g.fsub + g.near);  // far chunks (fsub units each), then the near units
     }
     return far + (b >= 1 ? (int64_t)g.T * (g.ub ? 1 : g.tb) : 0);
 }
@@ -791,7 +798,7 @@ int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, int hist)
     {
         const cuuint64_t dims[3] = {64u, rows, (cuuint64_t)(g.pitch / 128)};
         const cuuint64_t strides[2] = {(cuuint64_t)g.pitch, 128u};
-        const cuuint32_t box[3] = {64u, (cuuint32_t)g.RS, (cuuint32_t)(g.P / 64)};
+        const cuuint32_t box[3] = {64u, (cuuint32_t)g.RS, (cuuint32_t)(g.P / g.fsub / 64)};
         const cuuint32_t es[3] = {1u, 1u, 1u};
         if (enc(m, dt, 3, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -844,10 +851,8 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.ralign = g.ralign;
     I.near = g.near;
     I.tmap = L.tmap;
-    if (g.tc) {  // tensor-memory columns: P/128 point blocks of tb FP32 accumulators, a power of two
-        int cols = 32;
-        while (cols < (g.P / 128) * g.tb) cols *= 2;
-        I.tc_cols = cols;
+    if (g.tc) {  // tensor-memory columns per half: the geometry's (at most 256, checked at init)
+        I.tc_cols = g.tmem_cols / g.halves;
     }
     I.npar = g.npar;
     I.stall = (p.flags & FD_FLAG_INJECT_STALL) ? 1 : 0;
@@ -992,6 +997,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.stages = h->g.NS;
     L.rmax = h->g.tb ? h->g.rwin : h->g.R;
     L.smem_half = (int)h->g.smem_half;
+    L.fsub = h->g.fsub;
     L.queue = h->ctrl.queue;
     L.err = h->ctrl.err;
     L.nonfinite = h->ctrl.nonfinite;
@@ -1456,7 +1462,8 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
     // the launch's threads per (half-)CTA: the instances' resolved tile width (the tensor-core
     // kernels fix it by history type and block length), the same for every instance
     for (int i = 1; i < count; ++i)
-        if (b.g[i].threads != b.g[0].threads) return FD_ERR_INVALID_ARG;
+        if (b.g[i].threads != b.g[0].threads || b.g[i].fsub != b.g[0].fsub || b.g[i].RS != b.g[0].RS)
+            return FD_ERR_INVALID_ARG;
     b.threads = b.g[0].threads;
     b.RS = b.g[0].RS;
     b.NS = b.g[0].NS;
@@ -1590,6 +1597,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         L.stages = b->NS;
         L.rmax = b->rmax;
         L.smem_half = (int)b->smem_half;
+        L.fsub = b->g[0].fsub;
         L.queue = b->ctrl.queue;
         L.err = b->ctrl.err;
         L.nonfinite = b->ctrl.nonfinite;

@@ -150,6 +150,7 @@ struct Launch {
     int stage_rows, stages;
     int rmax;                // largest chunk (terms) over the launch's instances
     int smem_half;           // tensor-core kernels: dynamic shared memory of each half of a CTA
+    int fsub;                // tensor-core kernels: far units per (chunk, tile), each of P/fsub points
     unsigned long long *queue;
     int *err;
     unsigned *nonfinite;

@@ -43,6 +43,7 @@ namespace fdk {
 
 struct UnitTB {
     int valid, inst, b, tile, chunk, C, r0, r1;
+    int sub;  // far unit on the tensor cores: point range sub of the tile's fsub ranges
     int fix;  // 0: far unit; 1: update unit of step k; 2: block-long update unit; 3: near unit
     int k;
 };
@@ -192,6 +193,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     const int tid = threadIdx.x - half * nthr;
     const int RS = L.stage_rows, NS = L.stages;
     const int row_bytes = nthr * H4<TH>::BYTES;  // one history row of a tile in a stage
+    // tensor cores: a stage holds RS rows of one far unit's P/fsub points (16-bit; two planes for
+    // paired FP32 history)
+    const int stage_tc = TC ? RS * row_bytes / L.fsub : 0;
     // CTA (half) barriers
     auto csync = [&]() {
         if (TC)
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // at least TB x PLANES + 2 rows of FP32 float4 columns
     // (the tensor-core kernels have no block-long update units: their ring holds the stages only)
     const size_t ring_bytes =
-        TC ? (size_t)NS * RS * row_bytes : max((size_t)NS * RS * row_bytes, (size_t)(TB * PLANES + 2) * nthr * 16);
+        TC ? (size_t)NS * stage_tc : max((size_t)NS * RS * row_bytes, (size_t)(TB * PLANES + 2) * nthr * 16);
     float *psw = reinterpret_cast<float *>(smem + ring_bytes);  // psi window
     float *psw2 = psw + 4 * WS;                                 // psi' window (ADJ)
     float *rsc = psw + PLANES * 4 * WS;                         // FP16: the far rows' scales
@@ -277,6 +281,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // tensor memory for the far accumulators: P/128 blocks of TB FP32 columns per half (tc_cols,
     // a power of two), allocated once per CTA (one CTA per SM)
     const uint32_t tc_cols = TC ? (uint32_t)L.inst[0].tc_cols : 0u;
+    if (TC && (tc_cols < 32u || (tc_cols & (tc_cols - 1u)) || tc_cols * HALVES > 512u)) {
+        // not an allocatable column count: report and leave before any barrier (uniform)
+        if (threadIdx.x == 0) atomicCAS(L.err, ERR_NONE, ERR_PIPE);
+        return;
+    }
     if (TC && threadIdx.x < 32) tc::tmem_alloc(&s_tmem, tc_cols * HALVES);
     if (TC) tc::fence_before();
     __syncthreads();
@@ -389,7 +398,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     U.b = gb;
                     U.C = far_chunks<TB>(I, gb);
                     U.tile = (int)(f % I.T);
-                    U.chunk = (int)(f / I.T);
+                    U.sub = (int)((f / I.T) % L.fsub);
+                    U.chunk = (int)(f / I.T / L.fsub);
                     U.r0 = min(rhi, far_origin<TB>(I, gb) + U.chunk * Rb);
                     U.r1 = min(rhi, U.r0 + Rb);
                     U.k = 0;
@@ -431,7 +441,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 // ============================================== far unit on the tensor cores
                 // D[p][t] = sum over rows r in [r0, r1) of H[r][p] * c(t, r), c(t, r) = w(kb + t - r):
                 // M = 128 points, N = TB steps, K = 16 rows per MMA, FP32 accumulators in tensor
-                // memory (block m of the tile's P/128 point blocks at columns m*TB ...).  The
+                // memory (block m of the unit's Pf/128 point blocks at columns m*TB ...; the unit
+                // covers the tile's points sub*Pf .. (sub+1)*Pf-1, Pf = P/fsub).  The
                 // weights are split into 16-bit hi + lo halves (two MMAs per K slice), so they keep
                 // about 16 (BF16) or 22 (FP16) significant bits; paired FP32 history adds its lo
                 // plane (a third MMA).  Roles: warp 0 lane 0 issues the tensor-map copies of the
@@ -440,7 +451,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;  // whole stages (multiples of RS)
                 const int nst = nrow / RS;
                 const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
-                const int MB = I.P / 128;
+                const int Pf = I.P / L.fsub, p0 = tile * I.P + U.sub * Pf;  // the unit's points
+                const int MB = Pf / 128;
                 int rlo_t, rhi_t;
                 far_rows<TB>(I, b, rlo_t, rhi_t);  // rows below rlo_t are not far rows of this block
                 {
@@ -510,20 +522,20 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 if (warp == 0) {
                     if (lane == 0) {  // history stages: 64 points x RS rows per point group
                         // (paired history: the hi plane's box, then the lo plane's, cap rows on)
-                        const size_t plane_bytes = (size_t)RS * I.P * 2;
+                        const size_t plane_bytes = (size_t)RS * Pf * 2;
                         for (int s = 0; s < nst; ++s) {
                             const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
                             if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
-                            unsigned char *a = stages + (size_t)slot * RS * row_bytes;
-                            mbar_expect_tx(&full[slot], (uint32_t)(RS * row_bytes));
+                            unsigned char *a = stages + (size_t)slot * stage_tc;
+                            mbar_expect_tx(&full[slot], (uint32_t)stage_tc);
                             for (int pl = 0; pl < (PAIR ? 2 : 1); ++pl) {
                                 unsigned char *ap = a + pl * plane_bytes;
                                 const int y = r0 + s * RS + pl * I.cap;
                                 if (I.tmap_rank == 3)  // one box: 64 points x RS rows x P/64 point groups
-                                    tc::tma_load_3d(ap, I.tmap, 0, y, tile * (I.P / 64), &full[slot]);
+                                    tc::tma_load_3d(ap, I.tmap, 0, y, p0 / 64, &full[slot]);
                                 else
-                                    for (int j = 0; j < I.P / 64; ++j)
-                                        tc::tma_load_2d(ap + (size_t)j * RS * 128, I.tmap, tile * I.P + 64 * j, y,
+                                    for (int j = 0; j < Pf / 64; ++j)
+                                        tc::tma_load_2d(ap + (size_t)j * RS * 128, I.tmap, p0 + 64 * j, y,
                                                         &full[slot]);
                             }
                             s_iss = s + 1;
@@ -536,11 +548,11 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             const uint32_t ph = (use / (uint32_t)NS) & 1u;
                             if (!wait_bar(&full[slot], ph, s) || !wait_bar(&bfull[slot], ph, s)) break;
                             tc::fence_after();
-                            const uint32_t a0 = tc::saddr(stages + (size_t)slot * RS * row_bytes);
+                            const uint32_t a0 = tc::saddr(stages + (size_t)slot * stage_tc);
                             const uint32_t bh = tc::saddr(bring + (size_t)slot * BBLK), bl = bh + (uint32_t)(RS * 2);
                             if (PAIR) {
                                 // A: hi plane as below, the lo plane RS*P*2 bytes further
-                                const uint32_t lo_off = (uint32_t)(RS * I.P * 2);
+                                const uint32_t lo_off = (uint32_t)(RS * Pf * 2);
                                 for (int m = 0; m < MB; ++m)
                                     for (int kk = 0; kk < RS / 16; ++kk) {
                                         const uint32_t ah = a0 + (uint32_t)(2 * m * RS * 128 + kk * 2048);
@@ -648,7 +660,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 // m = w / 4, w / 4 + nwarp / 4, ...; each thread holds one point's TB sums
                 const int q = warp & 3;
                 for (int m = warp >> 2; m < MB; m += nwarp >> 2) {
-                    const int j = tile * I.P + m * 128 + q * 32 + lane;
+                    const int j = p0 + m * 128 + q * 32 + lane;
                     float v[TB];
                     if (nst > 0) {
 #pragma unroll
@@ -1502,9 +1514,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         if (tid < 32) {  // the two waits run in parallel lanes
             int ok = 1;
             if (tid == 0) {  // the far chunks and, with near units, the near partial
-                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C + I.near), L, 512);
+                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C * L.fsub + I.near), L, 512);
                 if (w < 0)
-                    note_failure(L, 3, k, tile, arrive_target(b, C + I.near), ld_acquire(&I.arrive[par * I.T + tile]),
+                    note_failure(L, 3, k, tile, arrive_target(b, C * L.fsub + I.near), ld_acquire(&I.arrive[par * I.T + tile]),
                                  L.k0, 0);
                 ok = w > 0;
             }

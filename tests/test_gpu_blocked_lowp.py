@@ -95,8 +95,9 @@ def test_config3_full_size_lowp_vs_fp32_history():
 
 
 # ------------------------------------------------------------------ tensor-core far units
-# BF16 history with blocks of 16 or 32: the far rows are multiplied by tcgen05 MMAs (weights as
-# BF16 hi + lo halves, FP32 accumulation in tensor memory).  Checked against the oracle at the
+# BF16 history with blocks of 16, 32 or 64: the far rows are multiplied by tcgen05 MMAs (weights as
+# BF16 hi + lo halves, FP32 accumulation in tensor memory); blocks of 64 at 256 threads, and stages of
+# 32 rows at 256 threads, split each tile into two far units of 512 points.  Checked against the oracle at the
 # BF16 tolerance, against the oracle with the same BF16 storage rule at the FP32 tolerance, and
 # (blocks of 16) against the CUDA-core far loop over the same BF16 rows.
 
@@ -105,7 +106,8 @@ TC_MODES = [("full", synth.MEM_FULL, 0, 0), ("short40", synth.MEM_SHORT, 40, 0),
 
 
 @pytest.mark.parametrize("step_updates", [False, True])
-@pytest.mark.parametrize("tb,rs,threads", [(16, 16, 256), (32, 16, 256), (32, 32, 128), (16, 16, 128), (64, 16, 128)])
+@pytest.mark.parametrize("tb,rs,threads", [(16, 16, 256), (32, 16, 256), (32, 32, 128), (16, 16, 128), (64, 16, 128),
+                                            (64, 16, 256), (32, 32, 256)])
 @pytest.mark.parametrize("name,mode,L,a", TC_MODES, ids=[m[0] for m in TC_MODES])
 @pytest.mark.parametrize("hist", ["bf16", "f16"])
 def test_tensor_core_far_units_match_oracle_and_cuda_cores(hist, name, mode, L, a, tb, rs, threads, step_updates):

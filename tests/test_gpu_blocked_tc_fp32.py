@@ -1,8 +1,10 @@
 """Temporally blocked engine with FP32 history whose far rows run on the tensor cores (blocks of 32
-and 64 steps): each stage of FP32 rows, scaled per (row, tile) by a power of two, is split in
-shared memory into FP16 hi and lo parts, and three FP16 MMAs per K slice (hi.hi + hi.lo + lo.hi)
-accumulate in FP32.  The split keeps about 22 significant bits of every row value and weight, so
-the FP32 tolerance of the FP64 oracle holds (1e-5, infinity norm relative to max |u_ref|)."""
+and 64 steps): every history row is stored as two FP16 planes, hi = fp16(delta 2^e) and
+lo = fp16(delta 2^e - hi) with a power of two 2^-e per (row, tile), and three FP16 MMAs per K
+slice (hi.hi + hi.lo + lo.hi) accumulate in FP32.  The pair keeps about 22 significant bits of
+every row value and weight, so the FP32 tolerance of the FP64 oracle holds (1e-5, infinity norm
+relative to max |u_ref|).  With 256 threads per half-CTA each far unit covers half a tile (far
+sub-tiles of 512 points), with 128 threads the whole tile."""
 import numpy as np
 import pytest
 
@@ -36,15 +38,16 @@ MODES = [("full", synth.MEM_FULL, 0, 0), ("short40", synth.MEM_SHORT, 40, 0),
          ("adapt3", synth.MEM_ADAPTIVE, 0, 3), ("adapt10", synth.MEM_ADAPTIVE, 0, 10)]
 
 
+@pytest.mark.parametrize("threads", [256, 128])
 @pytest.mark.parametrize("step_updates", [False, True])
 @pytest.mark.parametrize("tb", [32, 64])
 @pytest.mark.parametrize("name,mode,L,a", MODES, ids=[m[0] for m in MODES])
-def test_fp32_tensor_core_far_units_match_oracle(name, mode, L, a, tb, step_updates):
-    """45 x 37 points (four ragged tiles of 512), 300 steps, chunks of two stages."""
+def test_fp32_tensor_core_far_units_match_oracle(name, mode, L, a, tb, step_updates, threads):
+    """45 x 37 points (two ragged tiles of 1024, or four of 512), 300 steps, chunks of two stages."""
     p = ragged(synth.BC_NOFLUX, mode, L, a, K=300)
-    got, s = run(p, time_block=tb, chunk_terms=32, step_updates=step_updates)
+    got, s = run(p, time_block=tb, chunk_terms=32, step_updates=step_updates, tile_threads=threads)
     g = s.geometry()
-    assert g["far_tensor_cores"] == 1 and g["time_block"] == tb and g["tile_threads"] == 128
+    assert g["far_tensor_cores"] == 1 and g["time_block"] == tb and g["tile_threads"] == threads
     ref = oracle.run(p)
     assert rel_inf(got, ref) < TOL
     fma, s2 = run(p, time_block=16, step_updates=step_updates)  # CUDA-core far loop, same rows
