@@ -42,8 +42,8 @@ CONFIG_NAMES = {
           "{full, short L=500, adaptive a=10}, FP32",
     "c1": "1-D N=256 Dirichlet, gamma=0.5, S=0.2, 1000 steps, full memory, FP64",
     "c3": "2-D 512x512 Dirichlet, gamma=0.6, alpha=1, f=u(1-u)-0.05u, S=0.1, U[0,0.1] noise, 20000 "
-          "steps, full memory; history BF16 and FP16 (row-tile scaled), far rows on tcgen05 tensor "
-          "cores in blocks of 32 steps, and FP32, far rows on CUDA cores in blocks of 16; FP32 state and "
+          "steps, full memory; history BF16, FP16 (row-tile scaled) and FP32 (row-tile scaled FP16 hi "
+          "+ lo planes), blocks of 64 steps with the far rows on tcgen05 tensor cores; FP32 state and "
           "accumulation, FP64-generated weights",
     "c4": "64 instances (32 1-D N 64-4096, 32 2-D side 64-384), gamma~U[0.3,0.95], steps "
           "U{1000..8000}, one persistent launch (CUDA graph), {full, adaptive a=10}, FP32",
@@ -132,12 +132,14 @@ def alg_bytes(geo: dict, p: dict, kw: dict) -> int:
     """History rows the launch's kernel must read plus, per step, the u read/write and the delta
     write.  Per-step kernel: every lag >= 1 of every step.  Temporally blocked kernel: the far rows
     once per block in the history's precision, plus each step's newest rows; with 16-bit history
-    those come from the FP32 ring, which every step also writes."""
+    (and FP32 history kept as two FP16 planes for the tensor cores) those come from the FP32 ring,
+    which every step also writes."""
     N = p["nx"] * p["ny"] * p.get("nz", 1)
     sh = HBYTES[kw.get("hist", kw.get("state", "f32"))]
     ss = 8 if kw.get("state") == "f64" else 4
     rows = geo.get("stream_rows_total", geo["hist_rows_total"])
-    if not geo.get("time_block") or sh == ss:
+    ring = sh != ss or bool(geo.get("far_tensor_cores"))
+    if not geo.get("time_block") or not ring:
         return rows * N * sh + p["K"] * N * (2 * ss + sh)
     head = geo["head_rows_total"]
     return (rows - head) * N * sh + head * N * 4 + p["K"] * N * (2 * ss + sh + 4)

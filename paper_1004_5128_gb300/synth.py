@@ -234,11 +234,11 @@ def workload_runs(name: str, K: int = 0, modes: str = ""):
     elif name == "c1":
         runs = [("full", config1(), {"state": "f64"})]
     elif name == "c3":
-        # temporally blocked: BF16 and FP16 far rows on the tensor cores (blocks of 32), FP32 far
-        # rows on the CUDA cores (blocks of 16)
-        runs = [("bf16", config3(), {"hist": "bf16", "time_block": 32}),
-                ("f16", config3(), {"hist": "f16", "time_block": 32}),
-                ("f32", config3(), {"time_block": 16})]
+        # temporally blocked, blocks of 64, far rows on the tensor cores (FP32 history as a pair of
+        # FP16 planes)
+        runs = [("bf16", config3(), {"hist": "bf16", "time_block": 64}),
+                ("f16", config3(), {"hist": "f16", "time_block": 64}),
+                ("f32", config3(), {"time_block": 64})]
     elif name == "c4":
         runs = [("full", config4(MEM_FULL), {}), ("adaptive", config4(MEM_ADAPTIVE), {})]
     elif name == "c5":
