@@ -207,7 +207,8 @@ ERROR_SITES = {0: "none", 1: "blocked far unit: history rows", 2: "blocked far u
                3: "blocked update: far count", 4: "blocked update: own rows",
                5: "blocked update: halo tile", 6: "chunk: history rows", 7: "chunk: bulk copy",
                8: "fixup: halo tile", 9: "injected stall", 10: "blocked far unit: running sum",
-               11: "tensor-core far unit: copy, coefficients or MMAs"}
+               11: "tensor-core far unit: copy, coefficients or MMAs",
+               12: "blocked near unit: previous block's rows", 13: "blocked mid unit: the block's earlier rows"}
 
 
 def fd_get_error_info(h: int) -> dict:

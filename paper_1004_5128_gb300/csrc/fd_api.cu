@@ -244,6 +244,7 @@ struct Geo {
     size_t smem_half;  // tensor cores: dynamic shared memory of one half
     int tmem_cols;     // tensor cores: tensor-memory columns a CTA allocates (at most 512)
     int near;        // blocked, per-step update units, blocks of 16+: one near unit per (block, tile)
+    int mid;         // blocked, near units, blocks of 32+: mid units per (block, tile), tb/16 - 1
     int ralign;      // blocked: far chunks start on multiples of ralign rows (tensor cores: RS)
     int hring_sep;   // separate state-precision head ring
     int hring_cap;
@@ -402,6 +403,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.nblocks = g.tb ? (p.max_steps + g.tb - 1) / g.tb : 0;
     g.ub = 0;
     g.near = 0;
+    g.mid = 0;
     g.smem_half = 0;
     g.cmax = 0;
     g.rwin = g.R;
@@ -449,7 +451,10 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         // rows enter each step through one partial row (after the far chunks') instead of as
         // TB head lags read by every step's update
         g.near = !g.ub && g.tb >= 16;
-        g.maxC = (int)cmaxb + g.near;
+        // Mid units: with blocks of 32 or more, sub-block j = 1 .. tb/16-1 (16 steps each) gets the
+        // block's rows before it as one more partial row, so an update sums at most 15 head lags
+        g.mid = (g.near && g.tb >= 32) ? g.tb / 16 - 1 : 0;
+        g.maxC = (int)cmaxb + g.near + (g.mid ? 1 : 0);
         g.rwin = (int)rwin;
     }
     g.pitch = (int64_t)align_up((size_t)N * g.sh, kAlign);
@@ -486,12 +491,13 @@ inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
         block_chunks(p, g, b, Rb, Cb);
         far = (int64_t)g.T * (Cb * g.fsub + g.near);  // far chunks (fsub units each), then the near units
     }
-    return far + (b >= 1 ? (int64_t)g.T * (g.ub ? 1 : g.tb) : 0);
+    return far + (b >= 1 ? (int64_t)g.T * ((g.ub ? 1 : g.tb) + g.mid) : 0);
 }
 
 // History rows the blocked kernel reads over max_steps steps: the far rows once per block, then
-// every step's head rows (lags 1 .. min(k - kb + tb, n(k))), or, with block-long update units,
-// the previous block's rows once per block.
+// every step's head rows (lags 1 .. min(k - kb + tb, n(k)); with near units the block's own rows,
+// with mid units those of its own sub-block of 16 steps, plus the near and mid units' rows once
+// each), or, with block-long update units, the previous block's rows once per block.
 int64_t blocked_stream_rows(const fd_problem &p, const Geo &g, int64_t *head_rows = nullptr)
 {
     const int tb = g.tb;
@@ -511,8 +517,9 @@ int64_t blocked_stream_rows(const fd_problem &p, const Geo &g, int64_t *head_row
         for (int64_t k = 0; k < p.max_steps; ++k) {
             const int64_t nb = (p.mem_mode == FD_MEM_SHORT) ? std::min<int64_t>(p.mem_L, k) : k;
             const int64_t t = k - (k / tb) * tb;
-            hd += std::min<int64_t>(g.near ? t : t + tb, nb);
+            hd += std::min<int64_t>(g.near ? (g.mid ? t % 16 : t) : t + tb, nb);
             if (g.near && t == 0) hd += std::min<int64_t>(tb, k);  // the near unit's rows, once per block
+            if (g.mid && t > 0 && t % 16 == 0) hd += t;             // a mid unit's rows, once per sub-block
         }
     if (head_rows) *head_rows = hd;
     return st + hd;
@@ -601,14 +608,14 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     L.arrive = external_counters ? counters
                                  : (unsigned *)c.take(sizeof(unsigned) * (g.npar + 1) * (size_t)g.T);
     L.done = L.arrive ? L.arrive + g.npar * g.T : nullptr;
-    L.psi = c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa);  // blocked: window reads to kb+tb-1
-    L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1 + g.tb) * g.sa) : nullptr;
+    L.psi = c.take((size_t)(p.max_steps + 1 + 2 * g.tb) * g.sa);  // blocked: windows read lags up to 2 tb (near units)
+    L.dpsi = (p.flags & FD_FLAG_KEEP_TAPE) ? c.take((size_t)(p.max_steps + 1 + 2 * g.tb) * g.sa) : nullptr;
     L.sched = (int4 *)c.take(sizeof(int4) * (size_t)p.max_steps);
     const size_t ng = std::max<size_t>(1, s.G.size());
     L.glag = (int *)c.take(sizeof(int) * ng);
     L.gcoef = c.take((size_t)g.sa * ng);
     const bool btab = g.tb && p.mem_mode == FD_MEM_ADAPTIVE, aad = adaptive_adjoint(p);
-    const size_t wlen = (size_t)(p.max_steps + 1 + g.tb) * g.sa;
+    const size_t wlen = (size_t)(p.max_steps + 1 + 2 * g.tb) * g.sa;
     L.gw = (btab || aad) ? c.take(wlen) : nullptr;
     L.br0 = btab ? (int *)c.take(sizeof(int) * (size_t)(g.nblocks + 1)) : nullptr;
     L.dgw = aad ? c.take(wlen) : nullptr;
@@ -679,7 +686,7 @@ template <class TA> void to_acc(const std::vector<double> &x, std::vector<unsign
 
 void build_tables(const fd_problem &p, const Sched &s, const Geo &g, Tables &t)
 {
-    const int64_t n = (int64_t)p.max_steps + 1 + g.tb;
+    const int64_t n = (int64_t)p.max_steps + 1 + 2 * g.tb;
     t.psi.resize(n);
     t.dpsi.resize(n);
     gl_weights(p.gamma, n, t.psi.data(), t.dpsi.data());
@@ -850,6 +857,7 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.cmax = g.cmax;
     I.ralign = g.ralign;
     I.near = g.near;
+    I.mid = g.mid;
     I.tmap = L.tmap;
     if (g.tc) {  // tensor-memory columns per half: the geometry's (at most 256, checked at init)
         I.tc_cols = g.tmem_cols / g.halves;

@@ -63,6 +63,8 @@ struct Inst {
     int cmax;                // blocked kernel: most far chunks per block (0 = no limit)
     int ralign;              // blocked kernel: far chunks start on multiples of ralign rows (0, 1: any)
     int near;                // blocked kernel: one near unit per (block, tile) adds the previous block's rows
+    int mid;                 // blocked kernel: mid units per (block, tile): sub-blocks 1 .. mid of 16 steps
+                             // get the block's earlier rows as one partial row
     int tc_cols;             // blocked tensor-core kernel: tensor-memory columns per CTA
     int tmap_rank;           // blocked tensor-core kernel: 3 = one box per stage, 2 = one per 64 points
     const void *tmap;        // blocked tensor-core kernel: tensor map of the history rows

@@ -295,6 +295,10 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 
     uint32_t n_issued = 0, n_used = 0;
     int ghint = L.g_begin;
+    // thread 0: the group of the last claimed unit (units [cg_lo, cg_hi), info cgi), so that a
+    // claim in the same group reads no group table
+    long long cg_lo = 0, cg_hi = 0;
+    int2 cgi = make_int2(0, 0);
     const long long u_base = L.g_off[L.g_begin];
     const long long u_end = L.g_off[L.g_end];
 
@@ -309,21 +313,29 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             for (;;) {
                 // claimed when needed, never ahead: a CTA waiting inside a block-long update unit
                 // must not hold an unstarted unit that its neighbours' units wait for
+                // (the status word is read before the queue add, so the two latencies overlap)
+                const int err_now = ld_volatile(L.err);
                 const long long u = u_base + (long long)atomicAdd(L.queue, 1ull);
-                ok = (u < u_end) && (ld_volatile(L.err) == ERR_NONE);
+                ok = (u < u_end) && (err_now == ERR_NONE);
                 if (!ok) break;
-                const int g = find_group(L.g_off, ghint, L.g_end, u);
-                ghint = g;
-                const int2 gi = L.g_info[g];
+                if (u < cg_lo || u >= cg_hi) {
+                    const int g = find_group(L.g_off, ghint, L.g_end, u);
+                    ghint = g;
+                    cg_lo = L.g_off[g];
+                    cg_hi = L.g_off[g + 1];
+                    cgi = L.g_info[g];
+                }
+                const int2 gi = cgi;
                 if (gi.x != s_cur_inst) {
                     I = L.inst[gi.x];
                     s_cur_inst = gi.x;
                 }
-                const long long local = u - L.g_off[g];
+                const long long local = u - cg_lo, gsize = cg_hi - cg_lo;
                 const int gb = gi.y;  // group: far units of block gb, updates of block gb-1
                 const int k_end = min(L.k_end, I.ksteps);  // a batch runs each instance to its end
                 const int Tu = (gb >= 1) ? I.T * (I.ub ? 1 : TB) : 0;  // block gb-1's update units
-                const long long F = (L.g_off[g + 1] - L.g_off[g]) - (long long)Tu;  // block gb's far units
+                const int Mu = (gb >= 1) ? I.T * I.mid : 0;              // block gb-1's mid units
+                const long long F = gsize - (long long)(Tu + Mu);  // block gb's far units
                 long long f = -1;  // far unit index within block gb, or -1 for an update unit
                 U.inst = gi.x;
                 if (I.ub) {
@@ -347,14 +359,14 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     } else {
                         f = (local < F1) ? local : local - Tu;
                     }
-                } else if (I.near && gb * TB < I.ksteps && local >= (L.g_off[g + 1] - L.g_off[g]) - I.T) {
+                } else if (I.near && gb * TB < I.ksteps && local >= gsize - I.T) {
                     // near unit of block gb (the group's last T units): the previous block's rows
                     // for every step of block gb, once block gb-1's updates of the tile are done
                     const int kb = gb * TB;
                     if (kb >= k_end) continue;  // block starts at or after the launch's end
                     U.fix = 3;
                     U.b = gb;
-                    U.tile = (int)(local - ((L.g_off[g + 1] - L.g_off[g]) - I.T));
+                    U.tile = (int)(local - (gsize - I.T));
                     U.C = far_chunks<TB>(I, gb);
                     U.chunk = U.C;  // its partial rows follow the far chunks'
                     U.r0 = max(0, kb - TB);
@@ -367,13 +379,46 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     }
                     break;
                 } else {
-                    int sseg = 0;  // segment s: far slice s, then the T update units of step s
+                    // segment s: far slice s, then (s = 16 j, j = 1 .. mid) the T mid units of
+                    // sub-block j of block gb-1, then the T update units of step s
+                    int sseg = 0;
                     const int Ts = Tu / TB;
                     const long long F0 = F - (I.near && gb * TB < I.ksteps ? I.T : 0);  // far units proper
-                    while (sseg + 1 < TB && (long long)(sseg + 1) * Ts + (long long)(sseg + 1) * F0 / TB <= local) ++sseg;
+                    auto seg_start = [&](int sg) -> long long {
+                        const int mids = (Mu && sg >= 1) ? min(I.mid, (sg - 1) / 16) : 0;
+                        return (long long)sg * Ts + (long long)I.T * mids + (long long)sg * F0 / TB;
+                    };
+                    // segments are near equal: estimate, then step to the exact one
+                    sseg = (int)min((long long)(TB - 1), local * TB / max(1ll, (long long)TB * Ts + F0 + Mu));
+                    while (sseg > 0 && seg_start(sseg) > local) --sseg;
+                    while (sseg + 1 < TB && seg_start(sseg + 1) <= local) ++sseg;
                     const long long fs0 = (long long)sseg * F0 / TB;
                     const long long fsn = (long long)(sseg + 1) * F0 / TB - fs0;  // far units in slice s
-                    const long long off = local - ((long long)sseg * Ts + fs0);
+                    long long off = local - seg_start(sseg);
+                    const bool seg_mid = Mu && sseg >= 16 && sseg % 16 == 0;
+                    if (seg_mid && off >= fsn && off < fsn + I.T) {
+                        // mid unit: rows kb .. kb+s-1 of block gb-1 for its steps s .. s+15.  Skipped
+                        // only when no update of this launch needs it (the updates' arrival target
+                        // counts every earlier sub-block's mid unit, so those run even when their
+                        // own steps precede the launch).
+                        const int kb1 = (gb - 1) * TB;
+                        if (kb1 + sseg >= k_end || kb1 + TB <= L.k0) continue;
+                        U.fix = 4;
+                        U.b = gb - 1;
+                        U.tile = (int)(off - fsn);
+                        U.k = kb1 + sseg;
+                        U.C = far_chunks<TB>(I, gb - 1);
+                        U.chunk = U.C + 1;  // after the far chunks' and the near unit's rows
+                        U.r0 = kb1;
+                        U.r1 = kb1 + sseg;
+                        if (U.r1 - L.k0 > 0) {  // the tile's rows up to r1-1 written
+                            const int w = wait_until(&I.done[U.tile], (unsigned)(U.r1 - L.k0), L, 512);
+                            if (w < 0) note_failure(L, 13, gb, U.tile, U.r1 - L.k0, ld_acquire(&I.done[U.tile]), L.k0, 0);
+                            if (w <= 0) ok = 0;
+                        }
+                        break;
+                    }
+                    if (seg_mid && off >= fsn) off -= I.T;
                     if (off >= fsn) {  // update unit: block gb-1, step s
                         const int k = (gb - 1) * TB + sseg;
                         if (k < L.k0 || k >= k_end) continue;  // block edge outside this launch
@@ -1289,14 +1334,18 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             return true;
         };
 
-        if (U.fix == 3) {
+        if (U.fix == 3 || U.fix == 4) {
             // ======================= near unit: the previous block's rows for every step of block b
             // N_t = sum over rows r = kb-TB .. kb-1 (oldest first) of w_{kb+t}(kb+t-r) delta^r, from
             // the FP32 rows: psi (short memory: 0 beyond the window; adaptive memory: the settled
             // weight g(m) up to the step's e(k), psi beyond).  Written as partial row C of block b
             // and counted like a far chunk, so each step's update reads one row for these lags
             // instead of TB.  The weights are staged in the idle stage ring.
-            const int r0 = U.r0, r1 = U.r1, mlo = kb - r1 + 1;
+            // Mid unit (fix 4): the same sum over the block's own rows kb .. kb+s-1 for the steps
+            // t = s .. s+15 of sub-block s/16, written as partial row C+1; an update then reads at
+            // most 15 head rows, those of its own sub-block.
+            const int t_lo = (U.fix == 4) ? U.k - kb : 0, t_hi = (U.fix == 4) ? t_lo + 16 : TB;
+            const int r0 = U.r0, r1 = U.r1, mlo = kb + t_lo - r1 + 1;  // smallest lag
             float *spsi = reinterpret_cast<float *>(stages), *sgw = spsi + 2 * TB;
             const float *gwf = reinterpret_cast<const float *>(I.gw);
             for (int e = tid; e < 2 * TB; e += nthr) {
@@ -1307,8 +1356,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             }
             if (tid < TB) s_ek[tid] = (gwf && kb + tid < I.ksteps) ? settled_end(I, kb + tid) : 0x7fffffff;
             csync();
-            constexpr int TG = TB < 16 ? TB : 16;  // steps per pass (register budget)
-            for (int tg = 0; tg < TB; tg += TG) {
+            constexpr int TG = TB < 8 ? TB : 8;  // steps per pass (register budget: no spills)
+            for (int tg = t_lo; tg < t_hi; tg += TG) {
                 float2 acc[TG][2];
 #pragma unroll
                 for (int t = 0; t < TG; ++t) acc[t][0] = acc[t][1] = make_float2(0.f, 0.f);
@@ -1335,7 +1384,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
 #pragma unroll
                     for (int t = 0; t < TG; ++t)
                         if (kb + tg + t < I.ksteps)
-                            *reinterpret_cast<float4 *>(prow(C, tg + t, 0) + j0) =
+                            *reinterpret_cast<float4 *>(prow(U.chunk, tg + t, 0) + j0) =
                                 make_float4(acc[t][0].x, acc[t][0].y, acc[t][1].x, acc[t][1].y);
                 }
             }
@@ -1506,6 +1555,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         // ================================================== update unit: step k, this tile
         const int k = U.k, t = k - kb;
         const int rel = k - L.k0;
+        const int nmid = I.mid ? min(I.mid, t / 16) : 0;  // mid units of sub-blocks 1 .. t/16
         // Two phases keep the partial and head sums off the step-to-step chain.  Phase A needs
         // only the tile's far count and this tile's rows up to k-2 (its own step k-2), so it
         // runs while step k-1 is still being updated; phase B waits for u^k on the halo tiles
@@ -1513,10 +1563,10 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         // partials by chunk, then lags hk .. 1.
         if (tid < 32) {  // the two waits run in parallel lanes
             int ok = 1;
-            if (tid == 0) {  // the far chunks and, with near units, the near partial
-                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C * L.fsub + I.near), L, 512);
+            if (tid == 0) {  // the far chunks and, with near units, the near (and mid) partials
+                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C * L.fsub + I.near + nmid), L, 512);
                 if (w < 0)
-                    note_failure(L, 3, k, tile, arrive_target(b, C * L.fsub + I.near), ld_acquire(&I.arrive[par * I.T + tile]),
+                    note_failure(L, 3, k, tile, arrive_target(b, C * L.fsub + I.near + nmid), ld_acquire(&I.arrive[par * I.T + tile]),
                                  L.k0, 0);
                 ok = w > 0;
             }
@@ -1534,8 +1584,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         const int nb = (I.mem_mode == 1) ? min(I.mem_L, k) : k;
         // head: lags 1 .. min(k-kb+T, n_base(k)), descending; with a near unit only the block's
         // own rows, lags 1 .. min(k-kb, n_base(k)) (the near partial holds the previous block's)
-        const int hk = I.near ? min(t, nb) : min(t + TB, nb);
-        const int CP = C + I.near;  // partial rows to sum
+        const int hk = I.near ? min(I.mid ? t % 16 : t, nb) : min(t + TB, nb);
+        const int CP = C + I.near + (nmid ? 1 : 0);  // partial rows to sum
         auto hrow = [&](int m) -> const float * { return hrow_at(k - m); };
         float H[V], H2[V], d[V];
 #pragma unroll
