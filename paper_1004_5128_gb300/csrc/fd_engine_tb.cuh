@@ -514,16 +514,24 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     if (SCALED) {
                         // FP16 rows hold delta * 2^e per (row, tile) (paired rows their hi and lo
                         // parts): the row's scale 2^-e joins its weights, and one power of two per
-                        // unit keeps the largest coefficient in [2^13, 2^14), so both FP16 halves
-                        // stay normal; the epilogue divides it out
+                        // unit keeps every coefficient below 2^14, so the FP16 halves cannot
+                        // overflow; the epilogue divides it out.  The bound is (largest weight) x
+                        // (largest row scale) over the whole unit: the two maxima are reduced
+                        // separately, as the largest weight and the largest scale may sit in
+                        // different threads' shares.
                         for (int a = tid; a < nrow; a += nthr) {
                             wsc[a] = __ldcg(I.hscale + (size_t)((r0 + a) % I.cap) * I.T + tile);
                             smax = fmaxf(smax, wsc[a]);
                         }
-                        float m = amax * smax;
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                        if ((tid & 31) == 0) s_wmax[tid >> 5] = m;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                            smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+                        }
+                        if ((tid & 31) == 0) {  // (at most 8 warps per half: 256 threads)
+                            s_wmax[tid >> 5] = amax;
+                            s_wmax[8 + (tid >> 5)] = smax;
+                        }
                     }
                     if (tid == 0) {
                         s_abort = 0;
@@ -534,8 +542,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 csync();
                 if (SCALED) {
                     if (tid == 0) {
-                        float m = 0.f;
-                        for (int w = 0; w < nthr / 32; ++w) m = fmaxf(m, s_wmax[w]);
+                        float am = 0.f, sm = 0.f;
+                        for (int w = 0; w < nthr / 32; ++w) {
+                            am = fmaxf(am, s_wmax[w]);
+                            sm = fmaxf(sm, s_wmax[8 + w]);
+                        }
+                        const float m = am * sm;
                         int ex = 0;
                         if (m > 0.f && isfinite(m)) frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1)
                         s_bnorm = ldexpf(1.f, max(-120, min(120, 14 - ex)));

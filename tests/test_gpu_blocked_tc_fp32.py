@@ -128,3 +128,31 @@ def test_config3_full_size_fp32_tensor_cores_vs_cuda_cores():
     got, s2 = run(p, time_block=32)
     assert s1.geometry()["far_tensor_cores"] == 0 and s2.geometry()["far_tensor_cores"] == 1
     assert rel_inf(got, ref) < TOL
+
+
+C2_CASES = [("full", synth.MEM_FULL, 32, 256, 4000), ("short", synth.MEM_SHORT, 64, 256, 1000),
+            ("adaptive", synth.MEM_ADAPTIVE, 32, 256, 2000), ("full128", synth.MEM_FULL, 32, 128, 2000)]
+
+
+@pytest.mark.parametrize("name,mode,tb,threads,K", C2_CASES, ids=[c[0] for c in C2_CASES])
+def test_fp32_tensor_cores_config2_row_scales_spread(name, mode, tb, threads, K):
+    """Config 2 (256^2, eight decaying Gaussians): the row scales of one far unit spread over many
+    octaves, so the coefficients' power of two must bound (largest weight) x (largest row scale)
+    over the unit, not the largest product within one thread's share (which overflowed FP16).
+    Against the CUDA-core run over the same FP32 rows."""
+    p = synth.config2(mode, K=K)
+    got, s = run(p, time_block=tb, tile_threads=threads)
+    assert s.geometry()["far_tensor_cores"] == 1
+    ref, _ = run(p, time_block=16)
+    assert rel_inf(got, ref) < TOL
+
+
+def test_fp16_tensor_cores_config2_row_scales_spread():
+    """The same bound on the FP16-history path, against the CUDA-core far loop over the same FP16
+    rows (what remains is FP32 summation order)."""
+    p = synth.config2(synth.MEM_FULL, K=4000)
+    got, s = run(p, hist="f16", time_block=32)
+    assert s.geometry()["far_tensor_cores"] == 1
+    ref, s2 = run(p, hist="f16", time_block=16, fma_far=True)
+    assert s2.geometry()["far_tensor_cores"] == 0
+    assert rel_inf(got, ref) < 5e-5
