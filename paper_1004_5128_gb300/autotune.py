@@ -29,7 +29,7 @@ from . import _lib as L
 from .frd import FRD, FRDBatch
 
 PARAMS = {
-    "time_block": [0, 8, 16, 32],
+    "time_block": [0, 8, 16, 32, 64],
     "step_updates": [0, 1],
     "tile_threads": [128, 256, 512],
     "chunk_terms": [32, 64, 128, 256, 512],
