@@ -65,8 +65,8 @@ enum { FD_F64 = 0, FD_F32 = 1, FD_BF16 = 2, FD_F16 = 3 };
                                       launch ends with FD_ERR_TIMEOUT (GPU stays usable) */
 #define FD_FLAG_STEP_UPDATES 32u   /* time_block: one update unit per step and tile even where
                                       block-long update units would fit (see time_block) */
-#define FD_FLAG_FMA_FAR 64u        /* time_block with BF16 history: multiply the far rows on the
-                                      CUDA cores instead of the tensor cores (see time_block) */
+#define FD_FLAG_FMA_FAR 64u        /* time_block with BF16 / F16 history: multiply the far rows on
+                                      the CUDA cores instead of the tensor cores (see time_block) */
 
 typedef struct fd_problem {
     int ndim;            /* 1, 2 or 3 (3-D: the 7-point analogue of eq. deltasimp) */
@@ -99,23 +99,27 @@ typedef struct fd_problem {
     int head_lags;       /* lags 1..head_lags are summed by the per-tile update from rows kept in
                             state precision (0 = 8 for F32/F64 history, 32 for BF16/F16) */
     int nz;              /* points along the third axis when ndim == 3, else 1 */
-    int time_block;      /* 0, or 4 / 8 / 16 (BF16 history also 32): temporally blocked sum (F32
-                            state and accumulation, F32 / BF16 / F16 history, no Kahan; with
+    int time_block;      /* 0, or 4 / 8 / 16 / 32 / 64: temporally blocked sum (F32 state and
+                            accumulation, F32 / BF16 / F16 history, no Kahan; with
                             FD_FLAG_KEEP_TAPE F32 history, full or short memory and 4 or 8).
-                            With BF16 history and blocks of 16 or 32 the far rows are multiplied
-                            on the tensor cores (tcgen05, FP32 accumulation in tensor memory, the
-                            weights split into BF16 hi + lo halves; tile_threads 128 or 256,
-                            stage_rows 16 or 32 dividing time_block) unless FD_FLAG_FMA_FAR.
-                            Low-precision history keeps the newest 2 time_block rows in FP32 as
-                            well.  Rows older than the current block of time_block steps
-                            are read once per block into time_block accumulators (the Toeplitz
-                            structure of eq. frac_norxn); the newest rows are summed per step.
-                            Adaptive memory: the older rows carry the weights that the medians
-                            settle on (psi on the base interval, d psi at a median, 0 between,
-                            Definition 3.2) and each step's tail rows (Proposition 3.1) are summed
-                            per step.  Same terms, grouped differently; history traffic drops by
-                            about time_block (adaptive: all rows are read once per block).  When the tiles are few against the grid (at most a
-                            quarter of its CTAs), one unit per tile carries a whole block's
+                            Rows older than the current block are read once per block into
+                            time_block accumulators (the Toeplitz structure of eq. frac_norxn);
+                            the newest rows are summed per step.  Far rows on the tensor cores
+                            (tcgen05, FP32 accumulation in tensor memory, weights split into
+                            16-bit hi + lo halves; tile_threads 128 or 256, stage_rows 16 or 32
+                            dividing time_block) unless FD_FLAG_FMA_FAR: BF16 / F16 history at
+                            16, 32 and 64; F32 history at 32 and 64, stored as FP16 hi + lo
+                            planes with a power-of-two scale per (row, tile).  4 / 8 / 16 on
+                            F32 history, and BF16 / F16 with FD_FLAG_FMA_FAR, use the CUDA
+                            cores.  Low-precision and paired history keep the newest
+                            2 time_block rows in FP32 as well.  Adaptive memory: the older rows
+                            carry the weights that the medians settle on (psi on the base
+                            interval, d psi at a median, 0 between, Definition 3.2) and each
+                            step's tail rows (Proposition 3.1) are summed per step.  Same terms,
+                            grouped differently; history traffic drops by about time_block
+                            (adaptive: all rows are read once per block).  When the tiles are
+                            few against the grid (at most a quarter of its CTAs) and the far rows
+                            run on the CUDA cores, one unit per tile carries a whole block's
                             updates and keeps the block's newest rows in on-chip memory, unless
                             FD_FLAG_STEP_UPDATES is set. */
 } fd_problem;
@@ -193,7 +197,8 @@ int fd_get_status(fd_handle *h);
  * waiting for its rows, 7 per-step chunk's bulk copy, 8 per-step fixup waiting for a halo
  * tile, 9 the stall injected by FD_FLAG_INJECT_STALL, 10 blocked far unit waiting for the
  * previous chunk's running sum, 11 tensor-core far unit waiting for a copy, its coefficient
- * block or its MMAs (operands as for site 2).  info[1..6] are the site's operands
+ * block or its MMAs (operands as for site 2), 12 near unit waiting for the previous block's
+ * rows, 13 mid unit waiting for its block's earlier rows.  info[1..6] are the site's operands
  * (step or block, tile, the counter target and the value last read, the launch's first step;
  * site 2 packs pairs into the high and low 32 bits), info[7] the CTA.  Only the first failure
  * since fd_set_state is kept.  Synchronises the stream. */
