@@ -279,13 +279,16 @@ inline size_t smem_bytes_tb(const Geo &g, int rwin, bool f16)
 
 // Tensor-core blocked kernel, one half of a CTA: stage ring (RS rows x P points of 16-bit history,
 // in two planes for paired FP32 history), 1 KB-aligned; NS coefficient blocks (tb/8 1 KB atoms, hi and lo halves
-// side by side); the coefficient window (and the row scales of FP16 or paired history); 3 NS + 1
+// side by side); the coefficient window (and the row scales of FP16 or paired history; with paired
+// history also the settled-weight window of a near or mid unit); 3 NS + 1
 // barriers; rounded up to 1 KB.  The CTA takes two halves plus 1 KB of slack to align the base.
 inline size_t smem_half_tc(const Geo &g, int rwin, bool scaled)
 {
     const size_t ring = (size_t)g.NS * g.RS * (g.threads * 4 / g.fsub) * g.sh * g.hplanes;  // no block-long update units
+    const size_t wr = (size_t)std::max(rwin, g.tb);  // a far chunk or a near unit's rows
     return align_up(align_up(ring, 1024) + (size_t)g.NS * (g.tb / 8) * 1024 +
-                        (size_t)(rwin + g.tb + (scaled ? rwin : 0)) * 4 + 16 + 8 * (size_t)(3 * g.NS + 1),
+                        (wr + g.tb + (scaled ? wr : 0) + (g.hplanes == 2 ? 2 * g.tb : 0)) * 4 + 16 +
+                        8 * (size_t)(3 * g.NS + 1),
                     1024);
 }
 
@@ -481,6 +484,10 @@ inline int64_t step_units(const Geo &g, const int4 &e)
     return (int64_t)g.T * std::max<int64_t>(1, (n + g.R - 1) / g.R);
 }
 
+// Near and mid units per (block, tile): with paired FP32 history they run on the tensor cores,
+// one per far sub-tile.
+inline int nsub_of(const Geo &g) { return (g.tc && g.hplanes == 2) ? g.fsub : 1; }
+
 // Units of group b of the blocked kernel: the far chunks of block b (none past the last block)
 // plus block b-1's update units (one per step and tile, or one per tile for the whole block).
 inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
@@ -489,9 +496,9 @@ inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
     if (b < g.nblocks) {
         int64_t Rb, Cb;
         block_chunks(p, g, b, Rb, Cb);
-        far = (int64_t)g.T * (Cb * g.fsub + g.near);  // far chunks (fsub units each), then the near units
+        far = (int64_t)g.T * (Cb * g.fsub + g.near * nsub_of(g));  // far chunks (fsub units each), near units
     }
-    return far + (b >= 1 ? (int64_t)g.T * ((g.ub ? 1 : g.tb) + g.mid) : 0);
+    return far + (b >= 1 ? (int64_t)g.T * ((g.ub ? 1 : g.tb) + g.mid * nsub_of(g)) : 0);
 }
 
 // History rows the blocked kernel reads over max_steps steps: the far rows once per block, then

@@ -196,6 +196,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // tensor cores: a stage holds RS rows of one far unit's P/fsub points (16-bit; two planes for
     // paired FP32 history)
     const int stage_tc = TC ? RS * row_bytes / L.fsub : 0;
+    // units per near or mid unit's (block, tile): with paired history they run on the tensor cores,
+    // one per far sub-tile
+    const int nsub = PAIR ? L.fsub : 1;
     // CTA (half) barriers
     auto csync = [&]() {
         if (TC)
@@ -241,10 +244,15 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // lo halves at K RS..2RS-1 of the same rows (RS <= 32)
     constexpr int BBLK = (TB / 8) * 1024;
     unsigned char *bring = smem + ((ring_bytes + 1023) & ~(size_t)1023);
+    // coefficient window and row scales cover the longest unit: a far chunk (rmax rows) or a near
+    // unit (TB rows, 2 TB - 1 lags)
+    const int WR = max(L.rmax, TB);
     float *win = reinterpret_cast<float *>(bring + (size_t)NS * BBLK);
-    float *wsc = win + L.rmax + TB;  // FP16 or paired history: the unit's row scales
+    float *wsc = win + WR + TB;  // FP16 or paired history: the unit's row scales
+    // paired history: the settled weights of a near or mid unit's lags (2 TB entries)
+    float *win2 = wsc + (SCALED ? WR : 0);
     if (TC)
-        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(wsc + (SCALED ? L.rmax : 0)) + 15) & ~uintptr_t(15));
+        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(win2 + (PAIR ? 2 * TB : 0)) + 15) & ~uintptr_t(15));
     uint64_t *full = bars, *empty = bars + NS, *bfull = bars + 2 * NS, *done_bar = bars + 3 * NS;
     __shared__ uint32_t s_tmem;
     // adaptive memory: bit j of gmask[lo] says w[lo + j] != 0 (the window of a four-row group);
@@ -334,7 +342,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const int gb = gi.y;  // group: far units of block gb, updates of block gb-1
                 const int k_end = min(L.k_end, I.ksteps);  // a batch runs each instance to its end
                 const int Tu = (gb >= 1) ? I.T * (I.ub ? 1 : TB) : 0;  // block gb-1's update units
-                const int Mu = (gb >= 1) ? I.T * I.mid : 0;              // block gb-1's mid units
+                const int Mu = (gb >= 1) ? I.T * I.mid * nsub : 0;       // block gb-1's mid units
                 const long long F = gsize - (long long)(Tu + Mu);  // block gb's far units
                 long long f = -1;  // far unit index within block gb, or -1 for an update unit
                 U.inst = gi.x;
@@ -359,14 +367,16 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     } else {
                         f = (local < F1) ? local : local - Tu;
                     }
-                } else if (I.near && gb * TB < I.ksteps && local >= gsize - I.T) {
+                } else if (I.near && gb * TB < I.ksteps && local >= gsize - I.T * nsub) {
                     // near unit of block gb (the group's last T units): the previous block's rows
                     // for every step of block gb, once block gb-1's updates of the tile are done
                     const int kb = gb * TB;
                     if (kb >= k_end) continue;  // block starts at or after the launch's end
                     U.fix = 3;
                     U.b = gb;
-                    U.tile = (int)(local - (gsize - I.T));
+                    const int nidx = (int)(local - (gsize - I.T * nsub));
+                    U.tile = nidx % I.T;
+                    U.sub = nidx / I.T;
                     U.C = far_chunks<TB>(I, gb);
                     U.chunk = U.C;  // its partial rows follow the far chunks'
                     U.r0 = max(0, kb - TB);
@@ -383,10 +393,10 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     // sub-block j of block gb-1, then the T update units of step s
                     int sseg = 0;
                     const int Ts = Tu / TB;
-                    const long long F0 = F - (I.near && gb * TB < I.ksteps ? I.T : 0);  // far units proper
+                    const long long F0 = F - (I.near && gb * TB < I.ksteps ? I.T * nsub : 0);  // far units proper
                     auto seg_start = [&](int sg) -> long long {
                         const int mids = (Mu && sg >= 1) ? min(I.mid, (sg - 1) / 16) : 0;
-                        return (long long)sg * Ts + (long long)I.T * mids + (long long)sg * F0 / TB;
+                        return (long long)sg * Ts + (long long)I.T * nsub * mids + (long long)sg * F0 / TB;
                     };
                     // segments are near equal: estimate, then step to the exact one
                     sseg = (int)min((long long)(TB - 1), local * TB / max(1ll, (long long)TB * Ts + F0 + Mu));
@@ -396,7 +406,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     const long long fsn = (long long)(sseg + 1) * F0 / TB - fs0;  // far units in slice s
                     long long off = local - seg_start(sseg);
                     const bool seg_mid = Mu && sseg >= 16 && sseg % 16 == 0;
-                    if (seg_mid && off >= fsn && off < fsn + I.T) {
+                    if (seg_mid && off >= fsn && off < fsn + I.T * nsub) {
                         // mid unit: rows kb .. kb+s-1 of block gb-1 for its steps s .. s+15.  Skipped
                         // only when no update of this launch needs it (the updates' arrival target
                         // counts every earlier sub-block's mid unit, so those run even when their
@@ -405,7 +415,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         if (kb1 + sseg >= k_end || kb1 + TB <= L.k0) continue;
                         U.fix = 4;
                         U.b = gb - 1;
-                        U.tile = (int)(off - fsn);
+                        U.tile = (int)((off - fsn) % I.T);
+                        U.sub = (int)((off - fsn) / I.T);
                         U.k = kb1 + sseg;
                         U.C = far_chunks<TB>(I, gb - 1);
                         U.chunk = U.C + 1;  // after the far chunks' and the near unit's rows
@@ -418,7 +429,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         }
                         break;
                     }
-                    if (seg_mid && off >= fsn) off -= I.T;
+                    if (seg_mid && off >= fsn) off -= I.T * nsub;
                     if (off >= fsn) {  // update unit: block gb-1, step s
                         const int k = (gb - 1) * TB + sseg;
                         if (k < L.k0 || k >= k_end) continue;  // block edge outside this launch
@@ -481,9 +492,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                                              ((size_t)(((par * I.maxC + c) * TB + t) * PLANES + plane)) * I.part_pitch);
         };
 
-        if (!U.fix) {
+        if (!U.fix || (PAIR && (U.fix == 3 || U.fix == 4))) {
             if constexpr (TC) {
                 // ============================================== far unit on the tensor cores
+                // (with paired FP32 history also the near and mid units: the same contraction over
+                // the previous block's rows for the block's steps, or over the block's earlier rows
+                // for one sub-block's 16 steps, from the pair planes of the history)
                 // D[p][t] = sum over rows r in [r0, r1) of H[r][p] * c(t, r), c(t, r) = w(kb + t - r):
                 // M = 128 points, N = TB steps, K = 16 rows per MMA, FP32 accumulators in tensor
                 // memory (block m of the unit's Pf/128 point blocks at columns m*TB ...; the unit
@@ -498,19 +512,33 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
                 const int Pf = I.P / L.fsub, p0 = tile * I.P + U.sub * Pf;  // the unit's points
                 const int MB = Pf / 128;
+                const bool nm = U.fix != 0;                    // near or mid unit
+                const int t_lo = (U.fix == 4) ? U.k - kb : 0;  // its steps: kb+t_lo .. kb+t_lo+NN-1
+                const int NN = (U.fix == 4) ? 16 : TB;
+                // near and mid rows take each step's own weight of their lag (adaptive memory: the
+                // settled weight up to the step's e(k), psi beyond), far rows the settled one
+                const bool per_step = nm && I.gw;
                 int rlo_t, rhi_t;
                 far_rows<TB>(I, b, rlo_t, rhi_t);  // rows below rlo_t are not far rows of this block
+                if (nm) rlo_t = r0;
                 {
-                    // coefficient window win[j] = w(lag0 + j), lag0 = kb - (r1 - 1): row r, step kb+t
-                    // uses win[(r1 - 1 - r) + t]; short memory cuts lags beyond its window
-                    const float *wsrc = reinterpret_cast<const float *>(I.gw ? I.gw : I.psi);
-                    const int lag0 = kb - (r1 - 1);
+                    // coefficient window win[j] = w(lag0 + j), lag0 = kb + t_lo - (r1 - 1): row r,
+                    // step kb+t_lo+t uses win[(r1 - 1 - r) + t]; short memory cuts lags beyond its
+                    // window; per-step weights take win (psi) or win2 (settled) by the step's e(k)
+                    const float *wsrc = reinterpret_cast<const float *>((I.gw && !nm) ? I.gw : I.psi);
+                    const int lag0 = kb + t_lo - (r1 - 1);
                     float amax = 0.f, smax = 0.f;
-                    for (int j = tid; j < nrow + TB - 1; j += nthr) {
+                    for (int j = tid; j < nrow + NN - 1; j += nthr) {
                         const int lag = lag0 + j;
-                        win[j] = (I.mem_mode == 1 && lag > I.mem_L) ? 0.f : wsrc[lag];
+                        const bool cut = I.mem_mode == 1 && lag > I.mem_L;
+                        win[j] = cut ? 0.f : wsrc[lag];
                         amax = fmaxf(amax, fabsf(win[j]));
+                        if (per_step) {
+                            win2[j] = cut ? 0.f : reinterpret_cast<const float *>(I.gw)[lag];
+                            amax = fmaxf(amax, fabsf(win2[j]));
+                        }
                     }
+                    if (per_step && tid < TB) s_ek[tid] = (kb + tid < I.ksteps) ? settled_end(I, kb + tid) : 0x7fffffff;
                     if (SCALED) {
                         // FP16 rows hold delta * 2^e per (row, tile) (paired rows their hi and lo
                         // parts): the row's scale 2^-e joins its weights, and one power of two per
@@ -576,6 +604,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     return true;
                 };
                 constexpr uint32_t IDESC = tc::idesc_f16_amn(128, TB, !SCALED);
+                constexpr uint32_t IDESC16 = tc::idesc_f16_amn(128, 16, !SCALED);  // mid units
+                const uint32_t idesc = (NN == TB) ? IDESC : IDESC16;
                 if (warp == 0) {
                     if (lane == 0) {  // history stages: 64 points x RS rows per point group
                         // (paired history: the hi plane's box, then the lo plane's, cap rows on)
@@ -618,9 +648,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                                         const uint32_t d = tmem + (uint32_t)(m * TB);
                                         const uint32_t acc = (s | kk) ? 1u : 0u;
                                         const uint64_t bdh = tc::desc_sw128(bh + (uint32_t)(kk * 32), 16u, 1024u);
-                                        tc::mma_f16(d, dh, bdh, IDESC, acc);
-                                        tc::mma_f16(d, dh, tc::desc_sw128(bl + (uint32_t)(kk * 32), 16u, 1024u), IDESC, 1u);
-                                        tc::mma_f16(d, dl, bdh, IDESC, 1u);
+                                        tc::mma_f16(d, dh, bdh, idesc, acc);
+                                        tc::mma_f16(d, dh, tc::desc_sw128(bl + (uint32_t)(kk * 32), 16u, 1024u), idesc, 1u);
+                                        tc::mma_f16(d, dl, bdh, idesc, 1u);
                                     }
                             } else
                             for (int m = 0; m < MB; ++m)
@@ -631,8 +661,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                                                                        (uint32_t)(RS * 128), 1024u);
                                     const uint32_t d = tmem + (uint32_t)(m * TB);
                                     const uint32_t acc = (s | kk) ? 1u : 0u;
-                                    tc::mma_f16(d, ad, tc::desc_sw128(bh + (uint32_t)(kk * 32), 16u, 1024u), IDESC, acc);
-                                    tc::mma_f16(d, ad, tc::desc_sw128(bl + (uint32_t)(kk * 32), 16u, 1024u), IDESC, 1u);
+                                    tc::mma_f16(d, ad, tc::desc_sw128(bh + (uint32_t)(kk * 32), 16u, 1024u), idesc, acc);
+                                    tc::mma_f16(d, ad, tc::desc_sw128(bl + (uint32_t)(kk * 32), 16u, 1024u), idesc, 1u);
                                 }
                             tc::commit(&empty[slot]);  // the slot is free once these MMAs are done
                             s_mma = s + 1;
@@ -647,10 +677,13 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
                         if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
                         unsigned char *bh = bring + (size_t)slot * BBLK;
-                        for (int e = me; e < TB * RS; e += nb) {
+                        for (int e = me; e < NN * RS; e += nb) {
                             const int t = e / RS, i = e - t * RS;
                             const int r = r0 + s * RS + i;
-                            float c = (r < rlo_t) ? 0.f : win[(r1 - 1 - r) + t];
+                            const int wi = (r1 - 1 - r) + t;
+                            float c = (r < rlo_t) ? 0.f
+                                      : (per_step && kb + t_lo + t - r <= s_ek[t_lo + t]) ? win2[wi]
+                                                                                         : win[wi];
                             if (SCALED) c *= wsc[r - r0] * bnorm;
                             TB16 hi, lo;
                             if constexpr (SCALED) {
@@ -714,29 +747,31 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 csync();
                 if (s_abort) break;
                 // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. of point blocks
-                // m = w / 4, w / 4 + nwarp / 4, ...; each thread holds one point's TB sums
+                // m = w / 4, w / 4 + nwarp / 4, ...; each thread takes one point's NN sums, 16
+                // columns at a time
                 const int q = warp & 3;
                 for (int m = warp >> 2; m < MB; m += nwarp >> 2) {
                     const int j = p0 + m * 128 + q * 32 + lane;
-                    float v[TB];
-                    if (nst > 0) {
+#pragma unroll 1
+                    for (int c = 0; c < NN; c += 16) {  // warp-uniform
+                        float v[16];
+                        if (nst > 0) {
+                            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(m * TB + c), v);
+                        } else {
 #pragma unroll
-                        for (int c = 0; c < TB; c += 16)
-                            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(m * TB + c), v + c);
-                    } else {
+                            for (int t = 0; t < 16; ++t) v[t] = 0.f;
+                        }
+                        if (SCALED) {  // exact: a power of two
 #pragma unroll
-                        for (int t = 0; t < TB; ++t) v[t] = 0.f;
-                    }
-                    if (SCALED) {  // exact: a power of two
+                            for (int t = 0; t < 16; ++t) v[t] *= binv;
+                        }
+                        if (j < I.N) {
 #pragma unroll
-                        for (int t = 0; t < TB; ++t) v[t] *= binv;
-                    }
-                    if (j < I.N) {
-#pragma unroll
-                        for (int t = 0; t < TB; ++t) {
-                            float sum = v[t];
-                            if (chain) sum = __ldcg(prow(c0 - 1, t, 0) + j) + v[t];
-                            prow(c0, t, 0)[j] = sum;
+                            for (int t = 0; t < 16; ++t) {
+                                float sum = v[t];
+                                if (chain) sum = __ldcg(prow(c0 - 1, c + t, 0) + j) + v[t];
+                                prow(c0, t_lo + c + t, 0)[j] = sum;
+                            }
                         }
                     }
                 }
@@ -1576,9 +1611,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         if (tid < 32) {  // the two waits run in parallel lanes
             int ok = 1;
             if (tid == 0) {  // the far chunks and, with near units, the near (and mid) partials
-                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C * L.fsub + I.near + nmid), L, 512);
+                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C * L.fsub + (I.near + nmid) * nsub), L, 512);
                 if (w < 0)
-                    note_failure(L, 3, k, tile, arrive_target(b, C * L.fsub + I.near + nmid), ld_acquire(&I.arrive[par * I.T + tile]),
+                    note_failure(L, 3, k, tile, arrive_target(b, C * L.fsub + (I.near + nmid) * nsub), ld_acquire(&I.arrive[par * I.T + tile]),
                                  L.k0, 0);
                 ok = w > 0;
             }
