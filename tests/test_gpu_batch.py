@@ -136,7 +136,8 @@ def test_config4_full_batch_large_instances_vs_scalar_recursions(mode):
         refs[i] = sum(c * oracle.scalar_mode(p, laplacian_eigenvalue(p, qx, qy))[-1] * synth.eigenmode(p, qx, qy)
                       for qx, qy, c in ms)
     out, b = run_batch(probs)
-    assert b.geometry(0)["time_block"] == 16   # the tuned batch geometry
+    g0 = b.geometry(0)   # the tuned batch geometry: tensor-core far units, paired FP32 history
+    assert g0["time_block"] == 32 and g0["far_tensor_cores"] == 1
     for i in big1 + big2:
         assert rel_inf(out[i], refs[i]) < 1e-5, (i, probs[i]["nx"], probs[i]["K"])
     for i in order[:3]:
