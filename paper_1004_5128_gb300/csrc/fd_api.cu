@@ -240,6 +240,8 @@ struct Geo {
     int tc;          // blocked: far units on the tensor cores
     int hplanes;     // history planes: 2 for FP32 history on the tensor cores (FP16 hi and lo), else 1
     int fsub;        // tensor cores: far units per (chunk, tile), each of P/fsub points (else 1)
+    int nmtc;        // tensor cores, blocks of 32+: near and mid units on the tensor cores
+    int lo_plane;    // the history stores a lo plane (paired FP32, or 16-bit history with nmtc)
     int halves;      // tensor cores: each CTA runs as two halves of `threads` threads
     size_t smem_half;  // tensor cores: dynamic shared memory of one half
     int tmem_cols;     // tensor cores: tensor-memory columns a CTA allocates (at most 512)
@@ -287,7 +289,7 @@ inline size_t smem_half_tc(const Geo &g, int rwin, bool scaled)
     const size_t ring = (size_t)g.NS * g.RS * (g.threads * 4 / g.fsub) * g.sh * g.hplanes;  // no block-long update units
     const size_t wr = (size_t)std::max(rwin, g.tb);  // a far chunk or a near unit's rows
     return align_up(align_up(ring, 1024) + (size_t)g.NS * (g.tb / 8) * 1024 +
-                        (wr + g.tb + (scaled ? wr : 0) + (g.hplanes == 2 ? 2 * g.tb : 0)) * 4 + 16 +
+                        (wr + g.tb + (scaled ? wr : 0) + (g.nmtc ? 2 * g.tb : 0)) * 4 + 16 +
                         8 * (size_t)(3 * g.NS + 1),
                     1024);
 }
@@ -359,8 +361,14 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.T = (int)((N + g.P - 1) / g.P);
     // tensor cores: stages of 16 rows (32 where the block allows at 128 threads of 16-bit history),
     // as many as fit in 88 KB per half of a CTA (2 .. 5)
-    const int tc_rs = (g.tc && p.time_block % 32 == 0 && th <= 128 && g.hplanes == 1) ? 32 : 16;
+    // (16-bit history with blocks of 32+: stages of 32 rows, the bytes of a near or mid unit's
+    // stage of 16 rows in two planes)
+    const int tc_rs = (g.tc && p.time_block % 32 == 0 && g.hplanes == 1) ? 32 : 16;
     g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
+    // near and mid units on the tensor cores: blocks of 32+, and a stage of 16 rows in two planes
+    // the size of a far stage
+    g.nmtc = g.tc && p.time_block >= 32 && g.RS * g.hplanes == 32;
+    g.lo_plane = g.hplanes == 2 || g.nmtc;
     // Far sub-tiles: a tensor-core far unit covers P/fsub points, so that both halves' accumulators
     // (P/fsub/128 x tb columns each) fit the 512 tensor-memory columns and a stage of RS rows
     // (two planes for paired history) stays within 32 KB; the update units keep the whole tile.
@@ -484,9 +492,8 @@ inline int64_t step_units(const Geo &g, const int4 &e)
     return (int64_t)g.T * std::max<int64_t>(1, (n + g.R - 1) / g.R);
 }
 
-// Near and mid units per (block, tile): with paired FP32 history they run on the tensor cores,
-// one per far sub-tile.
-inline int nsub_of(const Geo &g) { return (g.tc && g.hplanes == 2) ? g.fsub : 1; }
+// Near and mid units per (block, tile): on the tensor cores, one per far sub-tile.
+inline int nsub_of(const Geo &g) { return g.nmtc ? g.fsub : 1; }
 
 // Units of group b of the blocked kernel: the far chunks of block b (none past the last block)
 // plus block b-1's update units (one per step and tile, or one per tile for the whole block).
@@ -578,6 +585,7 @@ struct Layout {
     int *glag, *br0;
     int4 *sched;
     char *tmap;  // tensor-core path: tensor map of the history rows (128 bytes, 64-byte aligned)
+    char *tmap2;  // tensor-core near / mid units over 16-bit history: both planes, 16-row boxes
     // adjoint of adaptive memory: d/dgamma of the settled weights, the full-memory schedule the
     // per-step adjoint runs, and the tail terms by adjoint row
     char *dgw;
@@ -605,7 +613,7 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
         L.alo[i] = (comp && adj) ? c.take(ubytes) : nullptr;
         L.rlo[i] = (comp && adj) ? c.take(ubytes) : nullptr;
     }
-    L.hist = c.take((size_t)g.cap * g.pitch * g.hplanes);
+    L.hist = c.take((size_t)g.cap * g.pitch * (g.lo_plane ? 2 : 1));
     L.hring = g.hring_sep ? c.take((size_t)g.hring_cap * g.hring_pitch) : L.hist;
     // power-of-two scales per (row, tile): FP16 history, and paired FP32 history
     L.hscale = (p.hist_dtype == FD_F16 || g.hplanes == 2)
@@ -638,6 +646,7 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
         L.acorr = (fdk::AdjTail *)c.take(sizeof(fdk::AdjTail) * std::max<size_t>(1, tl.e.size()));
     }
     L.tmap = g.tc ? c.take(128) : nullptr;
+    L.tmap2 = (g.nmtc && g.hplanes == 1) ? c.take(128) : nullptr;
     L.ckpt = L.seg = L.rec[0] = L.rec[1] = L.ahist = L.abuf[0] = L.abuf[1] = nullptr;
     L.dots = nullptr;
     L.ckpt_rows = L.seg_rows = 0;
@@ -800,19 +809,20 @@ EncodeTiledFn encode_tiled()
 // rows, groups of 64 points; the group stride of 128 bytes is below the row pitch) whose one box
 // per stage covers all P/64 groups of a tile.  If the driver refuses that view, a 2-D view
 // (points, rows) with one box per group.  Points past the padded row read as zeros.  Encoded on
-// the host, copied into the workspace; returns the rank used (0 on failure).
-int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, int hist)
+// the host, copied into the workspace; returns the rank used (0 on failure).  `planes` planes of
+// cap rows each (the lo plane follows the rows), boxes of `box_rows` rows.
+int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, int hist, int planes, int box_rows)
 {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return 0;
     // (paired FP32 history: FP16, both planes as one tensor of 2 cap rows)
     const CUtensorMapDataType dt =
         hist == FD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const cuuint64_t rows = (cuuint64_t)g.cap * g.hplanes;
+    const cuuint64_t rows = (cuuint64_t)g.cap * planes;
     {
         const cuuint64_t dims[3] = {64u, rows, (cuuint64_t)(g.pitch / 128)};
         const cuuint64_t strides[2] = {(cuuint64_t)g.pitch, 128u};
-        const cuuint32_t box[3] = {64u, (cuuint32_t)g.RS, (cuuint32_t)(g.P / g.fsub / 64)};
+        const cuuint32_t box[3] = {64u, (cuuint32_t)box_rows, (cuuint32_t)(g.P / g.fsub / 64)};
         const cuuint32_t es[3] = {1u, 1u, 1u};
         if (enc(m, dt, 3, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -821,7 +831,7 @@ int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, int hist)
     }
     const cuuint64_t dims[2] = {(cuuint64_t)(g.pitch / 2), rows};
     const cuuint64_t strides[1] = {(cuuint64_t)g.pitch};
-    const cuuint32_t box[2] = {64u, (cuuint32_t)g.RS};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
     const cuuint32_t es[2] = {1u, 1u};
     if (enc(m, dt, 2, L.hist, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -833,10 +843,15 @@ int encode_tmap(const Geo &g, const Layout &L, CUtensorMap *m, int hist)
 int upload_tmap(const fd_problem &p, const Geo &g, const Layout &L, Inst &I, cudaStream_t st)
 {
     if (!g.tc) return FD_OK;
-    alignas(64) CUtensorMap m;
-    I.tmap_rank = encode_tmap(g, L, &m, p.hist_dtype);
+    alignas(64) CUtensorMap m, m2;
+    I.tmap_rank = encode_tmap(g, L, &m, p.hist_dtype, g.hplanes, g.RS);
     if (!I.tmap_rank) return FD_ERR_CUDA;
     CK(cudaMemcpyAsync(L.tmap, &m, sizeof(m), cudaMemcpyHostToDevice, st));
+    if (L.tmap2) {  // near and mid units over 16-bit history: both planes in boxes of 16 rows
+        I.tmap2_rank = encode_tmap(g, L, &m2, p.hist_dtype, 2, 16);
+        if (!I.tmap2_rank) return FD_ERR_CUDA;
+        CK(cudaMemcpyAsync(L.tmap2, &m2, sizeof(m2), cudaMemcpyHostToDevice, st));
+    }
     return FD_OK;
 }
 
@@ -866,6 +881,8 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.near = g.near;
     I.mid = g.mid;
     I.tmap = L.tmap;
+    I.tmap2 = L.tmap2;
+    I.lo_plane = g.lo_plane && !adj;
     if (g.tc) {  // tensor-memory columns per half: the geometry's (at most 256, checked at init)
         I.tc_cols = g.tmem_cols / g.halves;
     }
@@ -1013,6 +1030,7 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
     L.rmax = h->g.tb ? h->g.rwin : h->g.R;
     L.smem_half = (int)h->g.smem_half;
     L.fsub = h->g.fsub;
+    L.nm_tc = h->g.nmtc;
     L.queue = h->ctrl.queue;
     L.err = h->ctrl.err;
     L.nonfinite = h->ctrl.nonfinite;
@@ -1613,6 +1631,7 @@ int fd_batch_init(const fd_problem *probs, int count, void *workspace, size_t ws
         L.rmax = b->rmax;
         L.smem_half = (int)b->smem_half;
         L.fsub = b->g[0].fsub;
+        L.nm_tc = b->g[0].nmtc;
         L.queue = b->ctrl.queue;
         L.err = b->ctrl.err;
         L.nonfinite = b->ctrl.nonfinite;

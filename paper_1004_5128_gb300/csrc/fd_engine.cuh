@@ -68,6 +68,10 @@ struct Inst {
     int tc_cols;             // blocked tensor-core kernel: tensor-memory columns per CTA
     int tmap_rank;           // blocked tensor-core kernel: 3 = one box per stage, 2 = one per 64 points
     const void *tmap;        // blocked tensor-core kernel: tensor map of the history rows
+    const void *tmap2;       // tensor-core near / mid units over 16-bit history: both planes, 16-row boxes
+    int tmap2_rank;
+    int lo_plane;            // the history has a lo plane cap rows after its rows (16-bit: fp16/bf16 of
+                             // the rounding remainder), read by tensor-core near and mid units
     int tape_k0, tape_every, tape_rows;
     int adj_K, uadj_r0;      // adjoint: u^r is row (adj_K-1-k) - uadj_r0 of uadj
     double S, dt;
@@ -153,6 +157,7 @@ struct Launch {
     int rmax;                // largest chunk (terms) over the launch's instances
     int smem_half;           // tensor-core kernels: dynamic shared memory of each half of a CTA
     int fsub;                // tensor-core kernels: far units per (chunk, tile), each of P/fsub points
+    int nm_tc;               // tensor-core kernels: near and mid units on the tensor cores (one per sub-tile)
     unsigned long long *queue;
     int *err;
     unsigned *nonfinite;

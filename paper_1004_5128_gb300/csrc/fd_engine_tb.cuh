@@ -196,9 +196,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     // tensor cores: a stage holds RS rows of one far unit's P/fsub points (16-bit; two planes for
     // paired FP32 history)
     const int stage_tc = TC ? RS * row_bytes / L.fsub : 0;
-    // units per near or mid unit's (block, tile): with paired history they run on the tensor cores,
-    // one per far sub-tile
-    const int nsub = PAIR ? L.fsub : 1;
+    // units per near or mid unit's (block, tile): on the tensor cores, one per far sub-tile
+    const int nsub = (TC && L.nm_tc) ? L.fsub : 1;
     // CTA (half) barriers
     auto csync = [&]() {
         if (TC)
@@ -249,10 +248,10 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
     const int WR = max(L.rmax, TB);
     float *win = reinterpret_cast<float *>(bring + (size_t)NS * BBLK);
     float *wsc = win + WR + TB;  // FP16 or paired history: the unit's row scales
-    // paired history: the settled weights of a near or mid unit's lags (2 TB entries)
+    // tensor-core near and mid units: the settled weights of their lags (2 TB entries)
     float *win2 = wsc + (SCALED ? WR : 0);
     if (TC)
-        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(win2 + (PAIR ? 2 * TB : 0)) + 15) & ~uintptr_t(15));
+        bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(win2 + (L.nm_tc ? 2 * TB : 0)) + 15) & ~uintptr_t(15));
     uint64_t *full = bars, *empty = bars + NS, *bfull = bars + 2 * NS, *done_bar = bars + 3 * NS;
     __shared__ uint32_t s_tmem;
     // adaptive memory: bit j of gmask[lo] says w[lo + j] != 0 (the window of a four-row group);
@@ -492,12 +491,13 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                                              ((size_t)(((par * I.maxC + c) * TB + t) * PLANES + plane)) * I.part_pitch);
         };
 
-        if (!U.fix || (PAIR && (U.fix == 3 || U.fix == 4))) {
+        if (!U.fix || (TC && L.nm_tc && (U.fix == 3 || U.fix == 4))) {
             if constexpr (TC) {
                 // ============================================== far unit on the tensor cores
-                // (with paired FP32 history also the near and mid units: the same contraction over
+                // (and, with blocks of 32 or more, the near and mid units: the same contraction over
                 // the previous block's rows for the block's steps, or over the block's earlier rows
-                // for one sub-block's 16 steps, from the pair planes of the history)
+                // for one sub-block's 16 steps, from the history's hi and lo planes: the pair of
+                // paired FP32 history, or the 16-bit row and its rounding remainder)
                 // D[p][t] = sum over rows r in [r0, r1) of H[r][p] * c(t, r), c(t, r) = w(kb + t - r):
                 // M = 128 points, N = TB steps, K = 16 rows per MMA, FP32 accumulators in tensor
                 // memory (block m of the unit's Pf/128 point blocks at columns m*TB ...; the unit
@@ -507,12 +507,18 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 // plane (a third MMA).  Roles: warp 0 lane 0 issues the tensor-map copies of the
                 // history stages, warp 1 lane 0 issues the MMAs, the other warps write each
                 // stage's coefficient block; mbarriers order them, with no CTA barrier per stage.
-                const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;  // whole stages (multiples of RS)
-                const int nst = nrow / RS;
+                const bool nm = U.fix != 0;                    // near or mid unit
+                // near and mid units read both planes in stages of 16 rows (as paired far units
+                // do), 16-bit far units one plane in stages of RS rows: the same bytes per stage
+                const bool two = PAIR || nm;
+                const int RSu = nm ? 16 : RS;
+                const void *tmu = (nm && !PAIR) ? I.tmap2 : I.tmap;
+                const int rank_u = (nm && !PAIR) ? I.tmap2_rank : I.tmap_rank;
+                const int r0 = U.r0, r1 = U.r1, nrow = r1 - r0;  // whole stages (multiples of RSu)
+                const int nst = nrow / RSu;
                 const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
                 const int Pf = I.P / L.fsub, p0 = tile * I.P + U.sub * Pf;  // the unit's points
                 const int MB = Pf / 128;
-                const bool nm = U.fix != 0;                    // near or mid unit
                 const int t_lo = (U.fix == 4) ? U.k - kb : 0;  // its steps: kb+t_lo .. kb+t_lo+NN-1
                 const int NN = (U.fix == 4) ? 16 : TB;
                 // near and mid rows take each step's own weight of their lag (adaptive memory: the
@@ -608,21 +614,21 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const uint32_t idesc = (NN == TB) ? IDESC : IDESC16;
                 if (warp == 0) {
                     if (lane == 0) {  // history stages: 64 points x RS rows per point group
-                        // (paired history: the hi plane's box, then the lo plane's, cap rows on)
-                        const size_t plane_bytes = (size_t)RS * Pf * 2;
+                        // (two planes: the hi plane's box, then the lo plane's, cap rows on)
+                        const size_t plane_bytes = (size_t)RSu * Pf * 2;
                         for (int s = 0; s < nst; ++s) {
                             const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
                             if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
                             unsigned char *a = stages + (size_t)slot * stage_tc;
                             mbar_expect_tx(&full[slot], (uint32_t)stage_tc);
-                            for (int pl = 0; pl < (PAIR ? 2 : 1); ++pl) {
+                            for (int pl = 0; pl < (two ? 2 : 1); ++pl) {
                                 unsigned char *ap = a + pl * plane_bytes;
-                                const int y = r0 + s * RS + pl * I.cap;
-                                if (I.tmap_rank == 3)  // one box: 64 points x RS rows x P/64 point groups
-                                    tc::tma_load_3d(ap, I.tmap, 0, y, p0 / 64, &full[slot]);
+                                const int y = r0 + s * RSu + pl * I.cap;
+                                if (rank_u == 3)  // one box: 64 points x RSu rows x Pf/64 point groups
+                                    tc::tma_load_3d(ap, tmu, 0, y, p0 / 64, &full[slot]);
                                 else
                                     for (int j = 0; j < Pf / 64; ++j)
-                                        tc::tma_load_2d(ap + (size_t)j * RS * 128, I.tmap, p0 + 64 * j, y,
+                                        tc::tma_load_2d(ap + (size_t)j * RSu * 128, tmu, p0 + 64 * j, y,
                                                         &full[slot]);
                             }
                             s_iss = s + 1;
@@ -636,15 +642,15 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             if (!wait_bar(&full[slot], ph, s) || !wait_bar(&bfull[slot], ph, s)) break;
                             tc::fence_after();
                             const uint32_t a0 = tc::saddr(stages + (size_t)slot * stage_tc);
-                            const uint32_t bh = tc::saddr(bring + (size_t)slot * BBLK), bl = bh + (uint32_t)(RS * 2);
-                            if (PAIR) {
-                                // A: hi plane as below, the lo plane RS*P*2 bytes further
-                                const uint32_t lo_off = (uint32_t)(RS * Pf * 2);
+                            const uint32_t bh = tc::saddr(bring + (size_t)slot * BBLK), bl = bh + (uint32_t)(RSu * 2);
+                            if (two) {
+                                // A: hi plane as below, the lo plane RSu*Pf*2 bytes further
+                                const uint32_t lo_off = (uint32_t)(RSu * Pf * 2);
                                 for (int m = 0; m < MB; ++m)
-                                    for (int kk = 0; kk < RS / 16; ++kk) {
-                                        const uint32_t ah = a0 + (uint32_t)(2 * m * RS * 128 + kk * 2048);
-                                        const uint64_t dh = tc::desc_sw128(ah, (uint32_t)(RS * 128), 1024u);
-                                        const uint64_t dl = tc::desc_sw128(ah + lo_off, (uint32_t)(RS * 128), 1024u);
+                                    for (int kk = 0; kk < RSu / 16; ++kk) {
+                                        const uint32_t ah = a0 + (uint32_t)(2 * m * RSu * 128 + kk * 2048);
+                                        const uint64_t dh = tc::desc_sw128(ah, (uint32_t)(RSu * 128), 1024u);
+                                        const uint64_t dl = tc::desc_sw128(ah + lo_off, (uint32_t)(RSu * 128), 1024u);
                                         const uint32_t d = tmem + (uint32_t)(m * TB);
                                         const uint32_t acc = (s | kk) ? 1u : 0u;
                                         const uint64_t bdh = tc::desc_sw128(bh + (uint32_t)(kk * 32), 16u, 1024u);
@@ -677,9 +683,9 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         const uint32_t use = tc_use + (uint32_t)s, slot = use % (uint32_t)NS;
                         if (!wait_bar(&empty[slot], ((use / (uint32_t)NS) & 1u) ^ 1u, s)) break;
                         unsigned char *bh = bring + (size_t)slot * BBLK;
-                        for (int e = me; e < NN * RS; e += nb) {
-                            const int t = e / RS, i = e - t * RS;
-                            const int r = r0 + s * RS + i;
+                        for (int e = me; e < NN * RSu; e += nb) {
+                            const int t = e / RSu, i = e - t * RSu;
+                            const int r = r0 + s * RSu + i;
                             const int wi = (r1 - 1 - r) + t;
                             float c = (r < rlo_t) ? 0.f
                                       : (per_step && kb + t_lo + t - r <= s_ek[t_lo + t]) ? win2[wi]
@@ -696,7 +702,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             const int row = t & 7, base = (t >> 3) * 1024 + row * 128;
                             auto off = [&](int kq) { return base + (((kq >> 3) ^ row) << 4) + (kq & 7) * 2; };
                             *reinterpret_cast<TB16 *>(bh + off(i)) = hi;
-                            *reinterpret_cast<TB16 *>(bh + off(RS + i)) = lo;
+                            *reinterpret_cast<TB16 *>(bh + off(RSu + i)) = lo;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::saddr(&bfull[slot])) : "memory");
@@ -1307,8 +1313,16 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     // delta^k in FP32 for the near lags (for FP32 history, the history row itself)
                     *reinterpret_cast<float4 *>(I.hring + (size_t)(k % I.hring_cap) * I.hring_pitch + (size_t)j0 * 4) =
                         make_float4(d[0], d[1], d[2], d[3]);
-                    if (LOWP && !F16)
-                        H4<TH>::stg(I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * sizeof(TH), d, 1.f);
+                    if (LOWP && !F16) {
+                        char *row = I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * sizeof(TH);
+                        H4<TH>::stg(row, d, 1.f);
+                        if (TC && I.lo_plane) {  // the rounding remainder, for tensor-core near/mid units
+                            float dr[V];
+#pragma unroll
+                            for (int v = 0; v < V; ++v) dr[v] = d[v] - __bfloat162float(__float2bfloat16_rn(d[v]));
+                            H4<TH>::stg(row + (size_t)I.cap * I.pitch, dr, 1.f);
+                        }
+                    }
                 }
             }
             if (SCALED && I.hist_write) {
@@ -1335,6 +1349,12 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     char *row = I.hist + (size_t)(k % I.cap) * I.pitch + (size_t)j0 * 2;
                     if (F16) {
                         H4<__half>::stg(row, d, sc);
+                        if (TC && I.lo_plane) {  // the rounding remainder, for tensor-core near/mid units
+                            float dr[V];
+#pragma unroll
+                            for (int v = 0; v < V; ++v) dr[v] = d[v] * sc - __half2float(__float2half_rn(d[v] * sc));
+                            H4<__half>::stg(row + (size_t)I.cap * I.pitch, dr, 1.f);
+                        }
                     } else {  // paired: hi = fp16(d 2^e), lo = fp16(d 2^e - hi), both exact scalings
                         float dh[V], dr[V];
 #pragma unroll
