@@ -247,6 +247,7 @@ struct Geo {
     int tmem_cols;     // tensor cores: tensor-memory columns a CTA allocates (at most 512)
     int near;        // blocked, per-step update units, blocks of 16+: one near unit per (block, tile)
     int mid;         // blocked, near units, blocks of 32+: mid units per (block, tile), tb/16 - 1
+    int ug;          // blocked: tiles per per-step update unit (tensor cores: 2)
     int ralign;      // blocked: far chunks start on multiples of ralign rows (tensor cores: RS)
     int hring_sep;   // separate state-precision head ring
     int hring_cap;
@@ -415,6 +416,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.ub = 0;
     g.near = 0;
     g.mid = 0;
+    g.ug = 1;
     g.smem_half = 0;
     g.cmax = 0;
     g.rwin = g.R;
@@ -465,6 +467,11 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         // Mid units: with blocks of 32 or more, sub-block j = 1 .. tb/16-1 (16 steps each) gets the
         // block's rows before it as one more partial row, so an update sums at most 15 head lags
         g.mid = (g.near && g.tb >= 32) ? g.tb / 16 - 1 : 0;
+        // Tensor-core kernels with more tiles than half the grid's half-CTAs: two tiles per
+        // per-step update unit, so that a step's update units (T/2) leave half-CTAs free to claim
+        // the next step's while this one finishes (with fewer tiles the second tile's phase B
+        // would only lengthen the step-to-step chain)
+        g.ug = (g.tc && !g.ub && (int64_t)g.T * 2 > (int64_t)sms * g.halves) ? 2 : 1;  // (one CTA per SM)
         g.maxC = (int)cmaxb + g.near + (g.mid ? 1 : 0);
         g.rwin = (int)rwin;
     }
@@ -505,7 +512,8 @@ inline int64_t block_units(const fd_problem &p, const Geo &g, int64_t b)
         block_chunks(p, g, b, Rb, Cb);
         far = (int64_t)g.T * (Cb * g.fsub + g.near * nsub_of(g));  // far chunks (fsub units each), near units
     }
-    return far + (b >= 1 ? (int64_t)g.T * ((g.ub ? 1 : g.tb) + g.mid * nsub_of(g)) : 0);
+    const int64_t tg = (g.T + g.ug - 1) / g.ug;  // update units per step
+    return far + (b >= 1 ? (g.ub ? (int64_t)g.T : tg * g.tb) + (int64_t)g.T * g.mid * nsub_of(g) : 0);
 }
 
 // History rows the blocked kernel reads over max_steps steps: the far rows once per block, then
@@ -879,6 +887,7 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.cmax = g.cmax;
     I.ralign = g.ralign;
     I.near = g.near;
+    I.ug = g.ug;
     I.mid = g.mid;
     I.tmap = L.tmap;
     I.tmap2 = L.tmap2;

@@ -63,6 +63,7 @@ struct Inst {
     int cmax;                // blocked kernel: most far chunks per block (0 = no limit)
     int ralign;              // blocked kernel: far chunks start on multiples of ralign rows (0, 1: any)
     int near;                // blocked kernel: one near unit per (block, tile) adds the previous block's rows
+    int ug;                  // blocked kernel: tiles per per-step update unit
     int mid;                 // blocked kernel: mid units per (block, tile): sub-blocks 1 .. mid of 16 steps
                              // get the block's earlier rows as one partial row
     int tc_cols;             // blocked tensor-core kernel: tensor-memory columns per CTA

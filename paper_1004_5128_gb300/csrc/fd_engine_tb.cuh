@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                 const long long local = u - cg_lo, gsize = cg_hi - cg_lo;
                 const int gb = gi.y;  // group: far units of block gb, updates of block gb-1
                 const int k_end = min(L.k_end, I.ksteps);  // a batch runs each instance to its end
-                const int Tu = (gb >= 1) ? I.T * (I.ub ? 1 : TB) : 0;  // block gb-1's update units
+                // block gb-1's update units: per (block, tile), or per (step, group of ug tiles)
+                const int Tu = (gb >= 1) ? (I.ub ? I.T : (I.T + I.ug - 1) / I.ug * TB) : 0;
                 const int Mu = (gb >= 1) ? I.T * I.mid * nsub : 0;       // block gb-1's mid units
                 const long long F = gsize - (long long)(Tu + Mu);  // block gb's far units
                 long long f = -1;  // far unit index within block gb, or -1 for an update unit
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                         if (k < L.k0 || k >= k_end) continue;  // block edge outside this launch
                         U.fix = 1;
                         U.b = gb - 1;
-                        U.tile = (int)(off - fsn);
+                        U.tile = (int)(off - fsn) * I.ug;
                         U.k = k;
                         U.C = far_chunks<TB>(I, gb - 1);
                         U.chunk = 0;
@@ -477,7 +478,8 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         csync();
         if (!U.valid) break;
 
-        const int tile = U.tile, C = U.C, b = U.b, kb = b * TB;
+        int tile = U.tile;  // (a per-step update unit of several tiles moves it from tile to tile)
+        const int C = U.C, b = U.b, kb = b * TB;
         const int par = b % I.npar;
         // Arrival counters carry the block's generation within its parity in the high half
         // ((b - the launch's first block k0/TB) / npar), so a count left by block b - npar can never
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         auto arrive_target = [&](int bb, int count) -> unsigned {
             return ((unsigned)((bb - L.k0 / TB) / I.npar) << 16) + (unsigned)count;
         };
-        const int j0 = tile * I.P + tid * V;
+        int j0 = tile * I.P + tid * V;
         auto prow = [&](int c, int t, int plane) -> float * {
             return reinterpret_cast<float *>(I.part +
                                              ((size_t)(((par * I.maxC + c) * TB + t) * PLANES + plane)) * I.part_pitch);
@@ -1087,7 +1089,7 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         // With own != null (block-long units) the tile's own u^k and low parts come from the
         // unit itself: own[0..V) and own[V..2V) in registers, and us[P] in shared memory for the
         // stencil's in-tile neighbours (us_next receives u^{k+1}); only halo points are loaded.
-        const int t0p = tile * I.P;  // first point of the tile
+        int t0p = tile * I.P;  // first point of the tile
         auto phase_b = [&](int k, bool add_lag1, float *H, float *H2, float *d, bool last, float *own,
                            const float *us, float *us_next) -> bool {
             const int rel = k - L.k0;
@@ -1619,27 +1621,31 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             continue;
         }
 
-        // ================================================== update unit: step k, this tile
+        // ================================================== update unit: step k, tiles U.tile ..
+        // (tensor-core kernels: I.ug consecutive tiles per unit, so that a step has fewer units than
+        // the grid has half-CTAs and each unit's claim and waits are paid once for its tiles)
         const int k = U.k, t = k - kb;
         const int rel = k - L.k0;
         const int nmid = I.mid ? min(I.mid, t / 16) : 0;  // mid units of sub-blocks 1 .. t/16
+        const int ntl = min(I.ug, I.T - U.tile);          // tiles of this unit
         // Two phases keep the partial and head sums off the step-to-step chain.  Phase A needs
         // only the tile's far count and this tile's rows up to k-2 (its own step k-2), so it
         // runs while step k-1 is still being updated; phase B waits for u^k on the halo tiles
         // and row k-1, then adds lag 1 and updates.  The summation order is unchanged:
         // partials by chunk, then lags hk .. 1.
-        if (tid < 32) {  // the two waits run in parallel lanes
+        if (tid < 32) {  // the waits run in parallel lanes: far counts in lanes 0.., own rows in 16..
             int ok = 1;
-            if (tid == 0) {  // the far chunks and, with near units, the near (and mid) partials
-                const int w = wait_until(&I.arrive[par * I.T + tile], arrive_target(b, C * L.fsub + (I.near + nmid) * nsub), L, 512);
-                if (w < 0)
-                    note_failure(L, 3, k, tile, arrive_target(b, C * L.fsub + (I.near + nmid) * nsub), ld_acquire(&I.arrive[par * I.T + tile]),
-                                 L.k0, 0);
+            const unsigned tgt = arrive_target(b, C * L.fsub + (I.near + nmid) * nsub);
+            if (tid < ntl) {  // the far chunks and, with near units, the near (and mid) partials
+                const int tt = U.tile + tid;
+                const int w = wait_until(&I.arrive[par * I.T + tt], tgt, L, 512);
+                if (w < 0) note_failure(L, 3, k, tt, tgt, ld_acquire(&I.arrive[par * I.T + tt]), L.k0, 0);
                 ok = w > 0;
             }
-            if (tid == 1 && rel > 1) {
-                const int w = wait_until(&I.done[tile], (unsigned)(rel - 1), L, 512);
-                if (w < 0) note_failure(L, 4, k, tile, rel - 1, ld_acquire(&I.done[tile]), L.k0, 0);
+            if (tid >= 16 && tid < 16 + ntl && rel > 1) {
+                const int tt = U.tile + tid - 16;
+                const int w = wait_until(&I.done[tt], (unsigned)(rel - 1), L, 512);
+                if (w < 0) note_failure(L, 4, k, tt, rel - 1, ld_acquire(&I.done[tt]), L.k0, 0);
                 ok = w > 0;
             }
             ok = __all_sync(0xffffffffu, ok);
@@ -1654,112 +1660,133 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
         const int hk = I.near ? min(I.mid ? t % 16 : t, nb) : min(t + TB, nb);
         const int CP = C + I.near + (nmid ? 1 : 0);  // partial rows to sum
         auto hrow = [&](int m) -> const float * { return hrow_at(k - m); };
-        float H[V], H2[V], d[V];
+        constexpr int UG = TC ? 2 : 1;  // most tiles per update unit
+        float HG[UG][V], H2G[UG][V], d[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) H[v] = H2[v] = 0.f;
-        if (j0 < I.N) {
-            // far part: chunk partials in fixed order, G loads in flight (the unit is latency-bound:
-            // its loads are all it does before the halo wait)
-            constexpr int G = ADJ ? 4 : TC ? 16 : 8;
-            int c = 0;
-            for (; c + G <= CP; c += G) {
-                float4 w[G], w2[ADJ ? G : 1];
+        for (int g = 0; g < UG; ++g) {  // phase A of each tile
+            if (g >= ntl) break;
+            tile = U.tile + g;
+            j0 = tile * I.P + tid * V;
+            t0p = tile * I.P;
+            float *H = HG[g], *H2 = H2G[g];
 #pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 0) + j0));
-                    if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 1) + j0));
-                }
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    H[0] += w[i].x;
-                    H[1] += w[i].y;
-                    H[2] += w[i].z;
-                    H[3] += w[i].w;
-                    if (ADJ) {
-                        H2[0] += w2[ADJ ? i : 0].x;
-                        H2[1] += w2[ADJ ? i : 0].y;
-                        H2[2] += w2[ADJ ? i : 0].z;
-                        H2[3] += w2[ADJ ? i : 0].w;
+            for (int v = 0; v < V; ++v) H[v] = H2[v] = 0.f;
+            if (j0 < I.N) {
+                // far part: chunk partials in fixed order, G loads in flight (the unit is latency-bound:
+                // its loads are all it does before the halo wait)
+                constexpr int G = ADJ ? 4 : TC ? 16 : 8;
+                int c = 0;
+                for (; c + G <= CP; c += G) {
+                    float4 w[G], w2[ADJ ? G : 1];
+    #pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 0) + j0));
+                        if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 1) + j0));
+                    }
+    #pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        H[0] += w[i].x;
+                        H[1] += w[i].y;
+                        H[2] += w[i].z;
+                        H[3] += w[i].w;
+                        if (ADJ) {
+                            H2[0] += w2[ADJ ? i : 0].x;
+                            H2[1] += w2[ADJ ? i : 0].y;
+                            H2[2] += w2[ADJ ? i : 0].z;
+                            H2[3] += w2[ADJ ? i : 0].w;
+                        }
                     }
                 }
-            }
-            for (; c < CP; ++c) {
-                const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 0) + j0));
-                H[0] += w.x;
-                H[1] += w.y;
-                H[2] += w.z;
-                H[3] += w.w;
-                if (ADJ) {
-                    const float4 w2 = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 1) + j0));
-                    H2[0] += w2.x;
-                    H2[1] += w2.y;
-                    H2[2] += w2.z;
-                    H2[3] += w2.w;
+                for (; c < CP; ++c) {
+                    const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 0) + j0));
+                    H[0] += w.x;
+                    H[1] += w.y;
+                    H[2] += w.z;
+                    H[3] += w.w;
+                    if (ADJ) {
+                        const float4 w2 = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 1) + j0));
+                        H2[0] += w2.x;
+                        H2[1] += w2.y;
+                        H2[2] += w2.z;
+                        H2[3] += w2.w;
+                    }
                 }
-            }
-            // weight of lag m at this step (adaptive memory: settled or tail weight)
-            const int ek = I.gw ? settled_end(I, k) : 0x7fffffff;
-            auto wgt = [&](int m) -> float {
-                return (I.gw && m <= ek) ? reinterpret_cast<const float *>(I.gw)[m] : psi[m];
-            };
-            if (!ADJ && I.gw) {
-                // adaptive memory: the tail rows below the far rows, oldest first
-                int rlo, rhi;
-                far_rows<TB>(I, b, rlo, rhi);
-                for (int r = 0; r < rlo; r += 4) {
-                    float4 x[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) x[i] = (r + i < rlo) ? hist4(r + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (r + i >= rlo) continue;
-                        const float cc = wgt(k - (r + i));
+                // weight of lag m at this step (adaptive memory: settled or tail weight)
+                const int ek = I.gw ? settled_end(I, k) : 0x7fffffff;
+                auto wgt = [&](int m) -> float {
+                    return (I.gw && m <= ek) ? reinterpret_cast<const float *>(I.gw)[m] : psi[m];
+                };
+                if (!ADJ && I.gw) {
+                    // adaptive memory: the tail rows below the far rows, oldest first
+                    int rlo, rhi;
+                    far_rows<TB>(I, b, rlo, rhi);
+                    for (int r = 0; r < rlo; r += 4) {
+                        float4 x[4];
+    #pragma unroll
+                        for (int i = 0; i < 4; ++i) x[i] = (r + i < rlo) ? hist4(r + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    #pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (r + i >= rlo) continue;
+                            const float cc = wgt(k - (r + i));
+                            H[0] = fmaf(cc, x[i].x, H[0]);
+                            H[1] = fmaf(cc, x[i].y, H[1]);
+                            H[2] = fmaf(cc, x[i].z, H[2]);
+                            H[3] = fmaf(cc, x[i].w, H[3]);
+                        }
+                    }
+                }
+                // head lags hk .. 2: rows this tile wrote at steps up to k-2, G loads in flight
+                int m = hk;
+                for (; m - (G - 1) >= 2; m -= G) {
+                    float4 x[G];
+    #pragma unroll
+                    for (int i = 0; i < G; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(m - i)));
+    #pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        const float cc = wgt(m - i);
                         H[0] = fmaf(cc, x[i].x, H[0]);
                         H[1] = fmaf(cc, x[i].y, H[1]);
                         H[2] = fmaf(cc, x[i].z, H[2]);
                         H[3] = fmaf(cc, x[i].w, H[3]);
+                        if (ADJ) {
+                            const float c2 = dpsi[m - i];
+                            H2[0] = fmaf(c2, x[i].x, H2[0]);
+                            H2[1] = fmaf(c2, x[i].y, H2[1]);
+                            H2[2] = fmaf(c2, x[i].z, H2[2]);
+                            H2[3] = fmaf(c2, x[i].w, H2[3]);
+                        }
                     }
                 }
-            }
-            // head lags hk .. 2: rows this tile wrote at steps up to k-2, G loads in flight
-            int m = hk;
-            for (; m - (G - 1) >= 2; m -= G) {
-                float4 x[G];
-#pragma unroll
-                for (int i = 0; i < G; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(m - i)));
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    const float cc = wgt(m - i);
-                    H[0] = fmaf(cc, x[i].x, H[0]);
-                    H[1] = fmaf(cc, x[i].y, H[1]);
-                    H[2] = fmaf(cc, x[i].z, H[2]);
-                    H[3] = fmaf(cc, x[i].w, H[3]);
+                for (; m >= 2; --m) {
+                    const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow(m)));
+                    const float cc = wgt(m);
+                    H[0] = fmaf(cc, x.x, H[0]);
+                    H[1] = fmaf(cc, x.y, H[1]);
+                    H[2] = fmaf(cc, x.z, H[2]);
+                    H[3] = fmaf(cc, x.w, H[3]);
                     if (ADJ) {
-                        const float c2 = dpsi[m - i];
-                        H2[0] = fmaf(c2, x[i].x, H2[0]);
-                        H2[1] = fmaf(c2, x[i].y, H2[1]);
-                        H2[2] = fmaf(c2, x[i].z, H2[2]);
-                        H2[3] = fmaf(c2, x[i].w, H2[3]);
+                        const float c2 = dpsi[m];
+                        H2[0] = fmaf(c2, x.x, H2[0]);
+                        H2[1] = fmaf(c2, x.y, H2[1]);
+                        H2[2] = fmaf(c2, x.z, H2[2]);
+                        H2[3] = fmaf(c2, x.w, H2[3]);
                     }
-                }
-            }
-            for (; m >= 2; --m) {
-                const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow(m)));
-                const float cc = wgt(m);
-                H[0] = fmaf(cc, x.x, H[0]);
-                H[1] = fmaf(cc, x.y, H[1]);
-                H[2] = fmaf(cc, x.z, H[2]);
-                H[3] = fmaf(cc, x.w, H[3]);
-                if (ADJ) {
-                    const float c2 = dpsi[m];
-                    H2[0] = fmaf(c2, x.x, H2[0]);
-                    H2[1] = fmaf(c2, x.y, H2[1]);
-                    H2[2] = fmaf(c2, x.z, H2[2]);
-                    H2[3] = fmaf(c2, x.w, H2[3]);
                 }
             }
         }
-        if (!phase_b(k, hk >= 1, H, H2, d, k == min(kb + TB, kend) - 1, nullptr, nullptr, nullptr)) break;
+        bool units_ok = true;
+#pragma unroll
+        for (int g = 0; g < UG; ++g) {  // phase B of each tile, in tile order
+            if (g >= ntl) break;
+            tile = U.tile + g;
+            j0 = tile * I.P + tid * V;
+            t0p = tile * I.P;
+            if (!phase_b(k, hk >= 1, HG[g], H2G[g], d, k == min(kb + TB, kend) - 1, nullptr, nullptr, nullptr)) {
+                units_ok = false;
+                break;
+            }
+        }
+        if (!units_ok) break;
     }
     // every exit from the unit loop is CTA-uniform; the tensor memory goes back once all of the
     // CTA's tensor-core work has completed (a failed unit waits for its MMAs before it exits)
