@@ -440,10 +440,19 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
                 rmax = std::max(rmax, hi - lo);
             }
         if (!p.chunk_terms) {
-            // tensor cores: longer chunks, as each chunk writes tb FP32 partial rows against its
-            // 16-bit history rows (partial traffic 4 tb / R of the history's)
             int64_t r = (rmax * g.T + 4LL * g.grid - 1) / (4LL * g.grid);
-            r = std::min<int64_t>(std::max<int64_t>(r, 2 * g.RS), g.tc ? 2048 : 512);
+            r = std::min<int64_t>(std::max<int64_t>(r, 2 * g.RS), 512);
+            if (g.tc) {
+                // tensor cores: long chunks, as each chunk writes tb FP32 partial rows and every
+                // update reads one per chunk: about two far units per half-CTA and block, up to
+                // the longest chunk whose coefficient window two halves still hold in shared
+                // memory (config 3: 3072-row chunks 3% faster than 2048)
+                int64_t cap = 4096;
+                while (cap > 1024 && 2 * smem_half_tc(g, (int)cap, p.hist_dtype != FD_BF16) + 1024 > (223u << 10))
+                    cap -= 512;
+                r = (rmax * g.T * g.fsub + 2LL * sms * g.halves - 1) / (2LL * sms * g.halves);
+                r = std::min<int64_t>(std::max<int64_t>(r, 2 * g.RS), cap);
+            }
             g.R = (int)((r + g.RS - 1) / g.RS * g.RS);
         }
         if (g.ralign > 1) g.R = (g.R + g.ralign - 1) / g.ralign * g.ralign;
