@@ -156,3 +156,28 @@ def test_fp16_tensor_cores_config2_row_scales_spread():
     ref, s2 = run(p, hist="f16", time_block=16, fma_far=True)
     assert s2.geometry()["far_tensor_cores"] == 0
     assert rel_inf(got, ref) < 5e-5
+
+
+@pytest.mark.parametrize("hist", ["f32", "bf16"])
+def test_two_tile_update_units_match_oracle_and_split_invariance(hist):
+    """400 x 400 points are 157 tiles of 1024, more than half the 304 half-CTAs, so each per-step
+    update unit carries two tiles (phase A of both, then phase B of both); against the oracle (BF16
+    history at its tolerance, against the oracle with the BF16 storage rule at 5e-5), and a run split
+    into launches inside blocks gives the same bits."""
+    n, K = 400, 300
+    p = synth.problem(2, n, n, 0.6, 1.0, synth.dt_for_courant(0.1, 1.0, 1.0, 0.6), 1.0, synth.BC_DIRICHLET0,
+                      react=(0.0, 0.95, -1.0, 0.0), K=K, u0=0.1 * synth.SplitMix64(33).uniform(n * n, 0, 1))
+    kw = dict(time_block=64) if hist == "f32" else dict(time_block=64, hist="bf16")
+    got, s = run(p, **kw)
+    g = s.geometry()
+    assert g["far_tensor_cores"] == 1 and g["tiles"] == 157
+    if hist == "f32":
+        assert rel_inf(got, oracle.run(p)) < TOL
+    else:
+        assert rel_inf(got, oracle.run(p)) < 2e-3
+        assert rel_inf(got, oracle.run_bf16(p, 64, 64)) < 5e-5
+    b = FRD(p, **kw)
+    b.set_state(p["u0"])
+    for m in (77, 1, 100, 45):
+        b.step(m)
+    assert np.array_equal(got, b.run(K - 223).cpu().double().numpy())
