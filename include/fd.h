@@ -204,6 +204,20 @@ int fd_get_status(fd_handle *h);
  * since fd_set_state is kept.  Synchronises the stream. */
 int fd_get_error_info(fd_handle *h, int64_t info[8]);
 
+/* Checkpoint of a handle at its current step k, for resuming a run of eq. frac_final later
+ * (the paper has no counterpart): the step count, u^k (with the compensation part of an F32
+ * state), the history rows written so far (both planes where the history keeps two), the newest
+ * rows kept in state precision and the row scales.  Partial sums are not saved: every launch
+ * recomputes those of the blocks it starts in.  fd_save_bytes gives the size; fd_save writes it to
+ * buf (host or device memory, `bytes` at least that size) and synchronises the stream; fd_load
+ * restores it into a handle initialised for the same problem and launch geometry (the stored
+ * geometry is checked: FD_ERR_INVALID_ARG on a mismatch or a short buffer), after which fd_step /
+ * fd_run continue from step k with the bits an uninterrupted run gives.  Handles with
+ * FD_FLAG_KEEP_TAPE: FD_ERR_UNSUPPORTED. */
+int fd_save_bytes(fd_handle *h, size_t *bytes);
+int fd_save(fd_handle *h, void *buf, size_t bytes);
+int fd_load(fd_handle *h, const void *buf, size_t bytes);
+
 /* Release the handle (host memory only; the workspace stays the caller's). */
 int fd_destroy(fd_handle *h);
 

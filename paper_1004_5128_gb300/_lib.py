@@ -43,7 +43,7 @@ EXPORTS = (
     "fd_get_geometry", "fd_batch_workspace_bytes", "fd_batch_init", "fd_batch_set_state",
     "fd_batch_run", "fd_batch_get_state", "fd_batch_get_status", "fd_batch_get_geometry",
     "fd_batch_destroy",
-    "fd_run_batch", "fd_strerror", "fd_run_static",
+    "fd_run_batch", "fd_strerror", "fd_run_static", "fd_save_bytes", "fd_save", "fd_load",
 )
 
 
@@ -120,6 +120,9 @@ def lib():
             "fd_run_batch": [P, ctypes.c_int, ctypes.POINTER(vp), vp, ctypes.c_size_t, vp],
             "fd_strerror": [ctypes.c_int],
             "fd_run_static": [P, vp, ctypes.c_int, vp, vp],
+            "fd_save_bytes": [vp, sz],
+            "fd_save": [vp, vp, ctypes.c_size_t],
+            "fd_load": [vp, vp, ctypes.c_size_t],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -193,6 +196,20 @@ def fd_run(h: int, n: int, out_ptr: int | None):
 
 def fd_get_state(h: int, out_ptr: int):
     check(lib().fd_get_state(h, out_ptr), "fd_get_state")
+
+
+def fd_save_bytes(h: int) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().fd_save_bytes(h, ctypes.byref(b)), "fd_save_bytes")
+    return b.value
+
+
+def fd_save(h: int, buf_ptr: int, nbytes: int):
+    check(lib().fd_save(h, buf_ptr, nbytes), "fd_save")
+
+
+def fd_load(h: int, buf_ptr: int, nbytes: int):
+    check(lib().fd_load(h, buf_ptr, nbytes), "fd_load")
 
 
 def fd_current_step(h: int) -> int:

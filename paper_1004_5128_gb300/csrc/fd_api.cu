@@ -1403,6 +1403,134 @@ int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma
     return FD_OK;
 }
 
+// ------------------------------------------------------------------- checkpoints
+
+namespace {
+
+// Layout of a checkpoint: this header, then u^k, its compensation part (F32 state), the history
+// rows 0 .. rows-1 of each plane, the state-precision ring (when separate) and the row scales of
+// rows 0 .. rows-1.  rows = min(k, cap) when the history keeps every step, else the whole ring.
+struct SaveHeader {
+    char magic[8];
+    int64_t k, N, ss, comp, cap, pitch, planes, rows, hring_sep, hring_cap, hring_pitch, hscale, T;
+    int64_t nx, ny, nz, ndim, max_steps, mem_mode, mem_L, mem_a, rule, time_block, sdt, hdt, adt, flags, bc;
+    double gamma, alpha, dt, dx, react[4];
+};
+
+void save_plan(const fd_handle *h, int64_t k, SaveHeader &hd, size_t &total)
+{
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "FDSAVE1", 8);
+    const fd_problem &p = h->p;
+    const Geo &g = h->g;
+    hd.k = k;
+    hd.N = (int64_t)p.nx * p.ny * p.nz;
+    hd.ss = g.ss;
+    hd.comp = h->L.ulo[0] ? 1 : 0;
+    hd.cap = g.cap;
+    hd.pitch = g.pitch;
+    hd.planes = g.lo_plane ? 2 : 1;
+    hd.rows = (g.cap >= p.max_steps) ? std::min<int64_t>(k, g.cap) : g.cap;
+    hd.hring_sep = g.hring_sep;
+    hd.hring_cap = g.hring_sep ? g.hring_cap : 0;
+    hd.hring_pitch = g.hring_sep ? g.hring_pitch : 0;
+    hd.hscale = h->L.hscale ? 1 : 0;
+    hd.T = g.T;
+    hd.nx = p.nx;
+    hd.ny = p.ny;
+    hd.nz = p.nz;
+    hd.ndim = p.ndim;
+    hd.max_steps = p.max_steps;
+    hd.mem_mode = p.mem_mode;
+    hd.mem_L = p.mem_L;
+    hd.mem_a = p.mem_a;
+    hd.rule = p.adaptive_rule;
+    hd.time_block = p.time_block;
+    hd.sdt = p.state_dtype;
+    hd.hdt = p.hist_dtype;
+    hd.adt = p.accum_dtype;
+    hd.flags = p.flags;
+    hd.bc = p.bc;
+    hd.gamma = p.gamma;
+    hd.alpha = p.alpha;
+    hd.dt = p.dt;
+    hd.dx = p.dx;
+    for (int i = 0; i < 4; ++i) hd.react[i] = p.react[i];
+    total = sizeof(SaveHeader) + (size_t)hd.N * hd.ss * (1 + hd.comp) + (size_t)(hd.planes * hd.rows * hd.pitch) +
+            (size_t)(hd.hring_cap * hd.hring_pitch) + (size_t)(hd.hscale * hd.rows * hd.T) * sizeof(float);
+}
+
+// The pieces of a checkpoint in order: (device address, bytes).
+std::vector<std::pair<char *, size_t>> save_pieces(const fd_handle *h, const SaveHeader &hd)
+{
+    std::vector<std::pair<char *, size_t>> v;
+    const size_t ub = (size_t)hd.N * hd.ss;
+    v.emplace_back(h->L.ubuf[hd.k & 1], ub);
+    if (hd.comp) v.emplace_back(h->L.ulo[hd.k & 1], ub);
+    for (int64_t pl = 0; pl < hd.planes; ++pl)
+        v.emplace_back(h->L.hist + (size_t)(pl * hd.cap * hd.pitch), (size_t)(hd.rows * hd.pitch));
+    if (hd.hring_cap) v.emplace_back(h->L.hring, (size_t)(hd.hring_cap * hd.hring_pitch));
+    if (hd.hscale) v.emplace_back(reinterpret_cast<char *>(h->L.hscale), (size_t)(hd.rows * hd.T) * sizeof(float));
+    return v;
+}
+
+}  // namespace
+
+int fd_save_bytes(fd_handle *h, size_t *bytes)
+{
+    if (!h || !bytes) return FD_ERR_INVALID_ARG;
+    if (h->p.flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
+    SaveHeader hd;
+    save_plan(h, h->k, hd, *bytes);
+    return FD_OK;
+}
+
+int fd_save(fd_handle *h, void *buf, size_t bytes)
+{
+    if (!h || !buf) return FD_ERR_INVALID_ARG;
+    if (h->p.flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
+    if (h->bad) return FD_ERR_STATE;
+    SaveHeader hd;
+    size_t total = 0;
+    save_plan(h, h->k, hd, total);
+    if (bytes < total) return FD_ERR_INVALID_ARG;
+    char *out = static_cast<char *>(buf);
+    CK(cudaMemcpyAsync(out, &hd, sizeof(hd), cudaMemcpyDefault, h->st));
+    size_t off = sizeof(hd);
+    for (const auto &pc : save_pieces(h, hd)) {
+        if (pc.second) CK(cudaMemcpyAsync(out + off, pc.first, pc.second, cudaMemcpyDefault, h->st));
+        off += pc.second;
+    }
+    CK(cudaStreamSynchronize(h->st));  // (the header copy reads a host stack variable)
+    return FD_OK;
+}
+
+int fd_load(fd_handle *h, const void *buf, size_t bytes)
+{
+    if (!h || !buf || bytes < sizeof(SaveHeader)) return FD_ERR_INVALID_ARG;
+    if (h->p.flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
+    SaveHeader in;
+    CK(cudaMemcpy(&in, buf, sizeof(in), cudaMemcpyDefault));
+    if (std::memcmp(in.magic, "FDSAVE1", 8) || in.k < 0 || in.k > h->p.max_steps) return FD_ERR_INVALID_ARG;
+    SaveHeader hd;
+    size_t total = 0;
+    save_plan(h, in.k, hd, total);
+    if (std::memcmp(&in, &hd, sizeof(hd)) || bytes < total) return FD_ERR_INVALID_ARG;  // another problem
+    const char *src = static_cast<const char *>(buf);
+    size_t off = sizeof(hd);
+    for (const auto &pc : save_pieces(h, hd)) {
+        if (pc.second) CK(cudaMemcpyAsync(pc.first, src + off, pc.second, cudaMemcpyDefault, h->st));
+        off += pc.second;
+    }
+    CK(cudaMemsetAsync(h->ctrl.err, 0, sizeof(int), h->st));
+    CK(cudaMemsetAsync(h->ctrl.nonfinite, 0, sizeof(unsigned), h->st));
+    CK(cudaMemsetAsync(h->ctrl.err_info, 0, 8 * sizeof(long long), h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->k = in.k;
+    h->bad = 0;
+    return FD_OK;
+}
+
 int fd_get_geometry(fd_handle *h, fd_geometry *g)
 {
     if (!h || !g) return FD_ERR_INVALID_ARG;

@@ -120,6 +120,19 @@ class FRD:
         L.fd_get_state(self.h, out.data_ptr())
         return out
 
+    def save(self, device: bool = False) -> torch.Tensor:
+        """Checkpoint at the current step (fd_save): a uint8 tensor in host memory, or on the
+        handle's device with device=True."""
+        n = L.fd_save_bytes(self.h)
+        buf = torch.empty(n, dtype=torch.uint8, device=self.device if device else "cpu")
+        L.fd_save(self.h, buf.data_ptr(), n)
+        return buf
+
+    def load(self, buf: torch.Tensor):
+        """Resume from a checkpoint that save() wrote for the same problem and geometry (fd_load)."""
+        buf = buf.contiguous()
+        L.fd_load(self.h, buf.data_ptr(), buf.numel())
+
     @property
     def k(self) -> int:
         return L.fd_current_step(self.h)
