@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+
+#include <nvtx3/nvToolsExt.h>
 #include <new>
 #include <vector>
 
@@ -1066,8 +1068,19 @@ static int launch(fd_handle *h, const void *fn, const Inst *d_inst, int g_begin,
 
 // Steps [k0, k1) with fn: the per-step kernel's groups are steps; the blocked kernel's are the
 // blocks that intersect the span, plus the group holding the last block's updates.
+// NVTX range around a host call (header-only NVTX v3: free unless a profiler is attached), so that
+// a timeline shows the library's phases: set-up, forward launches, adjoint recompute and sweep,
+// batches, checkpoints.
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 static int launch_steps(fd_handle *h, const void *fn, const Inst *d_inst, int k0, int k1, bool adj_groups = false)
 {
+    NvtxRange r(fn == h->kfwd ? "fd: forward launch" : "fd: adjoint / recompute launch");
     const int tb = h->g.tb;
     if (tb) return launch(h, fn, d_inst, k0 / tb, (k1 + tb - 1) / tb + 1, k0, k1, adj_groups);
     return launch(h, fn, d_inst, k0, k1, k0, k1, adj_groups);
@@ -1154,6 +1167,7 @@ int fd_workspace_bytes(const fd_problem *p, size_t *bytes)
 
 int fd_init(const fd_problem *p, void *workspace, size_t ws_bytes, void *cuda_stream, fd_handle **out)
 {
+    NvtxRange r("fd_init: schedule, tables, workspace layout, uploads");
     if (!out) return FD_ERR_INVALID_ARG;
     fd_problem q;
     p = normalized(p, q);
@@ -1281,6 +1295,7 @@ int fd_set_state(fd_handle *h, const void *u0)
 
 int fd_step(fd_handle *h, int nsteps)
 {
+    NvtxRange r("fd_step");
     if (!h || nsteps < 0) return FD_ERR_INVALID_ARG;
     if (h->bad) return FD_ERR_STATE;
     if (h->k + nsteps > h->p.max_steps) return FD_ERR_STATE;
@@ -1338,6 +1353,7 @@ int fd_run(fd_handle *h, int nsteps, void *u_out)
 int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma, double *dJ_dalpha,
                double dJ_dreact[4])
 {
+    NvtxRange r("fd_adjoint: checkpoint recompute and reverse sweep");
     if (!h || !dJ_duK) return FD_ERR_INVALID_ARG;
     if (!(h->p.flags & FD_FLAG_KEEP_TAPE) || !h->kadj || h->bad || h->k < 1) return FD_ERR_STATE;
     const fd_problem &p = h->p;
@@ -1487,6 +1503,7 @@ int fd_save_bytes(fd_handle *h, size_t *bytes)
 
 int fd_save(fd_handle *h, void *buf, size_t bytes)
 {
+    NvtxRange r("fd_save");
     if (!h || !buf) return FD_ERR_INVALID_ARG;
     if (h->p.flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
     if (h->bad) return FD_ERR_STATE;
@@ -1507,6 +1524,7 @@ int fd_save(fd_handle *h, void *buf, size_t bytes)
 
 int fd_load(fd_handle *h, const void *buf, size_t bytes)
 {
+    NvtxRange r("fd_load");
     if (!h || !buf || bytes < sizeof(SaveHeader)) return FD_ERR_INVALID_ARG;
     if (h->p.flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
     SaveHeader in;
@@ -1832,6 +1850,7 @@ int fd_batch_set_state(fd_batch *b, int i, const void *u0)
 
 int fd_batch_run(fd_batch *b)
 {
+    NvtxRange r("fd_batch_run: graph launch");
     if (!b) return FD_ERR_INVALID_ARG;
     CK(cudaGraphLaunch(b->exec, b->st));
     return FD_OK;
