@@ -32,7 +32,7 @@ PARAMS = {
     "time_block": [0, 8, 16, 32, 64],
     "step_updates": [0, 1],
     "tile_threads": [128, 256, 512],
-    "chunk_terms": [32, 64, 128, 256, 512],
+    "chunk_terms": [32, 64, 128, 256, 512, 1024, 2048],
     "stage_rows": [4, 8, 16],
     "stages": [2, 3, 4, 6],
     "ctas_per_sm": [1, 2, 3],

@@ -46,7 +46,7 @@ def test_falls_back_to_the_shipped_table(cache):
 def test_handles_take_the_tuned_geometry_unless_given_one(cache):
     cache.write_text("{}")
     p = synth.config2(K=5000)
-    assert tuned_geometry(p, {}) == {"chunk_terms": 512, "time_block": 64}
+    assert tuned_geometry(p, {}) == {"time_block": 64}
     assert tuned_geometry(p, {"chunk_terms": 64}) == {}      # explicit geometry: no lookup
     # a taped handle caps the block at 8 steps (the blocked adjoint's limit)
     assert tuned_geometry(p, {"keep_tape": True})["time_block"] == 8
