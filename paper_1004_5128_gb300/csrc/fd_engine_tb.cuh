@@ -1,13 +1,17 @@
-// fd_engine_tb.cuh -- temporally blocked variant of the engine (FP32; full, short and adaptive
-// memory).
+// fd_engine_tb.cuh -- temporally blocked variant of the engine (FP32 state and accumulation;
+// FP32, BF16 or FP16 history; full, short and adaptive memory).
 //
 // The full-memory sum is a Toeplitz product: row delta^r enters step k with weight
 // psi_{k-r} (eq. frac_norxn), so the steps k = kb .. kb+T-1 of one block all use the same old
 // rows.  For block b (kb = bT) this kernel splits each step's sum into
 //   far:  rows r <= kb-T-1, read ONCE per block and multiplied into T accumulators with the
 //         sliding coefficient window psi_{kb-r} .. psi_{kb+T-1-r};
-//   head: lags 1 .. min(k-kb+T, n_base(k)), the at most 2T-1 newest rows, summed step by step
-//         in the per-tile update (these rows are written during the block itself).
+//   near: the previous block's rows kb-T .. kb-1, one near unit per (block, tile) once block b-1
+//         is done (blocks of 16 and more);
+//   mid:  with blocks of 32 and 64, the block's own rows of earlier 16-step sub-blocks, one mid
+//         unit per (block, sub-block, tile);
+//   head: the remaining newest rows (the step's own sub-block or block), summed step by step in
+//         the per-tile update.
 // Far rows of block b are complete once block b-2 has been updated, so the far streaming of
 // block b+1 overlaps the T sequential updates of block b.  History traffic drops by about T
 // while the multiply-adds stay the same: the sum is the paper's, only grouped differently.
@@ -15,23 +19,34 @@
 // Adaptive memory (Definitions 3.1-3.2) is the same product with the weights g(m) that the
 // medians settle on (psi_m on the base interval, d psi_m at a median, 0 between), for all rows
 // above the longest tail of the block's steps; the update units add those few oldest rows with
-// each step's own weights, and the far loop skips the zero weights.
+// each step's own weights, and the CUDA-core far loop skips the zero weights.
+// The far product is a contraction: on CUDA cores (packed FMAs, blocks of 4 to 16) or, with TC,
+// on the tcgen05 tensor cores (fd_tc.cuh; blocks of 16 to 64): M = 128 points, N = T steps,
+// K = 16 rows per MMA, FP32 accumulators in tensor memory, the weights split into 16-bit hi + lo
+// halves.  FP32 history on the tensor cores is stored as FP16 hi + lo planes with a power-of-two
+// scale per (row, tile) (PAIR); with blocks of 32+ the near and mid units run on the tensor cores
+// too, over the history's two planes (the 16-bit history stores the rounding remainder as a lo
+// plane).  A tensor-core CTA runs as two independent halves (tensor memory limits a kernel to one
+// CTA per SM), and a far unit may cover part of a tile (far sub-tiles) so that two halves' stages
+// and accumulators fit.
 // The reverse-time adjoint (ADJ) has the same structure in adjoint steps over the rows
 // mu = L lambda, with a second accumulator for psi' = d psi / d gamma (see engine_kernel).
 //
-// Work units.  Group g holds the far units of block g (T_tiles x C: tile, chunk of R far rows;
-// each writes T partial rows and counts itself in the tile's arrival counter) interleaved with
-// the update units of block g-1 (one per step and tile, step-major): the s-th slice of block
-// g's far units precedes the updates of step s, so an update is claimed only after a slice of
-// streaming work, by which time its previous step is usually done.  An update waits for its
-// tile's far count (group g-1) and its halo tiles' previous step (earlier in group g or in g-1);
-// a far unit of block g waits for block g-2's updates (group g-1).  Every wait therefore
-// targets units with smaller numbers, so the persistent grid cannot deadlock whatever the
-// residency.  Where the tiles are few, one block-long update unit per (block, tile) carries all
-// of the block's steps instead (placed after one wave of block g's far units, which never wait
-// for it); its sibling units must then be co-resident, which the host's tile limit ensures.
-// Determinism, bounded waits, status words and the memory-ordering protocol are those of
-// engine_kernel.
+// Work units.  Group g holds the far units of block g (T_tiles x C x fsub: tile, chunk of R far
+// rows, sub-tile; each writes T partial rows and counts itself in the tile's arrival counter)
+// interleaved with the update units of block g-1 (one per step and tile, or per step and pair of
+// tiles on the tensor-core kernels with many tiles; step-major): the s-th slice of block g's far
+// units precedes the updates of step s, so an update is claimed only after a slice of streaming
+// work, by which time its previous step is usually done.  Mid units of block g-1 precede the
+// updates of steps 16, 32, 48; the group ends with block g's near units.  An update waits for
+// its tile's far, near and mid counts and its halo tiles' previous step; a far unit of block g
+// waits for block g-2's updates, a near or mid unit for its own tile's earlier steps.  Every wait
+// therefore targets units with smaller numbers, so the persistent grid cannot deadlock whatever
+// the residency.  Where the tiles are few (CUDA-core kernels), one block-long update unit per
+// (block, tile) carries all of the block's steps instead (placed after one wave of block g's far
+// units, which never wait for it); its sibling units must then be co-resident, which the host's
+// tile limit ensures.  Determinism, bounded waits, status words and the memory-ordering protocol
+// are those of engine_kernel.
 #pragma once
 
 #include <type_traits>
