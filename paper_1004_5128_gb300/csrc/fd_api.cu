@@ -163,8 +163,9 @@ inline int4 full_step(int64_t k) { return make_int4((int)k, 0, 1, 0); }
 
 // ------------------------------------------------------------------ validation
 
-// Blocked runs with BF16 or FP16 history and blocks of 16 or 32 multiply their far rows on the
-// tensor cores unless FD_FLAG_FMA_FAR asks for the CUDA-core loop.
+// Blocked runs multiply their far rows on the tensor cores with BF16 or FP16 history and blocks of
+// 16, 32 or 64, and with FP32 history (as FP16 hi + lo planes) and blocks of 32 or 64, unless
+// FD_FLAG_FMA_FAR asks for the CUDA-core loop; taped (adjoint) runs use the CUDA cores.
 inline bool tc_far(const fd_problem &p)
 {
     const bool lowp = (p.time_block == 16 || p.time_block == 32 || p.time_block == 64) &&
@@ -362,10 +363,8 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
     g.threads = th;
     g.P = th * g.V;
     g.T = (int)((N + g.P - 1) / g.P);
-    // tensor cores: stages of 16 rows (32 where the block allows at 128 threads of 16-bit history),
-    // as many as fit in 88 KB per half of a CTA (2 .. 5)
-    // (16-bit history with blocks of 32+: stages of 32 rows, the bytes of a near or mid unit's
-    // stage of 16 rows in two planes)
+    // tensor cores: stages of 16 rows, or 32 for 16-bit history with blocks of 32+ (the bytes of a
+    // near or mid unit's stage of 16 rows in two planes); as many as fit in 88 KB per half (2 .. 5)
     const int tc_rs = (g.tc && p.time_block % 32 == 0 && g.hplanes == 1) ? 32 : 16;
     g.RS = p.stage_rows ? p.stage_rows : g.tc ? tc_rs : 8;
     // near and mid units on the tensor cores: blocks of 32+, and a stage of 16 rows in two planes

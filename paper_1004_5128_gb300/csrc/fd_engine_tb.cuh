@@ -168,8 +168,6 @@ template <int TB> __device__ __forceinline__ int far_chunks(const Inst &I, int b
     return max(1, (rhi - far_origin<TB>(I, b) + Rb - 1) / Rb);
 }
 
-// TC: the far units run on the tensor cores (BF16 or FP16 history; one update unit per step and
-// tile).
 // Shared state of one unit-processing CTA (the tensor-core kernels run two per CTA, see below).
 struct VShared {
     Inst I;

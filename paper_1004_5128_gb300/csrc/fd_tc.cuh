@@ -2,7 +2,7 @@
 // written as inline PTX for sm_103a.
 //
 // The temporally blocked far product is a contraction: T steps x P points x R rows per unit
-// (the Toeplitz form of the memory sum, eq. frac_norxn).  With BF16 or FP16 history it runs as
+// (the Toeplitz form of the memory sum, eq. frac_norxn).  With 16-bit history it runs as
 //     D[p][t] += sum_r H[r][p] * C[r][t]        (M = 128 points, N = T steps, K = 16 rows)
 // with the history tile H^T as the MN-major A operand, loaded by the tensor-map unit with a
 // 128-byte swizzle, the coefficient block C as the K-major B operand written by the CTA with the
