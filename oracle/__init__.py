@@ -63,7 +63,7 @@ def lib():
                                 dp, dp]
         L.or_adjoint.argtypes = [pp, dp, ctypes.c_long, dp, dp, dp, dp, dp, dp, ctypes.c_int]
         L.or_run_bf16.argtypes = [pp, dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, dp, ctypes.c_int]
-        L.or_run_closed.argtypes = [pp, dp, ctypes.c_long, ctypes.c_double, dp, lp, ctypes.c_int]
+        L.or_run_closed.argtypes = [pp, dp, ctypes.c_long, ctypes.c_double, dp, lp, dp, ctypes.c_int]
         L.or_round_bf16.argtypes = [ctypes.c_double]
         L.or_round_bf16.restype = ctypes.c_double
         L.or_scalar_mode.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int, ctypes.c_long,
@@ -139,19 +139,22 @@ def run_bf16(p: dict, blk: int, head: int, K: int | None = None, threads: int = 
     return uK
 
 
-def run_closed(p: dict, tau: float, K: int | None = None, threads: int = 0):
+def run_closed(p: dict, tau: float, K: int | None = None, threads: int = 0, margin: bool = False):
     """Closed-loop adaptive memory (reading of the Discussion): (u^K, terms used over the run).
     A median stands for its increment only while the history's relative variation across the
-    increment, from per-row maxima of |delta^r - delta^(r-1)| and |delta^r|, stays below tau."""
+    increment, from per-row maxima of |delta^r - delta^(r-1)| and |delta^r|, stays below tau.
+    margin=True appends the smallest |V - tau| / tau over the run's decisions (inf if none)."""
     K = p["K"] if K is None else K
     u0 = np.ascontiguousarray(p["u0"], dtype=np.float64)
     uK = np.empty(p["nx"] * p["ny"] * p.get("nz", 1))
     n = ctypes.c_long(0)
+    mg = ctypes.c_double(0.0)
     s = _problem(p)
-    rc = lib().or_run_closed(ctypes.byref(s), _dp(u0), K, float(tau), _dp(uK), ctypes.byref(n), threads)
+    rc = lib().or_run_closed(ctypes.byref(s), _dp(u0), K, float(tau), _dp(uK), ctypes.byref(n),
+                             ctypes.byref(mg), threads)
     if rc != 0:
         raise ValueError(f"or_run_closed failed ({rc})")
-    return uK, int(n.value)
+    return (uK, int(n.value), float(mg.value)) if margin else (uK, int(n.value))
 
 
 def round_bf16(x: float) -> float:

@@ -354,7 +354,7 @@ int or_run_bf16(const or_problem *p, const double *u0, long K, long blk, long he
 /* ------------------------------------------------ closed-loop adaptive memory */
 
 int or_run_closed(const or_problem *p, const double *u0, long K, double tau, double *uK, long *nterms,
-                  int threads)
+                  double *margin, int threads)
 {
     if (check_problem(p, K) || !u0 || !uK || p->mem_mode != OR_MEM_ADAPTIVE || !(tau >= 0.0)) return -1;
     const long N = (long)p->nx * p->ny * p->nz;
@@ -382,6 +382,7 @@ int or_run_closed(const or_problem *p, const double *u0, long K, double tau, dou
     (void)threads;
 #endif
     long total = 0;
+    double mg = INFINITY; /* closest decision to the threshold, relative to it */
     for (long k = 0; k < K; ++k) {
         double *row = hist + (size_t)k * (size_t)N;
         apply_L(p, u, row); /* delta^k */
@@ -402,6 +403,7 @@ int or_run_closed(const or_problem *p, const double *u0, long K, double tau, dou
             for (long r = k - hi + 1; r <= k - lo; ++r) var += D[r];
             const double ref = M[k - m];
             const int smooth = isinf(tau) || ((ref > 0.0) ? (var / ref < tau) : (var == 0.0 && tau > 0.0));
+            if (!isinf(tau) && tau > 0.0 && ref > 0.0) mg = fmin(mg, fabs(var / ref - tau) / tau);
             if (smooth) {
                 tl[nt] = m; tc[nt] = (double)d * psi[m]; ++nt;
             } else {
@@ -422,6 +424,7 @@ int or_run_closed(const or_problem *p, const double *u0, long K, double tau, dou
     }
     memcpy(uK, u, sizeof(double) * (size_t)N);
     if (nterms) *nterms = total;
+    if (margin) *margin = mg;
     free(psi); free(hist); free(D); free(M); free(u); free(un); free(lag); free(mult); free(tl); free(tc);
     return 0;
 }

@@ -88,9 +88,12 @@ int or_run_bf16(const or_problem *p, const double *u0, long K, long blk, long he
  * every point shares one schedule; tau = +inf keeps every median).  Otherwise the increment's lags are summed one by one with
  * weight psi.  tau = +inf gives or_run's adaptive result bit for bit; tau = 0 with the partition
  * rule gives full memory.  *nterms (if not NULL) receives the number of (lag, weight) terms used
- * over the run, lag 0 included.  Returns as or_run. */
+ * over the run, lag 0 included.  *margin (if not NULL) receives the smallest |V - tau| / tau over
+ * the decisions with M_{k-m} > 0 (+inf for tau = +inf or 0, or without such decisions): how far
+ * every decision lies from flipping, for comparisons with runs whose delta differs by rounding.
+ * Returns as or_run. */
 int or_run_closed(const or_problem *p, const double *u0, long K, double tau, double *uK, long *nterms,
-                  int threads);
+                  double *margin, int threads);
 
 /* Forward run in double complex (complex-step differentiation): the
  * imaginary parts of u0, gamma, alpha and react carry the perturbation.

@@ -70,3 +70,19 @@ def test_feedback_rescues_oscillating_superdiffusion():
     assert e_open > 1.0
     assert e1 < 1e-2 and e2 < 5e-3
     assert n_open < n1 <= n2 <= p["K"] * (p["K"] + 1) // 2
+
+
+def test_decision_margin():
+    """The margin is the distance of the closest decision to the threshold, relative to it: no
+    decision at tau = inf, and a threshold placed on a decision's own ratio has margin 0 there."""
+    p = base(3, synth.ADAPT_PARTITION, K=120)
+    assert oracle.run_closed(p, math.inf, margin=True)[2] == math.inf
+    u, n, mg = oracle.run_closed(p, 0.2, margin=True)
+    assert 0.0 < mg < math.inf
+    # moving the threshold by less than the margin keeps every decision (same terms, same field)
+    u2, n2, _ = oracle.run_closed(p, 0.2 * (1 + 0.5 * mg), margin=True)
+    assert n2 == n and np.array_equal(u2, u)
+    # moving it by more than the margin flips at least the closest decision
+    u3, n3, _ = oracle.run_closed(p, 0.2 * (1 + 1.5 * mg), margin=True)
+    u4, n4, _ = oracle.run_closed(p, 0.2 * (1 - 1.5 * mg), margin=True)
+    assert n3 != n or n4 != n
