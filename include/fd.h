@@ -67,6 +67,7 @@ enum { FD_F64 = 0, FD_F32 = 1, FD_BF16 = 2, FD_F16 = 3 };
                                       block-long update units would fit (see time_block) */
 #define FD_FLAG_FMA_FAR 64u        /* time_block with BF16 / F16 history: multiply the far rows on
                                       the CUDA cores instead of the tensor cores (see time_block) */
+#define FD_FLAG_CLOSED_LOOP 128u   /* adaptive memory with feedback from the history (see mem_tau) */
 
 typedef struct fd_problem {
     int ndim;            /* 1, 2 or 3 (3-D: the 7-point analogue of eq. deltasimp) */
@@ -122,6 +123,21 @@ typedef struct fd_problem {
                             run on the CUDA cores, one unit per tile carries a whole block's
                             updates and keeps the block's newest rows in on-chip memory, unless
                             FD_FLAG_STEP_UPDATES is set. */
+    double mem_tau;      /* FD_FLAG_CLOSED_LOOP: threshold tau >= 0 (+inf allowed) of closed-loop
+                            adaptive memory, a reading of the Discussion (Section 4: the backward
+                            sum's spacing follows the derivative of the past history).  At step k
+                            a median m of Proposition 3.1, standing for the d = 2i-1 lags
+                            m-(i-1) .. m+(i-1), keeps the weight d psi_m while
+                            V = sum_{r = k-m-(i-1)+1}^{k-m+(i-1)} D_r / M_{k-m} < tau, with
+                            D_r = max_j |delta^r_j - delta^{r-1}_j| and M_r = max_j |delta^r_j|
+                            over the whole field (one schedule for every point); otherwise its d
+                            lags are summed one by one with weight psi (M = 0: kept only when
+                            V = 0 and tau > 0).  tau = +inf is the open-loop rule; tau = 0 with
+                            FD_ADAPT_PARTITION is full memory.  Requires FD_MEM_ADAPTIVE,
+                            hist_dtype == state_dtype (F32 or F64), time_block 0 and no
+                            FD_FLAG_KEEP_TAPE (FD_ERR_UNSUPPORTED otherwise); single handles only
+                            (fd_batch_*, fd_run_batch and fd_run_static: FD_ERR_UNSUPPORTED).
+                            Ignored without the flag. */
 } fd_problem;
 
 typedef struct fd_handle fd_handle;
@@ -187,6 +203,13 @@ int64_t fd_current_step(fd_handle *h);
 int fd_adjoint(fd_handle *h, const void *dJ_duK, void *dJ_du0, double *dJ_dgamma,
                double *dJ_dalpha, double dJ_dreact[4]);
 
+/* Memory terms (lag, weight) used by the steps run since fd_set_state (or restored by fd_load),
+ * lag 0 included: the sum over those steps of |sched(k)| + 1.  Closed-loop adaptive memory
+ * (FD_FLAG_CLOSED_LOOP) counts them on the device as the steps run (synchronises the stream);
+ * the other modes take them from the schedule.  The count the paper compares its memory forms by
+ * (Section 3.2). */
+int fd_memory_terms(fd_handle *h, int64_t *terms);
+
 /* Sticky device status of the last launches (synchronises the stream). */
 int fd_get_status(fd_handle *h);
 
@@ -198,7 +221,9 @@ int fd_get_status(fd_handle *h);
  * tile, 9 the stall injected by FD_FLAG_INJECT_STALL, 10 blocked far unit waiting for the
  * previous chunk's running sum, 11 tensor-core far unit waiting for a copy, its coefficient
  * block or its MMAs (operands as for site 2), 12 near unit waiting for the previous block's
- * rows, 13 mid unit waiting for its block's earlier rows.  info[1..6] are the site's operands
+ * rows, 13 mid unit waiting for its block's earlier rows, 14 closed-loop chunk waiting for the
+ * field-wide maxima of the rows its decisions read (operands: step, tile, row, count read, tiles).
+ * info[1..6] are the site's operands
  * (step or block, tile, the counter target and the value last read, the launch's first step;
  * site 2 packs pairs into the high and low 32 bits), info[7] the CTA.  Only the first failure
  * since fd_set_state is kept.  Synchronises the stream. */

@@ -34,6 +34,7 @@ FD_FLAG_INJECT_STALL = 8
 FD_FLAG_PLAIN_STATE = 16
 FD_FLAG_STEP_UPDATES = 32
 FD_FLAG_FMA_FAR = 64
+FD_FLAG_CLOSED_LOOP = 128
 
 # every function include/fd.h declares
 EXPORTS = (
@@ -44,6 +45,7 @@ EXPORTS = (
     "fd_batch_run", "fd_batch_get_state", "fd_batch_get_status", "fd_batch_get_geometry",
     "fd_batch_destroy",
     "fd_run_batch", "fd_strerror", "fd_run_static", "fd_save_bytes", "fd_save", "fd_load",
+    "fd_memory_terms",
 )
 
 
@@ -66,7 +68,7 @@ class FdProblem(ctypes.Structure):
         ("timeout_ms", ctypes.c_int),
         ("tile_threads", ctypes.c_int), ("chunk_terms", ctypes.c_int), ("stage_rows", ctypes.c_int),
         ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("head_lags", ctypes.c_int),
-        ("nz", ctypes.c_int), ("time_block", ctypes.c_int),
+        ("nz", ctypes.c_int), ("time_block", ctypes.c_int), ("mem_tau", ctypes.c_double),
     ]
 
 
@@ -123,6 +125,7 @@ def lib():
             "fd_save_bytes": [vp, sz],
             "fd_save": [vp, vp, ctypes.c_size_t],
             "fd_load": [vp, vp, ctypes.c_size_t],
+            "fd_memory_terms": [vp, ctypes.POINTER(ctypes.c_int64)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -220,12 +223,21 @@ def fd_get_status(h: int) -> int:
     return int(lib().fd_get_status(h))
 
 
+def fd_memory_terms(h: int) -> int:
+    """Memory terms used by the steps run so far, lag 0 included (closed loop: counted on the
+    device)."""
+    n = ctypes.c_int64(0)
+    check(lib().fd_memory_terms(h, ctypes.byref(n)), "fd_memory_terms")
+    return int(n.value)
+
+
 ERROR_SITES = {0: "none", 1: "blocked far unit: history rows", 2: "blocked far unit: bulk copy",
                3: "blocked update: far count", 4: "blocked update: own rows",
                5: "blocked update: halo tile", 6: "chunk: history rows", 7: "chunk: bulk copy",
                8: "fixup: halo tile", 9: "injected stall", 10: "blocked far unit: running sum",
                11: "tensor-core far unit: copy, coefficients or MMAs",
-               12: "blocked near unit: previous block's rows", 13: "blocked mid unit: the block's earlier rows"}
+               12: "blocked near unit: previous block's rows", 13: "blocked mid unit: the block's earlier rows",
+               14: "closed-loop chunk: row maxima of every tile"}
 
 
 def fd_get_error_info(h: int) -> dict:

@@ -147,6 +147,8 @@ int build_schedule(const fd_problem &p, int64_t K, Sched &s)
 
 inline int64_t n_terms(const int4 &e) { return (int64_t)e.x + e.y + (e.w >= e.z ? e.w - e.z + 1 : 0); }
 
+inline bool closed_loop(const fd_problem &p) { return (p.flags & FD_FLAG_CLOSED_LOOP) != 0; }
+
 // The adjoint of adaptive memory runs the full-memory adjoint with the settled weights (plus the
 // tail terms' corrections): its work units are those of full memory.
 inline bool adaptive_adjoint(const fd_problem &p)
@@ -205,6 +207,11 @@ int validate(const fd_problem *p)
     if (!fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, kahan, false))
         return FD_ERR_UNSUPPORTED;
     if (adj && !fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, false, true)) return FD_ERR_UNSUPPORTED;
+    if (closed_loop(*p)) {  // closed-loop adaptive memory: per-step kernel, history in state precision
+        if (std::isnan(p->mem_tau) || p->mem_tau < 0.0) return FD_ERR_INVALID_ARG;
+        if (p->mem_mode != FD_MEM_ADAPTIVE || p->hist_dtype != p->state_dtype || p->time_block || adj)
+            return FD_ERR_UNSUPPORTED;
+    }
     if (p->time_block) {
         const bool tc = tc_far(*p);
         if (p->time_block != 4 && p->time_block != 8 && p->time_block != 16 &&
@@ -266,10 +273,12 @@ struct Geo {
     std::vector<int> br0;
 };
 
-// Dynamic shared memory: stage ring, per-unit term tables (R coefficients x2, R slots), barriers.
-inline size_t smem_bytes(const Geo &g, int rmax)
+// Dynamic shared memory: stage ring, per-unit term tables (R coefficients x2, R slots), barriers,
+// and for closed-loop memory the R + 1 entry offsets of a unit's terms and two doubles per warp.
+inline size_t smem_bytes(const Geo &g, int rmax, bool closed = false)
 {
-    return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)rmax * (2 * g.sa + 4) + 32 + 8 * (size_t)g.NS;
+    return (size_t)g.NS * g.RS * g.threads * 16 + (size_t)rmax * (2 * g.sa + 4) + 32 + 8 * (size_t)g.NS +
+           (closed ? (size_t)(rmax + 1) * 4 + 8 + 16 * (size_t)(g.threads / 32) : 0);
 }
 
 // Blocked kernel: stage ring (block-long update units keep their steps' memory sums and their
@@ -499,7 +508,7 @@ void make_geo(const fd_problem &p, const Sched &s, int threads_override, Geo &g)
         g.ctas = std::max(1, std::min(g.ctas, 512 / (cols * g.halves)));
         g.smem_half = smem_half_tc(g, g.rwin, p.hist_dtype != FD_BF16);
     }
-    g.smem = g.tc ? g.halves * g.smem_half + 1024 : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R);
+    g.smem = g.tc ? g.halves * g.smem_half + 1024 : g.tb ? smem_bytes_tb(g, g.rwin, p.hist_dtype == FD_F16) : smem_bytes(g, g.R, closed_loop(p));
 }
 
 // Units per step: T tiles x max(1, ceil(n(k)/R)) chunks.
@@ -615,6 +624,12 @@ struct Layout {
     char *ckpt, *seg, *rec[2], *ahist, *abuf[2];
     double *dots;
     int ckpt_rows, seg_rows;
+    // closed-loop adaptive memory: row maxima D, M and the tiles counted into them (max_steps rows
+    // each), the terms counter, the increment length of each median
+    double *clD, *clM;
+    unsigned *clrows;
+    unsigned long long *clterms;
+    int *gd;
 };
 
 void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s, Layout &L,
@@ -665,6 +680,17 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     }
     L.tmap = g.tc ? c.take(128) : nullptr;
     L.tmap2 = (g.nmtc && g.hplanes == 1) ? c.take(128) : nullptr;
+    L.clD = L.clM = nullptr;
+    L.clrows = nullptr;
+    L.clterms = nullptr;
+    L.gd = nullptr;
+    if (closed_loop(p)) {
+        L.clD = (double *)c.take(sizeof(double) * (size_t)p.max_steps);
+        L.clM = (double *)c.take(sizeof(double) * (size_t)p.max_steps);
+        L.clrows = (unsigned *)c.take(sizeof(unsigned) * (size_t)p.max_steps);
+        L.clterms = (unsigned long long *)c.take(sizeof(unsigned long long));
+        L.gd = (int *)c.take(sizeof(int) * ng);
+    }
     L.ckpt = L.seg = L.rec[0] = L.rec[1] = L.ahist = L.abuf[0] = L.abuf[1] = nullptr;
     L.dots = nullptr;
     L.ckpt_rows = L.seg_rows = 0;
@@ -706,7 +732,7 @@ Ctrl carve_ctrl(Carve &c)
 struct Tables {
     std::vector<double> psi, dpsi;
     std::vector<unsigned char> psi_a, dpsi_a, gcoef_a, gw_a, dgw_a;
-    std::vector<int> glag, br0;
+    std::vector<int> glag, br0, gd;
     std::vector<int4> asched;
     TailList tail;
 };
@@ -726,9 +752,11 @@ void build_tables(const fd_problem &p, const Sched &s, const Geo &g, Tables &t)
     gl_weights(p.gamma, n, t.psi.data(), t.dpsi.data());
     std::vector<double> gc(std::max<size_t>(1, s.G.size()), 0.0);
     t.glag.assign(gc.size(), 0);
+    t.gd.assign(gc.size(), 1);
     for (size_t i = 0; i < s.G.size(); ++i) {
         gc[i] = (double)s.G[i].mult * t.psi[s.G[i].lag];
         t.glag[i] = s.G[i].lag;
+        t.gd[i] = s.G[i].mult;
     }
     // blocked adaptive memory: g(m) = psi_m on the base interval [0, a], d psi_m at a median,
     // 0 at the other lags (each median's weight, as the per-step schedule uses it)
@@ -787,6 +815,7 @@ int upload_tables(const fd_problem &p, const Sched &s, const Tables &t, const La
     CK(cudaMemcpyAsync(L.sched, s.step.data(), sizeof(int4) * s.step.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(L.glag, t.glag.data(), sizeof(int) * t.glag.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(L.gcoef, t.gcoef_a.data(), t.gcoef_a.size(), cudaMemcpyHostToDevice, st));
+    if (L.gd) CK(cudaMemcpyAsync(L.gd, t.gd.data(), sizeof(int) * t.gd.size(), cudaMemcpyHostToDevice, st));
     if (L.gw) CK(cudaMemcpyAsync(L.gw, t.gw_a.data(), t.gw_a.size(), cudaMemcpyHostToDevice, st));
     if (L.br0) CK(cudaMemcpyAsync(L.br0, t.br0.data(), sizeof(int) * t.br0.size(), cudaMemcpyHostToDevice, st));
     if (L.dgw) CK(cudaMemcpyAsync(L.dgw, t.dgw_a.data(), t.dgw_a.size(), cudaMemcpyHostToDevice, st));
@@ -934,6 +963,14 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
     I.g_coef = L.gcoef;
     I.gw = L.gw;
     I.br0 = L.br0;
+    if (!adj && L.clD) {
+        I.cl_D = L.clD;
+        I.cl_M = L.clM;
+        I.cl_rows = L.clrows;
+        I.cl_terms = L.clterms;
+        I.g_d = L.gd;
+        I.cl_tau = p.mem_tau;
+    }
     if (!adj && L.ckpt) {
         I.tape = L.ckpt;
         I.tape_k0 = 0;
@@ -1287,6 +1324,13 @@ int fd_set_state(fd_handle *h, const void *u0)
     CK(cudaMemsetAsync(h->ctrl.err, 0, sizeof(int), h->st));
     CK(cudaMemsetAsync(h->ctrl.nonfinite, 0, sizeof(unsigned), h->st));
     CK(cudaMemsetAsync(h->ctrl.err_info, 0, 8 * sizeof(long long), h->st));
+    if (h->L.clD) {
+        const size_t K = (size_t)h->p.max_steps;
+        CK(cudaMemsetAsync(h->L.clD, 0, K * sizeof(double), h->st));
+        CK(cudaMemsetAsync(h->L.clM, 0, K * sizeof(double), h->st));
+        CK(cudaMemsetAsync(h->L.clrows, 0, K * sizeof(unsigned), h->st));
+        CK(cudaMemsetAsync(h->L.clterms, 0, sizeof(unsigned long long), h->st));
+    }
     h->k = 0;
     h->bad = 0;
     return FD_OK;
@@ -1326,6 +1370,22 @@ int fd_get_status(fd_handle *h)
     const int s = status_from(err, nf);
     if (s == FD_ERR_TIMEOUT) h->bad = 1;
     return s;
+}
+
+int fd_memory_terms(fd_handle *h, int64_t *terms)
+{
+    if (!h || !terms) return FD_ERR_INVALID_ARG;
+    if (h->L.clterms) {
+        unsigned long long n = 0;
+        CK(cudaMemcpyAsync(&n, h->L.clterms, sizeof(n), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        *terms = (int64_t)n;
+        return FD_OK;
+    }
+    int64_t n = 0;
+    for (int64_t k = 0; k < h->k; ++k) n += n_terms(h->s.step[k]) + 1;
+    *terms = n;
+    return FD_OK;
 }
 
 int fd_get_error_info(fd_handle *h, int64_t info[8])
@@ -1429,13 +1489,14 @@ struct SaveHeader {
     char magic[8];
     int64_t k, N, ss, comp, cap, pitch, planes, rows, hring_sep, hring_cap, hring_pitch, hscale, T;
     int64_t nx, ny, nz, ndim, max_steps, mem_mode, mem_L, mem_a, rule, time_block, sdt, hdt, adt, flags, bc;
-    double gamma, alpha, dt, dx, react[4];
+    int64_t closed;  // closed-loop memory: the rows' maxima and counts, and the terms counter follow
+    double gamma, alpha, dt, dx, react[4], tau;
 };
 
 void save_plan(const fd_handle *h, int64_t k, SaveHeader &hd, size_t &total)
 {
     std::memset(&hd, 0, sizeof(hd));
-    std::memcpy(hd.magic, "FDSAVE1", 8);
+    std::memcpy(hd.magic, "FDSAVE2", 8);
     const fd_problem &p = h->p;
     const Geo &g = h->g;
     hd.k = k;
@@ -1471,8 +1532,11 @@ void save_plan(const fd_handle *h, int64_t k, SaveHeader &hd, size_t &total)
     hd.dt = p.dt;
     hd.dx = p.dx;
     for (int i = 0; i < 4; ++i) hd.react[i] = p.react[i];
+    hd.closed = h->L.clD ? 1 : 0;
+    hd.tau = hd.closed ? p.mem_tau : 0.0;
     total = sizeof(SaveHeader) + (size_t)hd.N * hd.ss * (1 + hd.comp) + (size_t)(hd.planes * hd.rows * hd.pitch) +
-            (size_t)(hd.hring_cap * hd.hring_pitch) + (size_t)(hd.hscale * hd.rows * hd.T) * sizeof(float);
+            (size_t)(hd.hring_cap * hd.hring_pitch) + (size_t)(hd.hscale * hd.rows * hd.T) * sizeof(float) +
+            (size_t)hd.closed * ((size_t)k * (2 * sizeof(double) + sizeof(unsigned)) + sizeof(unsigned long long));
 }
 
 // The pieces of a checkpoint in order: (device address, bytes).
@@ -1486,6 +1550,12 @@ std::vector<std::pair<char *, size_t>> save_pieces(const fd_handle *h, const Sav
         v.emplace_back(h->L.hist + (size_t)(pl * hd.cap * hd.pitch), (size_t)(hd.rows * hd.pitch));
     if (hd.hring_cap) v.emplace_back(h->L.hring, (size_t)(hd.hring_cap * hd.hring_pitch));
     if (hd.hscale) v.emplace_back(reinterpret_cast<char *>(h->L.hscale), (size_t)(hd.rows * hd.T) * sizeof(float));
+    if (hd.closed) {
+        v.emplace_back(reinterpret_cast<char *>(h->L.clD), (size_t)hd.k * sizeof(double));
+        v.emplace_back(reinterpret_cast<char *>(h->L.clM), (size_t)hd.k * sizeof(double));
+        v.emplace_back(reinterpret_cast<char *>(h->L.clrows), (size_t)hd.k * sizeof(unsigned));
+        v.emplace_back(reinterpret_cast<char *>(h->L.clterms), sizeof(unsigned long long));
+    }
     return v;
 }
 
@@ -1528,7 +1598,7 @@ int fd_load(fd_handle *h, const void *buf, size_t bytes)
     if (h->p.flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
     SaveHeader in;
     CK(cudaMemcpy(&in, buf, sizeof(in), cudaMemcpyDefault));
-    if (std::memcmp(in.magic, "FDSAVE1", 8) || in.k < 0 || in.k > h->p.max_steps) return FD_ERR_INVALID_ARG;
+    if (std::memcmp(in.magic, "FDSAVE2", 8) || in.k < 0 || in.k > h->p.max_steps) return FD_ERR_INVALID_ARG;
     SaveHeader hd;
     size_t total = 0;
     save_plan(h, in.k, hd, total);
@@ -1538,6 +1608,12 @@ int fd_load(fd_handle *h, const void *buf, size_t bytes)
     for (const auto &pc : save_pieces(h, hd)) {
         if (pc.second) CK(cudaMemcpyAsync(pc.first, src + off, pc.second, cudaMemcpyDefault, h->st));
         off += pc.second;
+    }
+    if (hd.closed && in.k < h->p.max_steps) {  // rows from k on: not yet written (the handle may have run further)
+        const size_t rest = (size_t)(h->p.max_steps - in.k);
+        CK(cudaMemsetAsync(h->L.clD + in.k, 0, rest * sizeof(double), h->st));
+        CK(cudaMemsetAsync(h->L.clM + in.k, 0, rest * sizeof(double), h->st));
+        CK(cudaMemsetAsync(h->L.clrows + in.k, 0, rest * sizeof(unsigned), h->st));
     }
     CK(cudaMemsetAsync(h->ctrl.err, 0, sizeof(int), h->st));
     CK(cudaMemsetAsync(h->ctrl.nonfinite, 0, sizeof(unsigned), h->st));
@@ -1640,7 +1716,7 @@ int batch_plan(const fd_problem *probs_in, int count, fd_batch &b, size_t *bytes
             probs[i].accum_dtype != probs[0].accum_dtype ||
             ((probs[i].flags ^ probs[0].flags) & (FD_FLAG_KAHAN | FD_FLAG_KEEP_TAPE)))
             return FD_ERR_INVALID_ARG;
-        if (probs[i].flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;
+        if (probs[i].flags & (FD_FLAG_KEEP_TAPE | FD_FLAG_CLOSED_LOOP)) return FD_ERR_UNSUPPORTED;
         if (probs[i].time_block != probs[0].time_block) return FD_ERR_INVALID_ARG;  // one kernel per batch
     }
     b.p.assign(probs, probs + count);

@@ -101,6 +101,18 @@ struct Inst {
     const int *acorr_off;    // adjoint of adaptive memory: tail terms of row r at [off[r], off[r+1])
     const struct AdjTail *acorr;
     int acorr_rows;          // rows r = 0 .. acorr_rows-1 have tail terms
+    // Closed-loop adaptive memory (per-step kernel; null = open loop).  Per history row r the
+    // field-wide largest change from row r-1, D_r = max_j |delta^r_j - delta^{r-1}_j|, and largest
+    // magnitude M_r = max_j |delta^r_j| (doubles, raised with integer atomics on their bits: for
+    // non-negative doubles the order of the bits is the order of the values), and the tiles that
+    // have added row r to them.  A median stands for its increment while
+    // V = sum_{rows of the increment but its oldest} D / M_{k-m} < cl_tau, else the increment's
+    // lags are summed one by one with weight psi.
+    double *cl_D, *cl_M;
+    unsigned *cl_rows;
+    unsigned long long *cl_terms;  // memory terms used, lag 0 included (counted by tile 0)
+    const int *g_d;                // increment length d of each median
+    double cl_tau;
 };
 
 // Adjoint of adaptive memory.  The adjoint sums every (step k, lag m) pair with the weight g(m)
@@ -422,6 +434,20 @@ __device__ __forceinline__ void term_of(const Inst &I, const int4 sc, int tau, i
     }
 }
 
+// Closed-loop adaptive memory: does the median at lag m of step k stand for its increment of d
+// lags?  Reads the maxima of rows k-m-(d-1)/2+1 .. k-m+(d-1)/2, which the caller has waited for.
+// Ascending rows, FP64, the rule's comparison as written (tau = +inf keeps every median; a zero
+// reference keeps it only for zero variation and tau > 0).
+__device__ __forceinline__ bool cl_smooth(const Inst &I, int k, int m, int d)
+{
+    const int h = (d - 1) / 2;
+    double var = 0.0;
+    for (int r = k - m - h + 1; r <= k - m + h; ++r) var += __ldcg(I.cl_D + r);
+    const double ref = __ldcg(I.cl_M + (k - m));
+    if (isinf(I.cl_tau)) return true;
+    return (ref > 0.0) ? (var / ref < I.cl_tau) : (var == 0.0 && I.cl_tau > 0.0);
+}
+
 // Neighbour masks of the V consecutive points j0 .. j0+V-1: bit e set when neighbour e (+x, -x,
 // +y, -y, +z, -z) lies inside the grid.  One division of j0, then a running (x, y, z).
 template <int V> __device__ __forceinline__ void grid_masks(const Inst &I, int j0, unsigned *inb)
@@ -485,6 +511,10 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
     int *toff = reinterpret_cast<int *>(coef2 + L.rmax);                   // history slot per term
     uint64_t *bars = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(toff + L.rmax) + 15) & ~uintptr_t(15));
+    // closed loop: entry offsets of a unit's terms (rmax + 1), then the per-warp row maxima
+    int *eoff = reinterpret_cast<int *>(bars + NS);
+    double *clmax = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(eoff + L.rmax + 1) + 7) & ~uintptr_t(7));
 
     __shared__ Inst I;
     __shared__ Unit U;
@@ -552,6 +582,16 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     if (w < 0) note_failure(L, 6, gi.y, U.tile, need, ld_acquire(&I.done[U.tile]), L.k0, 0);
                     if (w <= 0) ok = 0;
                 }
+                // closed loop: the maxima of every row the chunk's decisions read, on every tile.
+                // The chunk's first median has the oldest-ending increment's newest row, k - lo;
+                // tiles complete their rows in order, so that row's count covers the older ones.
+                if (ok && I.cl_D && U.tau0 < sc.x + sc.y && U.tau1 > sc.x) {
+                    const int g0 = max(U.tau0, sc.x) - sc.x;
+                    const int r = gi.y - (I.g_lag[g0] - (I.g_d[g0] - 1) / 2);
+                    const int w = wait_until(&I.cl_rows[r], (unsigned)I.T, L, 512);
+                    if (w < 0) note_failure(L, 14, gi.y, U.tile, r, ld_acquire(&I.cl_rows[r]), I.T, 0);
+                    if (w <= 0) ok = 0;
+                }
             }
             U.valid = ok;
         }
@@ -561,7 +601,6 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         const int tile = U.tile, k = U.k, C = U.C;
         const int tau0 = U.tau0, tau1 = U.tau1;
         const int nterm = tau1 - tau0;
-        const int nst = (nterm + RS - 1) / RS;
         const int j0 = tile * I.P + tid * V;  // first point of this thread's vector
         long long tile_bytes = (long long)min(I.P, I.N - tile * I.P) * (long long)sizeof(TH);
         tile_bytes = (tile_bytes + 15) & ~15ll;
@@ -571,93 +610,151 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         for (int v = 0; v < V; ++v) acc[v] = cmp[v] = acc2[v] = TA(0);
 
         // ------------------------------------------------- stream the chunk
-        // term tables of this unit, built by the whole CTA: coefficient(s) and history slot
-        for (int t = tid; t < nterm; t += nthr) {
-            int lag;
-            TA c, c2;
-            term_of<TA, ADJ>(I, U.sc, tau0 + t, lag, c, c2);
-            const int slot = (k - lag) % I.cap;
-            if (I.hscale) c = c * (TA)__ldcg(I.hscale + (size_t)slot * I.T + tile);
-            coef[t] = c;
-            if (ADJ) coef2[t] = c2;
-            toff[t] = slot;
+        // Closed loop: the entries each term expands to (1, or d for a median whose increment is
+        // not smooth), prefix-summed into eoff[0..nterm] by warp 0; the unit then streams ntot
+        // entries in rounds of at most rmax (open loop: one round of the nterm terms).
+        int ntot = nterm;
+        if (I.cl_D && nterm > 0) {
+            for (int t = tid; t < nterm; t += nthr) {
+                const int tau = tau0 + t;
+                int cnt = 1;
+                if (tau >= U.sc.x && tau < U.sc.x + U.sc.y) {
+                    const int g = tau - U.sc.x, d = I.g_d[g];
+                    if (d > 1 && !cl_smooth(I, k, I.g_lag[g], d)) cnt = d;
+                }
+                eoff[t + 1] = cnt;
+            }
+            __syncthreads();
+            if (tid < 32) {
+                const int seg = (nterm + 31) / 32, a = min(nterm, tid * seg), b = min(nterm, a + seg);
+                int sum = 0;
+                for (int t = a; t < b; ++t) sum += eoff[t + 1];
+                int pre = sum;  // inclusive warp scan of the segment sums
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, pre, o);
+                    if (tid >= o) pre += y;
+                }
+                int run = pre - sum;
+                for (int t = a; t < b; ++t) {
+                    run += eoff[t + 1];
+                    eoff[t + 1] = run;
+                }
+                if (tid == 0) eoff[0] = 0;
+            }
+            __syncthreads();
+            ntot = eoff[nterm];
+            if (tid == 0 && tile == 0) atomicAdd(I.cl_terms, (unsigned long long)ntot);
         }
-        __syncthreads();
-        // Stage s of this unit into ring slot `slot` % NS, by warp s mod (warps), one lane per
-        // row: the copies of a stage go out together and the issue work rotates over the warps
-        // instead of delaying one warp at every stage barrier.  All lanes of the warp call it.
         const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-        auto issue = [&](int s, uint32_t slot) {
-            const int b = (int)(slot % (uint32_t)NS);
-            const int t0 = s * RS;
-            const int t1 = min(nterm, t0 + RS);
-            if (lane == 0) mbar_expect_tx(&bars[b], (uint32_t)(tile_bytes * (t1 - t0)));
-            __syncwarp();
-            const char *col = I.hist + (size_t)tile * I.P * sizeof(TH);
-            for (int t = t0 + lane; t < t1; t += 32)
-                bulk_g2s(stages + ((size_t)b * RS + (t - t0)) * row_bytes, col + (size_t)toff[t] * I.pitch,
-                         (uint32_t)tile_bytes, &bars[b]);
-        };
-        // every lane that issues copies orders the rows it acquired before the async proxy
-        if (lane < RS) fence_proxy_async_global();
-        {
-            const int pre = min(NS, nst);
-            for (int s = 0; s < pre; ++s)
-                if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
-            n_issued += (uint32_t)pre;
-        }
         int aborted = 0;
-        for (int s = 0; s < nst; ++s) {
-            const int b = (int)(n_used % (uint32_t)NS);
-            const uint32_t par = (n_used / (uint32_t)NS) & 1u;
-            int tmo = 0;
-            if (!mbar_try_wait(&bars[b], par)) {
-                const long long t0 = globaltimer();
-                while (!mbar_try_wait(&bars[b], par)) {
-                    if (globaltimer() - t0 > L.timeout_ns) {
-                        if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE) note_failure(L, 7, U.k, U.tile, 0, 0, 0, 0);
-                        tmo = 1;  // the copy is still owed to this slot; see below
-                        break;
-                    }
-                }
-            }
-            const int rows = tmo ? 0 : min(RS, nterm - s * RS);
-            const unsigned char *base = stages + (size_t)b * RS * row_bytes + (size_t)tid * 16;
-            for (int r = 0; r < rows; ++r) {
-                const uint4 w = *reinterpret_cast<const uint4 *>(base + (size_t)r * row_bytes);
-                TA x[V];
-                HVec<TH>::unpack(w, x);
-                const TA c = coef[s * RS + r];
-                if (KAHAN) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const TA y = c * x[v] - cmp[v];
-                        const TA t = acc[v] + y;
-                        cmp[v] = (t - acc[v]) - y;
-                        acc[v] = t;
-                    }
+        for (int e0 = 0; e0 == 0 || e0 < ntot; e0 += L.rmax) {
+            const int ne = min(L.rmax, ntot - e0);
+            const int nst = (ne + RS - 1) / RS;
+            if (e0) __syncthreads();  // the previous round's tables are read
+            // term tables of this round, built by the whole CTA: coefficient(s) and history slot
+            for (int t = tid; t < ne; t += nthr) {
+                int lag;
+                TA c, c2;
+                if (!I.cl_D) {
+                    term_of<TA, ADJ>(I, U.sc, tau0 + t, lag, c, c2);
                 } else {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] = fma(c, x[v], acc[v]);
+                    const int e = e0 + t;
+                    int lo = 0, hi = nterm;  // the term holding entry e: eoff[lo] <= e < eoff[lo + 1]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (eoff[mid] <= e) lo = mid;
+                        else hi = mid;
+                    }
+                    term_of<TA, ADJ>(I, U.sc, tau0 + lo, lag, c, c2);
+                    const int cnt = eoff[lo + 1] - eoff[lo];
+                    if (cnt > 1) {  // lag lo + i of the expanded increment, weight psi
+                        lag = lag - (cnt - 1) / 2 + (e - eoff[lo]);
+                        c = reinterpret_cast<const TA *>(I.psi)[lag];
+                    }
                 }
-                if (ADJ) {
-                    const TA c2 = coef2[s * RS + r];
+                const int slot = (k - lag) % I.cap;
+                if (I.hscale) c = c * (TA)__ldcg(I.hscale + (size_t)slot * I.T + tile);
+                coef[t] = c;
+                if (ADJ) coef2[t] = c2;
+                toff[t] = slot;
+            }
+            __syncthreads();
+            // Stage s of this round into ring slot `slot` % NS, by warp s mod (warps), one lane per
+            // row: the copies of a stage go out together and the issue work rotates over the warps
+            // instead of delaying one warp at every stage barrier.  All lanes of the warp call it.
+            auto issue = [&](int s, uint32_t slot) {
+                const int b = (int)(slot % (uint32_t)NS);
+                const int t0 = s * RS;
+                const int t1 = min(ne, t0 + RS);
+                if (lane == 0) mbar_expect_tx(&bars[b], (uint32_t)(tile_bytes * (t1 - t0)));
+                __syncwarp();
+                const char *col = I.hist + (size_t)tile * I.P * sizeof(TH);
+                for (int t = t0 + lane; t < t1; t += 32)
+                    bulk_g2s(stages + ((size_t)b * RS + (t - t0)) * row_bytes, col + (size_t)toff[t] * I.pitch,
+                             (uint32_t)tile_bytes, &bars[b]);
+            };
+            // every lane that issues copies orders the rows it acquired before the async proxy
+            if (lane < RS) fence_proxy_async_global();
+            {
+                const int pre = min(NS, nst);
+                for (int s = 0; s < pre; ++s)
+                    if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
+                n_issued += (uint32_t)pre;
+            }
+            for (int s = 0; s < nst; ++s) {
+                const int b = (int)(n_used % (uint32_t)NS);
+                const uint32_t par = (n_used / (uint32_t)NS) & 1u;
+                int tmo = 0;
+                if (!mbar_try_wait(&bars[b], par)) {
+                    const long long t0 = globaltimer();
+                    while (!mbar_try_wait(&bars[b], par)) {
+                        if (globaltimer() - t0 > L.timeout_ns) {
+                            if (atomicCAS(L.err, ERR_NONE, ERR_PIPE) == ERR_NONE) note_failure(L, 7, U.k, U.tile, 0, 0, 0, 0);
+                            tmo = 1;  // the copy is still owed to this slot; see below
+                            break;
+                        }
+                    }
+                }
+                const int rows = tmo ? 0 : min(RS, ne - s * RS);
+                const unsigned char *base = stages + (size_t)b * RS * row_bytes + (size_t)tid * 16;
+                for (int r = 0; r < rows; ++r) {
+                    const uint4 w = *reinterpret_cast<const uint4 *>(base + (size_t)r * row_bytes);
+                    TA x[V];
+                    HVec<TH>::unpack(w, x);
+                    const TA c = coef[s * RS + r];
+                    if (KAHAN) {
 #pragma unroll
-                    for (int v = 0; v < V; ++v) acc2[v] = fma(c2, x[v], acc2[v]);
+                        for (int v = 0; v < V; ++v) {
+                            const TA y = c * x[v] - cmp[v];
+                            const TA t = acc[v] + y;
+                            cmp[v] = (t - acc[v]) - y;
+                            acc[v] = t;
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = fma(c, x[v], acc[v]);
+                    }
+                    if (ADJ) {
+                        const TA c2 = coef2[s * RS + r];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc2[v] = fma(c2, x[v], acc2[v]);
+                    }
+                }
+                // slot b fully read by every thread.  A stage that any thread gave up on stops the
+                // unit: nothing more is issued, and the stage stays owed (n_used not advanced) for
+                // the drain below.
+                if (__syncthreads_or(tmo)) {
+                    aborted = 1;
+                    break;
+                }
+                ++n_used;
+                if (s + NS < nst) {
+                    if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
+                    ++n_issued;
                 }
             }
-            // slot b fully read by every thread.  A stage that any thread gave up on stops the
-            // unit: nothing more is issued, and the stage stays owed (n_used not advanced) for
-            // the drain below.
-            if (__syncthreads_or(tmo)) {
-                aborted = 1;
-                break;
-            }
-            ++n_used;
-            if (s + NS < nst) {
-                if (warp == (s + NS) % nwarp) issue(s + NS, n_issued);
-                ++n_issued;
-            }
+            if (aborted) break;
         }
         if (tid == 0) s_pipe = aborted || (ld_volatile(L.err) == ERR_PIPE);
         __syncthreads();
@@ -912,6 +1009,31 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             amax = fmaxf(amax, fabsf((float)d[v]));
         }
 
+        // closed loop: this tile's share of the row maxima D_k and M_k (published with the step)
+        if (I.cl_D) {
+            double dm = 0.0, mm = 0.0;
+            if (j0 < I.N) {
+                TS xp[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) xp[v] = (k >= 1 && j0 + v < I.N) ? __ldcg(head_row(1) + v) : TS(0);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (j0 + v < I.N) {
+                        mm = fmax(mm, fabs((double)d[v]));
+                        if (k >= 1) dm = fmax(dm, fabs((double)d[v] - (double)xp[v]));
+                    }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+                mm = fmax(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+            }
+            if ((tid & 31) == 0) {
+                clmax[2 * (tid >> 5)] = dm;
+                clmax[2 * (tid >> 5) + 1] = mm;
+            }
+        }
+
         // history row k (FP16: per (row, tile) power-of-two scale)
         float hsc = 1.f;
         const int slot = k % I.cap;
@@ -1042,6 +1164,17 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     for (int w = 0; w < (nthr + 31) / 32; ++w) s += s_dred[w][i];
                     dd[i] += s;
                 }
+            }
+            if (I.cl_D) {
+                double dm = 0.0, mm = 0.0;
+                for (int w = 0; w < (nthr + 31) / 32; ++w) {
+                    dm = fmax(dm, clmax[2 * w]);
+                    mm = fmax(mm, clmax[2 * w + 1]);
+                }
+                atomicMax(reinterpret_cast<unsigned long long *>(I.cl_D + k), (unsigned long long)__double_as_longlong(dm));
+                atomicMax(reinterpret_cast<unsigned long long *>(I.cl_M + k), (unsigned long long)__double_as_longlong(mm));
+                if (tile == 0) atomicAdd(I.cl_terms, (unsigned long long)(1 + hh));  // lag 0 and the head lags
+                atom_add_acq_rel(&I.cl_rows[k], 1u);  // releases the maxima: row k done on this tile
             }
             st_release(&I.done[tile], (unsigned)(rel + 1));
         }

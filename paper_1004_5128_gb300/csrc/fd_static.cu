@@ -87,6 +87,7 @@ int check_problem(const fd_problem *p, int nsteps)
         p->ctas_per_sm < 0 || p->ctas_per_sm > 8)
         return FD_ERR_INVALID_ARG;
     if (p->flags & FD_FLAG_KEEP_TAPE) return FD_ERR_UNSUPPORTED;  // forward only
+    if (p->flags & FD_FLAG_CLOSED_LOOP) return FD_ERR_UNSUPPORTED;  // open-loop schedules only
     if (p->time_block) return FD_ERR_UNSUPPORTED;                 // per-step kernel only
     if (!fdk::kernel_for(p->state_dtype, p->hist_dtype, p->accum_dtype, p->flags & FD_FLAG_KAHAN, false))
         return FD_ERR_UNSUPPORTED;

@@ -21,8 +21,10 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
                  inject_stall: bool = False, tile_threads: int = 0, chunk_terms: int = 0,
                  stage_rows: int = 0, stages: int = 0, ctas_per_sm: int = 0,
                  head_lags: int = 0, plain_state: bool = False, time_block: int = 0,
-                 step_updates: bool = False, fma_far: bool = False) -> L.FdProblem:
-    """fd_problem for a synth-style problem dict."""
+                 step_updates: bool = False, fma_far: bool = False,
+                 closed_tau: float | None = None) -> L.FdProblem:
+    """fd_problem for a synth-style problem dict.  closed_tau: closed-loop adaptive memory with
+    that threshold (FD_FLAG_CLOSED_LOOP)."""
     s = L.FdProblem()
     s.ndim, s.nx, s.ny = p["ndim"], p["nx"], p["ny"]
     s.gamma, s.alpha, s.dt, s.dx = p["gamma"], p["alpha"], p["dt"], p["dx"]
@@ -39,7 +41,9 @@ def make_problem(p: dict, max_steps: int | None = None, state: str = "f32", hist
                (L.FD_FLAG_INJECT_STALL if inject_stall else 0) |
                (L.FD_FLAG_PLAIN_STATE if plain_state else 0) |
                (L.FD_FLAG_STEP_UPDATES if step_updates else 0) |
-               (L.FD_FLAG_FMA_FAR if fma_far else 0))
+               (L.FD_FLAG_FMA_FAR if fma_far else 0) |
+               (L.FD_FLAG_CLOSED_LOOP if closed_tau is not None else 0))
+    s.mem_tau = float(closed_tau) if closed_tau is not None else 0.0
     s.max_steps = int(max_steps if max_steps is not None else p["K"])
     s.ckpt_every, s.timeout_ms = ckpt_every, timeout_ms
     s.tile_threads, s.chunk_terms, s.stage_rows = tile_threads, chunk_terms, stage_rows
@@ -62,8 +66,8 @@ GEOMETRY_KEYS = ("tile_threads", "chunk_terms", "stage_rows", "stages", "ctas_pe
 def tuned_geometry(p: dict, kw: dict) -> dict:
     """The autotuner's geometry for a handle with options kw, unless kw sets one itself.  A
     taped handle (adjoint) takes blocks of at most 8 steps, the blocked adjoint's limit."""
-    if any(k in kw for k in GEOMETRY_KEYS):
-        return {}
+    if any(k in kw for k in GEOMETRY_KEYS) or kw.get("closed_tau") is not None:
+        return {}  # explicit geometry, or closed-loop memory (per-step kernel, built-in geometry)
     from .autotune import lookup
     geo = lookup(p, kw.get("state", "f32"), kw.get("hist"), kw.get("kahan", False))
     if kw.get("keep_tape") and geo.get("time_block", 0) > 8:
@@ -139,6 +143,10 @@ class FRD:
 
     def status(self) -> int:
         return L.fd_get_status(self.h)
+
+    def memory_terms(self) -> int:
+        """Memory terms (lag, weight) used by the steps run so far, lag 0 included."""
+        return L.fd_memory_terms(self.h)
 
     def error_info(self) -> dict:
         """Where a device wait gave up after a timeout (site and raw words)."""

@@ -1,0 +1,155 @@
+"""GPU parity of closed-loop adaptive memory (FD_FLAG_CLOSED_LOOP, the reading of the Discussion
+in which a median stands for its increment only while the history's relative variation across it
+stays below tau) against the FP64 oracle's or_run_closed.
+
+The decisions are integers decided by floating point: each case first asserts, on the oracle,
+that its closest decision lies further from tau than the GPU's rounding can move it (relative
+margin above 1e-9 for FP64 state, 1e-3 for FP32), so the decisions are unique; then the memory
+terms used (the decisions' integer trace) must equal the oracle's exactly and the field must
+match within the dtype's tolerance (infinity norm relative to max |u_ref|)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_5128_gb300 import FRD, FdError, synth
+from paper_1004_5128_gb300 import _lib as L
+from tests.helpers import rel_inf
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+MARGIN = {"f64": 1e-9, "f32": 1e-3}
+
+
+def small(a, rule, K=160, gamma=0.75, nx=13, ny=11, seed=19):
+    return synth.problem(2, nx, ny, gamma, 0.7, synth.dt_for_courant(0.12, 0.7, 1.0, gamma), 1.0,
+                         synth.BC_NOFLUX, react=(0.01, -0.2, 0.3, -0.4), mem_mode=synth.MEM_ADAPTIVE,
+                         mem_a=a, adaptive_rule=rule, K=K,
+                         u0=synth.SplitMix64(seed).uniform(nx * ny, 0, 1))
+
+
+def ragged(a=3, rule=synth.ADAPT_PARTITION, K=300):
+    """70 x 53 (several tiles, ragged last one), Dirichlet, linear decay."""
+    return synth.problem(2, 70, 53, 0.8, 0.5, synth.dt_for_courant(0.1, 0.5, 1.0, 0.8), 1.0,
+                         synth.BC_DIRICHLET0, react=(0, -0.1, 0, 0), mem_mode=synth.MEM_ADAPTIVE,
+                         mem_a=a, adaptive_rule=rule, K=K, u0=synth.SplitMix64(5).uniform(70 * 53, 0, 1))
+
+
+def gpu_closed(p, tau, state="f64", K=None, **kw):
+    K = p["K"] if K is None else K
+    s = FRD(p, state=state, max_steps=max(K, 1), closed_tau=tau, **kw)
+    s.set_state(p["u0"])
+    out = s.run(K).cpu().double().numpy()
+    assert s.status() == 0
+    return out, s.memory_terms(), s
+
+
+def check(p, tau, state, **kw):
+    ref, n_ref, mg = oracle.run_closed(p, tau, margin=True)
+    if not math.isinf(tau) and tau > 0:
+        assert mg > MARGIN[state], f"decision within {mg:.1e} of tau: not unique at {state}"
+    got, n, _ = gpu_closed(p, tau, state, **kw)
+    assert n == n_ref
+    assert rel_inf(got, ref) < TOL[state]
+    return got, n
+
+
+CASES = [(2, synth.ADAPT_PAPER, 1.0), (2, synth.ADAPT_PAPER, 0.1), (3, synth.ADAPT_PAPER, 0.3),
+         (3, synth.ADAPT_PARTITION, 0.1), (2, synth.ADAPT_PARTITION, 0.3), (3, synth.ADAPT_PAPER, 0.01)]
+
+
+@pytest.mark.parametrize("a,rule,tau", CASES)
+@pytest.mark.parametrize("state", ["f64", "f32"])
+def test_small_grid(a, rule, tau, state):
+    """13 x 11, no-flux, cubic reaction, 160 steps; chunks of 8 terms so that expanded increments
+    spill over several rounds of the unit's term tables."""
+    check(small(a, rule), tau, state, chunk_terms=8)
+
+
+@pytest.mark.parametrize("tau", [0.3, 0.1, 0.05, 0.02])
+@pytest.mark.parametrize("state", ["f64", "f32"])
+def test_ragged_tiles(tau, state):
+    """70 x 53 on tiles of 64 threads: several tiles wait for each other's row maxima."""
+    check(ragged(), tau, state, tile_threads=64, chunk_terms=16)
+
+
+def test_limits():
+    """tau = +inf is the open-loop rule: the same units and terms as the open-loop handle, so the
+    same bits; tau = 0 with the partition rule sums every lag (full memory's terms)."""
+    p = ragged(3, synth.ADAPT_PARTITION, K=200)
+    kw = dict(state="f64", max_steps=200, tuned=False, chunk_terms=16)
+    s = FRD(p, **kw)
+    s.set_state(p["u0"])
+    open_loop = s.run(200).cpu().numpy()
+    got, n, _ = gpu_closed(p, math.inf, chunk_terms=16)
+    assert np.array_equal(got, open_loop)
+    assert n == s.memory_terms() == oracle.run_closed(p, math.inf)[1]
+    full = synth.with_mode(p, synth.MEM_FULL)
+    got0, n0, _ = gpu_closed(p, 0.0, chunk_terms=16)
+    assert n0 == 200 * 201 // 2
+    assert rel_inf(got0, oracle.run(full)) < TOL["f64"]
+
+
+def test_3d_and_1d():
+    p3 = synth.problem(3, 20, 17, 0.7, 0.4, synth.dt_for_courant(0.08, 0.4, 1.0, 0.7), 1.0,
+                       synth.BC_NOFLUX, react=(0, -0.05, 0, 0), mem_mode=synth.MEM_ADAPTIVE, mem_a=2,
+                       adaptive_rule=synth.ADAPT_PAPER, K=150, nz=13,
+                       u0=synth.SplitMix64(3).uniform(20 * 17 * 13, 0, 1))
+    check(p3, 0.2, "f64", chunk_terms=12)
+    p1 = synth.problem(1, 3001, 1, 0.55, 1.0, synth.dt_for_courant(0.2, 1.0, 1.0, 0.55), 1.0,
+                       synth.BC_DIRICHLET0, react=(0, -0.05, 0, 0), mem_mode=synth.MEM_ADAPTIVE,
+                       mem_a=5, K=400, u0=synth.SplitMix64(8).uniform(3001, -1, 1))
+    check(p1, 0.1, "f64", tile_threads=64, chunk_terms=24)
+
+
+def test_superdiffusion_feedback():
+    """The oscillating superdiffusion of the oracle's pin (gamma = 1.3, one high mode): the GPU's
+    closed loop matches the oracle's closed loop, which stays within 1e-2 of full memory."""
+    p = synth.problem(1, 31, 1, 1.3, 1.0,
+                      synth.dt_for_courant(0.6 * synth.stability_bound(1.3, 1), 1.0, 1.0, 1.3), 1.0,
+                      synth.BC_DIRICHLET0, mem_mode=synth.MEM_ADAPTIVE, mem_a=3,
+                      adaptive_rule=synth.ADAPT_PARTITION, K=400)
+    p["u0"] = synth.eigenmode(p, 25)
+    got, n = check(p, 0.03, "f64")
+    full = oracle.run(synth.with_mode(p, synth.MEM_FULL))
+    assert rel_inf(got, full) < 1e-2
+
+
+def test_split_launches_and_checkpoint():
+    """Steps in several launches give the bits of one launch (the row maxima and their counts
+    persist between launches); a checkpoint taken midway resumes to the same bits and count."""
+    p = ragged(2, synth.ADAPT_PAPER, K=240)
+    one, n_one, _ = gpu_closed(p, 0.1, "f32", chunk_terms=16)
+    s = FRD(p, state="f32", max_steps=240, closed_tau=0.1, chunk_terms=16)
+    s.set_state(p["u0"])
+    s.step(70)
+    s.step(50)
+    buf = s.save()
+    s.step(120)
+    assert np.array_equal(s.state().cpu().double().numpy(), one)
+    assert s.memory_terms() == n_one
+    r = FRD(p, state="f32", max_steps=240, closed_tau=0.1, chunk_terms=16)
+    r.set_state(p["u0"])
+    r.step(200)  # runs past the checkpoint first: the load must clear the later rows' maxima
+    r.load(buf)
+    assert r.k == 120
+    r.step(120)
+    assert np.array_equal(r.state().cpu().double().numpy(), one)
+    assert r.memory_terms() == n_one
+
+
+def test_medium_size():
+    """64 x 64, 2000 steps, a = 10 (the configuration-2 schedule), tau = 0.1, FP32, default
+    geometry."""
+    check(synth.config2(synth.MEM_ADAPTIVE, K=2000, n=64), 0.1, "f32")
+
+
+def test_rejections():
+    p = small(3, synth.ADAPT_PAPER)
+    for kw, code in ((dict(time_block=8), L.FD_ERR_UNSUPPORTED), (dict(hist="bf16"), L.FD_ERR_UNSUPPORTED),
+                     (dict(keep_tape=True), L.FD_ERR_UNSUPPORTED)):
+        with pytest.raises(FdError) as e:
+            FRD(p, closed_tau=0.1, **kw)
+        assert e.value.code == code

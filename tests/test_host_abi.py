@@ -188,3 +188,33 @@ def test_bench_traffic_entries_follow_the_kernel_code(tmp_path):
     other = dict(e["geometry"], tile_threads=e["geometry"]["tile_threads"] // 2)
     assert bench.measured_traffic(e["key"], other) is None
     assert bench.measured_traffic("no such run", dict(e["geometry"])) is None
+
+
+def test_closed_loop_validation():
+    """Closed-loop adaptive memory: adaptive schedules on the per-step kernel with history in state
+    precision, forward only, single handles; a threshold tau >= 0 (+inf allowed)."""
+    import math
+    ad = synth.with_mode(synth.config2(K=100), synth.MEM_ADAPTIVE, a=10)
+    open_bytes = L.fd_workspace_bytes(make_problem(ad))
+    for tau in (0.0, 0.1, math.inf):
+        for state in ("f32", "f64"):
+            assert L.fd_workspace_bytes(make_problem(ad, state=state, closed_tau=tau)) > \
+                L.fd_workspace_bytes(make_problem(ad, state=state))
+    assert L.fd_workspace_bytes(make_problem(ad, closed_tau=0.1)) > open_bytes
+    for kw, code in ((dict(closed_tau=-1.0), L.FD_ERR_INVALID_ARG),
+                     (dict(closed_tau=math.nan), L.FD_ERR_INVALID_ARG),
+                     (dict(closed_tau=0.1, time_block=8), L.FD_ERR_UNSUPPORTED),
+                     (dict(closed_tau=0.1, hist="bf16"), L.FD_ERR_UNSUPPORTED),
+                     (dict(closed_tau=0.1, keep_tape=True), L.FD_ERR_UNSUPPORTED)):
+        with pytest.raises(L.FdError) as e:
+            L.fd_workspace_bytes(make_problem(ad, **kw))
+        assert e.value.code == code
+    with pytest.raises(L.FdError) as e:
+        L.fd_workspace_bytes(make_problem(synth.config2(K=100), closed_tau=0.1))  # full memory
+    assert e.value.code == L.FD_ERR_UNSUPPORTED
+    with pytest.raises(L.FdError) as e:
+        L.fd_batch_workspace_bytes([make_problem(ad, closed_tau=0.1)] * 2)
+    assert e.value.code == L.FD_ERR_UNSUPPORTED
+    # the tuned table's geometry (blocks of 64 for this schedule) is not applied to a closed loop
+    from paper_1004_5128_gb300.frd import tuned_geometry
+    assert tuned_geometry(synth.config2(synth.MEM_ADAPTIVE), {"closed_tau": 0.1}) == {}
