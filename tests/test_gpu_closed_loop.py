@@ -46,13 +46,17 @@ def gpu_closed(p, tau, state="f64", K=None, **kw):
     return out, s.memory_terms(), s
 
 
-def check(p, tau, state, **kw):
+def check(p, tau, state, scale=None, **kw):
+    """scale: the magnitude the error is measured against (default max |u_ref|)."""
     ref, n_ref, mg = oracle.run_closed(p, tau, margin=True)
     if not math.isinf(tau) and tau > 0:
         assert mg > MARGIN[state], f"decision within {mg:.1e} of tau: not unique at {state}"
     got, n, _ = gpu_closed(p, tau, state, **kw)
     assert n == n_ref
-    assert rel_inf(got, ref) < TOL[state]
+    if scale is None:
+        assert rel_inf(got, ref) < TOL[state]
+    else:
+        assert np.max(np.abs(got - ref)) / scale < TOL[state]
     return got, n
 
 
@@ -106,13 +110,15 @@ def test_3d_and_1d():
 
 def test_superdiffusion_feedback():
     """The oscillating superdiffusion of the oracle's pin (gamma = 1.3, one high mode): the GPU's
-    closed loop matches the oracle's closed loop, which stays within 1e-2 of full memory."""
+    closed loop matches the oracle's closed loop, which stays within 1e-2 of full memory.  The mode
+    decays by about 1e4 over the run while its early history is O(1), so FP64 rounding is measured
+    against max |u^0|: an absolute floor near 1e-15 is 3e-11 of the final field."""
     p = synth.problem(1, 31, 1, 1.3, 1.0,
                       synth.dt_for_courant(0.6 * synth.stability_bound(1.3, 1), 1.0, 1.0, 1.3), 1.0,
                       synth.BC_DIRICHLET0, mem_mode=synth.MEM_ADAPTIVE, mem_a=3,
                       adaptive_rule=synth.ADAPT_PARTITION, K=400)
     p["u0"] = synth.eigenmode(p, 25)
-    got, n = check(p, 0.03, "f64")
+    got, n = check(p, 0.03, "f64", scale=np.max(np.abs(p["u0"])))
     full = oracle.run(synth.with_mode(p, synth.MEM_FULL))
     assert rel_inf(got, full) < 1e-2
 
