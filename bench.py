@@ -10,9 +10,11 @@ forward + adjoint rate against a plain FP32 forward.  Other workloads:
   c2  2-D 256x256 no-flux, 5000 steps, full / short L=500 / adaptive a=10 memory, FP32
   c4  64 uneven instances in one persistent launch (full and adaptive memory)
   c5  128x128, 4000 steps: forward + checkpointed adjoint, against a plain FP32 forward
+  c2cl config 2's adaptive schedule (a=10) in closed loop, tau 0.1 and 0.01, and open loop,
+       on the per-step kernel, FP32
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
-                  [--workload c2|c1|c3|c4|c5] [--K k] [--modes a,b] [--geom k=v,...]
+                  [--workload c2|c1|c3|c4|c5|c2cl] [--K k] [--modes a,b] [--geom k=v,...]
 
 `--impl reference` times the FP64 CPU oracle on bounded samples of the same workload (the
 oracle is the only reference this method has).
@@ -50,6 +52,9 @@ CONFIG_NAMES = {
     "c5": "2-D 128x128 Dirichlet, gamma=0.7, alpha=0.8, f=-0.1u, 4000 steps, FP32: forward with "
           "checkpoints every 200 + reverse-time adjoint (grad gamma, alpha, react, u0) vs plain "
           "FP32 forward",
+    "c2cl": "2-D 256x256 no-flux, gamma=0.8, alpha=0.5, f=-0.1u, S=0.1, 8 Gaussians, 5000 steps, "
+            "adaptive a=10: closed loop (tau 0.1, 0.01; medians kept while the history's relative "
+            "variation across their increment stays below tau) and open loop, per-step kernel, FP32",
 }
 
 
@@ -193,6 +198,14 @@ class SingleRun:
         self.alg = alg_bytes(self.geo, p, kw)
         self.u0 = torch.from_numpy(p["u0"]).to(dev, self.s.dtype)
         self.launches = 1
+        if kw.get("closed_tau") is not None:
+            # closed loop: the terms follow the decisions, counted on the device by one run
+            self.launch()
+            n, N = self.s.memory_terms(), p["nx"] * p["ny"] * p.get("nz", 1)
+            self.terms = n * N
+            rows = n - p["K"]  # lags >= 1
+            self.geo = dict(self.geo, terms_total=self.terms, hist_rows_total=rows, stream_rows_total=rows)
+            self.alg = alg_bytes(self.geo, p, kw)
 
     def launch(self):
         self.s.set_state(self.u0)
@@ -317,6 +330,30 @@ class AdjointRun:
 def _rel_inf(a, ref) -> float:
     a, ref = np.asarray(a, dtype=np.float64), np.asarray(ref, dtype=np.float64)
     return float(np.max(np.abs(a - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def closed_loop_checks(runs, dev) -> dict:
+    """Measured outside the timed region: each closed-loop run's kernel options on config 2's
+    schedule at 64x64, 2000 steps, against the FP64 oracle's closed loop (field error, terms used
+    and the oracle's closest decision to tau, relative), and the open-loop run against or_run."""
+    import oracle
+    from paper_1004_5128_gb300 import FRD, synth
+    q = synth.config2(synth.MEM_ADAPTIVE, K=2000, n=64)
+    out = {"tolerance": 1e-5, "errors": {}}
+    for r in runs:
+        s = FRD(q, device=dev, max_steps=q["K"], **r.kw)
+        s.set_state(q["u0"])
+        got = s.run(q["K"]).cpu().double().numpy()
+        tau = r.kw.get("closed_tau")
+        if tau is None:
+            e = {"vs_oracle_64x64_K2000": _rel_inf(got, oracle.run(q, threads=0))}
+        else:
+            ref, n, mg = oracle.run_closed(q, tau, threads=0, margin=True)
+            e = {"vs_oracle_64x64_K2000": _rel_inf(got, ref), "terms": s.memory_terms(),
+                 "oracle_terms": n, "oracle_decision_margin": mg}
+        s.close()
+        out["errors"][r.name] = e
+    return out
 
 
 def side_measurements(runs, dev) -> dict:
@@ -475,6 +512,8 @@ def run_ours(args):
         modes[r.name]["roofline_launch"] = "plain FP32 forward"
     if args.workload == "c3" and not args.no_extra and rank == 0:
         extra = side_measurements(runs, dev)
+    if args.workload == "c2cl" and not args.no_extra and rank == 0:
+        extra = closed_loop_checks(runs, dev)
     dom = max(modes, key=lambda k: modes[k]["ms"])
     peak, which = peaks()
     ach = modes[dom]["gbs"]
@@ -559,6 +598,12 @@ def _oracle_sample(args, kp, threads):
             continue
         for q in (p[:: max(1, len(p) // 8)] if isinstance(p, list) else [p]):
             K = min(kp, q["K"])
+            if kw.get("closed_tau") is not None:
+                w = time.perf_counter()
+                n = oracle.run_closed(q, kw["closed_tau"], K=K, threads=threads)[1]
+                t += time.perf_counter() - w
+                terms += n * q["nx"] * q["ny"] * q.get("nz", 1)
+                continue
             n = _sample_terms(q, K)
             w = time.perf_counter()
             oracle.run(q, K=K, threads=threads)
@@ -618,7 +663,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "c2", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c1", "c2", "c4", "c5", "c2cl"])
     ap.add_argument("--no-extra", action="store_true", help="skip the error and adjoint side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")

@@ -225,7 +225,8 @@ def workload_runs(name: str, K: int = 0, modes: str = ""):
     """Named workloads as [(run name, problem or list of problems, solver options)].
 
     c1: config 1 (FP64); c2: config 2 in its three memory modes; c3: config 3 with BF16, FP16
-    and FP32 history; c4: the 64-instance batch, full and adaptive; c5: the adjoint problem.
+    and FP32 history; c4: the 64-instance batch, full and adaptive; c5: the adjoint problem;
+    c2cl: config 2's adaptive schedule in closed loop (tau 0.1 and 0.01) and open loop.
     K overrides every step count; modes keeps only the named runs.
     """
     if name == "c2":
@@ -243,6 +244,12 @@ def workload_runs(name: str, K: int = 0, modes: str = ""):
         runs = [("full", config4(MEM_FULL), {}), ("adaptive", config4(MEM_ADAPTIVE), {})]
     elif name == "c5":
         runs = [("adjoint", config5(), {})]
+    elif name == "c2cl":
+        # config 2's adaptive schedule (a = 10) with feedback from the history, against the open
+        # loop on the same per-step kernel
+        runs = [("open", config2(MEM_ADAPTIVE), {"time_block": 0}),
+                ("tau0.1", config2(MEM_ADAPTIVE), {"closed_tau": 0.1}),
+                ("tau0.01", config2(MEM_ADAPTIVE), {"closed_tau": 0.01})]
     else:
         raise ValueError(f"unknown workload {name}")
     if modes:
