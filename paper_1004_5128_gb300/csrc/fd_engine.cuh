@@ -223,6 +223,12 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Release reduction without a result: orders this thread's earlier writes (atomics included)
+// before the increment, and does not wait for the round trip.
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
 {
     unsigned old;
@@ -440,10 +446,17 @@ __device__ __forceinline__ void term_of(const Inst &I, const int4 sc, int tau, i
 // reference keeps it only for zero variation and tau > 0).
 __device__ __forceinline__ bool cl_smooth(const Inst &I, int k, int m, int d)
 {
-    const int h = (d - 1) / 2;
-    double var = 0.0;
-    for (int r = k - m - h + 1; r <= k - m + h; ++r) var += __ldcg(I.cl_D + r);
+    const int h = (d - 1) / 2, r1 = k - m + h;
     const double ref = __ldcg(I.cl_M + (k - m));
+    double var = 0.0;
+    for (int r = k - m - h + 1; r <= r1; r += 8) {  // eight loads in flight, added in row order
+        double x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = (r + i <= r1) ? __ldcg(I.cl_D + r + i) : 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (r + i <= r1) var += x[i];
+    }
     if (isinf(I.cl_tau)) return true;
     return (ref > 0.0) ? (var / ref < I.cl_tau) : (var == 0.0 && I.cl_tau > 0.0);
 }
@@ -614,7 +627,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         // not smooth), prefix-summed into eoff[0..nterm] by warp 0; the unit then streams ntot
         // entries in rounds of at most rmax (open loop: one round of the nterm terms).
         int ntot = nterm;
-        if (I.cl_D && nterm > 0) {
+        const bool expand = I.cl_D && nterm > 0 && tau0 < U.sc.x + U.sc.y && tau1 > U.sc.x;  // holds medians
+        if (expand) {
             for (int t = tid; t < nterm; t += nthr) {
                 const int tau = tau0 + t;
                 int cnt = 1;
@@ -644,8 +658,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             }
             __syncthreads();
             ntot = eoff[nterm];
-            if (tid == 0 && tile == 0) atomicAdd(I.cl_terms, (unsigned long long)ntot);
         }
+        if (I.cl_D && tid == 0 && tile == 0 && nterm > 0) atomicAdd(I.cl_terms, (unsigned long long)ntot);
         const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
         int aborted = 0;
         for (int e0 = 0; e0 == 0 || e0 < ntot; e0 += L.rmax) {
@@ -656,7 +670,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             for (int t = tid; t < ne; t += nthr) {
                 int lag;
                 TA c, c2;
-                if (!I.cl_D) {
+                if (!expand) {
                     term_of<TA, ADJ>(I, U.sc, tau0 + t, lag, c, c2);
                 } else {
                     const int e = e0 + t;
@@ -1165,7 +1179,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     dd[i] += s;
                 }
             }
-            if (I.cl_D) {
+            st_release(&I.done[tile], (unsigned)(rel + 1));
+            if (I.cl_D) {  // off the step chain: nothing waits on these before the next steps' units
                 double dm = 0.0, mm = 0.0;
                 for (int w = 0; w < (nthr + 31) / 32; ++w) {
                     dm = fmax(dm, clmax[2 * w]);
@@ -1174,9 +1189,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 atomicMax(reinterpret_cast<unsigned long long *>(I.cl_D + k), (unsigned long long)__double_as_longlong(dm));
                 atomicMax(reinterpret_cast<unsigned long long *>(I.cl_M + k), (unsigned long long)__double_as_longlong(mm));
                 if (tile == 0) atomicAdd(I.cl_terms, (unsigned long long)(1 + hh));  // lag 0 and the head lags
-                atom_add_acq_rel(&I.cl_rows[k], 1u);  // releases the maxima: row k done on this tile
+                red_add_release(&I.cl_rows[k], 1u);  // releases the maxima: row k done on this tile
             }
-            st_release(&I.done[tile], (unsigned)(rel + 1));
         }
     }
 }
