@@ -970,6 +970,9 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
         I.cl_terms = L.clterms;
         I.g_d = L.gd;
         I.cl_tau = p.mem_tau;
+        // every increment lies above the base interval [0, a] (both rules): none reaches a lag
+        // below a + 1
+        I.cl_lo = p.mem_a + 1;
     }
     if (!adj && L.ckpt) {
         I.tape = L.ckpt;

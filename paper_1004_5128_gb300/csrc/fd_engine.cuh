@@ -113,6 +113,7 @@ struct Inst {
     unsigned long long *cl_terms;  // memory terms used, lag 0 included (counted by tile 0)
     const int *g_d;                // increment length d of each median
     double cl_tau;
+    int cl_lo;                     // smallest lag of any median's increment (the first one's)
 };
 
 // Adjoint of adaptive memory.  The adjoint sums every (step k, lag m) pair with the weight g(m)
@@ -596,11 +597,11 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     if (w <= 0) ok = 0;
                 }
                 // closed loop: the maxima of every row the chunk's decisions read, on every tile.
-                // The chunk's first median has the oldest-ending increment's newest row, k - lo;
-                // tiles complete their rows in order, so that row's count covers the older ones.
+                // No increment reaches a lag below the first one's, cl_lo, so row k - cl_lo is
+                // the newest any decision of step k reads; tiles complete their rows in order, so
+                // that row's count covers the older ones.
                 if (ok && I.cl_D && U.tau0 < sc.x + sc.y && U.tau1 > sc.x) {
-                    const int g0 = max(U.tau0, sc.x) - sc.x;
-                    const int r = gi.y - (I.g_lag[g0] - (I.g_d[g0] - 1) / 2);
+                    const int r = gi.y - I.cl_lo;
                     const int w = wait_until(&I.cl_rows[r], (unsigned)I.T, L, 512);
                     if (w < 0) note_failure(L, 14, gi.y, U.tile, r, ld_acquire(&I.cl_rows[r]), I.T, 0);
                     if (w <= 0) ok = 0;
@@ -1029,7 +1030,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             if (j0 < I.N) {
                 TS xp[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) xp[v] = (k >= 1 && j0 + v < I.N) ? __ldcg(head_row(1) + v) : TS(0);
+                for (int v = 0; v < V; ++v)
+                    xp[v] = lag1 ? x1[v] : (k >= 1 && j0 + v < I.N) ? __ldcg(head_row(1) + v) : TS(0);
 #pragma unroll
                 for (int v = 0; v < V; ++v)
                     if (j0 + v < I.N) {
