@@ -534,6 +534,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
     __shared__ Unit U;
     __shared__ int s_cur_inst;
     __shared__ int s_ok, s_ok2;
+    __shared__ int s_nexp;  // closed loop: expanded medians of the unit
     __shared__ int s_pipe;
     __shared__ float s_red[32];
     __shared__ double s_dred[32][6];
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 // No increment reaches a lag below the first one's, cl_lo, so row k - cl_lo is
                 // the newest any decision of step k reads; tiles complete their rows in order, so
                 // that row's count covers the older ones.
-                if (ok && I.cl_D && U.tau0 < sc.x + sc.y && U.tau1 > sc.x) {
+                if (!ADJ && ok && I.cl_D && U.tau0 < sc.x + sc.y && U.tau1 > sc.x) {
                     const int r = gi.y - I.cl_lo;
                     const int w = wait_until(&I.cl_rows[r], (unsigned)I.T, L, 512);
                     if (w < 0) note_failure(L, 14, gi.y, U.tile, r, ld_acquire(&I.cl_rows[r]), I.T, 0);
@@ -624,54 +625,22 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         for (int v = 0; v < V; ++v) acc[v] = cmp[v] = acc2[v] = TA(0);
 
         // ------------------------------------------------- stream the chunk
-        // Closed loop: the entries each term expands to (1, or d for a median whose increment is
-        // not smooth), prefix-summed into eoff[0..nterm] by warp 0; the unit then streams ntot
-        // entries in rounds of at most rmax (open loop: one round of the nterm terms).
-        int ntot = nterm;
-        const bool expand = I.cl_D && nterm > 0 && tau0 < U.sc.x + U.sc.y && tau1 > U.sc.x;  // holds medians
-        if (expand) {
-            for (int t = tid; t < nterm; t += nthr) {
-                const int tau = tau0 + t;
-                int cnt = 1;
-                if (tau >= U.sc.x && tau < U.sc.x + U.sc.y) {
-                    const int g = tau - U.sc.x, d = I.g_d[g];
-                    if (d > 1 && !cl_smooth(I, k, I.g_lag[g], d)) cnt = d;
-                }
-                eoff[t + 1] = cnt;
-            }
-            __syncthreads();
-            if (tid < 32) {
-                const int seg = (nterm + 31) / 32, a = min(nterm, tid * seg), b = min(nterm, a + seg);
-                int sum = 0;
-                for (int t = a; t < b; ++t) sum += eoff[t + 1];
-                int pre = sum;  // inclusive warp scan of the segment sums
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, pre, o);
-                    if (tid >= o) pre += y;
-                }
-                int run = pre - sum;
-                for (int t = a; t < b; ++t) {
-                    run += eoff[t + 1];
-                    eoff[t + 1] = run;
-                }
-                if (tid == 0) eoff[0] = 0;
-            }
-            __syncthreads();
-            ntot = eoff[nterm];
-        }
-        if (I.cl_D && tid == 0 && tile == 0 && nterm > 0) atomicAdd(I.cl_terms, (unsigned long long)ntot);
+        // Pass 0 streams the chunk's terms as scheduled.  Closed loop: while its first stages are
+        // in flight, each median decides whether it stands for its increment (eoff[t + 1] = 0) or
+        // not (d); where any does not, warp 0 prefix-sums eoff[0..nterm] and correction passes
+        // stream, in rounds of at most rmax entries, each such increment's lags with weight psi
+        // (psi_m - d psi_m at the median itself, whose d psi_m pass 0 already added).
+        const bool cl_chunk = !ADJ && I.cl_D && nterm > 0 && tau0 < U.sc.x + U.sc.y && tau1 > U.sc.x;  // holds medians
         const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
-        int aborted = 0;
-        for (int e0 = 0; e0 == 0 || e0 < ntot; e0 += L.rmax) {
-            const int ne = min(L.rmax, ntot - e0);
+        int aborted = 0, ncorr = 0, nexp = 0;
+        for (int pass = 0, e0 = 0;;) {
+            const int ne = pass ? min(L.rmax, ncorr - e0) : nterm;
             const int nst = (ne + RS - 1) / RS;
-            if (e0) __syncthreads();  // the previous round's tables are read
             // term tables of this round, built by the whole CTA: coefficient(s) and history slot
             for (int t = tid; t < ne; t += nthr) {
                 int lag;
                 TA c, c2;
-                if (!expand) {
+                if (!pass) {
                     term_of<TA, ADJ>(I, U.sc, tau0 + t, lag, c, c2);
                 } else {
                     const int e = e0 + t;
@@ -681,12 +650,13 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                         if (eoff[mid] <= e) lo = mid;
                         else hi = mid;
                     }
-                    term_of<TA, ADJ>(I, U.sc, tau0 + lo, lag, c, c2);
+                    int m;
+                    TA cm;
+                    term_of<TA, ADJ>(I, U.sc, tau0 + lo, m, cm, c2);
                     const int cnt = eoff[lo + 1] - eoff[lo];
-                    if (cnt > 1) {  // lag lo + i of the expanded increment, weight psi
-                        lag = lag - (cnt - 1) / 2 + (e - eoff[lo]);
-                        c = reinterpret_cast<const TA *>(I.psi)[lag];
-                    }
+                    lag = m - (cnt - 1) / 2 + (e - eoff[lo]);
+                    c = reinterpret_cast<const TA *>(I.psi)[lag];
+                    if (lag == m) c -= cm;
                 }
                 const int slot = (k - lag) % I.cap;
                 if (I.hscale) c = c * (TA)__ldcg(I.hscale + (size_t)slot * I.T + tile);
@@ -716,6 +686,19 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 for (int s = 0; s < pre; ++s)
                     if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
                 n_issued += (uint32_t)pre;
+            }
+            int my_exp = 0;
+            if (!pass && cl_chunk) {  // the decisions, behind the first stages' copies
+                for (int t = tid; t < nterm; t += nthr) {
+                    const int tau = tau0 + t;
+                    int cnt = 0;
+                    if (tau >= U.sc.x && tau < U.sc.x + U.sc.y) {
+                        const int g = tau - U.sc.x, d = I.g_d[g];
+                        if (d > 1 && !cl_smooth(I, k, I.g_lag[g], d)) cnt = d;
+                    }
+                    eoff[t + 1] = cnt;
+                    my_exp |= cnt;
+                }
             }
             for (int s = 0; s < nst; ++s) {
                 const int b = (int)(n_used % (uint32_t)NS);
@@ -770,7 +753,47 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 }
             }
             if (aborted) break;
+            if (!pass) {
+                // the barrier also publishes every thread's eoff entries to warp 0
+                if (!cl_chunk || !__syncthreads_or(my_exp)) break;
+                if (tid < 32) {  // exclusive offsets of the correction entries; expanded medians
+                    const int seg = (nterm + 31) / 32, a = min(nterm, tid * seg), b = min(nterm, a + seg);
+                    int sum = 0, cntx = 0;
+                    for (int t = a; t < b; ++t) {
+                        sum += eoff[t + 1];
+                        cntx += eoff[t + 1] > 0;
+                    }
+                    int pre = sum;  // inclusive warp scan of the segment sums
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, pre, o);
+                        if (tid >= o) pre += y;
+                    }
+                    int run = pre - sum;
+                    for (int t = a; t < b; ++t) {
+                        run += eoff[t + 1];
+                        eoff[t + 1] = run;
+                    }
+                    cntx = __reduce_add_sync(0xffffffffu, cntx);
+                    if (tid == 0) {
+                        eoff[0] = 0;
+                        s_nexp = cntx;
+                    }
+                }
+                __syncthreads();
+                ncorr = eoff[nterm];
+                nexp = s_nexp;
+                pass = 1;
+                e0 = 0;
+            } else {
+                e0 += ne;
+                if (e0 >= ncorr) break;
+                __syncthreads();  // this round's tables are read
+            }
         }
+        // closed loop: terms used = the chunk's terms, each expanded median counted d times
+        if (!ADJ && I.cl_D && tid == 0 && tile == 0 && nterm > 0 && !aborted)
+            atomicAdd(I.cl_terms, (unsigned long long)(nterm + ncorr - nexp));
         if (tid == 0) s_pipe = aborted || (ld_volatile(L.err) == ERR_PIPE);
         __syncthreads();
         if (s_pipe) {
@@ -1024,8 +1047,9 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             amax = fmaxf(amax, fabsf((float)d[v]));
         }
 
-        // closed loop: this tile's share of the row maxima D_k and M_k (published with the step)
-        if (I.cl_D) {
+        // closed loop (forward only): this tile's share of the row maxima D_k and M_k (published
+        // with the step)
+        if (!ADJ && I.cl_D) {
             double dm = 0.0, mm = 0.0;
             if (j0 < I.N) {
                 TS xp[V];
@@ -1182,7 +1206,7 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 }
             }
             st_release(&I.done[tile], (unsigned)(rel + 1));
-            if (I.cl_D) {  // off the step chain: nothing waits on these before the next steps' units
+            if (!ADJ && I.cl_D) {  // off the step chain: nothing waits on these before the next steps' units
                 double dm = 0.0, mm = 0.0;
                 for (int w = 0; w < (nthr + 31) / 32; ++w) {
                     dm = fmax(dm, clmax[2 * w]);
