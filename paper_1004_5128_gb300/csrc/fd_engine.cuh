@@ -597,16 +597,6 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     if (w < 0) note_failure(L, 6, gi.y, U.tile, need, ld_acquire(&I.done[U.tile]), L.k0, 0);
                     if (w <= 0) ok = 0;
                 }
-                // closed loop: the maxima of every row the chunk's decisions read, on every tile.
-                // No increment reaches a lag below the first one's, cl_lo, so row k - cl_lo is
-                // the newest any decision of step k reads; tiles complete their rows in order, so
-                // that row's count covers the older ones.
-                if (!ADJ && ok && I.cl_D && U.tau0 < sc.x + sc.y && U.tau1 > sc.x) {
-                    const int r = gi.y - I.cl_lo;
-                    const int w = wait_until(&I.cl_rows[r], (unsigned)I.T, L, 512);
-                    if (w < 0) note_failure(L, 14, gi.y, U.tile, r, ld_acquire(&I.cl_rows[r]), I.T, 0);
-                    if (w <= 0) ok = 0;
-                }
             }
             U.valid = ok;
         }
@@ -689,10 +679,24 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             }
             int my_exp = 0;
             if (!pass && cl_chunk) {  // the decisions, behind the first stages' copies
+                // Every deciding thread first acquires the maxima of every row its decisions read,
+                // on every tile.  No increment reaches a lag below the first one's, cl_lo, so row
+                // k - cl_lo is the newest any decision of step k reads; tiles complete their rows
+                // in order, so that row's count covers the older ones (and the expanded rows of
+                // this tile, which a correction pass streams after the barrier below).  A wait
+                // that gives up records the failure and keeps the medians (the launch then ends
+                // with FD_ERR_TIMEOUT).
+                const int r = k - I.cl_lo;
+                bool ready = true;
+                if (tid < nterm) {
+                    const int w = wait_until(&I.cl_rows[r], (unsigned)I.T, L, 512);
+                    if (w < 0) note_failure(L, 14, k, tile, r, ld_acquire(&I.cl_rows[r]), I.T, 0);
+                    ready = w > 0;
+                }
                 for (int t = tid; t < nterm; t += nthr) {
                     const int tau = tau0 + t;
                     int cnt = 0;
-                    if (tau >= U.sc.x && tau < U.sc.x + U.sc.y) {
+                    if (ready && tau >= U.sc.x && tau < U.sc.x + U.sc.y) {
                         const int g = tau - U.sc.x, d = I.g_d[g];
                         if (d > 1 && !cl_smooth(I, k, I.g_lag[g], d)) cnt = d;
                     }
