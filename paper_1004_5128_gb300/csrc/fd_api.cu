@@ -630,6 +630,10 @@ struct Layout {
     unsigned *clrows;
     unsigned long long *clterms;
     int *gd;
+    // the ring of per-step decisions: a + 1 slots of per-median lengths and per-chunk words
+    unsigned char *clcnt;
+    unsigned long long *clword;
+    int clslots, clgmax;
 };
 
 void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s, Layout &L,
@@ -684,12 +688,19 @@ void carve_instance(Carve &c, const fd_problem &p, const Geo &g, const Sched &s,
     L.clrows = nullptr;
     L.clterms = nullptr;
     L.gd = nullptr;
+    L.clcnt = nullptr;
+    L.clword = nullptr;
+    L.clslots = L.clgmax = 0;
     if (closed_loop(p)) {
         L.clD = (double *)c.take(sizeof(double) * (size_t)p.max_steps);
         L.clM = (double *)c.take(sizeof(double) * (size_t)p.max_steps);
         L.clrows = (unsigned *)c.take(sizeof(unsigned) * (size_t)p.max_steps);
         L.clterms = (unsigned long long *)c.take(sizeof(unsigned long long));
         L.gd = (int *)c.take(sizeof(int) * ng);
+        L.clslots = p.mem_a + 1;
+        L.clgmax = (int)ng;
+        L.clcnt = (unsigned char *)c.take((size_t)L.clslots * ng);
+        L.clword = (unsigned long long *)c.take(sizeof(unsigned long long) * (size_t)L.clslots * g.maxC);
     }
     L.ckpt = L.seg = L.rec[0] = L.rec[1] = L.ahist = L.abuf[0] = L.abuf[1] = nullptr;
     L.dots = nullptr;
@@ -973,6 +984,10 @@ Inst make_inst(const fd_problem &p, const Geo &g, const Layout &L, bool adj)
         // every increment lies above the base interval [0, a] (both rules): none reaches a lag
         // below a + 1
         I.cl_lo = p.mem_a + 1;
+        I.cl_cnt = L.clcnt;
+        I.cl_word = L.clword;
+        I.cl_slots = L.clslots;
+        I.cl_gmax = L.clgmax;
     }
     if (!adj && L.ckpt) {
         I.tape = L.ckpt;
@@ -1142,6 +1157,8 @@ static int prepare(const fd_problem *p, Sched &s, Geo &g, size_t *bytes, Layout 
     build_schedule(*p, p->max_steps, s);
     make_geo(*p, s, 0, g);
     if (g.tmem_cols > 512) return FD_ERR_INVALID_ARG;  // a CTA's tensor memory holds 512 columns
+    // closed loop: a step's per-chunk tallies fit the stage ring (the decider's scratch)
+    if (closed_loop(*p) && (size_t)g.maxC * 4 > (size_t)g.NS * g.RS * g.threads * 16) return FD_ERR_INVALID_ARG;
     Carve c(ws);
     Ctrl cc = carve_ctrl(c);
     Layout L;
@@ -1333,6 +1350,7 @@ int fd_set_state(fd_handle *h, const void *u0)
         CK(cudaMemsetAsync(h->L.clM, 0, K * sizeof(double), h->st));
         CK(cudaMemsetAsync(h->L.clrows, 0, K * sizeof(unsigned), h->st));
         CK(cudaMemsetAsync(h->L.clterms, 0, sizeof(unsigned long long), h->st));
+        CK(cudaMemsetAsync(h->L.clword, 0, sizeof(unsigned long long) * (size_t)h->L.clslots * h->g.maxC, h->st));
     }
     h->k = 0;
     h->bad = 0;
@@ -1539,7 +1557,8 @@ void save_plan(const fd_handle *h, int64_t k, SaveHeader &hd, size_t &total)
     hd.tau = hd.closed ? p.mem_tau : 0.0;
     total = sizeof(SaveHeader) + (size_t)hd.N * hd.ss * (1 + hd.comp) + (size_t)(hd.planes * hd.rows * hd.pitch) +
             (size_t)(hd.hring_cap * hd.hring_pitch) + (size_t)(hd.hscale * hd.rows * hd.T) * sizeof(float) +
-            (size_t)hd.closed * ((size_t)k * (2 * sizeof(double) + sizeof(unsigned)) + sizeof(unsigned long long));
+            (size_t)hd.closed * ((size_t)k * (2 * sizeof(double) + sizeof(unsigned)) + sizeof(unsigned long long) +
+                                 (size_t)h->L.clslots * (h->L.clgmax + sizeof(unsigned long long) * g.maxC));
 }
 
 // The pieces of a checkpoint in order: (device address, bytes).
@@ -1558,6 +1577,9 @@ std::vector<std::pair<char *, size_t>> save_pieces(const fd_handle *h, const Sav
         v.emplace_back(reinterpret_cast<char *>(h->L.clM), (size_t)hd.k * sizeof(double));
         v.emplace_back(reinterpret_cast<char *>(h->L.clrows), (size_t)hd.k * sizeof(unsigned));
         v.emplace_back(reinterpret_cast<char *>(h->L.clterms), sizeof(unsigned long long));
+        // the decisions already made for the steps after k (by rows before k)
+        v.emplace_back(reinterpret_cast<char *>(h->L.clcnt), (size_t)h->L.clslots * h->L.clgmax);
+        v.emplace_back(reinterpret_cast<char *>(h->L.clword), sizeof(unsigned long long) * (size_t)h->L.clslots * h->g.maxC);
     }
     return v;
 }

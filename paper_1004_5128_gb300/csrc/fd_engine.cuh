@@ -114,6 +114,14 @@ struct Inst {
     const int *g_d;                // increment length d of each median
     double cl_tau;
     int cl_lo;                     // smallest lag of any median's increment (the first one's)
+    // Step k's decisions, made once for the field by the update that completes row k - cl_lo on
+    // the last tile, in slot k % cl_slots (cl_slots = cl_lo: step k's units have all finished
+    // when row k is complete, before step k + cl_slots is decided): per median its expanded
+    // length (0 = it stands for its increment), per chunk one word (k + 1) << 32 | expanded
+    // medians in the chunk, stored after the lengths with release semantics.
+    unsigned char *cl_cnt;         // [cl_slots][cl_gmax]
+    unsigned long long *cl_word;   // [cl_slots][maxC]
+    int cl_slots, cl_gmax;
 };
 
 // Adjoint of adaptive memory.  The adjoint sums every (step k, lag m) pair with the weight g(m)
@@ -224,11 +232,21 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// Release reduction without a result: orders this thread's earlier writes (atomics included)
-// before the increment, and does not wait for the round trip.
-__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
 {
@@ -267,6 +285,27 @@ __device__ __forceinline__ int wait_until(const unsigned *p, unsigned need, cons
         if (globaltimer() - t0 > L.timeout_ns) {
             atomicCAS(L.err, ERR_NONE, ERR_TIMEOUT);
             return -1;
+        }
+    }
+}
+
+// Bounded wait until the word's high half holds `gen`; returns the word (acquired), or 0 after the
+// launch's error flag is set or the limit passes (which sets FD_ERR_TIMEOUT).
+__device__ __forceinline__ unsigned long long wait_word(const unsigned long long *p, unsigned gen, const Launch &L)
+{
+    unsigned long long w = ld_acquire_u64(p);
+    if ((unsigned)(w >> 32) == gen) return w;
+    const long long t0 = globaltimer();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+        w = ld_acquire_u64(p);
+        if ((unsigned)(w >> 32) == gen) return w;
+        if (ld_volatile(L.err) != ERR_NONE) return 0;
+        if (globaltimer() - t0 > L.timeout_ns) {
+            atomicCAS(L.err, ERR_NONE, ERR_TIMEOUT);
+            return 0;
         }
     }
 }
@@ -418,6 +457,7 @@ struct Unit {
     int valid, inst, k, tile, chunk, C, tau0, tau1;
     int4 sc;
     int last;  // set for the arrival election
+    unsigned long long clw;  // closed loop: the chunk's decision word as read at the claim
 };
 
 // Term tau of sched(k) (lags >= 1, ascending): lag and coefficient(s).
@@ -534,7 +574,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
     __shared__ Unit U;
     __shared__ int s_cur_inst;
     __shared__ int s_ok, s_ok2;
-    __shared__ int s_nexp;  // closed loop: expanded medians of the unit
+    __shared__ int s_nexp;    // closed loop: expanded medians of the unit
+    __shared__ int s_decide;  // closed loop: the step this update decides for the field, or -1
     __shared__ int s_pipe;
     __shared__ float s_red[32];
     __shared__ double s_dred[32][6];
@@ -592,11 +633,17 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 }
                 // partial rows of step k-npar consumed by its fixup
                 if (C > 1 && rel - I.npar + 1 > need) need = rel - I.npar + 1;
+                // closed loop: the chunk's decision word, read now (relaxed) and used after the
+                // chunk has streamed, so that its latency hides behind the waits and copies
+                unsigned long long clw = 0;
+                if (!ADJ && I.cl_D && U.tau0 < sc.x + sc.y && U.tau1 > sc.x)
+                    clw = ld_relaxed_u64(I.cl_word + (size_t)(gi.y % I.cl_slots) * I.maxC + U.chunk);
                 if (need > 0) {
                     const int w = wait_until(&I.done[U.tile], (unsigned)need, L, 512);
                     if (w < 0) note_failure(L, 6, gi.y, U.tile, need, ld_acquire(&I.done[U.tile]), L.k0, 0);
                     if (w <= 0) ok = 0;
                 }
+                U.clw = clw;
             }
             U.valid = ok;
         }
@@ -615,11 +662,12 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
         for (int v = 0; v < V; ++v) acc[v] = cmp[v] = acc2[v] = TA(0);
 
         // ------------------------------------------------- stream the chunk
-        // Pass 0 streams the chunk's terms as scheduled.  Closed loop: while its first stages are
-        // in flight, each median decides whether it stands for its increment (eoff[t + 1] = 0) or
-        // not (d); where any does not, warp 0 prefix-sums eoff[0..nterm] and correction passes
-        // stream, in rounds of at most rmax entries, each such increment's lags with weight psi
-        // (psi_m - d psi_m at the median itself, whose d psi_m pass 0 already added).
+        // Pass 0 streams the chunk's terms as scheduled.  Closed loop: then the chunk's decision
+        // word (read at the claim; acquired again if it was not yet written or shows expanded
+        // medians) says whether every median stands for its increment.  Where one does not, the
+        // step's expanded lengths give eoff[0..nterm] (warp 0 prefix-sums them) and correction
+        // passes stream, in rounds of at most rmax entries, each such increment's lags with weight
+        // psi (psi_m - d psi_m at the median itself, whose d psi_m pass 0 already added).
         const bool cl_chunk = !ADJ && I.cl_D && nterm > 0 && tau0 < U.sc.x + U.sc.y && tau1 > U.sc.x;  // holds medians
         const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
         int aborted = 0, ncorr = 0, nexp = 0;
@@ -677,33 +725,6 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                     if (warp == s % nwarp) issue(s, n_issued + (uint32_t)s);
                 n_issued += (uint32_t)pre;
             }
-            int my_exp = 0;
-            if (!pass && cl_chunk) {  // the decisions, behind the first stages' copies
-                // Every deciding thread first acquires the maxima of every row its decisions read,
-                // on every tile.  No increment reaches a lag below the first one's, cl_lo, so row
-                // k - cl_lo is the newest any decision of step k reads; tiles complete their rows
-                // in order, so that row's count covers the older ones (and the expanded rows of
-                // this tile, which a correction pass streams after the barrier below).  A wait
-                // that gives up records the failure and keeps the medians (the launch then ends
-                // with FD_ERR_TIMEOUT).
-                const int r = k - I.cl_lo;
-                bool ready = true;
-                if (tid < nterm) {
-                    const int w = wait_until(&I.cl_rows[r], (unsigned)I.T, L, 512);
-                    if (w < 0) note_failure(L, 14, k, tile, r, ld_acquire(&I.cl_rows[r]), I.T, 0);
-                    ready = w > 0;
-                }
-                for (int t = tid; t < nterm; t += nthr) {
-                    const int tau = tau0 + t;
-                    int cnt = 0;
-                    if (ready && tau >= U.sc.x && tau < U.sc.x + U.sc.y) {
-                        const int g = tau - U.sc.x, d = I.g_d[g];
-                        if (d > 1 && !cl_smooth(I, k, I.g_lag[g], d)) cnt = d;
-                    }
-                    eoff[t + 1] = cnt;
-                    my_exp |= cnt;
-                }
-            }
             for (int s = 0; s < nst; ++s) {
                 const int b = (int)(n_used % (uint32_t)NS);
                 const uint32_t par = (n_used / (uint32_t)NS) & 1u;
@@ -758,8 +779,29 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
             }
             if (aborted) break;
             if (!pass) {
-                // the barrier also publishes every thread's eoff entries to warp 0
-                if (!cl_chunk || !__syncthreads_or(my_exp)) break;
+                if (!cl_chunk) break;
+                if (tid == 0) {
+                    const unsigned gen = (unsigned)k + 1u;
+                    unsigned long long w = U.clw;
+                    if ((unsigned)(w >> 32) != gen || (unsigned)w != 0u) {
+                        // not decided when claimed, or expanded medians to read: acquire the word
+                        const unsigned long long *wp = I.cl_word + (size_t)(k % I.cl_slots) * I.maxC + U.chunk;
+                        w = wait_word(wp, gen, L);
+                        if (!w) note_failure(L, 14, k, tile, U.chunk, (long long)ld_acquire_u64(wp), gen, 0);
+                    }
+                    s_nexp = (int)(unsigned)w;  // 0 after a failed wait: the launch ends with its error
+                }
+                __syncthreads();
+                nexp = s_nexp;
+                if (!nexp) break;
+                {
+                    const unsigned char *cnt = I.cl_cnt + (size_t)(k % I.cl_slots) * I.cl_gmax;
+                    for (int t = tid; t < nterm; t += nthr) {
+                        const int tau = tau0 + t;
+                        eoff[t + 1] = (tau >= U.sc.x && tau < U.sc.x + U.sc.y) ? (int)__ldcg(cnt + (tau - U.sc.x)) : 0;
+                    }
+                }
+                __syncthreads();
                 if (tid < 32) {  // exclusive offsets of the correction entries; expanded medians
                     const int seg = (nterm + 31) / 32, a = min(nterm, tid * seg), b = min(nterm, a + seg);
                     int sum = 0, cntx = 0;
@@ -1219,7 +1261,44 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(const Launch L)
                 atomicMax(reinterpret_cast<unsigned long long *>(I.cl_D + k), (unsigned long long)__double_as_longlong(dm));
                 atomicMax(reinterpret_cast<unsigned long long *>(I.cl_M + k), (unsigned long long)__double_as_longlong(mm));
                 if (tile == 0) atomicAdd(I.cl_terms, (unsigned long long)(1 + hh));  // lag 0 and the head lags
-                red_add_release(&I.cl_rows[k], 1u);  // releases the maxima: row k done on this tile
+                // releases the maxima (row k done on this tile); the last tile acquires every
+                // tile's, and decides step k + cl_lo, the first to read row k
+                const unsigned old = atom_add_acq_rel(&I.cl_rows[k], 1u);
+                const int kd = k + I.cl_lo;
+                s_decide = (old + 1u == (unsigned)I.T && kd < I.ksteps) ? kd : -1;
+            }
+        }
+        if (!ADJ && I.cl_D) {
+            __syncthreads();
+            const int kd = s_decide;
+            if (kd >= 0) {
+                // Step kd's decisions for the whole field, once: each median's expanded length
+                // and, per chunk, the number of expanded medians (tallied in the stage ring, idle
+                // between units; the host keeps a step's chunks within it).
+                const int4 sc = I.sched[kd];
+                const int hd = min(I.head, sc.x);
+                const int n = sc.x + sc.y + (sc.w >= sc.z ? sc.w - sc.z + 1 : 0);
+                const int Ck = max(1, (n - hd + I.R - 1) / I.R);
+                int *tally = reinterpret_cast<int *>(stages);
+                for (int c = tid; c < Ck; c += nthr) tally[c] = 0;
+                __syncthreads();
+                unsigned char *cnt = I.cl_cnt + (size_t)(kd % I.cl_slots) * I.cl_gmax;
+                for (int g = tid; g < sc.y; g += nthr) {
+                    const int d = I.g_d[g];
+                    const int e = (d > 1 && !cl_smooth(I, kd, I.g_lag[g], d)) ? d : 0;
+                    cnt[g] = (unsigned char)e;
+                    if (e) atomicAdd(&tally[(sc.x + g - hd) / I.R], 1);
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();  // every thread's lengths (behind the barrier) before the words
+                    unsigned long long *word = I.cl_word + (size_t)(kd % I.cl_slots) * I.maxC;
+                    const unsigned long long gen = (unsigned long long)(unsigned)(kd + 1) << 32;
+                    for (int c = 0; c < Ck; ++c) st_relaxed_u64(word + c, gen | (unsigned)tally[c]);
+                }
+                // the ring's next writes come from bulk copies (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
             }
         }
     }
