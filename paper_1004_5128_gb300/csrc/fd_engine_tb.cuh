@@ -51,7 +51,7 @@
 
 #include <type_traits>
 
-#include "fd_engine.cuh"
+#include "fd_common.cuh"
 #include "fd_tc.cuh"
 
 namespace fdk {

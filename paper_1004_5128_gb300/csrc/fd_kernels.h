@@ -1,5 +1,6 @@
 // fd_kernels.h -- registry of the engine's template instantiations (internal).
 #pragma once
+#include "fd_engine.cuh"
 #include "fd_engine_tb.cuh"
 
 namespace fdk {
