@@ -1687,17 +1687,22 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
             if (j0 < I.N) {
                 // far part: chunk partials in fixed order, G loads in flight (the unit is latency-bound:
                 // its loads are all it does before the halo wait)
-                constexpr int G = ADJ ? 4 : TC ? 16 : 8;
-                int c = 0;
-                for (; c + G <= CP; c += G) {
+                // Batches of G rows whose last one re-reads a valid row in place of the missing
+                // ones and leaves them out of the sums, so that every load of a batch is in flight
+                // together: a step has about one batch of partial rows and up to two of head rows,
+                // and a partial batch must not fall back to one row per round trip.
+                constexpr int G = ADJ ? 4 : 8;
+                for (int c = 0; c < CP; c += G) {
                     float4 w[G], w2[ADJ ? G : 1];
     #pragma unroll
                     for (int i = 0; i < G; ++i) {
-                        w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 0) + j0));
-                        if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(c + i, t, 1) + j0));
+                        const int ci = min(c + i, CP - 1);
+                        w[i] = __ldcg(reinterpret_cast<const float4 *>(prow(ci, t, 0) + j0));
+                        if (ADJ) w2[ADJ ? i : 0] = __ldcg(reinterpret_cast<const float4 *>(prow(ci, t, 1) + j0));
                     }
     #pragma unroll
                     for (int i = 0; i < G; ++i) {
+                        if (c + i >= CP) continue;
                         H[0] += w[i].x;
                         H[1] += w[i].y;
                         H[2] += w[i].z;
@@ -1708,20 +1713,6 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             H2[2] += w2[ADJ ? i : 0].z;
                             H2[3] += w2[ADJ ? i : 0].w;
                         }
-                    }
-                }
-                for (; c < CP; ++c) {
-                    const float4 w = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 0) + j0));
-                    H[0] += w.x;
-                    H[1] += w.y;
-                    H[2] += w.z;
-                    H[3] += w.w;
-                    if (ADJ) {
-                        const float4 w2 = __ldcg(reinterpret_cast<const float4 *>(prow(c, t, 1) + j0));
-                        H2[0] += w2.x;
-                        H2[1] += w2.y;
-                        H2[2] += w2.z;
-                        H2[3] += w2.w;
                     }
                 }
                 // weight of lag m at this step (adaptive memory: settled or tail weight)
@@ -1749,13 +1740,13 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                     }
                 }
                 // head lags hk .. 2: rows this tile wrote at steps up to k-2, G loads in flight
-                int m = hk;
-                for (; m - (G - 1) >= 2; m -= G) {
+                for (int m = hk; m >= 2; m -= G) {
                     float4 x[G];
     #pragma unroll
-                    for (int i = 0; i < G; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(m - i)));
+                    for (int i = 0; i < G; ++i) x[i] = __ldcg(reinterpret_cast<const float4 *>(hrow(max(m - i, 2))));
     #pragma unroll
                     for (int i = 0; i < G; ++i) {
+                        if (m - i < 2) continue;
                         const float cc = wgt(m - i);
                         H[0] = fmaf(cc, x[i].x, H[0]);
                         H[1] = fmaf(cc, x[i].y, H[1]);
@@ -1768,21 +1759,6 @@ __global__ void __launch_bounds__(512, 1) engine_tb_kernel(const Launch L)
                             H2[2] = fmaf(c2, x[i].z, H2[2]);
                             H2[3] = fmaf(c2, x[i].w, H2[3]);
                         }
-                    }
-                }
-                for (; m >= 2; --m) {
-                    const float4 x = __ldcg(reinterpret_cast<const float4 *>(hrow(m)));
-                    const float cc = wgt(m);
-                    H[0] = fmaf(cc, x.x, H[0]);
-                    H[1] = fmaf(cc, x.y, H[1]);
-                    H[2] = fmaf(cc, x.z, H[2]);
-                    H[3] = fmaf(cc, x.w, H[3]);
-                    if (ADJ) {
-                        const float c2 = dpsi[m];
-                        H2[0] = fmaf(c2, x.x, H2[0]);
-                        H2[1] = fmaf(c2, x.y, H2[1]);
-                        H2[2] = fmaf(c2, x.z, H2[2]);
-                        H2[3] = fmaf(c2, x.w, H2[3]);
                     }
                 }
             }
