@@ -221,8 +221,8 @@ int fd_get_status(fd_handle *h);
  * tile, 9 the stall injected by FD_FLAG_INJECT_STALL, 10 blocked far unit waiting for the
  * previous chunk's running sum, 11 tensor-core far unit waiting for a copy, its coefficient
  * block or its MMAs (operands as for site 2), 12 near unit waiting for the previous block's
- * rows, 13 mid unit waiting for its block's earlier rows, 14 closed-loop chunk waiting for the
- * field-wide maxima of the rows its decisions read (operands: step, tile, row, count read, tiles).
+ * rows, 13 mid unit waiting for its block's earlier rows, 14 closed-loop chunk waiting for its
+ * step's decisions (operands: step, tile, chunk, the decision word read, the step + 1 it waits for).
  * info[1..6] are the site's operands
  * (step or block, tile, the counter target and the value last read, the launch's first step;
  * site 2 packs pairs into the high and low 32 bits), info[7] the CTA.  Only the first failure

@@ -237,7 +237,7 @@ ERROR_SITES = {0: "none", 1: "blocked far unit: history rows", 2: "blocked far u
                8: "fixup: halo tile", 9: "injected stall", 10: "blocked far unit: running sum",
                11: "tensor-core far unit: copy, coefficients or MMAs",
                12: "blocked near unit: previous block's rows", 13: "blocked mid unit: the block's earlier rows",
-               14: "closed-loop chunk: row maxima of every tile"}
+               14: "closed-loop chunk: its step's decisions"}
 
 
 def fd_get_error_info(h: int) -> dict:
