@@ -86,3 +86,16 @@ def test_decision_margin():
     u3, n3, _ = oracle.run_closed(p, 0.2 * (1 + 1.5 * mg), margin=True)
     u4, n4, _ = oracle.run_closed(p, 0.2 * (1 - 1.5 * mg), margin=True)
     assert n3 != n or n4 != n
+
+
+@pytest.mark.parametrize("a", [2, 3, 5, 10])
+@pytest.mark.parametrize("rule", [synth.ADAPT_PAPER, synth.ADAPT_PARTITION])
+def test_increments_start_above_the_base_interval(a, rule):
+    """Every increment a median stands for lies at lags >= a + 1 (both rules), so the decisions of
+    step k read rows up to k - a - 1 only: the GPU decides step k once row k - a - 1 is complete
+    everywhere.  Increment lengths stay far below 256 (the GPU keeps them in one byte)."""
+    for k in (a + 3, 50, 400, 3000):
+        lags, mult = oracle.schedule(synth.MEM_ADAPTIVE, 0, a, rule, k)
+        los = [m - (d - 1) // 2 for m, d in zip(lags, mult) if d > 1]
+        assert los and min(los) == a + 1
+        assert max(mult) < 64
